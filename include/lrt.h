@@ -1,0 +1,134 @@
+/*
+ * lrt.h -- C ABI of the GB300 DMRG linear-response library.
+ *
+ * The library evaluates the effective-Hamiltonian sigma vector H_eff x of the
+ * DMRG sweep (Nakatani, Wouters, Van Neck, Chan, "Linear response theory for
+ * the density matrix renormalization group", Sec. "Time-Independent DMRG
+ * Equation", Eq. dmrg) for one- and two-site wavefunctions in the
+ * mixed-canonical gauge, contracted from renormalized normal and complementary
+ * operator blocks (Sec. "Sweep algorithm for the projected Hamiltonian",
+ * Eqs. hzero_sb and lopr1st: the "x" summation), and the block
+ * renormalization O' = L^T [O x h] L that feeds it.
+ *
+ * Conventions shared by every entry point
+ *  - Spatial orbitals 0..k-1; spin orbitals p = 2*i + sigma (alpha first);
+ *    H = sum_ij h_ij E_ij + 1/2 sum_ijkl (ij|kl)(E_ij E_kl - delta_jk E_il) + e_core.
+ *  - Site states |0>, |a>, |b>, |ab> = a+_a a+_b |0>; U(1)xU(1) labels (N_a, N_b).
+ *  - Bond b (0..k) separates sites 0..b-1 from b..k-1; a bond sector is labelled
+ *    by the electrons LEFT of the bond and has a dimension D.
+ *  - Site tensors and one-site wavefunctions use the "left-fused" layout: for
+ *    each sector q_r of the right bond (table order) a row-major block whose
+ *    rows are the sub-blocks n = 0..3 (left sector q_r - n, skipped if absent,
+ *    D(q_l) rows each) and whose D(q_r) columns are the right states.
+ *    Two-site wavefunctions on sites (i, i+1): for each sector q_m of bond i+1
+ *    (table order) with non-empty fusions, a row-major block with rows (n1, l)
+ *    over bond i and columns (n2, r) over bond i+2.  wfn_layout() returns sizes.
+ *  - All floating point is IEEE binary64 unless `precision` selects the mixed
+ *    path.
+ *
+ * Errors: every function returns 0 on success or a negative LRT_E* code; no
+ * C++ exception or abort crosses the ABI.  lrt_last_error() describes the
+ * last failure of a context.
+ * Ownership: host arrays passed in are copied and stay owned by the caller;
+ * device buffers passed in (x, y) belong to the caller; everything the
+ * library allocates is freed by lrt_destroy().
+ * Threading: a context is used by one host thread at a time; all device work
+ * of a context is issued on the stream given to lrt_create().
+ */
+#ifndef LRT_H
+#define LRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LRT_OK 0
+#define LRT_EINVAL (-1)   /* bad argument, size or layout */
+#define LRT_ENOMEM (-2)   /* device or host allocation failed */
+#define LRT_ECUDA (-3)    /* a CUDA call failed */
+#define LRT_ENOCONV (-4)  /* iteration limit reached; results written, residual above tolerance */
+#define LRT_ETIMEOUT (-5) /* a bounded device wait expired */
+#define LRT_ESTATE (-6)   /* call order: a required object has not been built */
+
+#define LRT_FP64 0        /* all products in binary64 on the CUDA cores */
+#define LRT_MIXED 1       /* split-TF32 tensor-core products, FP32 accumulation */
+
+typedef struct lrt_ctx* lrt_t;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream). */
+int lrt_create(lrt_t* out, int device, void* cuda_stream);
+int lrt_destroy(lrt_t ctx);
+/* Message of the last failure of `ctx` (or of the last lrt_create when ctx is NULL);
+ * valid until the next call on the context. */
+const char* lrt_last_error(lrt_t ctx);
+
+/* Hamiltonian (the Hamiltonian of Sec. "Illustrative Applications", ab initio form).
+ * h: k*k row-major one-electron integrals; eri: k^4 chemist (ij|kl) row-major, or NULL
+ * when the factor B (n_factor*k*k, (ij|kl) = sum_L B[L,i,j] B[L,k,l]) is given instead.
+ * Integrals must have the 8-fold real symmetry.  Replaces any previous Hamiltonian
+ * and drops all renormalized blocks. */
+int op_build(lrt_t ctx, int k, const double* h, const double* eri, int n_factor,
+             const double* B, double e_core);
+
+/* Matrix product state (Eqs. mps_wave_gen, mps_wave).  bond_nsect[b] sectors for
+ * b = 0..k; bond_sectors holds (N_a, N_b, D) triples of all bonds concatenated;
+ * site_data[i] is the host pointer to site i in the left-fused layout.  Bond 0
+ * must be the single sector (0,0,1) and bond k the single sector (n_alpha, n_beta, 1).
+ * Renormalization assumes site tensors left of the working site left-orthonormal
+ * and those right of it right-orthonormal (the mixed-canonical gauge).  Copied to
+ * the device; drops all renormalized blocks. */
+typedef struct {
+  int k;
+  int n_alpha;
+  int n_beta;
+  const int* bond_nsect;
+  const int* bond_sectors;
+  const double* const* site_data;
+  int center;
+} lrt_mps_desc;
+int mps_load(lrt_t ctx, const lrt_mps_desc* mps);
+
+/* Size in doubles of a one-site (nsite=1, sites site) or two-site (nsite=2, sites
+ * site, site+1) wavefunction; block_offsets, if non-NULL, receives the start of every
+ * fused block (one per right-bond sector for nsite=1, one per populated middle sector
+ * for nsite=2) and must have room for the count returned in *nblocks. */
+int wfn_layout(lrt_t ctx, int site, int nsite, int64_t* nelem, int* nblocks, int64_t* block_offsets);
+
+/* Block renormalization (Eqs. gauge-shift and lopr1st/ropr1st, zeroth order):
+ * dir = +1 builds the left block of bond site+1 from the left block of bond site and
+ * the (left-orthonormal) tensor of `site`; dir = -1 builds the right block of bond
+ * `site` from the right block of bond site+1 and the (right-orthonormal) tensor of
+ * `site`.  Left block 0 and right block k are the vacuum and always exist. */
+int renormalize(lrt_t ctx, int site, int dir, int precision);
+
+/* sigma = H_eff x (Eq. dmrg) for `nvec` wavefunctions stored back to back in the
+ * wfn_layout order: nsite = 1 uses the left block of bond `site` and the right block
+ * of bond site+1; nsite = 2 uses the left block of bond `site` and the right block of
+ * bond site+2.  x_dev, y_dev: device pointers of nvec * nelem doubles; must not
+ * overlap. */
+int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double* y_dev,
+          int precision);
+
+/* Diagonal of H_eff (the preconditioner of Eq. error) in the same layout as sigma. */
+int heff_diag(lrt_t ctx, int site, int nsite, double* d_dev);
+
+/* Statistics of the last sigma call: algorithmic FLOPs (2mnk summed over the
+ * block products actually needed), number of GPU kernel launches, and the total
+ * bytes of operator data read. */
+typedef struct {
+  double flops;
+  double op_bytes;
+  int launches;
+  int n_terms;
+  int n_products;
+} lrt_sigma_stats;
+int sigma_stats(lrt_t ctx, lrt_sigma_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRT_H */

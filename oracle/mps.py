@@ -25,16 +25,16 @@ def pack_site(blocks, left, right):
     return out
 
 
-def unpack_twosite(arr, left, mid, right):
+def unpack_twosite(arr, left, right):
     out = {}
-    for (ql, n1, n2, qr, dl, dr, off, ro, co, rows, cols, boff) in twosite_layout(left, mid, right):
+    for (ql, n1, n2, qr, dl, dr, off, ro, co, rows, cols, boff) in twosite_layout(left, right):
         blk = arr[boff:boff + rows * cols].reshape(rows, cols)
         out[(ql, n1, n2, qr)] = blk[ro:ro + dl, co:co + dr].copy()
     return out
 
 
-def pack_twosite(blocks, left, mid, right):
-    lay = twosite_layout(left, mid, right)
+def pack_twosite(blocks, left, right):
+    lay = twosite_layout(left, right)
     size = 0
     for e in lay:
         size = max(size, e[11] + e[9] * e[10])
@@ -128,19 +128,16 @@ def product_basis_onesite(sites, i, k, dets):
     return np.hstack(cols), index
 
 
-def product_basis_twosite(sites, i, k, dets, mid_table):
+def product_basis_twosite(sites, i, k, dets):
     """Columns |l_i n1 n2 r_{i+2}> on `dets`; index[(q_l, n1, n2, q_r)] = (col, D_l, D_r)."""
     EL = expand_left(sites, i)
     ER = expand_right(sites, i + 2, k)
     pos = {int(d): j for j, d in enumerate(dets)}
-    mids = {(a, b) for a, b, _ in mid_table}
     cols, index, c0 = [], {}, 0
     for ql in sorted(EL):
         lb, Lm = EL[ql]
         for n1, s1 in enumerate(QN_SITE):
             qm = (ql[0] + s1[0], ql[1] + s1[1])
-            if qm not in mids:
-                continue
             for n2, s2 in enumerate(QN_SITE):
                 qr = (qm[0] + s2[0], qm[1] + s2[1])
                 if qr not in ER:

@@ -1,0 +1,166 @@
+"""GB300 DMRG effective-Hamiltonian library: Python binding of the C ABI in include/lrt.h.
+
+Argument marshalling only: every step of sigma, renormalization and the
+diagonal runs in the CUDA library liblrt.so (built by `build.build()`).  Device
+buffers are torch CUDA tensors (float64, contiguous); host arrays are NumPy.
+There is no CPU fallback: without the library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblrt.so")
+
+LRT_FP64 = 0
+LRT_MIXED = 1
+
+EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
+           "renormalize", "sigma", "heff_diag", "sigma_stats"]
+
+_lib = None
+
+
+class MpsDesc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_alpha", ctypes.c_int), ("n_beta", ctypes.c_int),
+                ("bond_nsect", ctypes.POINTER(ctypes.c_int)),
+                ("bond_sectors", ctypes.POINTER(ctypes.c_int)),
+                ("site_data", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("center", ctypes.c_int)]
+
+
+class SigmaStats(ctypes.Structure):
+    _fields_ = [("flops", ctypes.c_double), ("op_bytes", ctypes.c_double), ("launches", ctypes.c_int),
+                ("n_terms", ctypes.c_int), ("n_products", ctypes.c_int)]
+
+
+class LrtError(RuntimeError):
+    pass
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise LrtError(f"CUDA library missing: {path} (run paper_1311_1646_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.lrt_create.argtypes = [ctypes.POINTER(vp), i, vp]
+    lib.lrt_destroy.argtypes = [vp]
+    lib.lrt_last_error.argtypes = [vp]
+    lib.lrt_last_error.restype = ctypes.c_char_p
+    lib.op_build.argtypes = [vp, i, dp, dp, i, dp, d]
+    lib.mps_load.argtypes = [vp, ctypes.POINTER(MpsDesc)]
+    lib.wfn_layout.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int64)]
+    lib.renormalize.argtypes = [vp, i, i, i]
+    lib.sigma.argtypes = [vp, i, i, i, vp, vp, i]
+    lib.heff_diag.argtypes = [vp, i, i, vp]
+    lib.sigma_stats.argtypes = [vp, ctypes.POINTER(SigmaStats)]
+    for name in EXPORTS:
+        if name != "lrt_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tensor_ptr(t, nelem: int) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise LrtError("expected a contiguous float64 CUDA tensor")
+    if t.numel() < nelem:
+        raise LrtError(f"tensor has {t.numel()} elements, need {nelem}")
+    return t.data_ptr()
+
+
+class Context:
+    """One library context on one device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        h = ctypes.c_void_p()
+        rc = self.lib.lrt_create(ctypes.byref(h), device, ctypes.c_void_p(stream))
+        if rc != 0:
+            raise LrtError(f"lrt_create failed ({rc}): {self.lib.lrt_last_error(None).decode()}")
+        self.h = h
+        self.device = device
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc != 0:
+            msg = self.lib.lrt_last_error(self.h).decode()
+            raise LrtError(f"{what} failed ({rc}): {msg}")
+
+    def op_build(self, k: int, h: np.ndarray, eri: np.ndarray | None = None, B: np.ndarray | None = None,
+                 e_core: float = 0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        e = np.ascontiguousarray(eri, dtype=np.float64) if eri is not None else None
+        b = np.ascontiguousarray(B, dtype=np.float64) if B is not None else None
+        nL = 0 if b is None else b.shape[0]
+        self._check(self.lib.op_build(self.h, k, _dptr(h), _dptr(e) if e is not None else None, nL,
+                                      _dptr(b) if b is not None else None, float(e_core)), "op_build")
+
+    def mps_load(self, k: int, n_alpha: int, n_beta: int, bonds: list, sites: list, center: int = 0):
+        nsect = np.array([len(t) for t in bonds], dtype=np.int32)
+        secs = np.array([x for t in bonds for s in t for x in s], dtype=np.int32)
+        arrs = [np.ascontiguousarray(s, dtype=np.float64) for s in sites]
+        ptrs = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in arrs])
+        desc = MpsDesc(k, n_alpha, n_beta, nsect.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                       secs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptrs, center)
+        self._check(self.lib.mps_load(self.h, ctypes.byref(desc)), "mps_load")
+
+    def wfn_layout(self, site: int, nsite: int):
+        n = ctypes.c_int64()
+        nb = ctypes.c_int()
+        self._check(self.lib.wfn_layout(self.h, site, nsite, ctypes.byref(n), ctypes.byref(nb), None),
+                    "wfn_layout")
+        offs = (ctypes.c_int64 * max(nb.value, 1))()
+        self._check(self.lib.wfn_layout(self.h, site, nsite, ctypes.byref(n), ctypes.byref(nb), offs),
+                    "wfn_layout")
+        return n.value, list(offs)[:nb.value]
+
+    def renormalize(self, site: int, direction: int, precision: int = LRT_FP64):
+        self._check(self.lib.renormalize(self.h, site, direction, precision), "renormalize")
+
+    def sigma(self, site: int, nsite: int, x, y, nvec: int = 1, precision: int = LRT_FP64):
+        n, _ = self.wfn_layout(site, nsite)
+        self._check(self.lib.sigma(self.h, site, nsite, nvec, ctypes.c_void_p(_tensor_ptr(x, n * nvec)),
+                                   ctypes.c_void_p(_tensor_ptr(y, n * nvec)), precision), "sigma")
+
+    def heff_diag(self, site: int, nsite: int, d):
+        n, _ = self.wfn_layout(site, nsite)
+        self._check(self.lib.heff_diag(self.h, site, nsite, ctypes.c_void_p(_tensor_ptr(d, n))), "heff_diag")
+
+    def stats(self) -> dict:
+        s = SigmaStats()
+        self._check(self.lib.sigma_stats(self.h, ctypes.byref(s)), "sigma_stats")
+        return {"flops": s.flops, "op_bytes": s.op_bytes, "launches": s.launches,
+                "n_terms": s.n_terms, "n_products": s.n_products}

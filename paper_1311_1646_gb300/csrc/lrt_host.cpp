@@ -1,0 +1,1394 @@
+// Host side of the DMRG sigma / renormalization library: context, operator-set
+// planning and the C ABI declared in include/lrt.h.
+//
+// The Hamiltonian is split across every cut X | Y of the chain into renormalized
+// normal and complementary operators (the "x" of Eqs. hzero_sb and lopr1st):
+//
+//   H = H^X + H^Y + sum_{x in X} (C_x S^Y_x - c_x S^Y_x^T) + sum_{y in Y} (S^X_y^T c_y - S^X_y C_y)
+//     + [X normal] sum_{p<q in X} (A_pq P^Y_pq + A_pq^T P^Y_pq^T) + sum_{p,q in X} B_pq Q^Y_pq
+//     | [Y normal] sum_{r<s in Y} (P^X_rs^T A_rs^T + P^X_rs A_rs) + sum_{u,w in Y} Q^X_uw B_uw
+//
+// with C_p = a+_p, c_p = a_p, A_pq = C_p C_q, B_pq = C_p c_q and, for a block Z,
+//   S^Z_x = 1/2 sum_{q in Z} t_xq c_q + sum_{q,r,s in Z} v_xqrs C_q c_s c_r,
+//   P^Z_pq = sum_{r,s in Z} v_pqrs c_s c_r,  Q^Z_pq = sum_{r,s in Z} (v_prqs - v_prsq) C_r c_s,
+// v_pqrs = <pq|rs>.  A product X_op Y_op acts on |x>|y> with the sign
+// (-1)^{parity(Y_op) N(x)}.  The normal side of cut b is the left one when 2b <= k.
+//
+// Blocks are enlarged by one site ("blocking") with formulas that express every
+// operator of X (+) Y through operators of X and Y; a site is a 4-state space whose
+// operators are built directly.  Enlarged operators live in a fused basis: the
+// states of label Q are the sub-blocks n = 0..3 in order, each the states of the
+// neighbouring bond sector Q -/+ n.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/lrt.h"
+#include "lrt_kernels.h"
+
+namespace lrt {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw Error(LRT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+static const int QNA[4] = {0, 1, 0, 1};
+static const int QNB[4] = {0, 0, 1, 1};
+
+// ---------------------------------------------------------------------------
+// sector tables
+// ---------------------------------------------------------------------------
+struct Sectors {
+  std::vector<int> a, b, d;
+  std::unordered_map<int, int> idx;
+  static int key(int qa, int qb) { return (qa + 512) * 2048 + (qb + 512); }
+  int find(int qa, int qb) const {
+    auto it = idx.find(key(qa, qb));
+    return it == idx.end() ? -1 : it->second;
+  }
+  int add(int qa, int qb, int dim) {
+    int i = (int)a.size();
+    a.push_back(qa);
+    b.push_back(qb);
+    d.push_back(dim);
+    idx[key(qa, qb)] = i;
+    return i;
+  }
+  int n() const { return (int)a.size(); }
+};
+
+// fused (enlarged) basis of L (+) site (right = false) or site (+) R (right = true)
+struct Fused {
+  Sectors s;                        // fused labels and total dims
+  std::vector<std::array<int, 4>> sub;   // source sector of sub-block n, or -1
+  std::vector<std::array<int, 4>> off;   // row/col offset of sub-block n
+};
+
+static Fused fuse(const Sectors& src, bool right) {
+  std::map<std::pair<int, int>, int> labels;
+  for (int s = 0; s < src.n(); ++s)
+    for (int n = 0; n < 4; ++n) {
+      int qa = right ? src.a[s] - QNA[n] : src.a[s] + QNA[n];
+      int qb = right ? src.b[s] - QNB[n] : src.b[s] + QNB[n];
+      labels[{qa, qb}] = 1;
+    }
+  Fused f;
+  for (auto& kv : labels) {
+    std::array<int, 4> sub, off;
+    int tot = 0;
+    for (int n = 0; n < 4; ++n) {
+      int qa = right ? kv.first.first + QNA[n] : kv.first.first - QNA[n];
+      int qb = right ? kv.first.second + QNB[n] : kv.first.second - QNB[n];
+      int s = src.find(qa, qb);
+      sub[n] = s;
+      off[n] = tot;
+      if (s >= 0) tot += src.d[s];
+    }
+    if (tot == 0) continue;
+    f.s.add(kv.first.first, kv.first.second, tot);
+    f.sub.push_back(sub);
+    f.off.push_back(off);
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// integrals
+// ---------------------------------------------------------------------------
+struct Ints {
+  int k = 0, nso = 0;
+  std::vector<double> t;   // nso^2
+  std::vector<double> v;   // nso^4, v[p,q,r,s] = <pq|rs>
+  double e_core = 0.0;
+  double T(int p, int q) const { return t[(size_t)p * nso + q]; }
+  double V(int p, int q, int r, int s) const {
+    return v[(((size_t)p * nso + q) * nso + r) * nso + s];
+  }
+};
+
+static void build_ints(Ints& I, int k, const double* h, const double* eri, int nL, const double* B,
+                       double e_core) {
+  I.k = k;
+  I.nso = 2 * k;
+  const int n = I.nso;
+  I.t.assign((size_t)n * n, 0.0);
+  I.v.assign((size_t)n * n * n * n, 0.0);
+  I.e_core = e_core;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j)
+      for (int s = 0; s < 2; ++s) I.t[(size_t)(2 * i + s) * n + 2 * j + s] = h[i * k + j];
+  std::vector<double> chem((size_t)k * k * k * k);
+  if (eri) {
+    std::memcpy(chem.data(), eri, chem.size() * sizeof(double));
+  } else {
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j)
+        for (int a = 0; a < k; ++a)
+          for (int b = 0; b < k; ++b) {
+            double acc = 0.0;
+            for (int L = 0; L < nL; ++L) acc += B[((size_t)L * k + i) * k + j] * B[((size_t)L * k + a) * k + b];
+            chem[(((size_t)i * k + j) * k + a) * k + b] = acc;
+          }
+  }
+  // <pq|rs> = (pr|qs) with spin(p) = spin(r), spin(q) = spin(s)
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r) {
+        if ((p & 1) != (r & 1)) continue;
+        for (int s = 0; s < n; ++s) {
+          if ((q & 1) != (s & 1)) continue;
+          I.v[(((size_t)p * n + q) * n + r) * n + s] =
+              chem[(((size_t)(p / 2) * k + r / 2) * k + q / 2) * k + s / 2];
+        }
+      }
+}
+
+// ---------------------------------------------------------------------------
+// operator sets
+// ---------------------------------------------------------------------------
+enum Kind : int { KI = 0, KH, KC, KS, KA, KB, KP, KQ };
+
+struct Key {
+  int kind, p, q;
+  bool operator<(const Key& o) const { return std::tie(kind, p, q) < std::tie(o.kind, o.p, o.q); }
+};
+
+static int kind_parity(int kind) { return (kind == KC || kind == KS) ? 1 : 0; }
+
+// change of the block's own (N_a, N_b) caused by the operator
+static void key_delta(const Key& k, int& da, int& db) {
+  da = db = 0;
+  auto add = [&](int p, int s) {
+    if (p & 1) db += s; else da += s;
+  };
+  switch (k.kind) {
+    case KC: add(k.p, +1); break;
+    case KS: add(k.p, -1); break;
+    case KA: add(k.p, +1); add(k.q, +1); break;
+    case KB: add(k.p, +1); add(k.q, -1); break;
+    case KP: add(k.p, -1); add(k.q, -1); break;
+    case KQ: add(k.q, +1); add(k.p, -1); break;
+    default: break;
+  }
+}
+
+struct OpSet {
+  Sectors basis;          // bond labels (left: own count; right: N - own count)
+  bool right = false;
+  std::vector<int> orbs;
+  std::vector<char> in;
+  char mode = 'N';
+  std::vector<Key> keys;
+  std::map<Key, int> index;
+  std::vector<int> da, db, par;
+  std::vector<int> bra;        // [op * ns + ket] -> bra sector or -1
+  std::vector<int64_t> off;    // [op * ns + ket] -> offset (doubles) or -1
+  int64_t total = 0;
+  double* d = nullptr;
+  std::unique_ptr<Fused> fused;   // for enlarged sets
+  OpSet() = default;
+  OpSet(const OpSet&) = delete;
+  ~OpSet() {
+    if (d) cudaFree(d);
+  }
+  int ns() const { return basis.n(); }
+  int find(const Key& k) const {
+    auto it = index.find(k);
+    return it == index.end() ? -1 : it->second;
+  }
+  int bra_of(int op, int ket) const { return bra[(size_t)op * ns() + ket]; }
+  int64_t off_of(int op, int ket) const { return off[(size_t)op * ns() + ket]; }
+};
+
+static void make_keys(OpSet& S, const std::vector<int>& orbs, char mode, int nso) {
+  S.orbs = orbs;
+  S.in.assign(nso, 0);
+  for (int p : orbs) S.in[p] = 1;
+  S.mode = mode;
+  std::vector<int> out;
+  for (int p = 0; p < nso; ++p)
+    if (!S.in[p]) out.push_back(p);
+  auto push = [&](int kind, int p, int q) {
+    Key k{kind, p, q};
+    S.index[k] = (int)S.keys.size();
+    S.keys.push_back(k);
+  };
+  push(KI, -1, -1);
+  push(KH, -1, -1);
+  for (int p : orbs) push(KC, p, -1);
+  for (int z : out) push(KS, z, -1);
+  const std::vector<int>& pr = (mode == 'N') ? orbs : out;
+  const int A = (mode == 'N') ? KA : KP, B = (mode == 'N') ? KB : KQ;
+  for (size_t i = 0; i < pr.size(); ++i)
+    for (size_t j = i + 1; j < pr.size(); ++j) push(A, pr[i], pr[j]);
+  for (size_t i = 0; i < pr.size(); ++i)
+    for (size_t j = i; j < pr.size(); ++j) push(B, pr[i], pr[j]);
+  const int nop = (int)S.keys.size();
+  S.da.resize(nop);
+  S.db.resize(nop);
+  S.par.resize(nop);
+  for (int o = 0; o < nop; ++o) {
+    key_delta(S.keys[o], S.da[o], S.db[o]);
+    S.par[o] = kind_parity(S.keys[o].kind);
+  }
+}
+
+static void layout_blocks(OpSet& S) {
+  const int ns = S.ns(), nop = (int)S.keys.size();
+  const int sg = S.right ? -1 : 1;
+  S.bra.assign((size_t)nop * ns, -1);
+  S.off.assign((size_t)nop * ns, -1);
+  S.total = 0;
+  for (int o = 0; o < nop; ++o)
+    for (int s = 0; s < ns; ++s) {
+      int b = S.basis.find(S.basis.a[s] + sg * S.da[o], S.basis.b[s] + sg * S.db[o]);
+      if (b < 0) continue;
+      S.bra[(size_t)o * ns + s] = b;
+      S.off[(size_t)o * ns + s] = S.total;
+      S.total += (int64_t)S.basis.d[b] * S.basis.d[s];
+    }
+}
+
+static void alloc_zero(OpSet& S, cudaStream_t st) {
+  if (S.total <= 0) return;
+  cudaError_t e = cudaMalloc(&S.d, (size_t)S.total * sizeof(double));
+  if (e != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation of an operator set failed");
+  CK(cudaMemsetAsync(S.d, 0, (size_t)S.total * sizeof(double), st));
+}
+
+// ---------------------------------------------------------------------------
+// single-site operators (4 x 4, basis |0>, |a>, |b>, |ab> = C_a C_b |0>)
+// ---------------------------------------------------------------------------
+struct Mat4 {
+  double m[16];
+  Mat4() { std::fill(m, m + 16, 0.0); }
+  double& operator()(int i, int j) { return m[i * 4 + j]; }
+  double operator()(int i, int j) const { return m[i * 4 + j]; }
+  Mat4 operator*(const Mat4& o) const {
+    Mat4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        double s = 0.0;
+        for (int l = 0; l < 4; ++l) s += m[i * 4 + l] * o.m[l * 4 + j];
+        r.m[i * 4 + j] = s;
+      }
+    return r;
+  }
+  Mat4& axpy(double c, const Mat4& o) {
+    for (int i = 0; i < 16; ++i) m[i] += c * o.m[i];
+    return *this;
+  }
+  Mat4 T() const {
+    Mat4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) r.m[j * 4 + i] = m[i * 4 + j];
+    return r;
+  }
+  bool zero() const {
+    for (double x : m)
+      if (x != 0.0) return false;
+    return true;
+  }
+};
+
+struct Site {
+  int i;
+  Mat4 ann[2], cre[2];   // local a_alpha, a_beta and their transposes
+  explicit Site(int site) : i(site) {
+    // a_alpha: |a> -> |0>, |ab> -> |b>;  a_beta: |b> -> |0>, |ab> = C_a C_b|0> -> -C_a|0> = -|a>
+    ann[0](0, 1) = 1.0;
+    ann[0](2, 3) = 1.0;
+    ann[1](0, 2) = 1.0;
+    ann[1](1, 3) = -1.0;
+    cre[0] = ann[0].T();
+    cre[1] = ann[1].T();
+  }
+  bool local(int p) const { return p / 2 == i; }
+  const Mat4& C(int p) const { return cre[p & 1]; }
+  const Mat4& c(int p) const { return ann[p & 1]; }
+  Mat4 op(const Ints& I, int kind, int p, int q, int trans) const {
+    Mat4 r;
+    const int lo[2] = {2 * i, 2 * i + 1};
+    switch (kind) {
+      case KI:
+        for (int a = 0; a < 4; ++a) r(a, a) = 1.0;
+        break;
+      case KH:
+        for (int x : lo)
+          for (int y : lo) r.axpy(I.T(x, y), C(x) * c(y));
+        for (int pp : lo)
+          for (int qq : lo)
+            for (int rr : lo)
+              for (int ss : lo) r.axpy(0.5 * I.V(pp, qq, rr, ss), C(pp) * C(qq) * c(ss) * c(rr));
+        break;
+      case KC:
+        r = C(p);
+        break;
+      case KS:
+        for (int x : lo) r.axpy(0.5 * I.T(p, x), c(x));
+        for (int qq : lo)
+          for (int rr : lo)
+            for (int ss : lo) r.axpy(I.V(p, qq, rr, ss), C(qq) * c(ss) * c(rr));
+        break;
+      case KA:
+        r = C(p) * C(q);
+        break;
+      case KB:
+        r = C(p) * c(q);
+        break;
+      case KP:
+        for (int rr : lo)
+          for (int ss : lo) r.axpy(I.V(p, q, rr, ss), c(ss) * c(rr));
+        break;
+      case KQ:
+        for (int rr : lo)
+          for (int ss : lo) r.axpy(I.V(p, rr, q, ss) - I.V(p, rr, ss, q), C(rr) * c(ss));
+        break;
+    }
+    return trans ? r.T() : r;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// operator references: a requested operator as a combination of stored ones
+// ---------------------------------------------------------------------------
+struct Ref {
+  int op;
+  int t;
+  double c;
+};
+
+static void get_refs(const OpSet& S, const Ints& I, int kind, int p, int q, int t, double c,
+                     std::vector<Ref>& out) {
+  auto stored = [&](int kk, int a, int b, int tt, double cc) {
+    int o = S.find(Key{kk, a, b});
+    if (o >= 0) out.push_back(Ref{o, tt, cc});
+  };
+  switch (kind) {
+    case KI: stored(KI, -1, -1, t, c); return;
+    case KH: stored(KH, -1, -1, t, c); return;
+    case KC: stored(KC, p, -1, t, c); return;
+    case KS: stored(KS, p, -1, t, c); return;
+    case KA:
+      if (p == q) return;
+      if (p < q) stored(KA, p, q, t, c); else stored(KA, q, p, t, -c);
+      return;
+    case KB:
+      if (p <= q) stored(KB, p, q, t, c); else stored(KB, q, p, 1 - t, c);
+      return;
+    case KP:
+      if (p == q) return;
+      if (p > q) { get_refs(S, I, KP, q, p, t, -c, out); return; }
+      if (S.mode == 'C') { stored(KP, p, q, t, c); return; }
+      // P_pq = sum_{r<s in Z} (v_pqrs - v_pqsr) A_rs^T
+      for (size_t i = 0; i < S.orbs.size(); ++i)
+        for (size_t j = i + 1; j < S.orbs.size(); ++j) {
+          const int r = S.orbs[i], s = S.orbs[j];
+          const double w = I.V(p, q, r, s) - I.V(p, q, s, r);
+          if (w != 0.0) stored(KA, r, s, 1 - t, c * w);
+        }
+      return;
+    case KQ:
+      if (p > q) { get_refs(S, I, KQ, q, p, 1 - t, c, out); return; }
+      if (S.mode == 'C') { stored(KQ, p, q, t, c); return; }
+      // Q_pq = sum_{r,s in Z} (v_prqs - v_prsq) B_rs
+      for (int r : S.orbs)
+        for (int s : S.orbs) {
+          const double w = I.V(p, r, q, s) - I.V(p, r, s, q);
+          if (w != 0.0) get_refs(S, I, KB, r, s, t, c * w, out);
+        }
+      return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// terms: (coef, X spec, Y spec)
+// ---------------------------------------------------------------------------
+struct Spec {
+  int kind, p, q, t;
+};
+struct Term {
+  double c;
+  Spec x, y;
+};
+
+static void cross_terms(const std::vector<int>& X, const std::vector<int>& Y, bool x_normal,
+                        std::vector<Term>& T) {
+  for (int x : X) {
+    T.push_back({1.0, {KC, x, -1, 0}, {KS, x, -1, 0}});
+    T.push_back({-1.0, {KC, x, -1, 1}, {KS, x, -1, 1}});
+  }
+  for (int y : Y) {
+    T.push_back({1.0, {KS, y, -1, 1}, {KC, y, -1, 1}});
+    T.push_back({-1.0, {KS, y, -1, 0}, {KC, y, -1, 0}});
+  }
+  const std::vector<int>& N = x_normal ? X : Y;
+  for (size_t i = 0; i < N.size(); ++i)
+    for (size_t j = i + 1; j < N.size(); ++j) {
+      const int p = N[i], q = N[j];
+      if (x_normal) {
+        T.push_back({1.0, {KA, p, q, 0}, {KP, p, q, 0}});
+        T.push_back({1.0, {KA, p, q, 1}, {KP, p, q, 1}});
+      } else {
+        T.push_back({1.0, {KP, p, q, 1}, {KA, p, q, 1}});
+        T.push_back({1.0, {KP, p, q, 0}, {KA, p, q, 0}});
+      }
+    }
+  for (size_t i = 0; i < N.size(); ++i)
+    for (size_t j = i; j < N.size(); ++j) {
+      const int p = N[i], q = N[j];
+      if (x_normal) {
+        T.push_back({1.0, {KB, p, q, 0}, {KQ, p, q, 0}});
+        if (p != q) T.push_back({1.0, {KB, p, q, 1}, {KQ, p, q, 1}});
+      } else {
+        T.push_back({1.0, {KQ, p, q, 0}, {KB, p, q, 0}});
+        if (p != q) T.push_back({1.0, {KQ, p, q, 1}, {KB, p, q, 1}});
+      }
+    }
+}
+
+// terms of every operator of X (+) Y (X before Y), keyed like the new set
+static std::vector<std::vector<Term>> blocking_terms(const OpSet& New, const std::vector<int>& X,
+                                                      const std::vector<int>& Y, const Ints& I) {
+  std::vector<char> inX(I.nso, 0), inY(I.nso, 0);
+  for (int p : X) inX[p] = 1;
+  for (int p : Y) inY[p] = 1;
+  std::vector<std::vector<Term>> out(New.keys.size());
+  for (size_t o = 0; o < New.keys.size(); ++o) {
+    const Key& k = New.keys[o];
+    std::vector<Term>& T = out[o];
+    switch (k.kind) {
+      case KI:
+        T.push_back({1.0, {KI, -1, -1, 0}, {KI, -1, -1, 0}});
+        break;
+      case KH:
+        T.push_back({1.0, {KH, -1, -1, 0}, {KI, -1, -1, 0}});
+        T.push_back({1.0, {KI, -1, -1, 0}, {KH, -1, -1, 0}});
+        cross_terms(X, Y, X.size() < Y.size(), T);
+        break;
+      case KC:
+        if (inX[k.p]) T.push_back({1.0, {KC, k.p, -1, 0}, {KI, -1, -1, 0}});
+        else T.push_back({1.0, {KI, -1, -1, 0}, {KC, k.p, -1, 0}});
+        break;
+      case KS: {
+        const int z = k.p;
+        T.push_back({1.0, {KS, z, -1, 0}, {KI, -1, -1, 0}});
+        T.push_back({1.0, {KI, -1, -1, 0}, {KS, z, -1, 0}});
+        for (int q : X) T.push_back({1.0, {KC, q, -1, 0}, {KP, z, q, 0}});
+        for (int q : Y) T.push_back({1.0, {KP, z, q, 0}, {KC, q, -1, 0}});
+        for (int w : Y) T.push_back({1.0, {KQ, z, w, 0}, {KC, w, -1, 1}});
+        for (int u : X) T.push_back({1.0, {KC, u, -1, 1}, {KQ, z, u, 0}});
+        break;
+      }
+      case KA:
+        if (inX[k.p] && inX[k.q]) T.push_back({1.0, {KA, k.p, k.q, 0}, {KI, -1, -1, 0}});
+        else if (inY[k.p] && inY[k.q]) T.push_back({1.0, {KI, -1, -1, 0}, {KA, k.p, k.q, 0}});
+        else T.push_back({1.0, {KC, k.p, -1, 0}, {KC, k.q, -1, 0}});
+        break;
+      case KB:
+        if (inX[k.p] && inX[k.q]) T.push_back({1.0, {KB, k.p, k.q, 0}, {KI, -1, -1, 0}});
+        else if (inY[k.p] && inY[k.q]) T.push_back({1.0, {KI, -1, -1, 0}, {KB, k.p, k.q, 0}});
+        else T.push_back({1.0, {KC, k.p, -1, 0}, {KC, k.q, -1, 1}});
+        break;
+      case KP: {
+        const int p = k.p, q = k.q;
+        T.push_back({1.0, {KP, p, q, 0}, {KI, -1, -1, 0}});
+        T.push_back({1.0, {KI, -1, -1, 0}, {KP, p, q, 0}});
+        for (int x : X)
+          for (int y : Y) {
+            const double w = I.V(p, q, y, x) - I.V(p, q, x, y);
+            if (w != 0.0) T.push_back({w, {KC, x, -1, 1}, {KC, y, -1, 1}});
+          }
+        break;
+      }
+      case KQ: {
+        const int p = k.p, q = k.q;
+        T.push_back({1.0, {KQ, p, q, 0}, {KI, -1, -1, 0}});
+        T.push_back({1.0, {KI, -1, -1, 0}, {KQ, p, q, 0}});
+        for (int x : X)
+          for (int y : Y) {
+            const double w1 = I.V(p, x, q, y) - I.V(p, x, y, q);
+            if (w1 != 0.0) T.push_back({w1, {KC, x, -1, 0}, {KC, y, -1, 1}});
+            const double w2 = -(I.V(p, y, q, x) - I.V(p, y, x, q));
+            if (w2 != 0.0) T.push_back({w2, {KC, x, -1, 1}, {KC, y, -1, 0}});
+          }
+        break;
+      }
+    }
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// device upload helper
+// ---------------------------------------------------------------------------
+template <class T>
+struct DevArray {
+  T* p = nullptr;
+  size_t n = 0;
+  DevArray() = default;
+  DevArray(const DevArray&) = delete;
+  ~DevArray() {
+    if (p) cudaFree(p);
+  }
+  void upload(const std::vector<T>& v, cudaStream_t st) {
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+    }
+    n = v.size();
+    if (n == 0) return;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation failed");
+    CK(cudaMemcpyAsync(p, v.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+};
+
+struct GatherPlan {
+  DevArray<GatherTask> tasks;
+  DevArray<GatherSrc> srcs;
+  DevArray<int3> tiles;
+  int ntiles = 0;
+  void run(cudaStream_t st) const { launch_gather(tasks.p, srcs.p, tiles.p, ntiles, st); }
+};
+
+struct GemmPlan {
+  DevArray<GemmOut> outs;
+  DevArray<GemmSeg> segs;
+  DevArray<int3> tiles;
+  int ntiles = 0;
+  double flops = 0.0;
+  void run(cudaStream_t st, const double* xb, double* yb) const {
+    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, st);
+  }
+};
+
+static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vector<GatherSrc>& srcs,
+                         cudaStream_t st) {
+  std::vector<int3> tiles;
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const int tr = (tasks[i].rows + GATHER_TILE - 1) / GATHER_TILE;
+    const int tc = (tasks[i].cols + GATHER_TILE - 1) / GATHER_TILE;
+    for (int a = 0; a < tr; ++a)
+      for (int b = 0; b < tc; ++b) tiles.push_back(make_int3((int)i, a, b));
+  }
+  P.tasks.upload(tasks, st);
+  P.srcs.upload(srcs, st);
+  P.tiles.upload(tiles, st);
+  P.ntiles = (int)tiles.size();
+}
+
+static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std::vector<GemmSeg>& segs,
+                       cudaStream_t st) {
+  std::vector<int3> tiles;
+  double fl = 0.0;
+  for (size_t i = 0; i < outs.size(); ++i) {
+    const int tm = (outs[i].m + GEMM_TILE - 1) / GEMM_TILE;
+    const int tn = (outs[i].n + GEMM_TILE - 1) / GEMM_TILE;
+    for (int a = 0; a < tm; ++a)
+      for (int b = 0; b < tn; ++b) tiles.push_back(make_int3((int)i, a, b));
+    for (int s = 0; s < outs[i].seg_count; ++s)
+      fl += 2.0 * outs[i].m * (double)outs[i].n * segs[outs[i].seg_begin + s].k;
+  }
+  // larger products first so the tail of the grid is short
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) {
+    const GemmOut& oa = outs[a.x];
+    const GemmOut& ob = outs[b.x];
+    int64_t ka = 0, kb = 0;
+    for (int s = 0; s < oa.seg_count; ++s) ka += segs[oa.seg_begin + s].k;
+    for (int s = 0; s < ob.seg_count; ++s) kb += segs[ob.seg_begin + s].k;
+    return ka > kb;
+  });
+  P.outs.upload(outs, st);
+  P.segs.upload(segs, st);
+  P.tiles.upload(tiles, st);
+  P.ntiles = (int)tiles.size();
+  P.flops = fl;
+}
+
+}  // namespace lrt
+
+// ===========================================================================
+// context
+// ===========================================================================
+namespace lrt {
+
+struct SiteTensor {
+  std::vector<int64_t> blk_off;     // per right-bond sector: start of its fused block (-1 if empty)
+  std::vector<int> blk_rows;        // fused rows of that block
+  // sub-block (q_l, n): offset of the D_l x D_r sub-block and its right sector
+  std::vector<std::array<int64_t, 4>> sub_off;   // per left-bond sector
+  std::vector<std::array<int, 4>> sub_qr;
+  int64_t total = 0;
+  double* d = nullptr;
+  SiteTensor() = default;
+  SiteTensor(SiteTensor&& o) noexcept
+      : blk_off(std::move(o.blk_off)), blk_rows(std::move(o.blk_rows)), sub_off(std::move(o.sub_off)),
+        sub_qr(std::move(o.sub_qr)), total(o.total), d(o.d) {
+    o.d = nullptr;
+  }
+  SiteTensor(const SiteTensor&) = delete;
+  ~SiteTensor() {
+    if (d) cudaFree(d);
+  }
+};
+
+static void site_layout(SiteTensor& S, const Sectors& L, const Sectors& R) {
+  S.blk_off.assign(R.n(), -1);
+  S.blk_rows.assign(R.n(), 0);
+  S.sub_off.assign(L.n(), {-1, -1, -1, -1});
+  S.sub_qr.assign(L.n(), {-1, -1, -1, -1});
+  int64_t off = 0;
+  for (int r = 0; r < R.n(); ++r) {
+    int rows = 0;
+    const int64_t start = off;
+    for (int n = 0; n < 4; ++n) {
+      const int l = L.find(R.a[r] - QNA[n], R.b[r] - QNB[n]);
+      if (l < 0) continue;
+      S.sub_off[l][n] = start + (int64_t)rows * R.d[r];
+      S.sub_qr[l][n] = r;
+      rows += L.d[l];
+    }
+    if (rows > 0) {
+      S.blk_off[r] = start;
+      S.blk_rows[r] = rows;
+    }
+    off += (int64_t)rows * R.d[r];
+  }
+  S.total = off;
+}
+
+struct SigmaPlan {
+  GemmPlan p1, p2;
+  DevArray<DiagOut> douts;
+  DevArray<DiagTerm> dterms;
+  int ndiag = 0;
+  double* tbuf = nullptr;
+  int64_t nelem = 0;
+  int n_terms = 0, n_products = 0;
+  double op_bytes = 0.0;
+  ~SigmaPlan() {
+    if (tbuf) cudaFree(tbuf);
+  }
+};
+
+}  // namespace lrt
+
+struct lrt_ctx {
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  bool have_ham = false;
+  lrt::Ints I;
+  bool have_mps = false;
+  int k = 0, na = 0, nb = 0;
+  std::vector<lrt::Sectors> bonds;
+  std::vector<lrt::SiteTensor> sites;
+  std::vector<std::unique_ptr<lrt::OpSet>> L, R, XL, YR;
+  std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
+  lrt_sigma_stats last{};
+};
+
+namespace lrt {
+
+static char left_mode(int b, int k) { return (2 * b <= k) ? 'N' : 'C'; }
+static char right_mode(int b, int k) { return (2 * b <= k) ? 'C' : 'N'; }
+
+static void drop_plans(lrt_ctx* c) { c->plans.clear(); }
+
+static std::unique_ptr<OpSet> vacuum(lrt_ctx* c, bool right) {
+  auto S = std::make_unique<OpSet>();
+  S->right = right;
+  const int b = right ? c->k : 0;
+  const Sectors& bt = c->bonds[b];
+  S->basis.add(bt.a[0], bt.b[0], 1);
+  make_keys(*S, {}, right ? right_mode(b, c->k) : left_mode(b, c->k), c->I.nso);
+  layout_blocks(*S);
+  alloc_zero(*S, c->st);
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(S->d + S->off_of(S->find(Key{KI, -1, -1}), 0), &one, sizeof(double),
+                     cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return S;
+}
+
+static void reset_env(lrt_ctx* c) {
+  drop_plans(c);
+  c->L.clear();
+  c->R.clear();
+  c->XL.clear();
+  c->YR.clear();
+  if (!c->have_mps || !c->have_ham) return;
+  c->L.resize(c->k + 1);
+  c->R.resize(c->k + 1);
+  c->XL.resize(c->k);
+  c->YR.resize(c->k);
+  c->L[0] = vacuum(c, false);
+  c->R[c->k] = vacuum(c, true);
+}
+
+// L[b] (+) site b  (right = false)   or   site b (+) R[b+1]  (right = true)
+static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
+  const Ints& I = c->I;
+  const OpSet& X = right ? *c->R[b + 1] : *c->L[b];
+  const Site site(b);
+  auto E = std::make_unique<OpSet>();
+  E->right = right;
+  E->fused = std::make_unique<Fused>(fuse(X.basis, right));
+  E->basis = E->fused->s;
+  std::vector<int> sorbs = {2 * b, 2 * b + 1};
+  std::vector<int> orbs;
+  if (right) {
+    orbs = sorbs;
+    orbs.insert(orbs.end(), X.orbs.begin(), X.orbs.end());
+  } else {
+    orbs = X.orbs;
+    orbs.insert(orbs.end(), sorbs.begin(), sorbs.end());
+  }
+  make_keys(*E, orbs, right ? right_mode(b, c->k) : left_mode(b + 1, c->k), I.nso);
+  layout_blocks(*E);
+  alloc_zero(*E, c->st);
+  const Fused& F = *E->fused;
+  auto terms = right ? blocking_terms(*E, sorbs, X.orbs, I) : blocking_terms(*E, X.orbs, sorbs, I);
+
+  std::vector<GatherTask> tasks;
+  std::vector<std::vector<GatherSrc>> tsrc;
+  std::unordered_map<const double*, int> task_of;
+  std::vector<Ref> refs;
+  for (size_t o = 0; o < E->keys.size(); ++o) {
+    std::map<std::pair<int, int>, Mat4> acc;
+    for (const Term& t : terms[o]) {
+      refs.clear();
+      Mat4 e4;
+      if (right) {
+        e4 = site.op(I, t.x.kind, t.x.p, t.x.q, t.x.t);
+        get_refs(X, I, t.y.kind, t.y.p, t.y.q, t.y.t, t.c, refs);
+      } else {
+        get_refs(X, I, t.x.kind, t.x.p, t.x.q, t.x.t, t.c, refs);
+        e4 = site.op(I, t.y.kind, t.y.p, t.y.q, t.y.t);
+      }
+      if (e4.zero()) continue;
+      for (const Ref& r : refs) acc[{r.op, r.t}].axpy(r.c, e4);
+    }
+    for (auto& kv : acc) {
+      const int j = kv.first.first, tr = kv.first.second;
+      const Mat4& e4 = kv.second;
+      if (e4.zero()) continue;
+      for (int s = 0; s < X.ns(); ++s) {
+        const int sb = X.bra_of(j, s);
+        if (sb < 0) continue;
+        const int be = tr ? s : sb, ke = tr ? sb : s;
+        const double* src = X.d + X.off_of(j, s);
+        const int ld = X.basis.d[s];
+        for (int n1 = 0; n1 < 4; ++n1)
+          for (int n0 = 0; n0 < 4; ++n0) {
+            const double e = e4(n1, n0);
+            if (e == 0.0) continue;
+            int fk, fb, sign;
+            if (right) {
+              fk = F.s.find(X.basis.a[ke] - QNA[n0], X.basis.b[ke] - QNB[n0]);
+              fb = F.s.find(X.basis.a[be] - QNA[n1], X.basis.b[be] - QNB[n1]);
+              sign = (X.par[j] && ((QNA[n0] + QNB[n0]) & 1)) ? -1 : 1;
+            } else {
+              fk = F.s.find(X.basis.a[ke] + QNA[n0], X.basis.b[ke] + QNB[n0]);
+              fb = F.s.find(X.basis.a[be] + QNA[n1], X.basis.b[be] + QNB[n1]);
+              const int sp = (QNA[n1] + QNB[n1] + QNA[n0] + QNB[n0]) & 1;
+              sign = (sp && ((X.basis.a[ke] + X.basis.b[ke]) & 1)) ? -1 : 1;
+            }
+            if (fk < 0 || fb < 0 || E->bra_of((int)o, fk) != fb)
+              throw Error(LRT_EINVAL, "internal: blocking term outside the operator's sector");
+            const int ldd = F.s.d[fk];
+            double* dst = E->d + E->off_of((int)o, fk) + (int64_t)F.off[fb][n1] * ldd + F.off[fk][n0];
+            auto it = task_of.find(dst);
+            int ti;
+            if (it == task_of.end()) {
+              ti = (int)tasks.size();
+              task_of[dst] = ti;
+              tasks.push_back(GatherTask{dst, ldd, X.basis.d[be], X.basis.d[ke], 0, 0});
+              tsrc.emplace_back();
+            } else {
+              ti = it->second;
+            }
+            tsrc[ti].push_back(GatherSrc{src, ld, tr, sign * e});
+          }
+      }
+    }
+  }
+  std::vector<GatherSrc> srcs;
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    tasks[i].src_begin = (int)srcs.size();
+    tasks[i].src_count = (int)tsrc[i].size();
+    srcs.insert(srcs.end(), tsrc[i].begin(), tsrc[i].end());
+  }
+  GatherPlan gp;
+  build_gather(gp, tasks, srcs, c->st);
+  gp.run(c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return E;
+}
+
+static OpSet& enlarged(lrt_ctx* c, int b, bool right) {
+  auto& slot = right ? c->YR[b] : c->XL[b];
+  if (!slot) {
+    if (right && !c->R[b + 1]) throw Error(LRT_ESTATE, "right block of bond " + std::to_string(b + 1) + " not built");
+    if (!right && !c->L[b]) throw Error(LRT_ESTATE, "left block of bond " + std::to_string(b) + " not built");
+    slot = enlarge(c, b, right);
+  }
+  return *slot;
+}
+
+static void renorm_left(lrt_ctx* c, int b) {
+  OpSet& E = enlarged(c, b, false);
+  const Fused& F = *E.fused;
+  const SiteTensor& T = c->sites[b];
+  auto N = std::make_unique<OpSet>();
+  N->right = false;
+  N->basis = c->bonds[b + 1];
+  make_keys(*N, E.orbs, E.mode, c->I.nso);
+  layout_blocks(*N);
+  alloc_zero(*N, c->st);
+  std::vector<GemmOut> o1, o2;
+  std::vector<GemmSeg> s1, s2;
+  int64_t toff = 0;
+  std::vector<int64_t> tpos;
+  for (size_t o = 0; o < N->keys.size(); ++o)
+    for (int q = 0; q < N->ns(); ++q) {
+      const int qb = N->bra_of((int)o, q);
+      if (qb < 0) continue;
+      const int fk = F.s.find(N->basis.a[q], N->basis.b[q]);
+      const int fb = F.s.find(N->basis.a[qb], N->basis.b[qb]);
+      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb) continue;
+      if (T.blk_off[q] < 0 || T.blk_off[qb] < 0) continue;
+      const int Dq = N->basis.d[q], Dqb = N->basis.d[qb];
+      const int rk = F.s.d[fk], rb = F.s.d[fb];
+      if (T.blk_rows[q] != rk || T.blk_rows[qb] != rb)
+        throw Error(LRT_EINVAL, "site tensor rows do not match the enlarged basis");
+      tpos.push_back(toff);
+      o1.push_back(GemmOut{nullptr, toff, Dq, rb, Dq, (int)s1.size(), 1, 0, 0});
+      s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), T.d + T.blk_off[q], 0, 0, rk, Dq, rk, 0, 0, 0, 0, 1.0});
+      o2.push_back(GemmOut{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 1, 0, 0});
+      s2.push_back(GemmSeg{T.d + T.blk_off[qb], nullptr, 0, toff, Dqb, Dq, rb, 1, 0, 0, 0, 1.0});
+      toff += (int64_t)rb * Dq;
+    }
+  double* tmp = nullptr;
+  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "renormalize workspace");
+  for (auto& x : o1) x.C = tmp + x.c_off;
+  for (auto& x : s2) x.B = tmp + x.b_off;
+  GemmPlan p1, p2;
+  build_gemm(p1, o1, s1, c->st);
+  build_gemm(p2, o2, s2, c->st);
+  p1.run(c->st, nullptr, nullptr);
+  p2.run(c->st, nullptr, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  if (tmp) cudaFree(tmp);
+  c->L[b + 1] = std::move(N);
+  for (int x = b + 2; x <= c->k; ++x) c->L[x].reset();
+  for (int x = b + 1; x < c->k; ++x) c->XL[x].reset();
+  drop_plans(c);
+}
+
+static void renorm_right(lrt_ctx* c, int b) {
+  OpSet& E = enlarged(c, b, true);
+  const Fused& F = *E.fused;
+  const SiteTensor& T = c->sites[b];
+  const Sectors& Lb = c->bonds[b];
+  // right-fused copy of the site tensor: per left sector q, D_q x fused(q), sub-blocks n side by side
+  std::vector<int64_t> rf_off(Lb.n(), -1);
+  int64_t rtot = 0;
+  for (int q = 0; q < Lb.n(); ++q) {
+    const int f = F.s.find(Lb.a[q], Lb.b[q]);
+    if (f < 0) continue;
+    rf_off[q] = rtot;
+    rtot += (int64_t)Lb.d[q] * F.s.d[f];
+  }
+  double* rf = nullptr;
+  if (rtot > 0 && cudaMalloc(&rf, (size_t)rtot * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "renormalize workspace");
+  CK(cudaMemsetAsync(rf, 0, (size_t)rtot * sizeof(double), c->st));
+  {
+    std::vector<GatherTask> tasks;
+    std::vector<GatherSrc> srcs;
+    for (int q = 0; q < Lb.n(); ++q) {
+      if (rf_off[q] < 0) continue;
+      const int f = F.s.find(Lb.a[q], Lb.b[q]);
+      for (int n = 0; n < 4; ++n) {
+        if (T.sub_off[q][n] < 0) continue;
+        const int qr = T.sub_qr[q][n];
+        const int Dr = c->bonds[b + 1].d[qr];
+        tasks.push_back(GatherTask{rf + rf_off[q] + F.off[f][n], F.s.d[f], Lb.d[q], Dr, (int)srcs.size(), 1});
+        srcs.push_back(GatherSrc{T.d + T.sub_off[q][n], Dr, 0, 1.0});
+      }
+    }
+    GatherPlan gp;
+    build_gather(gp, tasks, srcs, c->st);
+    gp.run(c->st);
+  }
+  auto N = std::make_unique<OpSet>();
+  N->right = true;
+  N->basis = Lb;
+  make_keys(*N, E.orbs, E.mode, c->I.nso);
+  layout_blocks(*N);
+  alloc_zero(*N, c->st);
+  std::vector<GemmOut> o1, o2;
+  std::vector<GemmSeg> s1, s2;
+  int64_t toff = 0;
+  for (size_t o = 0; o < N->keys.size(); ++o)
+    for (int q = 0; q < N->ns(); ++q) {
+      const int qb = N->bra_of((int)o, q);
+      if (qb < 0 || rf_off[q] < 0 || rf_off[qb] < 0) continue;
+      const int fk = F.s.find(Lb.a[q], Lb.b[q]);
+      const int fb = F.s.find(Lb.a[qb], Lb.b[qb]);
+      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb) continue;
+      const int Dq = Lb.d[q], Dqb = Lb.d[qb];
+      const int ck = F.s.d[fk], cb = F.s.d[fb];
+      o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 0});
+      s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), rf + rf_off[q], 0, 0, ck, ck, ck, 0, 1, 0, 0, 1.0});
+      o2.push_back(GemmOut{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 1, 0, 0});
+      s2.push_back(GemmSeg{rf + rf_off[qb], nullptr, 0, toff, cb, Dq, cb, 0, 0, 0, 0, 1.0});
+      toff += (int64_t)cb * Dq;
+    }
+  double* tmp = nullptr;
+  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess) {
+    cudaFree(rf);
+    throw Error(LRT_ENOMEM, "renormalize workspace");
+  }
+  for (auto& x : o1) x.C = tmp + x.c_off;
+  for (auto& x : s2) x.B = tmp + x.b_off;
+  GemmPlan p1, p2;
+  build_gemm(p1, o1, s1, c->st);
+  build_gemm(p2, o2, s2, c->st);
+  p1.run(c->st, nullptr, nullptr);
+  p2.run(c->st, nullptr, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  if (tmp) cudaFree(tmp);
+  if (rf) cudaFree(rf);
+  c->R[b] = std::move(N);
+  for (int x = 0; x < b; ++x) c->R[x].reset();
+  for (int x = 0; x < b; ++x) c->YR[x].reset();
+  drop_plans(c);
+}
+
+// ---------------------------------------------------------------------------
+// wavefunction layouts
+// ---------------------------------------------------------------------------
+struct WfnBlock {
+  int label_a, label_b;
+  int rows, cols;
+  int64_t off;
+};
+
+static std::vector<WfnBlock> wfn_blocks(lrt_ctx* c, int site, int nsite) {
+  std::vector<WfnBlock> out;
+  int64_t off = 0;
+  if (nsite == 1) {
+    const SiteTensor& T = c->sites[site];
+    const Sectors& R = c->bonds[site + 1];
+    for (int r = 0; r < R.n(); ++r) {
+      if (T.blk_rows[r] == 0) continue;
+      out.push_back(WfnBlock{R.a[r], R.b[r], T.blk_rows[r], R.d[r], off});
+      off += (int64_t)T.blk_rows[r] * R.d[r];
+    }
+    return out;
+  }
+  const Fused fl = fuse(c->bonds[site], false);
+  const Fused fr = fuse(c->bonds[site + 2], true);
+  for (int m = 0; m < fl.s.n(); ++m) {
+    const int j = fr.s.find(fl.s.a[m], fl.s.b[m]);
+    if (j < 0) continue;
+    out.push_back(WfnBlock{fl.s.a[m], fl.s.b[m], fl.s.d[m], fr.s.d[j], off});
+    off += (int64_t)fl.s.d[m] * fr.s.d[j];
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// sigma planning: y = sum_terms coef * sign * X_t psi Y_t^T
+// ---------------------------------------------------------------------------
+static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec) {
+  const Ints& I = c->I;
+  const int k = c->k;
+  OpSet& X = enlarged(c, site, false);
+  OpSet* Yp;
+  if (nsite == 1) {
+    if (!c->R[site + 1]) throw Error(LRT_ESTATE, "right block of bond " + std::to_string(site + 1) + " not built");
+    Yp = c->R[site + 1].get();
+  } else {
+    Yp = &enlarged(c, site + 1, true);
+  }
+  OpSet& Y = *Yp;
+  const std::vector<WfnBlock> wb = wfn_blocks(c, site, nsite);
+  std::unordered_map<int, int> blk_of;   // label key -> wfn block
+  for (size_t i = 0; i < wb.size(); ++i) blk_of[Sectors::key(wb[i].label_a, wb[i].label_b)] = (int)i;
+  int64_t nelem = 0;
+  for (auto& w : wb) nelem = std::max(nelem, w.off + (int64_t)w.rows * w.cols);
+
+  std::vector<Term> terms;
+  terms.push_back({1.0, {KH, -1, -1, 0}, {KI, -1, -1, 0}});
+  terms.push_back({1.0, {KI, -1, -1, 0}, {KH, -1, -1, 0}});
+  cross_terms(X.orbs, Y.orbs, 2 * (site + 1) <= k, terms);
+  if (I.e_core != 0.0) terms.push_back({I.e_core, {KI, -1, -1, 0}, {KI, -1, -1, 0}});
+
+  auto plan = std::make_unique<SigmaPlan>();
+  plan->nelem = nelem;
+  plan->n_terms = (int)terms.size();
+  // per output block: list of phase-2 segments (before replication over vectors)
+  std::vector<std::vector<GemmSeg>> seg2(wb.size());
+  std::vector<GemmOut> o1;
+  std::vector<GemmSeg> s1;
+  std::map<std::tuple<int, int, int>, int64_t> tcache;   // (X op, trans, X ket fused) -> T offset
+  int64_t toff = 0;
+  std::vector<DiagTerm> dt_all;
+  std::vector<std::vector<DiagTerm>> dterm(wb.size());
+  std::vector<Ref> rx, ry;
+  double op_bytes = 0.0;
+  int nprod = 0;
+  const int Ikey = X.find(Key{KI, -1, -1});
+  for (const Term& t : terms) {
+    rx.clear();
+    ry.clear();
+    get_refs(X, I, t.x.kind, t.x.p, t.x.q, t.x.t, 1.0, rx);
+    get_refs(Y, I, t.y.kind, t.y.p, t.y.q, t.y.t, 1.0, ry);
+    for (const Ref& a : rx)
+      for (const Ref& bref : ry) {
+        const double coef = t.c * a.c * bref.c;
+        for (int f = 0; f < X.ns(); ++f) {
+          const int fb0 = X.bra_of(a.op, f);
+          if (fb0 < 0) continue;
+          const int be = a.t ? f : fb0, ke = a.t ? fb0 : f;
+          auto ik = blk_of.find(Sectors::key(X.basis.a[ke], X.basis.b[ke]));
+          auto ib = blk_of.find(Sectors::key(X.basis.a[be], X.basis.b[be]));
+          if (ik == blk_of.end() || ib == blk_of.end()) continue;
+          const WfnBlock& wk = wb[ik->second];
+          const WfnBlock& wbb = wb[ib->second];
+          // Y block with effective ket label = ket label, effective bra label = bra label
+          const int yk = Y.basis.find(wk.label_a, wk.label_b);
+          const int ybb = Y.basis.find(wbb.label_a, wbb.label_b);
+          if (yk < 0 || ybb < 0) continue;
+          const double* Bp;
+          int transB, ldb;
+          if (!bref.t) {
+            if (Y.bra_of(bref.op, yk) != ybb) continue;
+            Bp = Y.d + Y.off_of(bref.op, yk);
+            transB = 1;
+            ldb = Y.basis.d[yk];
+          } else {
+            if (Y.bra_of(bref.op, ybb) != yk) continue;
+            Bp = Y.d + Y.off_of(bref.op, ybb);
+            transB = 0;
+            ldb = Y.basis.d[ybb];
+          }
+          const int sign = (Y.par[bref.op] && ((wk.label_a + wk.label_b) & 1)) ? -1 : 1;
+          const double sc = coef * sign;
+          ++nprod;
+          op_bytes += 8.0 * ((double)Y.basis.d[yk] * Y.basis.d[ybb]);
+          GemmSeg g2{};
+          g2.B = Bp;
+          g2.ldb = ldb;
+          g2.transB = transB;
+          g2.k = wk.cols;
+          g2.scale = sc;
+          if (a.op == Ikey) {
+            g2.a_rel = 1;
+            g2.a_off = wk.off;
+            g2.lda = wk.cols;
+          } else {
+            const auto key = std::make_tuple(a.op, a.t, f);
+            auto it = tcache.find(key);
+            int64_t tp;
+            if (it == tcache.end()) {
+              tp = toff;
+              tcache[key] = tp;
+              o1.push_back(GemmOut{nullptr, tp, wk.cols, wbb.rows, wk.cols, (int)s1.size(), 1, 0, 0});
+              GemmSeg g1{};
+              g1.A = X.d + X.off_of(a.op, f);
+              g1.lda = X.basis.d[f];
+              g1.transA = a.t;
+              g1.b_rel = 1;
+              g1.b_off = wk.off;
+              g1.ldb = wk.cols;
+              g1.k = wk.rows;
+              g1.scale = 1.0;
+              s1.push_back(g1);
+              toff += (int64_t)wbb.rows * wk.cols;
+              op_bytes += 8.0 * ((double)wbb.rows * wk.rows);
+            } else {
+              tp = it->second;
+            }
+            g2.A = nullptr;
+            g2.a_off = tp;
+            g2.lda = wk.cols;
+          }
+          seg2[ib->second].push_back(g2);
+          // diagonal contribution
+          if (be == ke && yk == ybb) {
+            DiagTerm d{};
+            d.x = (a.op == Ikey) ? nullptr : X.d + X.off_of(a.op, f);
+            d.xs = X.basis.d[f] + 1;
+            d.y = Bp;
+            d.ys = Y.basis.d[yk] + 1;
+            d.scale = sc;
+            dterm[ik->second].push_back(d);
+          }
+        }
+      }
+  }
+  // device workspace for the intermediates of all vectors
+  if (toff > 0 && cudaMalloc(&plan->tbuf, (size_t)toff * nvec * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "sigma workspace");
+  std::vector<GemmOut> O1, O2;
+  std::vector<GemmSeg> S1, S2;
+  for (int v = 0; v < nvec; ++v) {
+    for (const GemmOut& x : o1) {
+      GemmOut y = x;
+      y.C = plan->tbuf + x.c_off + (int64_t)v * toff;
+      y.c_off = 0;
+      y.seg_begin = (int)S1.size();
+      S1.push_back(s1[x.seg_begin]);
+      S1.back().b_off += (int64_t)v * nelem;
+      O1.push_back(y);
+    }
+    for (size_t w = 0; w < wb.size(); ++w) {
+      GemmOut y{nullptr, wb[w].off + (int64_t)v * nelem, wb[w].cols, wb[w].rows, wb[w].cols,
+                (int)S2.size(), (int)seg2[w].size(), 0, 1};
+      for (GemmSeg g : seg2[w]) {
+        if (g.a_rel) g.a_off += (int64_t)v * nelem;
+        else g.A = plan->tbuf + g.a_off + (int64_t)v * toff;
+        S2.push_back(g);
+      }
+      O2.push_back(y);
+    }
+  }
+  build_gemm(plan->p1, O1, S1, c->st);
+  build_gemm(plan->p2, O2, S2, c->st);
+  std::vector<DiagOut> dout;
+  std::vector<DiagTerm> dts;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    dout.push_back(DiagOut{wb[w].off, wb[w].rows, wb[w].cols, (int)dts.size(), (int)dterm[w].size()});
+    dts.insert(dts.end(), dterm[w].begin(), dterm[w].end());
+  }
+  plan->douts.upload(dout, c->st);
+  plan->dterms.upload(dts, c->st);
+  plan->ndiag = (int)dout.size();
+  plan->n_products = nprod;
+  plan->op_bytes = op_bytes;
+  CK(cudaStreamSynchronize(c->st));
+  return plan;
+}
+
+static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
+  auto key = std::make_tuple(site, nsite, nvec);
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) return *it->second;
+  auto p = plan_sigma(c, site, nsite, nvec);
+  SigmaPlan& ref = *p;
+  c->plans[key] = std::move(p);
+  return ref;
+}
+
+}  // namespace lrt
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace lrt;
+
+static thread_local std::string g_create_err;
+
+template <class F>
+static int guard(lrt_ctx* c, F&& f) {
+  if (!c) return LRT_EINVAL;
+  try {
+    CK(cudaSetDevice(c->dev));
+    f();
+    c->err.clear();
+    return LRT_OK;
+  } catch (const Error& e) {
+    c->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return LRT_ENOMEM;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return LRT_EINVAL;
+  }
+}
+
+extern "C" {
+
+int lrt_create(lrt_t* out, int device, void* cuda_stream) {
+  if (!out) return LRT_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    g_create_err = "no CUDA device " + std::to_string(device);
+    return LRT_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    g_create_err = "cudaSetDevice failed";
+    return LRT_ECUDA;
+  }
+  auto* c = new (std::nothrow) lrt_ctx();
+  if (!c) return LRT_ENOMEM;
+  c->dev = device;
+  c->st = (cudaStream_t)cuda_stream;
+  *out = c;
+  return LRT_OK;
+}
+
+int lrt_destroy(lrt_t ctx) {
+  if (!ctx) return LRT_EINVAL;
+  cudaSetDevice(ctx->dev);
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+  return LRT_OK;
+}
+
+const char* lrt_last_error(lrt_t ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int op_build(lrt_t ctx, int k, const double* h, const double* eri, int n_factor, const double* B,
+             double e_core) {
+  return guard(ctx, [&] {
+    if (k <= 0 || k > 128 || !h || (!eri && (!B || n_factor <= 0)))
+      throw Error(LRT_EINVAL, "op_build: bad arguments");
+    if (ctx->have_mps && ctx->k != k) throw Error(LRT_EINVAL, "op_build: k differs from the loaded MPS");
+    build_ints(ctx->I, k, h, eri, n_factor, B, e_core);
+    ctx->have_ham = true;
+    reset_env(ctx);
+  });
+}
+
+int mps_load(lrt_t ctx, const lrt_mps_desc* m) {
+  return guard(ctx, [&] {
+    if (!m || m->k <= 0 || !m->bond_nsect || !m->bond_sectors || !m->site_data)
+      throw Error(LRT_EINVAL, "mps_load: bad descriptor");
+    if (ctx->have_ham && ctx->I.k != m->k) throw Error(LRT_EINVAL, "mps_load: k differs from op_build");
+    std::vector<Sectors> bonds(m->k + 1);
+    int pos = 0;
+    for (int b = 0; b <= m->k; ++b) {
+      if (m->bond_nsect[b] <= 0) throw Error(LRT_EINVAL, "mps_load: empty bond " + std::to_string(b));
+      for (int s = 0; s < m->bond_nsect[b]; ++s, ++pos) {
+        const int* t = m->bond_sectors + 3 * pos;
+        if (t[2] <= 0) throw Error(LRT_EINVAL, "mps_load: non-positive sector dimension");
+        if (bonds[b].find(t[0], t[1]) >= 0) throw Error(LRT_EINVAL, "mps_load: duplicate sector");
+        bonds[b].add(t[0], t[1], t[2]);
+      }
+    }
+    if (bonds[0].n() != 1 || bonds[0].a[0] != 0 || bonds[0].b[0] != 0 || bonds[0].d[0] != 1)
+      throw Error(LRT_EINVAL, "mps_load: bond 0 must be the single sector (0,0,1)");
+    if (bonds[m->k].n() != 1 || bonds[m->k].a[0] != m->n_alpha || bonds[m->k].b[0] != m->n_beta ||
+        bonds[m->k].d[0] != 1)
+      throw Error(LRT_EINVAL, "mps_load: bond k must be the single sector (n_alpha,n_beta,1)");
+    std::vector<SiteTensor> sites(m->k);
+    for (int i = 0; i < m->k; ++i) {
+      site_layout(sites[i], bonds[i], bonds[i + 1]);
+      if (sites[i].total > 0) {
+        if (!m->site_data[i]) throw Error(LRT_EINVAL, "mps_load: missing site data");
+        if (cudaMalloc(&sites[i].d, (size_t)sites[i].total * sizeof(double)) != cudaSuccess)
+          throw Error(LRT_ENOMEM, "mps_load: device allocation");
+        CK(cudaMemcpyAsync(sites[i].d, m->site_data[i], (size_t)sites[i].total * sizeof(double),
+                           cudaMemcpyHostToDevice, ctx->st));
+      }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->k = m->k;
+    ctx->na = m->n_alpha;
+    ctx->nb = m->n_beta;
+    ctx->bonds = std::move(bonds);
+    ctx->sites = std::move(sites);
+    ctx->have_mps = true;
+    reset_env(ctx);
+  });
+}
+
+int wfn_layout(lrt_t ctx, int site, int nsite, int64_t* nelem, int* nblocks, int64_t* block_offsets) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps) throw Error(LRT_ESTATE, "wfn_layout: no MPS loaded");
+    if (nsite < 1 || nsite > 2 || site < 0 || site + nsite > ctx->k) throw Error(LRT_EINVAL, "wfn_layout: bad site");
+    auto wb = wfn_blocks(ctx, site, nsite);
+    int64_t n = 0;
+    for (auto& w : wb) n = std::max(n, w.off + (int64_t)w.rows * w.cols);
+    if (nelem) *nelem = n;
+    if (nblocks) *nblocks = (int)wb.size();
+    if (block_offsets)
+      for (size_t i = 0; i < wb.size(); ++i) block_offsets[i] = wb[i].off;
+  });
+}
+
+int renormalize(lrt_t ctx, int site, int dir, int precision) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "renormalize: op_build and mps_load first");
+    if (site < 0 || site >= ctx->k || (dir != 1 && dir != -1)) throw Error(LRT_EINVAL, "renormalize: bad site/dir");
+    if (precision != LRT_FP64 && precision != LRT_MIXED) throw Error(LRT_EINVAL, "renormalize: bad precision");
+    if (dir == 1) {
+      if (!ctx->L[site]) throw Error(LRT_ESTATE, "renormalize: left block of bond " + std::to_string(site) + " missing");
+      renorm_left(ctx, site);
+    } else {
+      if (!ctx->R[site + 1]) throw Error(LRT_ESTATE, "renormalize: right block of bond " + std::to_string(site + 1) + " missing");
+      renorm_right(ctx, site);
+    }
+  });
+}
+
+int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double* y_dev, int precision) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "sigma: op_build and mps_load first");
+    if (nsite < 1 || nsite > 2 || site < 0 || site + nsite > ctx->k || nvec <= 0 || !x_dev || !y_dev)
+      throw Error(LRT_EINVAL, "sigma: bad arguments");
+    if (precision != LRT_FP64 && precision != LRT_MIXED) throw Error(LRT_EINVAL, "sigma: bad precision");
+    if (!ctx->L[site]) throw Error(LRT_ESTATE, "sigma: left block of bond " + std::to_string(site) + " missing");
+    SigmaPlan& p = get_plan(ctx, site, nsite, nvec);
+    if ((const double*)y_dev < x_dev + p.nelem * nvec && x_dev < (const double*)y_dev + p.nelem * nvec)
+      throw Error(LRT_EINVAL, "sigma: x and y overlap");
+    p.p1.run(ctx->st, x_dev, y_dev);
+    p.p2.run(ctx->st, x_dev, y_dev);
+    CK(cudaGetLastError());
+    ctx->last.flops = p.p1.flops + p.p2.flops;
+    ctx->last.launches = (p.p1.ntiles > 0) + (p.p2.ntiles > 0);
+    ctx->last.n_terms = p.n_terms;
+    ctx->last.n_products = p.n_products;
+    ctx->last.op_bytes = p.op_bytes;
+  });
+}
+
+int heff_diag(lrt_t ctx, int site, int nsite, double* d_dev) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "heff_diag: op_build and mps_load first");
+    if (nsite < 1 || nsite > 2 || site < 0 || site + nsite > ctx->k || !d_dev) throw Error(LRT_EINVAL, "heff_diag: bad arguments");
+    if (!ctx->L[site]) throw Error(LRT_ESTATE, "heff_diag: left block missing");
+    SigmaPlan& p = get_plan(ctx, site, nsite, 1);
+    launch_diag(p.douts.p, p.dterms.p, p.ndiag, d_dev, ctx->st);
+    CK(cudaGetLastError());
+  });
+}
+
+int sigma_stats(lrt_t ctx, lrt_sigma_stats* out) {
+  return guard(ctx, [&] {
+    if (!out) throw Error(LRT_EINVAL, "sigma_stats: NULL");
+    *out = ctx->last;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Device work descriptors and kernel launchers of the DMRG sigma / renormalization path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lrt {
+
+// dst (rows x cols, leading dimension ld_dst) = sum_s scale_s * op(src_s), op = transpose or not.
+struct GatherTask {
+  double* dst;
+  int ld_dst;
+  int rows, cols;
+  int src_begin, src_count;
+};
+struct GatherSrc {
+  const double* src;
+  int ld;
+  int trans;
+  double scale;
+};
+
+// C (m x n, ldc) = [C +] sum_s scale_s * op(A_s) (m x k_s) * op(B_s) (k_s x n).
+// Pointers flagged *_rel are offsets (in doubles) from the x (A, B) or y (C) base
+// pointer passed at launch, so one plan serves any caller buffers.
+struct GemmOut {
+  double* C;
+  int64_t c_off;
+  int ldc;
+  int m, n;
+  int seg_begin, seg_count;
+  int accumulate;
+  int c_rel;
+};
+struct GemmSeg {
+  const double* A;
+  const double* B;
+  int64_t a_off, b_off;
+  int lda, ldb;
+  int k;
+  int transA, transB;
+  int a_rel, b_rel;
+  double scale;
+};
+
+// diag (rows x cols block, row-major) += sum_t scale_t * x_t[i] * y_t[j]   (x_t, y_t strided diagonals)
+struct DiagOut {
+  int64_t d_off;     // offset of the output block from the base pointer passed at launch
+  int rows, cols;
+  int term_begin, term_count;
+};
+struct DiagTerm {
+  const double* x;   // diagonal of the X block: x[i * xs], or NULL for the identity
+  const double* y;   // diagonal of the Y block: y[j * ys], or NULL for the identity
+  int xs, ys;
+  double scale;
+};
+
+// work items: (task index, tile row, tile col) packed as int3
+void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
+                   cudaStream_t st);
+void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                      const double* xbase, double* ybase, cudaStream_t st);
+void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
+
+constexpr int GATHER_TILE = 32;
+constexpr int GEMM_TILE = 64;
+
+}  // namespace lrt

@@ -328,17 +328,23 @@ def layout_size(layout: list[tuple]) -> int:
     return sum(e[3] * e[4] for e in layout)
 
 
-def twosite_layout(left: list, mid: list, right: list) -> list[tuple]:
-    """Layout of a two-site wavefunction on bonds (left, mid, right).
+def twosite_layout(left: list, right: list) -> list[tuple]:
+    """Layout of a two-site wavefunction between bond tables `left` (bond i) and `right` (bond i+2).
 
-    Returns [(q_l, n1, n2, q_r, D_l, D_r, offset, row_off, col_off, rows, cols, block_off)]
+    The middle label q_m runs over every sector reachable from both sides
+    (q_l + n1 = q_m = q_r - n2), in (N_alpha, N_beta) order.  Returns
+    [(q_l, n1, n2, q_r, D_l, D_r, offset, row_off, col_off, rows, cols, block_off)]
     in storage order, one entry per sub-block.
     """
     ldim = {(a, b): d for a, b, d in left}
     rdim = {(a, b): d for a, b, d in right}
+    mids = set()
+    for ql in ldim:
+        for s in QN_SITE:
+            mids.add((ql[0] + s[0], ql[1] + s[1]))
     out = []
     off = 0
-    for (ma, mb, _dm) in mid:
+    for (ma, mb) in sorted(mids):
         lsub = []
         for n1, s in enumerate(QN_SITE):
             ql = (ma - s[0], mb - s[1])
@@ -364,6 +370,10 @@ def twosite_layout(left: list, mid: list, right: list) -> list[tuple]:
     return out
 
 
+def twosite_size(layout: list[tuple]) -> int:
+    return max((e[11] + e[9] * e[10] for e in layout), default=0)
+
+
 @dataclass
 class MPS:
     """Matrix product state in the shared packed format (see module docstring)."""
@@ -378,8 +388,14 @@ class MPS:
         return site_layout(self.bonds[i], self.bonds[i + 1])
 
 
-def random_mps(k: int, n_alpha: int, n_beta: int, M: int, seed: int) -> MPS:
-    """Random MPS: every sub-block ~ N(0,1) / sqrt(fused rows of its block)."""
+def random_mps(k: int, n_alpha: int, n_beta: int, M: int, seed: int, canonical: str | None = None) -> MPS:
+    """Random MPS: every sub-block ~ N(0,1) / sqrt(fused rows of its block).
+
+    canonical="left" turns every fused block (rows (n, l), columns r) into a
+    random isometry with orthonormal columns, canonical="right" every
+    right-fused block (rows l, columns (n, r)) into one with orthonormal rows
+    (Householder QR of the Gaussian draw, signs fixed by the diagonal of R).
+    """
     bonds = bond_tables(k, n_alpha, n_beta, M)
     sites = []
     for i in range(k):
@@ -391,8 +407,57 @@ def random_mps(k: int, n_alpha: int, n_beta: int, M: int, seed: int) -> MPS:
             rows[qr] = rows.get(qr, 0) + dl
         for (ql, n, qr, dl, dr, off) in lay:
             arr[off:off + dl * dr] = st.normal(dl * dr) / math.sqrt(rows[qr])
+        if canonical == "left":
+            _isometrize_left(arr, lay)
+        elif canonical == "right":
+            _isometrize_right(arr, lay)
         sites.append(arr)
     return MPS(k, n_alpha, n_beta, bonds, sites)
+
+
+def _orthonormal_columns(G: np.ndarray) -> np.ndarray:
+    Q, R = np.linalg.qr(G)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d
+
+
+def _isometrize_left(arr, lay):
+    by_r = {}
+    for e in lay:
+        by_r.setdefault(e[2], []).append(e)
+    for qr, ents in by_r.items():
+        dr = ents[0][4]
+        G = np.vstack([arr[e[5]:e[5] + e[3] * dr].reshape(e[3], dr) for e in ents])
+        Q = _orthonormal_columns(G)
+        r0 = 0
+        for e in ents:
+            arr[e[5]:e[5] + e[3] * dr] = Q[r0:r0 + e[3]].ravel()
+            r0 += e[3]
+
+
+def _isometrize_right(arr, lay):
+    by_l = {}
+    for e in lay:
+        by_l.setdefault(e[0], []).append(e)
+    for ql, ents in by_l.items():
+        dl = ents[0][3]
+        G = np.hstack([arr[e[5]:e[5] + dl * e[4]].reshape(dl, e[4]) for e in ents])
+        Q = _orthonormal_columns(G.T).T
+        c0 = 0
+        for e in ents:
+            arr[e[5]:e[5] + dl * e[4]] = Q[:, c0:c0 + e[4]].ravel()
+            c0 += e[4]
+
+
+def mixed_mps(k: int, n_alpha: int, n_beta: int, M: int, seed: int, center: int) -> MPS:
+    """Random MPS in a mixed-canonical gauge: sites < center left-orthonormal,
+    sites > center right-orthonormal, the centre site Gaussian."""
+    A = random_mps(k, n_alpha, n_beta, M, seed, "left")
+    B = random_mps(k, n_alpha, n_beta, M, seed + 7777, "right")
+    C = random_mps(k, n_alpha, n_beta, M, seed + 9999)
+    sites = [A.sites[i] if i < center else (C.sites[i] if i == center else B.sites[i]) for i in range(k)]
+    return MPS(k, n_alpha, n_beta, A.bonds, sites, center)
 
 
 def random_vector(n: int, seed: int) -> np.ndarray:

@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function of include/lrt.h (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "lrt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1311_1646_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load",
+                     "wfn_layout", "renormalize", "sigma", "heff_diag", "sigma_stats"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    import paper_1311_1646_gb300 as pkg
+    assert set(_declared_functions()) <= set(pkg.EXPORTS)
+
+
+def test_bad_arguments_are_rejected_without_a_gpu(lib):
+    # NULL handles and NULL outputs return LRT_EINVAL before any CUDA call
+    lib.lrt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert lib.lrt_create(None, 0, None) == -1
+    lib.sigma.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_int]
+    assert lib.sigma(None, 0, 1, 1, None, None, 0) == -1
+    lib.lrt_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.lrt_destroy(None) == -1
+
+
+def test_product_path_fails_loudly_without_the_library(tmp_path):
+    import paper_1311_1646_gb300 as pkg
+    saved = pkg._lib
+    try:
+        pkg._lib = None
+        with pytest.raises(pkg.LrtError):
+            pkg.load(str(tmp_path / "missing.so"))
+    finally:
+        pkg._lib = saved

@@ -219,7 +219,7 @@ def test_sigma_twosite_equals_projected_H(k, na, nb, M):
         env.grow_right(b, sites[b])
     rng = np.random.default_rng(1)
     for i in range(k - 1):
-        P, idx = om.product_basis_twosite(sites, i, k, dets, m.bonds[i + 1])
+        P, idx = om.product_basis_twosite(sites, i, k, dets)
         x = rng.standard_normal(P.shape[1])
         y0 = P.T @ (Hd @ (P @ x))
         y = om.blocks_to_vec(ob.sigma_twosite(env, i, om.vec_to_blocks(x, idx)), idx)
@@ -238,14 +238,13 @@ def test_sigma_hermitian_and_packing_roundtrip():
     for b in range(2):
         env.grow_left(b, sites[b])
     i = 2
-    lay = synth.twosite_layout(m.bonds[i], m.bonds[i + 1], m.bonds[i + 2])
-    n = max(e[11] + e[9] * e[10] for e in lay)
+    lt, rt = m.bonds[i], m.bonds[i + 2]
+    n = synth.twosite_size(synth.twosite_layout(lt, rt))
     x = synth.random_vector(n, 1)
     y = synth.random_vector(n, 2)
-    assert np.array_equal(om.pack_twosite(om.unpack_twosite(x, *[m.bonds[j] for j in (i, i + 1, i + 2)]),
-                                          *[m.bonds[j] for j in (i, i + 1, i + 2)]), x)
-    bx = om.unpack_twosite(x, m.bonds[i], m.bonds[i + 1], m.bonds[i + 2])
-    by = om.unpack_twosite(y, m.bonds[i], m.bonds[i + 1], m.bonds[i + 2])
+    assert np.array_equal(om.pack_twosite(om.unpack_twosite(x, lt, rt), lt, rt), x)
+    bx = om.unpack_twosite(x, lt, rt)
+    by = om.unpack_twosite(y, lt, rt)
     Hx = ob.sigma_twosite(env, i, bx)
     Hy = ob.sigma_twosite(env, i, by)
     a = sum(np.sum(by[kk] * Hx[kk]) for kk in bx)
