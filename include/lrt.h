@@ -73,13 +73,14 @@ const char* lrt_last_error(lrt_t ctx);
 int op_build(lrt_t ctx, int k, const double* h, const double* eri, int n_factor,
              const double* B, double e_core);
 
-/* Matrix product state (Eqs. mps_wave_gen, mps_wave).  bond_nsect[b] sectors for
- * b = 0..k; bond_sectors holds (N_a, N_b, D) triples of all bonds concatenated;
- * site_data[i] is the host pointer to site i in the left-fused layout.  Bond 0
- * must be the single sector (0,0,1) and bond k the single sector (n_alpha, n_beta, 1).
- * Renormalization assumes site tensors left of the working site left-orthonormal
- * and those right of it right-orthonormal (the mixed-canonical gauge).  Copied to
- * the device; drops all renormalized blocks. */
+/* Matrix product state (Eqs. mps_wave_gen, mps_wave, gauge-shift).  bond_nsect[b]
+ * sectors for b = 0..k; bond_sectors holds (N_a, N_b, D) triples of all bonds
+ * concatenated; site_data[i] is the host pointer to site i in the left-fused layout.
+ * Bond 0 must be the single sector (0,0,1) and bond k the single sector
+ * (n_alpha, n_beta, 1).  Left blocks are renormalized with site_data (the
+ * left-orthonormal L_i of the mixed-canonical gauge) and right blocks with
+ * site_data_right (the right-orthonormal R_i, same layout), or with site_data when
+ * site_data_right is NULL.  Copied to the device; drops all renormalized blocks. */
 typedef struct {
   int k;
   int n_alpha;
@@ -88,6 +89,7 @@ typedef struct {
   const int* bond_sectors;
   const double* const* site_data;
   int center;
+  const double* const* site_data_right;
 } lrt_mps_desc;
 int mps_load(lrt_t ctx, const lrt_mps_desc* mps);
 
@@ -116,10 +118,13 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
 int heff_diag(lrt_t ctx, int site, int nsite, double* d_dev);
 
 /* Statistics of the last sigma call: algorithmic FLOPs (2mnk summed over the
- * block products actually needed), number of GPU kernel launches, and the total
- * bytes of operator data read. */
+ * products of non-zero sub-blocks of the operators, zero padding excluded),
+ * FLOPs issued by the kernels (fused blocks, zero sub-blocks included), bytes
+ * of operator data read, kernel launches, terms of the decomposition and
+ * block products. */
 typedef struct {
   double flops;
+  double flops_issued;
   double op_bytes;
   int launches;
   int n_terms;

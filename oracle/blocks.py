@@ -517,10 +517,14 @@ class Environment:
 # ----------------------------------------------------------------------------
 # sigma = H_eff x (Eq. dmrg) and its diagonal (Eq. error)
 # ----------------------------------------------------------------------------
+FLOP_COUNTER = [0.0]    # 2mnk of every block product done by apply_terms
+
+
 def apply_terms(X: Block, Y: Block, terms, psi):
     """y = sum_t coef_t (X_t (x) Y_t) psi, psi: dict (x_label, y_label) -> matrix.
 
     In matrix form each term is Y[x', y'] += sign * X_t[x', x] @ psi[x, y] @ Y_t[y', y]^T.
+    FLOP_COUNTER accumulates the multiply-add count of the block products.
     """
     out = {kk: np.zeros_like(m) for kk, m in psi.items()}
     by_x = {}
@@ -545,11 +549,13 @@ def apply_terms(X: Block, Y: Block, terms, psi):
                 if yl not in ymap:
                     continue
                 t1 = mx @ m
+                FLOP_COUNTER[0] += 2.0 * mx.shape[0] * mx.shape[1] * m.shape[1]
                 for yb, my in ymap[yl]:
                     key = (xb, yb)
                     if key not in out:
                         continue          # outside the target sector: zero by symmetry
                     out[key] = out[key] + (coef * sgn) * (t1 @ my.T)
+                    FLOP_COUNTER[0] += 2.0 * t1.shape[0] * t1.shape[1] * my.shape[0]
     return out
 
 

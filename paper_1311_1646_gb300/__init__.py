@@ -29,11 +29,13 @@ class MpsDesc(ctypes.Structure):
                 ("bond_nsect", ctypes.POINTER(ctypes.c_int)),
                 ("bond_sectors", ctypes.POINTER(ctypes.c_int)),
                 ("site_data", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
-                ("center", ctypes.c_int)]
+                ("center", ctypes.c_int),
+                ("site_data_right", ctypes.POINTER(ctypes.POINTER(ctypes.c_double)))]
 
 
 class SigmaStats(ctypes.Structure):
-    _fields_ = [("flops", ctypes.c_double), ("op_bytes", ctypes.c_double), ("launches", ctypes.c_int),
+    _fields_ = [("flops", ctypes.c_double), ("flops_issued", ctypes.c_double), ("op_bytes", ctypes.c_double),
+                ("launches", ctypes.c_int),
                 ("n_terms", ctypes.c_int), ("n_products", ctypes.c_int)]
 
 
@@ -128,13 +130,20 @@ class Context:
         self._check(self.lib.op_build(self.h, k, _dptr(h), _dptr(e) if e is not None else None, nL,
                                       _dptr(b) if b is not None else None, float(e_core)), "op_build")
 
-    def mps_load(self, k: int, n_alpha: int, n_beta: int, bonds: list, sites: list, center: int = 0):
+    def mps_load(self, k: int, n_alpha: int, n_beta: int, bonds: list, sites: list, center: int = 0,
+                 sites_right: list | None = None):
+        """Load an MPS: `sites` (left-orthonormal form, left-fused layout) and optionally the
+        right-orthonormal form `sites_right` of every site (same layout)."""
         nsect = np.array([len(t) for t in bonds], dtype=np.int32)
         secs = np.array([x for t in bonds for s in t for x in s], dtype=np.int32)
         arrs = [np.ascontiguousarray(s, dtype=np.float64) for s in sites]
         ptrs = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in arrs])
+        rptrs = None
+        if sites_right is not None:
+            rarrs = [np.ascontiguousarray(s, dtype=np.float64) for s in sites_right]
+            rptrs = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in rarrs])
         desc = MpsDesc(k, n_alpha, n_beta, nsect.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                       secs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptrs, center)
+                       secs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptrs, center, rptrs)
         self._check(self.lib.mps_load(self.h, ctypes.byref(desc)), "mps_load")
 
     def wfn_layout(self, site: int, nsite: int):
@@ -162,5 +171,5 @@ class Context:
     def stats(self) -> dict:
         s = SigmaStats()
         self._check(self.lib.sigma_stats(self.h, ctypes.byref(s)), "sigma_stats")
-        return {"flops": s.flops, "op_bytes": s.op_bytes, "launches": s.launches,
+        return {"flops": s.flops, "flops_issued": s.flops_issued, "op_bytes": s.op_bytes, "launches": s.launches,
                 "n_terms": s.n_terms, "n_products": s.n_products}

@@ -81,6 +81,7 @@ struct Fused {
   Sectors s;                        // fused labels and total dims
   std::vector<std::array<int, 4>> sub;   // source sector of sub-block n, or -1
   std::vector<std::array<int, 4>> off;   // row/col offset of sub-block n
+  std::vector<std::array<int, 4>> dim;   // dimension of sub-block n (0 if absent)
 };
 
 static Fused fuse(const Sectors& src, bool right) {
@@ -93,7 +94,7 @@ static Fused fuse(const Sectors& src, bool right) {
     }
   Fused f;
   for (auto& kv : labels) {
-    std::array<int, 4> sub, off;
+    std::array<int, 4> sub, off, dim;
     int tot = 0;
     for (int n = 0; n < 4; ++n) {
       int qa = right ? kv.first.first + QNA[n] : kv.first.first - QNA[n];
@@ -101,12 +102,14 @@ static Fused fuse(const Sectors& src, bool right) {
       int s = src.find(qa, qb);
       sub[n] = s;
       off[n] = tot;
-      if (s >= 0) tot += src.d[s];
+      dim[n] = s >= 0 ? src.d[s] : 0;
+      tot += dim[n];
     }
     if (tot == 0) continue;
     f.s.add(kv.first.first, kv.first.second, tot);
     f.sub.push_back(sub);
     f.off.push_back(off);
+    f.dim.push_back(dim);
   }
   return f;
 }
@@ -205,6 +208,16 @@ struct OpSet {
   int64_t total = 0;
   double* d = nullptr;
   std::unique_ptr<Fused> fused;   // for enlarged sets
+  std::vector<uint16_t> mask;     // enlarged sets: nonzero sub-blocks (bit 4*n_bra + n_ket) per block
+  std::vector<char> bnz;          // per block: not identically zero (structural zeros are skipped)
+  std::vector<char> onz;          // per operator: some block not identically zero
+  bool block_nz(int op, int ket) const { return bnz[(size_t)op * ns() + ket] != 0; }
+  void finish_nz() {
+    onz.assign(keys.size(), 0);
+    for (size_t o = 0; o < keys.size(); ++o)
+      for (int s = 0; s < ns(); ++s)
+        if (bnz[o * ns() + s]) onz[o] = 1;
+  }
   OpSet() = default;
   OpSet(const OpSet&) = delete;
   ~OpSet() {
@@ -257,6 +270,7 @@ static void layout_blocks(OpSet& S) {
   const int sg = S.right ? -1 : 1;
   S.bra.assign((size_t)nop * ns, -1);
   S.off.assign((size_t)nop * ns, -1);
+  S.bnz.assign((size_t)nop * ns, 0);
   S.total = 0;
   for (int o = 0; o < nop; ++o)
     for (int s = 0; s < ns; ++s) {
@@ -381,7 +395,7 @@ static void get_refs(const OpSet& S, const Ints& I, int kind, int p, int q, int 
                      std::vector<Ref>& out) {
   auto stored = [&](int kk, int a, int b, int tt, double cc) {
     int o = S.find(Key{kk, a, b});
-    if (o >= 0) out.push_back(Ref{o, tt, cc});
+    if (o >= 0 && (S.onz.empty() || S.onz[o])) out.push_back(Ref{o, tt, cc});
   };
   switch (kind) {
     case KI: stored(KI, -1, -1, t, c); return;
@@ -576,8 +590,8 @@ struct GemmPlan {
   DevArray<int3> tiles;
   int ntiles = 0;
   double flops = 0.0;
-  void run(cudaStream_t st, const double* xb, double* yb) const {
-    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, st);
+  void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr) const {
+    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st);
   }
 };
 
@@ -601,8 +615,8 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
   std::vector<int3> tiles;
   double fl = 0.0;
   for (size_t i = 0; i < outs.size(); ++i) {
-    const int tm = (outs[i].m + GEMM_TILE - 1) / GEMM_TILE;
-    const int tn = (outs[i].n + GEMM_TILE - 1) / GEMM_TILE;
+    const int tm = (outs[i].m + GEMM_TM - 1) / GEMM_TM;
+    const int tn = (outs[i].n + GEMM_TN - 1) / GEMM_TN;
     for (int a = 0; a < tm; ++a)
       for (int b = 0; b < tn; ++b) tiles.push_back(make_int3((int)i, a, b));
     for (int s = 0; s < outs[i].seg_count; ++s)
@@ -681,10 +695,12 @@ struct SigmaPlan {
   DevArray<DiagOut> douts;
   DevArray<DiagTerm> dterms;
   int ndiag = 0;
-  double* tbuf = nullptr;
+  double* tbuf = nullptr;   // workspace of the phase-1 intermediates
+  int64_t tsize = 0;        // its size in doubles
   int64_t nelem = 0;
   int n_terms = 0, n_products = 0;
   double op_bytes = 0.0;
+  double flops_alg = 0.0;   // products of non-zero sub-blocks only
   ~SigmaPlan() {
     if (tbuf) cudaFree(tbuf);
   }
@@ -701,7 +717,8 @@ struct lrt_ctx {
   bool have_mps = false;
   int k = 0, na = 0, nb = 0;
   std::vector<lrt::Sectors> bonds;
-  std::vector<lrt::SiteTensor> sites;
+  std::vector<lrt::SiteTensor> sites;     // left-canonical (or only) form
+  std::vector<lrt::SiteTensor> sites_r;   // right-canonical form, when given separately
   std::vector<std::unique_ptr<lrt::OpSet>> L, R, XL, YR;
   std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
   lrt_sigma_stats last{};
@@ -724,8 +741,10 @@ static std::unique_ptr<OpSet> vacuum(lrt_ctx* c, bool right) {
   layout_blocks(*S);
   alloc_zero(*S, c->st);
   const double one = 1.0;
-  CK(cudaMemcpyAsync(S->d + S->off_of(S->find(Key{KI, -1, -1}), 0), &one, sizeof(double),
-                     cudaMemcpyHostToDevice, c->st));
+  const int iop = S->find(Key{KI, -1, -1});
+  CK(cudaMemcpyAsync(S->d + S->off_of(iop, 0), &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  S->bnz[(size_t)iop * S->ns()] = 1;
+  S->finish_nz();
   CK(cudaStreamSynchronize(c->st));
   return S;
 }
@@ -766,6 +785,7 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
   make_keys(*E, orbs, right ? right_mode(b, c->k) : left_mode(b + 1, c->k), I.nso);
   layout_blocks(*E);
   alloc_zero(*E, c->st);
+  E->mask.assign(E->bra.size(), 0);
   const Fused& F = *E->fused;
   auto terms = right ? blocking_terms(*E, sorbs, X.orbs, I) : blocking_terms(*E, X.orbs, sorbs, I);
 
@@ -794,7 +814,7 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
       if (e4.zero()) continue;
       for (int s = 0; s < X.ns(); ++s) {
         const int sb = X.bra_of(j, s);
-        if (sb < 0) continue;
+        if (sb < 0 || !X.block_nz(j, s)) continue;
         const int be = tr ? s : sb, ke = tr ? sb : s;
         const double* src = X.d + X.off_of(j, s);
         const int ld = X.basis.d[s];
@@ -828,6 +848,8 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
               ti = it->second;
             }
             tsrc[ti].push_back(GatherSrc{src, ld, tr, sign * e});
+            E->mask[(size_t)o * E->ns() + fk] |= (uint16_t)(1u << (4 * n1 + n0));
+            E->bnz[(size_t)o * E->ns() + fk] = 1;
           }
       }
     }
@@ -843,6 +865,7 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
   gp.run(c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
+  E->finish_nz();
   return E;
 }
 
@@ -876,8 +899,9 @@ static void renorm_left(lrt_ctx* c, int b) {
       if (qb < 0) continue;
       const int fk = F.s.find(N->basis.a[q], N->basis.b[q]);
       const int fb = F.s.find(N->basis.a[qb], N->basis.b[qb]);
-      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb) continue;
+      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
       if (T.blk_off[q] < 0 || T.blk_off[qb] < 0) continue;
+      N->bnz[o * N->ns() + q] = 1;
       const int Dq = N->basis.d[q], Dqb = N->basis.d[qb];
       const int rk = F.s.d[fk], rb = F.s.d[fb];
       if (T.blk_rows[q] != rk || T.blk_rows[qb] != rb)
@@ -902,6 +926,7 @@ static void renorm_left(lrt_ctx* c, int b) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   if (tmp) cudaFree(tmp);
+  N->finish_nz();
   c->L[b + 1] = std::move(N);
   for (int x = b + 2; x <= c->k; ++x) c->L[x].reset();
   for (int x = b + 1; x < c->k; ++x) c->XL[x].reset();
@@ -911,7 +936,7 @@ static void renorm_left(lrt_ctx* c, int b) {
 static void renorm_right(lrt_ctx* c, int b) {
   OpSet& E = enlarged(c, b, true);
   const Fused& F = *E.fused;
-  const SiteTensor& T = c->sites[b];
+  const SiteTensor& T = c->sites_r.empty() ? c->sites[b] : c->sites_r[b];
   const Sectors& Lb = c->bonds[b];
   // right-fused copy of the site tensor: per left sector q, D_q x fused(q), sub-blocks n side by side
   std::vector<int64_t> rf_off(Lb.n(), -1);
@@ -959,7 +984,8 @@ static void renorm_right(lrt_ctx* c, int b) {
       if (qb < 0 || rf_off[q] < 0 || rf_off[qb] < 0) continue;
       const int fk = F.s.find(Lb.a[q], Lb.b[q]);
       const int fb = F.s.find(Lb.a[qb], Lb.b[qb]);
-      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb) continue;
+      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
+      N->bnz[o * N->ns() + q] = 1;
       const int Dq = Lb.d[q], Dqb = Lb.d[qb];
       const int ck = F.s.d[fk], cb = F.s.d[fb];
       o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 0});
@@ -984,6 +1010,7 @@ static void renorm_right(lrt_ctx* c, int b) {
   CK(cudaStreamSynchronize(c->st));
   if (tmp) cudaFree(tmp);
   if (rf) cudaFree(rf);
+  N->finish_nz();
   c->R[b] = std::move(N);
   for (int x = 0; x < b; ++x) c->R[x].reset();
   for (int x = 0; x < b; ++x) c->YR[x].reset();
@@ -1026,6 +1053,18 @@ static std::vector<WfnBlock> wfn_blocks(lrt_ctx* c, int site, int nsite) {
 // ---------------------------------------------------------------------------
 // sigma planning: y = sum_terms coef * sign * X_t psi Y_t^T
 // ---------------------------------------------------------------------------
+static uint16_t transpose_mask(uint16_t m) {
+  uint16_t r = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      if (m & (1u << (4 * a + b))) r |= (uint16_t)(1u << (4 * b + a));
+  return r;
+}
+
+// Products are formed at sub-block granularity so that zero sub-blocks of the
+// enlarged operators are never multiplied:
+//   phase 1: T[t](rows n') = sum_{n : X_t(n',n) != 0} X_t(n',n) psi_Q(rows n)
+//   phase 2: y_Q'(rows n' [, cols m']) = sum_t sign_t T[t](rows n' [, cols m]) Y_t(m',m)^T
 static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec) {
   const Ints& I = c->I;
   const int k = c->k;
@@ -1038,6 +1077,8 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
     Yp = &enlarged(c, site + 1, true);
   }
   OpSet& Y = *Yp;
+  const Fused& XF = *X.fused;
+  const Fused* YF = (nsite == 2) ? Y.fused.get() : nullptr;
   const std::vector<WfnBlock> wb = wfn_blocks(c, site, nsite);
   std::unordered_map<int, int> blk_of;   // label key -> wfn block
   for (size_t i = 0; i < wb.size(); ++i) blk_of[Sectors::key(wb[i].label_a, wb[i].label_b)] = (int)i;
@@ -1053,18 +1094,40 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   auto plan = std::make_unique<SigmaPlan>();
   plan->nelem = nelem;
   plan->n_terms = (int)terms.size();
-  // per output block: list of phase-2 segments (before replication over vectors)
-  std::vector<std::vector<GemmSeg>> seg2(wb.size());
+
+  // every sub-block of y is an output (written even when no product reaches it)
+  struct OutSub { int blk, r, mcol; };
+  std::vector<OutSub> osub;
+  std::map<std::tuple<int, int, int>, int> out_of;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    const int fx = XF.s.find(wb[w].label_a, wb[w].label_b);
+    for (int r = 0; r < 4; ++r) {
+      if (XF.dim[fx][r] == 0) continue;
+      if (nsite == 1) {
+        out_of[{(int)w, r, 0}] = (int)osub.size();
+        osub.push_back({(int)w, r, 0});
+      } else {
+        const int fy = YF->s.find(wb[w].label_a, wb[w].label_b);
+        for (int m = 0; m < 4; ++m) {
+          if (YF->dim[fy][m] == 0) continue;
+          out_of[{(int)w, r, m}] = (int)osub.size();
+          osub.push_back({(int)w, r, m});
+        }
+      }
+    }
+  }
+  std::vector<std::vector<GemmSeg>> seg2(osub.size());
   std::vector<GemmOut> o1;
   std::vector<GemmSeg> s1;
-  std::map<std::tuple<int, int, int>, int64_t> tcache;   // (X op, trans, X ket fused) -> T offset
+  struct TEntry { int64_t tp; uint16_t rows; };
+  std::map<std::tuple<int, int, int>, TEntry> tcache;   // (X op, trans, X ket fused) -> T
   int64_t toff = 0;
-  std::vector<DiagTerm> dt_all;
   std::vector<std::vector<DiagTerm>> dterm(wb.size());
   std::vector<Ref> rx, ry;
-  double op_bytes = 0.0;
+  double op_bytes = 0.0, falg = 0.0;
   int nprod = 0;
   const int Ikey = X.find(Key{KI, -1, -1});
+
   for (const Term& t : terms) {
     rx.clear();
     ry.clear();
@@ -1075,76 +1138,131 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
         const double coef = t.c * a.c * bref.c;
         for (int f = 0; f < X.ns(); ++f) {
           const int fb0 = X.bra_of(a.op, f);
-          if (fb0 < 0) continue;
+          if (fb0 < 0 || !X.block_nz(a.op, f)) continue;
           const int be = a.t ? f : fb0, ke = a.t ? fb0 : f;
           auto ik = blk_of.find(Sectors::key(X.basis.a[ke], X.basis.b[ke]));
           auto ib = blk_of.find(Sectors::key(X.basis.a[be], X.basis.b[be]));
           if (ik == blk_of.end() || ib == blk_of.end()) continue;
           const WfnBlock& wk = wb[ik->second];
           const WfnBlock& wbb = wb[ib->second];
-          // Y block with effective ket label = ket label, effective bra label = bra label
           const int yk = Y.basis.find(wk.label_a, wk.label_b);
           const int ybb = Y.basis.find(wbb.label_a, wbb.label_b);
           if (yk < 0 || ybb < 0) continue;
           const double* Bp;
           int transB, ldb;
+          uint16_t ymask = 1;   // stored blocks: one dense sub-block
           if (!bref.t) {
-            if (Y.bra_of(bref.op, yk) != ybb) continue;
+            if (Y.bra_of(bref.op, yk) != ybb || !Y.block_nz(bref.op, yk)) continue;
             Bp = Y.d + Y.off_of(bref.op, yk);
             transB = 1;
             ldb = Y.basis.d[yk];
+            if (YF) ymask = Y.mask[(size_t)bref.op * Y.ns() + yk];
           } else {
-            if (Y.bra_of(bref.op, ybb) != yk) continue;
+            if (Y.bra_of(bref.op, ybb) != yk || !Y.block_nz(bref.op, ybb)) continue;
             Bp = Y.d + Y.off_of(bref.op, ybb);
             transB = 0;
             ldb = Y.basis.d[ybb];
+            if (YF) ymask = transpose_mask(Y.mask[(size_t)bref.op * Y.ns() + ybb]);
           }
           const int sign = (Y.par[bref.op] && ((wk.label_a + wk.label_b) & 1)) ? -1 : 1;
           const double sc = coef * sign;
           ++nprod;
           op_bytes += 8.0 * ((double)Y.basis.d[yk] * Y.basis.d[ybb]);
-          GemmSeg g2{};
-          g2.B = Bp;
-          g2.ldb = ldb;
-          g2.transB = transB;
-          g2.k = wk.cols;
-          g2.scale = sc;
-          if (a.op == Ikey) {
-            g2.a_rel = 1;
-            g2.a_off = wk.off;
-            g2.lda = wk.cols;
+
+          // ---- phase 1 (shared by every Y partner of this X block)
+          uint16_t rows = 0;
+          int64_t tp = -1;
+          const bool ident = (a.op == Ikey);
+          if (ident) {
+            for (int r = 0; r < 4; ++r)
+              if (XF.dim[be][r]) rows |= (uint16_t)(1u << r);
           } else {
             const auto key = std::make_tuple(a.op, a.t, f);
             auto it = tcache.find(key);
-            int64_t tp;
             if (it == tcache.end()) {
+              uint16_t mx = X.mask[(size_t)a.op * X.ns() + f];
+              if (a.t) mx = transpose_mask(mx);
               tp = toff;
-              tcache[key] = tp;
-              o1.push_back(GemmOut{nullptr, tp, wk.cols, wbb.rows, wk.cols, (int)s1.size(), 1, 0, 0});
-              GemmSeg g1{};
-              g1.A = X.d + X.off_of(a.op, f);
-              g1.lda = X.basis.d[f];
-              g1.transA = a.t;
-              g1.b_rel = 1;
-              g1.b_off = wk.off;
-              g1.ldb = wk.cols;
-              g1.k = wk.rows;
-              g1.scale = 1.0;
-              s1.push_back(g1);
               toff += (int64_t)wbb.rows * wk.cols;
+              const double* base = X.d + X.off_of(a.op, f);
+              const int ld = X.basis.d[f];
               op_bytes += 8.0 * ((double)wbb.rows * wk.rows);
+              for (int r = 0; r < 4; ++r) {
+                bool any = false;
+                for (int cc = 0; cc < 4; ++cc)
+                  if (mx & (1u << (4 * r + cc))) any = true;
+                if (!any) continue;
+                rows |= (uint16_t)(1u << r);
+                GemmOut out{nullptr, tp + (int64_t)XF.off[be][r] * wk.cols, wk.cols, XF.dim[be][r], wk.cols,
+                            (int)s1.size(), 0, 0, 0};
+                for (int cc = 0; cc < 4; ++cc) {
+                  if (!(mx & (1u << (4 * r + cc)))) continue;
+                  GemmSeg g{};
+                  if (!a.t) {
+                    g.A = base + (int64_t)XF.off[be][r] * ld + XF.off[ke][cc];
+                    g.transA = 0;
+                  } else {
+                    g.A = base + (int64_t)XF.off[ke][cc] * ld + XF.off[be][r];
+                    g.transA = 1;
+                  }
+                  g.lda = ld;
+                  g.b_rel = 1;
+                  g.b_off = wk.off + (int64_t)XF.off[ke][cc] * wk.cols;
+                  g.ldb = wk.cols;
+                  g.k = XF.dim[ke][cc];
+                  g.scale = 1.0;
+                  s1.push_back(g);
+                  ++out.seg_count;
+                  falg += 2.0 * XF.dim[be][r] * XF.dim[ke][cc] * wk.cols;
+                }
+                o1.push_back(out);
+              }
+              tcache[key] = TEntry{tp, rows};
             } else {
-              tp = it->second;
+              tp = it->second.tp;
+              rows = it->second.rows;
             }
-            g2.A = nullptr;
-            g2.a_off = tp;
-            g2.lda = wk.cols;
           }
-          seg2[ib->second].push_back(g2);
-          // diagonal contribution
+          // ---- phase 2
+          for (int r = 0; r < 4; ++r) {
+            if (!(rows & (1u << r))) continue;
+            const int64_t arow = ident ? wk.off + (int64_t)XF.off[ke][r] * wk.cols
+                                       : tp + (int64_t)XF.off[be][r] * wk.cols;
+            if (nsite == 1) {
+              GemmSeg g{};
+              g.a_rel = ident ? 1 : 0;
+              g.a_off = arow;
+              g.lda = wk.cols;
+              g.B = Bp;
+              g.ldb = ldb;
+              g.transB = transB;
+              g.k = wk.cols;
+              g.scale = sc;
+              seg2[out_of.at({ib->second, r, 0})].push_back(g);
+              falg += 2.0 * XF.dim[be][r] * wk.cols * wbb.cols;
+            } else {
+              for (int mp = 0; mp < 4; ++mp)
+                for (int m = 0; m < 4; ++m) {
+                  if (!(ymask & (1u << (4 * mp + m)))) continue;
+                  GemmSeg g{};
+                  g.a_rel = ident ? 1 : 0;
+                  g.a_off = arow + YF->off[yk][m];
+                  g.lda = wk.cols;
+                  if (!bref.t) g.B = Bp + (int64_t)YF->off[ybb][mp] * ldb + YF->off[yk][m];
+                  else g.B = Bp + (int64_t)YF->off[yk][m] * ldb + YF->off[ybb][mp];
+                  g.ldb = ldb;
+                  g.transB = transB;
+                  g.k = YF->dim[yk][m];
+                  g.scale = sc;
+                  seg2[out_of.at({ib->second, r, mp})].push_back(g);
+                  falg += 2.0 * XF.dim[be][r] * YF->dim[yk][m] * YF->dim[ybb][mp];
+                }
+            }
+          }
+          // ---- diagonal contribution
           if (be == ke && yk == ybb) {
             DiagTerm d{};
-            d.x = (a.op == Ikey) ? nullptr : X.d + X.off_of(a.op, f);
+            d.x = ident ? nullptr : X.d + X.off_of(a.op, f);
             d.xs = X.basis.d[f] + 1;
             d.y = Bp;
             d.ys = Y.basis.d[yk] + 1;
@@ -1154,27 +1272,45 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
         }
       }
   }
-  // device workspace for the intermediates of all vectors
   if (toff > 0 && cudaMalloc(&plan->tbuf, (size_t)toff * nvec * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "sigma workspace");
   std::vector<GemmOut> O1, O2;
   std::vector<GemmSeg> S1, S2;
+  plan->tsize = toff * nvec;
   for (int v = 0; v < nvec; ++v) {
     for (const GemmOut& x : o1) {
       GemmOut y = x;
-      y.C = plan->tbuf + x.c_off + (int64_t)v * toff;
-      y.c_off = 0;
+      y.C = nullptr;
+      y.c_off = x.c_off + (int64_t)v * toff;
+      y.c_rel = 2;
       y.seg_begin = (int)S1.size();
-      S1.push_back(s1[x.seg_begin]);
-      S1.back().b_off += (int64_t)v * nelem;
+      for (int q = 0; q < x.seg_count; ++q) {
+        GemmSeg g = s1[x.seg_begin + q];
+        g.b_off += (int64_t)v * nelem;
+        S1.push_back(g);
+      }
       O1.push_back(y);
     }
-    for (size_t w = 0; w < wb.size(); ++w) {
-      GemmOut y{nullptr, wb[w].off + (int64_t)v * nelem, wb[w].cols, wb[w].rows, wb[w].cols,
-                (int)S2.size(), (int)seg2[w].size(), 0, 1};
-      for (GemmSeg g : seg2[w]) {
-        if (g.a_rel) g.a_off += (int64_t)v * nelem;
-        else g.A = plan->tbuf + g.a_off + (int64_t)v * toff;
+    for (size_t u = 0; u < osub.size(); ++u) {
+      const OutSub& os = osub[u];
+      const WfnBlock& w = wb[os.blk];
+      const int fx = XF.s.find(w.label_a, w.label_b);
+      int64_t coff = w.off + (int64_t)XF.off[fx][os.r] * w.cols;
+      int ncols = w.cols;
+      if (nsite == 2) {
+        const int fy = YF->s.find(w.label_a, w.label_b);
+        coff += YF->off[fy][os.mcol];
+        ncols = YF->dim[fy][os.mcol];
+      }
+      GemmOut y{nullptr, coff + (int64_t)v * nelem, w.cols, XF.dim[fx][os.r], ncols, (int)S2.size(),
+                (int)seg2[u].size(), 0, 1};
+      for (GemmSeg g : seg2[u]) {
+        if (g.a_rel) {
+          g.a_off += (int64_t)v * nelem;
+        } else {
+          g.a_rel = 2;
+          g.a_off += (int64_t)v * toff;
+        }
         S2.push_back(g);
       }
       O2.push_back(y);
@@ -1193,6 +1329,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   plan->ndiag = (int)dout.size();
   plan->n_products = nprod;
   plan->op_bytes = op_bytes;
+  plan->flops_alg = falg * nvec;
   CK(cudaStreamSynchronize(c->st));
   return plan;
 }
@@ -1301,23 +1438,29 @@ int mps_load(lrt_t ctx, const lrt_mps_desc* m) {
     if (bonds[m->k].n() != 1 || bonds[m->k].a[0] != m->n_alpha || bonds[m->k].b[0] != m->n_beta ||
         bonds[m->k].d[0] != 1)
       throw Error(LRT_EINVAL, "mps_load: bond k must be the single sector (n_alpha,n_beta,1)");
-    std::vector<SiteTensor> sites(m->k);
-    for (int i = 0; i < m->k; ++i) {
-      site_layout(sites[i], bonds[i], bonds[i + 1]);
-      if (sites[i].total > 0) {
-        if (!m->site_data[i]) throw Error(LRT_EINVAL, "mps_load: missing site data");
-        if (cudaMalloc(&sites[i].d, (size_t)sites[i].total * sizeof(double)) != cudaSuccess)
-          throw Error(LRT_ENOMEM, "mps_load: device allocation");
-        CK(cudaMemcpyAsync(sites[i].d, m->site_data[i], (size_t)sites[i].total * sizeof(double),
-                           cudaMemcpyHostToDevice, ctx->st));
+    auto upload = [&](const double* const* data, std::vector<SiteTensor>& out) {
+      out.resize(m->k);
+      for (int i = 0; i < m->k; ++i) {
+        site_layout(out[i], bonds[i], bonds[i + 1]);
+        if (out[i].total > 0) {
+          if (!data[i]) throw Error(LRT_EINVAL, "mps_load: missing site data");
+          if (cudaMalloc(&out[i].d, (size_t)out[i].total * sizeof(double)) != cudaSuccess)
+            throw Error(LRT_ENOMEM, "mps_load: device allocation");
+          CK(cudaMemcpyAsync(out[i].d, data[i], (size_t)out[i].total * sizeof(double),
+                             cudaMemcpyHostToDevice, ctx->st));
+        }
       }
-    }
+    };
+    std::vector<SiteTensor> sites, sites_r;
+    upload(m->site_data, sites);
+    if (m->site_data_right) upload(m->site_data_right, sites_r);
     CK(cudaStreamSynchronize(ctx->st));
     ctx->k = m->k;
     ctx->na = m->n_alpha;
     ctx->nb = m->n_beta;
     ctx->bonds = std::move(bonds);
     ctx->sites = std::move(sites);
+    ctx->sites_r = std::move(sites_r);
     ctx->have_mps = true;
     reset_env(ctx);
   });
@@ -1362,10 +1505,11 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     SigmaPlan& p = get_plan(ctx, site, nsite, nvec);
     if ((const double*)y_dev < x_dev + p.nelem * nvec && x_dev < (const double*)y_dev + p.nelem * nvec)
       throw Error(LRT_EINVAL, "sigma: x and y overlap");
-    p.p1.run(ctx->st, x_dev, y_dev);
-    p.p2.run(ctx->st, x_dev, y_dev);
+    p.p1.run(ctx->st, x_dev, y_dev, p.tbuf);
+    p.p2.run(ctx->st, x_dev, y_dev, p.tbuf);
     CK(cudaGetLastError());
-    ctx->last.flops = p.p1.flops + p.p2.flops;
+    ctx->last.flops = p.flops_alg;
+    ctx->last.flops_issued = p.p1.flops + p.p2.flops;
     ctx->last.launches = (p.p1.ntiles > 0) + (p.p2.ntiles > 0);
     ctx->last.n_terms = p.n_terms;
     ctx->last.n_products = p.n_products;

@@ -66,92 +66,84 @@ void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* t
 
 // ---------------------------------------------------------------------------
 // grouped FP64 GEMM with K-concatenated segments
+//
+// GB300 issues about 2 FP64 FMA per clock per SM, so the kernel is bound by the
+// number of DFMA warp instructions, not by operand bandwidth.  Register tiling
+// is therefore pointless and padding is the enemy: each lane owns individual
+// output elements of a <= GEMM_TM x GEMM_TN tile (flattened, so only the last
+// warp of a tile is partly idle) and the K loop runs the exact trip count.
 // ---------------------------------------------------------------------------
 constexpr int KC = 16;
+constexpr int GEMM_THREADS = 128;
+constexpr int GEMM_MAXE = GEMM_TM * GEMM_TN / GEMM_THREADS;   // outputs per thread
 
-__global__ void __launch_bounds__(256) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
-                                                        const GemmSeg* __restrict__ segs,
-                                                        const int3* __restrict__ tiles, int ntiles,
-                                                        const double* __restrict__ xbase,
-                                                        double* __restrict__ ybase) {
-  __shared__ double As[KC][GEMM_TILE + 2];
-  __shared__ double Bs[KC][GEMM_TILE + 2];
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
+                                                                 const GemmSeg* __restrict__ segs,
+                                                                 const int3* __restrict__ tiles, int ntiles,
+                                                                 const double* __restrict__ xbase,
+                                                                 double* __restrict__ ybase,
+                                                                 double* __restrict__ tbase) {
+  __shared__ double As[GEMM_TM][KC + 1];
+  __shared__ double Bs[KC][GEMM_TN + 1];
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
   const GemmOut o = outs[wi.x];
-  const int m0 = wi.y * GEMM_TILE, n0 = wi.z * GEMM_TILE;
+  const int m0 = wi.y * GEMM_TM, n0 = wi.z * GEMM_TN;
+  const int mt = min(GEMM_TM, o.m - m0), nt = min(GEMM_TN, o.n - n0);
+  const int ne = mt * nt;
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  int ri[GEMM_MAXE], ci[GEMM_MAXE];
+  double acc[GEMM_MAXE];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int j = 0; j < GEMM_MAXE; ++j) {
+    const int e = tid + GEMM_THREADS * j;
+    ri[j] = e < ne ? e / nt : 0;
+    ci[j] = e < ne ? e % nt : 0;
+    acc[j] = 0.0;
+  }
+  const int cnt = ne > tid ? (ne - tid + GEMM_THREADS - 1) / GEMM_THREADS : 0;
 
   for (int s = 0; s < o.seg_count; ++s) {
     GemmSeg g = segs[o.seg_begin + s];
-    if (g.a_rel) g.A = xbase + g.a_off;
-    if (g.b_rel) g.B = xbase + g.b_off;
+    if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : tbase) + g.a_off;
+    if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : tbase) + g.b_off;
     for (int k0 = 0; k0 < g.k; k0 += KC) {
-      // A tile: op(A)(m0 + i, k0 + kk) -> As[kk][i]
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int idx = tid + 256 * e;
+      const int kc = min(KC, g.k - k0);
+      for (int e = tid; e < mt * kc; e += GEMM_THREADS) {
         int i, kk;
-        if (!g.transA) { i = idx / KC; kk = idx % KC; } else { kk = idx / GEMM_TILE; i = idx % GEMM_TILE; }
+        if (!g.transA) { i = e / kc; kk = e % kc; } else { kk = e / mt; i = e % mt; }
         const int gi = m0 + i, gk = k0 + kk;
-        double v = 0.0;
-        if (gi < o.m && gk < g.k)
-          v = g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
-        As[kk][i] = v * g.scale;
+        As[i][kk] = g.scale * (g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk]);
       }
-      // B tile: op(B)(k0 + kk, n0 + j) -> Bs[kk][j]
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int idx = tid + 256 * e;
+      for (int e = tid; e < kc * nt; e += GEMM_THREADS) {
         int j, kk;
-        if (!g.transB) { kk = idx / GEMM_TILE; j = idx % GEMM_TILE; } else { j = idx / KC; kk = idx % KC; }
+        if (!g.transB) { kk = e / nt; j = e % nt; } else { j = e / kc; kk = e % kc; }
         const int gj = n0 + j, gk = k0 + kk;
-        double v = 0.0;
-        if (gj < o.n && gk < g.k)
-          v = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
-        Bs[kk][j] = v;
+        Bs[kk][j] = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
       }
       __syncthreads();
+      for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
-      for (int kk = 0; kk < KC; ++kk) {
-        double a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < GEMM_MAXE; ++j)
+          if (j < cnt) acc[j] = fma(As[ri[j]][kk], Bs[kk][ci[j]], acc[j]);
       }
       __syncthreads();
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gi = m0 + ty + 16 * i;
-    if (gi >= o.m) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gj = n0 + tx + 16 * j;
-      if (gj >= o.n) continue;
-      double* c = (o.c_rel ? ybase + o.c_off : o.C) + (int64_t)gi * o.ldc + gj;
-      *c = o.accumulate ? (*c + acc[i][j]) : acc[i][j];
-    }
+  for (int j = 0; j < GEMM_MAXE; ++j) {
+    if (j >= cnt) break;
+    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : tbase) + o.c_off : o.C) + (int64_t)(m0 + ri[j]) * o.ldc +
+                (n0 + ci[j]);
+    *c = o.accumulate ? (*c + acc[j]) : acc[j];
   }
 }
 
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                      const double* xbase, double* ybase, cudaStream_t st) {
+                      const double* xbase, double* ybase, double* tbase, cudaStream_t st) {
   if (ntiles <= 0) return;
-  gemm_fp64_kernel<<<ntiles, 256, 0, st>>>(outs, segs, tiles, ntiles, xbase, ybase);
+  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase);
 }
 
 // ---------------------------------------------------------------------------

@@ -20,8 +20,9 @@ struct GatherSrc {
 };
 
 // C (m x n, ldc) = [C +] sum_s scale_s * op(A_s) (m x k_s) * op(B_s) (k_s x n).
-// Pointers flagged *_rel are offsets (in doubles) from the x (A, B) or y (C) base
-// pointer passed at launch, so one plan serves any caller buffers.
+// Pointers flagged *_rel are offsets (in doubles) from a base pointer passed at
+// launch: 1 = the caller's x (A, B) or y (C) buffer, 2 = the workspace of
+// intermediates.  A plan therefore serves any caller buffers and workspace.
 struct GemmOut {
   double* C;
   int64_t c_off;
@@ -59,10 +60,11 @@ struct DiagTerm {
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
                    cudaStream_t st);
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                      const double* xbase, double* ybase, cudaStream_t st);
+                      const double* xbase, double* ybase, double* tbase, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
 constexpr int GATHER_TILE = 32;
-constexpr int GEMM_TILE = 64;
+constexpr int GEMM_TM = 64;   // output tile rows
+constexpr int GEMM_TN = 32;   // output tile columns
 
 }  // namespace lrt
