@@ -132,6 +132,29 @@ typedef struct {
 } lrt_sigma_stats;
 int sigma_stats(lrt_t ctx, lrt_sigma_stats* out);
 
+/* sigma_noalloc: the same H_eff x as sigma(), for callers that must not allocate
+ * GPU memory -- programs whose own memory pool owns the device, loops that cannot
+ * absorb the synchronization a cudaMalloc/cudaFree may cause, code where the CUDA
+ * allocator may not be entered.  The paper has no counterpart; this is a service of
+ * the library.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  The
+ *    intermediates live in one static device array of LRT_NOALLOC_SCRATCH_DOUBLES
+ *    doubles (32 MiB) that every GPU loading the library holds until process exit.
+ *  - Reuses the plan that a regular sigma() call with the same (site, nsite, nvec)
+ *    prepared after the last renormalize(); without one it returns LRT_ESTATE.
+ *    A plan whose intermediates exceed the static array is rejected with LRT_EINVAL
+ *    and a message giving both sizes.
+ *  - The first call on each device resolves the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the one array and overwrites it: calls that may overlap on
+ *    the GPU (other streams, other contexts, other threads) race and must be
+ *    serialized by the caller.  Nothing has to start at zero: each call writes every
+ *    intermediate before reading it.
+ *  - Arguments and results as for sigma() in FP64. */
+#define LRT_NOALLOC_SCRATCH_DOUBLES (4 * 1024 * 1024)
+#define LRT_NOALLOC_MAX_DEVICES 64
+int sigma_noalloc(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double* y_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ LRT_FP64 = 0
 LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
-           "renormalize", "sigma", "heff_diag", "sigma_stats"]
+           "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc"]
 
 _lib = None
 
@@ -66,6 +66,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.sigma.argtypes = [vp, i, i, i, vp, vp, i]
     lib.heff_diag.argtypes = [vp, i, i, vp]
     lib.sigma_stats.argtypes = [vp, ctypes.POINTER(SigmaStats)]
+    lib.sigma_noalloc.argtypes = [vp, i, i, i, vp, vp]
     for name in EXPORTS:
         if name != "lrt_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -163,6 +164,16 @@ class Context:
         n, _ = self.wfn_layout(site, nsite)
         self._check(self.lib.sigma(self.h, site, nsite, nvec, ctypes.c_void_p(_tensor_ptr(x, n * nvec)),
                                    ctypes.c_void_p(_tensor_ptr(y, n * nvec)), precision), "sigma")
+
+    def sigma_noalloc(self, site: int, nsite: int, x, y, nvec: int = 1):
+        """H_eff x without any GPU allocation, for callers that cannot allocate (a program
+        whose own pool owns the device memory, a loop that cannot absorb an allocator
+        synchronization).  Needs a plan prepared by an earlier sigma() call with the same
+        (site, nsite, nvec); shares one static 32 MiB device array across all calls, so
+        calls must not overlap on the GPU."""
+        n, _ = self.wfn_layout(site, nsite)
+        self._check(self.lib.sigma_noalloc(self.h, site, nsite, nvec, ctypes.c_void_p(_tensor_ptr(x, n * nvec)),
+                                           ctypes.c_void_p(_tensor_ptr(y, n * nvec))), "sigma_noalloc")
 
     def heff_diag(self, site: int, nsite: int, d):
         n, _ = self.wfn_layout(site, nsite)

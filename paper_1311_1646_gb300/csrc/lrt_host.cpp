@@ -1334,6 +1334,11 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   return plan;
 }
 
+static SigmaPlan* find_plan(lrt_ctx* c, int site, int nsite, int nvec) {
+  auto it = c->plans.find(std::make_tuple(site, nsite, nvec));
+  return it == c->plans.end() ? nullptr : it->second.get();
+}
+
 static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
   auto key = std::make_tuple(site, nsite, nvec);
   auto it = c->plans.find(key);
@@ -1350,6 +1355,45 @@ static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
 // C ABI
 // ===========================================================================
 using namespace lrt;
+
+namespace lrt {
+
+int ctx_device(lrt_ctx* ctx) { return ctx ? ctx->dev : -1; }
+void ctx_set_error(lrt_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+}
+
+// Launch an existing sigma plan with a caller-chosen workspace; allocates nothing.
+int sigma_launch_existing_plan(lrt_ctx* ctx, int site, int nsite, int nvec, const double* x_dev,
+                               double* y_dev, double* workspace, int64_t workspace_doubles) {
+  if (!ctx) return LRT_EINVAL;
+  try {
+    if (nsite < 1 || nsite > 2 || site < 0 || nvec <= 0 || !x_dev || !y_dev || !workspace)
+      throw Error(LRT_EINVAL, "sigma_noalloc: bad arguments");
+    SigmaPlan* p = find_plan(ctx, site, nsite, nvec);
+    if (!p)
+      throw Error(LRT_ESTATE, "sigma_noalloc: no prepared plan for this (site, nsite, nvec); call sigma() once "
+                              "with the same arguments after the last renormalize()");
+    if (p->tsize > workspace_doubles)
+      throw Error(LRT_EINVAL, "sigma_noalloc: needs " + std::to_string(p->tsize) +
+                                  " doubles of scratch, the static maximum is " + std::to_string(workspace_doubles));
+    if ((const double*)y_dev < x_dev + p->nelem * nvec && x_dev < (const double*)y_dev + p->nelem * nvec)
+      throw Error(LRT_EINVAL, "sigma_noalloc: x and y overlap");
+    p->p1.run(ctx->st, x_dev, y_dev, workspace);
+    p->p2.run(ctx->st, x_dev, y_dev, workspace);
+    CK(cudaGetLastError());
+    ctx->err.clear();
+    return LRT_OK;
+  } catch (const Error& e) {
+    ctx->err = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    ctx->err = e.what();
+    return LRT_EINVAL;
+  }
+}
+
+}  // namespace lrt
 
 static thread_local std::string g_create_err;
 
