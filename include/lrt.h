@@ -117,6 +117,34 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
 /* Diagonal of H_eff (the preconditioner of Eq. error) in the same layout as sigma. */
 int heff_diag(lrt_t ctx, int site, int nsite, double* d_dev);
 
+/* Ground state by two-site DMRG sweeps (Eq. dmrg solved by Davidson at every
+ * position with the diagonal preconditioner of Eq. error; decimation by the
+ * eigenvectors of the reduced density matrix of each (N_a, N_b) sector, keeping the
+ * M largest weights over all sectors; gauge shift and renormalization as in
+ * Eq. gauge-shift).  Starts from the loaded MPS, which must be right-orthonormal
+ * with the centre on site 0, and leaves the optimized MPS loaded (right-orthonormal,
+ * centre on site 0).  M_schedule[s] is the bond dimension of sweep s (the last entry
+ * repeats, each held for sweeps_per_M sweeps); sweeps stop when the energy of two
+ * consecutive sweeps at the final M differs by less than e_tol, or after max_sweeps.
+ * e0: the lowest eigenvalue of the last Davidson solve (total energy, Eh). */
+typedef struct {
+  int max_sweeps;
+  int n_schedule;
+  const int* M_schedule;
+  int sweeps_per_M;
+  double e_tol;
+  double dav_tol;        /* Davidson residual 2-norm */
+  int dav_max_iter;
+  int dav_max_space;     /* <= 48 */
+  double trunc_tol;      /* density-matrix weights below trunc_tol * largest are dropped */
+} lrt_gs_params;
+int sweep_gs(lrt_t ctx, const lrt_gs_params* params, double* e0);
+
+/* Read back the loaded MPS: bond tables (bond_nsect[k+1], bond_sectors[3 * total])
+ * and the left-fused data of one site (host_out may be NULL to query *nelem). */
+int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors);
+int mps_get_site(lrt_t ctx, int site, double* host_out, int64_t* nelem);
+
 /* Statistics of the last sigma call: algorithmic FLOPs (2mnk summed over the
  * products of non-zero sub-blocks of the operators, zero padding excluded),
  * FLOPs issued by the kernels (fused blocks, zero sub-blocks included), bytes

@@ -19,7 +19,8 @@ LRT_FP64 = 0
 LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
-           "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc"]
+           "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
+           "mps_get_bonds", "mps_get_site"]
 
 _lib = None
 
@@ -37,6 +38,13 @@ class SigmaStats(ctypes.Structure):
     _fields_ = [("flops", ctypes.c_double), ("flops_issued", ctypes.c_double), ("op_bytes", ctypes.c_double),
                 ("launches", ctypes.c_int),
                 ("n_terms", ctypes.c_int), ("n_products", ctypes.c_int)]
+
+
+class GsParams(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int), ("n_schedule", ctypes.c_int),
+                ("M_schedule", ctypes.POINTER(ctypes.c_int)), ("sweeps_per_M", ctypes.c_int),
+                ("e_tol", ctypes.c_double), ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int),
+                ("dav_max_space", ctypes.c_int), ("trunc_tol", ctypes.c_double)]
 
 
 class LrtError(RuntimeError):
@@ -67,6 +75,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.heff_diag.argtypes = [vp, i, i, vp]
     lib.sigma_stats.argtypes = [vp, ctypes.POINTER(SigmaStats)]
     lib.sigma_noalloc.argtypes = [vp, i, i, i, vp, vp]
+    lib.sweep_gs.argtypes = [vp, ctypes.POINTER(GsParams), ctypes.POINTER(ctypes.c_double)]
+    lib.mps_get_bonds.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    lib.mps_get_site.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_int64)]
     for name in EXPORTS:
         if name != "lrt_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -146,6 +158,7 @@ class Context:
         desc = MpsDesc(k, n_alpha, n_beta, nsect.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                        secs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptrs, center, rptrs)
         self._check(self.lib.mps_load(self.h, ctypes.byref(desc)), "mps_load")
+        self._k = k
 
     def wfn_layout(self, site: int, nsite: int):
         n = ctypes.c_int64()
@@ -178,6 +191,38 @@ class Context:
     def heff_diag(self, site: int, nsite: int, d):
         n, _ = self.wfn_layout(site, nsite)
         self._check(self.lib.heff_diag(self.h, site, nsite, ctypes.c_void_p(_tensor_ptr(d, n))), "heff_diag")
+
+    def sweep_gs(self, M_schedule, max_sweeps: int = 20, sweeps_per_M: int = 2, e_tol: float = 1e-10,
+                 dav_tol: float = 1e-8, dav_max_iter: int = 200, dav_max_space: int = 24,
+                 trunc_tol: float = 1e-14) -> float:
+        """Two-site ground-state sweeps on the loaded (right-orthonormal) MPS; returns E0."""
+        ms = (ctypes.c_int * len(M_schedule))(*M_schedule)
+        p = GsParams(max_sweeps, len(M_schedule), ms, sweeps_per_M, e_tol, dav_tol, dav_max_iter,
+                     dav_max_space, trunc_tol)
+        e = ctypes.c_double()
+        self._check(self.lib.sweep_gs(self.h, ctypes.byref(p), ctypes.byref(e)), "sweep_gs")
+        return e.value
+
+    def mps_get(self):
+        """The loaded MPS as (bonds, sites): bond tables [(na, nb, dim)] and left-fused site arrays."""
+        tot = ctypes.c_int()
+        self._check(self.lib.mps_get_bonds(self.h, None, None, ctypes.byref(tot)), "mps_get_bonds")
+        k = self._k
+        ns = (ctypes.c_int * (k + 1))()
+        sec = (ctypes.c_int * (3 * tot.value))()
+        self._check(self.lib.mps_get_bonds(self.h, ns, sec, ctypes.byref(tot)), "mps_get_bonds")
+        bonds, pos = [], 0
+        for b in range(k + 1):
+            bonds.append([(sec[3 * (pos + s)], sec[3 * (pos + s) + 1], sec[3 * (pos + s) + 2]) for s in range(ns[b])])
+            pos += ns[b]
+        sites = []
+        for i in range(k):
+            n = ctypes.c_int64()
+            self._check(self.lib.mps_get_site(self.h, i, None, ctypes.byref(n)), "mps_get_site")
+            a = np.empty(n.value)
+            self._check(self.lib.mps_get_site(self.h, i, _dptr(a), ctypes.byref(n)), "mps_get_site")
+            sites.append(a)
+        return bonds, sites
 
     def stats(self) -> dict:
         s = SigmaStats()

@@ -20,6 +20,7 @@
 // states of label Q are the sub-blocks n = 0..3 in order, each the states of the
 // neighbouring bond sector Q -/+ n.
 #include <cuda_runtime.h>
+#include <cusolverDn.h>
 
 #include <algorithm>
 #include <array>
@@ -660,6 +661,19 @@ struct SiteTensor {
     o.d = nullptr;
   }
   SiteTensor(const SiteTensor&) = delete;
+  SiteTensor& operator=(SiteTensor&& o) noexcept {
+    if (this != &o) {
+      if (d) cudaFree(d);
+      blk_off = std::move(o.blk_off);
+      blk_rows = std::move(o.blk_rows);
+      sub_off = std::move(o.sub_off);
+      sub_qr = std::move(o.sub_qr);
+      total = o.total;
+      d = o.d;
+      o.d = nullptr;
+    }
+    return *this;
+  }
   ~SiteTensor() {
     if (d) cudaFree(d);
   }
@@ -722,6 +736,7 @@ struct lrt_ctx {
   std::vector<std::unique_ptr<lrt::OpSet>> L, R, XL, YR;
   std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
   lrt_sigma_stats last{};
+  int last_sweeps = 0;
 };
 
 namespace lrt {
@@ -1352,6 +1367,432 @@ static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
 }  // namespace lrt
 
 // ===========================================================================
+// ground-state sweeps: two-site Davidson (Eq. dmrg) and density-matrix
+// decimation with the gauge shift of Eq. gauge-shift
+// ===========================================================================
+namespace lrt {
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  double* ensure(size_t need) {
+    if (need <= n && p) return p;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (need == 0) need = 1;
+    if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation (sweep)");
+    n = need;
+    return p;
+  }
+};
+
+struct SolverHandle {
+  cusolverDnHandle_t h = nullptr;
+  ~SolverHandle() {
+    if (h) cusolverDnDestroy(h);
+  }
+};
+
+static double dev_dot(const double* a, const double* b, int64_t n, double* dtmp, cudaStream_t st) {
+  launch_dots(a, n, 1, b, n, dtmp, st);
+  double r = 0.0;
+  CK(cudaMemcpyAsync(&r, dtmp, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return r;
+}
+
+static void upload_coef(double* dcoef, const std::vector<double>& c, cudaStream_t st) {
+  if (!c.empty()) CK(cudaMemcpyAsync(dcoef, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+}
+
+// Lowest eigenpair of H_eff at a two-site position; psi (device) is the start vector
+// and receives the eigenvector.  Returns the eigenvalue.
+static double davidson_twosite(lrt_ctx* c, int i, double* psi, const lrt_gs_params& P, int* iters_out) {
+  SigmaPlan& plan = get_plan(c, i, 2, 1);
+  const int64_t n = plan.nelem;
+  const int maxs = std::max(2, std::min(P.dav_max_space, JACOBI_MAXN));
+  DevBuf V, AV, diag, r, t, u, au, small, coef, Hd, Wd, Zd;
+  V.ensure((size_t)maxs * n);
+  AV.ensure((size_t)maxs * n);
+  diag.ensure(n);
+  r.ensure(n);
+  t.ensure(n);
+  u.ensure(n);
+  au.ensure(n);
+  small.ensure(JACOBI_MAXN + 8);
+  coef.ensure(JACOBI_MAXN + 8);
+  Hd.ensure(JACOBI_MAXN * JACOBI_MAXN);
+  Wd.ensure(JACOBI_MAXN);
+  Zd.ensure(JACOBI_MAXN * JACOBI_MAXN);
+  cudaStream_t st = c->st;
+  launch_diag(plan.douts.p, plan.dterms.p, plan.ndiag, diag.p, st);
+  CK(cudaMemcpyAsync(t.p, psi, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  std::vector<double> Hs((size_t)maxs * maxs, 0.0), hcol(maxs), w(maxs), Z((size_t)maxs * maxs);
+  int m = 0;
+  double theta = 0.0;
+  int it = 0;
+  for (; it < P.dav_max_iter; ++it) {
+    // orthogonalize the new direction against the subspace (twice) and normalize
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {
+      launch_dots(V.p, n, m, t.p, n, small.p, st);
+      std::vector<double> cc(m);
+      CK(cudaMemcpyAsync(cc.data(), small.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (double& x : cc) x = -x;
+      upload_coef(coef.p, cc, st);
+      launch_lincomb(V.p, n, m, coef.p, n, t.p, 1.0, st);
+    }
+    const double nt = std::sqrt(std::max(0.0, dev_dot(t.p, t.p, n, small.p, st)));
+    if (nt < 1e-14) break;
+    launch_lincomb(nullptr, n, 0, coef.p, n, t.p, 1.0 / nt, st);
+    CK(cudaMemcpyAsync(V.p + (size_t)m * n, t.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    plan.p1.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf);
+    plan.p2.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf);
+    launch_dots(V.p, n, m + 1, AV.p + (size_t)m * n, n, small.p, st);
+    CK(cudaMemcpyAsync(hcol.data(), small.p, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j <= m; ++j) {
+      Hs[(size_t)j * maxs + m] = hcol[j];
+      Hs[(size_t)m * maxs + j] = hcol[j];
+    }
+    ++m;
+    // subspace eigenproblem on the GPU
+    std::vector<double> Hc((size_t)m * m);
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) Hc[(size_t)a * m + b] = Hs[(size_t)a * maxs + b];
+    CK(cudaMemcpyAsync(Hd.p, Hc.data(), Hc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_jacobi_eigh(Hd.p, m, Wd.p, Zd.p, st);
+    CK(cudaMemcpyAsync(w.data(), Wd.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(Z.data(), Zd.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    theta = w[0];
+    std::vector<double> al(m);
+    for (int a = 0; a < m; ++a) al[a] = Z[(size_t)a * m + 0];
+    upload_coef(coef.p, al, st);
+    launch_lincomb(V.p, n, m, coef.p, n, u.p, 0.0, st);
+    launch_lincomb(AV.p, n, m, coef.p, n, au.p, 0.0, st);
+    CK(cudaMemcpyAsync(r.p, au.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> mt = {-theta};
+    upload_coef(coef.p, mt, st);
+    launch_lincomb(u.p, n, 1, coef.p, n, r.p, 1.0, st);
+    const double rn = std::sqrt(std::max(0.0, dev_dot(r.p, r.p, n, small.p, st)));
+    if (rn < P.dav_tol) {
+      ++it;
+      break;
+    }
+    launch_precond(r.p, diag.p, theta, n, t.p, st);
+    if (m == maxs) {   // restart with the Ritz vector
+      CK(cudaMemcpyAsync(V.p, u.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(AV.p, au.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      std::fill(Hs.begin(), Hs.end(), 0.0);
+      Hs[0] = theta;
+      m = 1;
+    }
+  }
+  CK(cudaMemcpyAsync(psi, u.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  if (iters_out) *iters_out = it;
+  return theta;
+}
+
+// right-fused copy (per left sector q: D_q x fused(q), sub-blocks n side by side) of site b
+static std::vector<int64_t> site_rfused(lrt_ctx* c, int b, DevBuf& buf, const Fused& F) {
+  const SiteTensor& T = c->sites[b];
+  const Sectors& Lb = c->bonds[b];
+  std::vector<int64_t> off(Lb.n(), -1);
+  int64_t tot = 0;
+  for (int q = 0; q < Lb.n(); ++q) {
+    const int f = F.s.find(Lb.a[q], Lb.b[q]);
+    if (f < 0) continue;
+    off[q] = tot;
+    tot += (int64_t)Lb.d[q] * F.s.d[f];
+  }
+  double* p = buf.ensure(tot);
+  CK(cudaMemsetAsync(p, 0, (size_t)std::max<int64_t>(tot, 1) * sizeof(double), c->st));
+  std::vector<GatherTask> tasks;
+  std::vector<GatherSrc> srcs;
+  for (int q = 0; q < Lb.n(); ++q) {
+    if (off[q] < 0) continue;
+    const int f = F.s.find(Lb.a[q], Lb.b[q]);
+    for (int n = 0; n < 4; ++n) {
+      if (T.sub_off[q][n] < 0) continue;
+      const int Dr = c->bonds[b + 1].d[T.sub_qr[q][n]];
+      tasks.push_back(GatherTask{p + off[q] + F.off[f][n], F.s.d[f], Lb.d[q], Dr, (int)srcs.size(), 1});
+      srcs.push_back(GatherSrc{T.d + T.sub_off[q][n], Dr, 0, 1.0});
+    }
+  }
+  GatherPlan gp;
+  build_gather(gp, tasks, srcs, c->st);
+  gp.run(c->st);
+  CK(cudaStreamSynchronize(c->st));
+  return off;
+}
+
+// theta(i) = site i (left-fused) x site i+1 (right-fused), in the two-site layout
+static void form_theta(lrt_ctx* c, int i, double* psi, const std::vector<WfnBlock>& wb) {
+  const Fused fr = fuse(c->bonds[i + 2], true);
+  DevBuf rf;
+  std::vector<int64_t> roff = site_rfused(c, i + 1, rf, fr);
+  const SiteTensor& A = c->sites[i];
+  const Sectors& mid = c->bonds[i + 1];
+  int64_t n = 0;
+  for (auto& w : wb) n = std::max(n, w.off + (int64_t)w.rows * w.cols);
+  CK(cudaMemsetAsync(psi, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(double), c->st));
+  std::vector<GemmOut> outs;
+  std::vector<GemmSeg> segs;
+  for (const WfnBlock& w : wb) {
+    const int q = mid.find(w.label_a, w.label_b);
+    if (q < 0 || A.blk_off[q] < 0 || roff[q] < 0) continue;
+    if (A.blk_rows[q] != w.rows) throw Error(LRT_EINVAL, "internal: theta rows mismatch");
+    outs.push_back(GemmOut{psi + w.off, 0, w.cols, w.rows, w.cols, (int)segs.size(), 1, 0, 0});
+    segs.push_back(GemmSeg{A.d + A.blk_off[q], rf.p + roff[q], 0, 0, mid.d[q], w.cols, mid.d[q], 0, 0, 0, 0, 1.0});
+  }
+  GemmPlan gp;
+  build_gemm(gp, outs, segs, c->st);
+  gp.run(c->st, nullptr, nullptr);
+  CK(cudaStreamSynchronize(c->st));
+}
+
+static void upload_site(lrt_ctx* c, int b, SiteTensor&& T) {
+  c->sites[b] = std::move(T);
+}
+
+// Split theta at bond i+1 keeping the M largest density-matrix weights; dir = +1
+// leaves site i left-orthonormal and the centre on site i+1, dir = -1 leaves site
+// i+1 right-orthonormal and the centre on site i.  Returns the discarded weight.
+static double decimate(lrt_ctx* c, int i, const double* psi, const std::vector<WfnBlock>& wb, int M,
+                       double trunc_tol, int dir, SolverHandle& sh) {
+  cudaStream_t st = c->st;
+  if (!sh.h) {
+    if (cusolverDnCreate(&sh.h) != CUSOLVER_STATUS_SUCCESS) throw Error(LRT_ECUDA, "cusolverDnCreate failed");
+  }
+  cusolverDnSetStream(sh.h, st);
+  // density matrices, one per middle sector: rho = psi psi^T (dir +1) or psi^T psi (dir -1)
+  std::vector<int64_t> roff(wb.size());
+  std::vector<int> rdim(wb.size());
+  int64_t rtot = 0;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    rdim[w] = dir > 0 ? wb[w].rows : wb[w].cols;
+    roff[w] = rtot;
+    rtot += (int64_t)rdim[w] * rdim[w];
+  }
+  DevBuf rho, ev;
+  rho.ensure(rtot);
+  int64_t etot = 0;
+  for (int d : rdim) etot += d;
+  ev.ensure(etot);
+  {
+    std::vector<GemmOut> outs;
+    std::vector<GemmSeg> segs;
+    for (size_t w = 0; w < wb.size(); ++w) {
+      const WfnBlock& b = wb[w];
+      outs.push_back(GemmOut{rho.p + roff[w], 0, rdim[w], rdim[w], rdim[w], (int)segs.size(), 1, 0, 0});
+      if (dir > 0)
+        segs.push_back(GemmSeg{psi + b.off, psi + b.off, 0, 0, b.cols, b.cols, b.cols, 0, 1, 0, 0, 1.0});
+      else
+        segs.push_back(GemmSeg{psi + b.off, psi + b.off, 0, 0, b.cols, b.cols, b.rows, 1, 0, 0, 0, 1.0});
+    }
+    GemmPlan gp;
+    build_gemm(gp, outs, segs, st);
+    gp.run(st, nullptr, nullptr);
+  }
+  // eigen-decomposition per sector (cuSOLVER, FP64 on the device)
+  int* dinfo = nullptr;
+  if (cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
+  DevBuf work;
+  std::vector<int64_t> eoff(wb.size());
+  int64_t eo = 0;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    eoff[w] = eo;
+    const int nn = rdim[w];
+    eo += nn;
+    if (nn == 0) continue;
+    int lw = 0;
+    if (cusolverDnDsyevd_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nn, rho.p + roff[w], nn,
+                                    ev.p + eoff[w], &lw) != CUSOLVER_STATUS_SUCCESS)
+      throw Error(LRT_ECUDA, "syevd buffer size failed");
+    work.ensure(std::max(lw, 1));
+    if (cusolverDnDsyevd(sh.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nn, rho.p + roff[w], nn,
+                         ev.p + eoff[w], work.p, lw, dinfo) != CUSOLVER_STATUS_SUCCESS)
+      throw Error(LRT_ECUDA, "syevd failed");
+  }
+  std::vector<double> evh(etot);
+  CK(cudaMemcpyAsync(evh.data(), ev.p, etot * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(dinfo);
+  if (info != 0) throw Error(LRT_ECUDA, "syevd reported info " + std::to_string(info));
+  // keep the M largest weights over all sectors (ties: sector order, then index)
+  struct W { double v; int w; int j; };
+  std::vector<W> all;
+  double vmax = 0.0;
+  for (size_t w = 0; w < wb.size(); ++w)
+    for (int j = 0; j < rdim[w]; ++j) {
+      all.push_back({evh[eoff[w] + j], (int)w, j});
+      vmax = std::max(vmax, evh[eoff[w] + j]);
+    }
+  std::stable_sort(all.begin(), all.end(), [](const W& a, const W& b) {
+    if (a.v != b.v) return a.v > b.v;
+    if (a.w != b.w) return a.w < b.w;
+    return a.j > b.j;
+  });
+  std::vector<int> keep(wb.size(), 0);
+  double disc = 0.0;
+  int kept = 0;
+  for (const W& x : all) {
+    if (kept < M && x.v > trunc_tol * vmax) {
+      ++keep[x.w];
+      ++kept;
+    } else {
+      disc += std::max(0.0, x.v);
+    }
+  }
+  // new bond table (bond i+1)
+  Sectors nb;
+  std::vector<int> wsec(wb.size(), -1);
+  for (size_t w = 0; w < wb.size(); ++w)
+    if (keep[w] > 0) wsec[w] = nb.add(wb[w].label_a, wb[w].label_b, keep[w]);
+  // the kept eigenvectors of a sector are its last keep[w] rows (ascending eigenvalues)
+  c->bonds[i + 1] = nb;
+  SiteTensor Ti, Tj;
+  site_layout(Ti, c->bonds[i], c->bonds[i + 1]);
+  site_layout(Tj, c->bonds[i + 1], c->bonds[i + 2]);
+  if (cudaMalloc(&Ti.d, (size_t)std::max<int64_t>(Ti.total, 1) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Tj.d, (size_t)std::max<int64_t>(Tj.total, 1) * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "site tensors");
+  CK(cudaMemsetAsync(Ti.d, 0, (size_t)std::max<int64_t>(Ti.total, 1) * sizeof(double), st));
+  CK(cudaMemsetAsync(Tj.d, 0, (size_t)std::max<int64_t>(Tj.total, 1) * sizeof(double), st));
+  const Fused fr = fuse(c->bonds[i + 2], true);
+  // right-fused buffer for the new site i+1 (D' x fused_R)
+  DevBuf rfb;
+  std::vector<int64_t> rfo(wb.size(), -1);
+  int64_t rft = 0;
+  for (size_t w = 0; w < wb.size(); ++w)
+    if (keep[w] > 0) {
+      rfo[w] = rft;
+      rft += (int64_t)keep[w] * wb[w].cols;
+    }
+  rfb.ensure(std::max<int64_t>(rft, 1));
+  CK(cudaMemsetAsync(rfb.p, 0, (size_t)std::max<int64_t>(rft, 1) * sizeof(double), st));   // gather accumulates
+  std::vector<GemmOut> outs;
+  std::vector<GemmSeg> segs;
+  std::vector<GatherTask> gt;
+  std::vector<GatherSrc> gs;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    if (keep[w] == 0) continue;
+    const WfnBlock& b = wb[w];
+    const int q = wsec[w], d = keep[w];
+    const double* vecs = rho.p + roff[w] + (int64_t)(rdim[w] - d) * rdim[w];   // d rows of length rdim
+    if (dir > 0) {
+      // site i block (rows x d) = vecs^T ; centre (d x cols) = vecs psi
+      gt.push_back(GatherTask{Ti.d + Ti.blk_off[q], d, b.rows, d, (int)gs.size(), 1});
+      gs.push_back(GatherSrc{vecs, rdim[w], 1, 1.0});
+      outs.push_back(GemmOut{rfb.p + rfo[w], 0, b.cols, d, b.cols, (int)segs.size(), 1, 0, 0});
+      segs.push_back(GemmSeg{vecs, psi + b.off, 0, 0, rdim[w], b.cols, b.rows, 0, 0, 0, 0, 1.0});
+    } else {
+      // site i+1 right-fused block (d x cols) = vecs ; centre on site i (rows x d) = psi vecs^T
+      gt.push_back(GatherTask{rfb.p + rfo[w], b.cols, d, b.cols, (int)gs.size(), 1});
+      gs.push_back(GatherSrc{vecs, rdim[w], 0, 1.0});
+      outs.push_back(GemmOut{Ti.d + Ti.blk_off[q], 0, d, b.rows, d, (int)segs.size(), 1, 0, 0});
+      segs.push_back(GemmSeg{psi + b.off, vecs, 0, 0, b.cols, rdim[w], b.cols, 0, 1, 0, 0, 1.0});
+    }
+  }
+  {
+    GatherPlan gp;
+    build_gather(gp, gt, gs, st);
+    gp.run(st);
+    GemmPlan mp;
+    build_gemm(mp, outs, segs, st);
+    mp.run(st, nullptr, nullptr);
+  }
+  // right-fused (d x fused_R) -> left-fused storage of site i+1
+  {
+    std::vector<GatherTask> t2;
+    std::vector<GatherSrc> s2;
+    for (size_t w = 0; w < wb.size(); ++w) {
+      if (keep[w] == 0) continue;
+      const int q = wsec[w];
+      const int f = fr.s.find(wb[w].label_a, wb[w].label_b);
+      for (int n = 0; n < 4; ++n) {
+        if (Tj.sub_off[q][n] < 0) continue;
+        const int Dr = c->bonds[i + 2].d[Tj.sub_qr[q][n]];
+        t2.push_back(GatherTask{Tj.d + Tj.sub_off[q][n], Dr, keep[w], Dr, (int)s2.size(), 1});
+        s2.push_back(GatherSrc{rfb.p + rfo[w] + fr.off[f][n], wb[w].cols, 0, 1.0});
+      }
+    }
+    GatherPlan gp;
+    build_gather(gp, t2, s2, st);
+    gp.run(st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  upload_site(c, i, std::move(Ti));
+  upload_site(c, i + 1, std::move(Tj));
+  return disc;
+}
+
+static double sweep_gs_impl(lrt_ctx* c, const lrt_gs_params& P, int* nsw) {
+  const int k = c->k;
+  if (k < 2) throw Error(LRT_EINVAL, "sweep_gs: needs at least two sites");
+  c->sites_r.clear();
+  drop_plans(c);
+  for (int b = 0; b < k; ++b) {
+    c->XL[b].reset();
+    c->YR[b].reset();
+  }
+  for (int b = 1; b < k; ++b) c->L[b].reset();
+  for (int b = 0; b < k; ++b) c->R[b].reset();
+  for (int b = k - 1; b >= 1; --b) renorm_right(c, b);   // sites right-orthonormal, centre at 0
+  SolverHandle sh;
+  DevBuf psi;
+  double E = 0.0, Eprev = 0.0;
+  int sweep = 0;
+  for (; sweep < P.max_sweeps; ++sweep) {
+    const int si = std::min(sweep / std::max(1, P.sweeps_per_M), P.n_schedule - 1);
+    const int M = P.M_schedule[si];
+    for (int dir : {+1, -1}) {
+      for (int step = 0; step < k - 1; ++step) {
+        const int i = dir > 0 ? step : k - 2 - step;
+        std::vector<WfnBlock> wb = wfn_blocks(c, i, 2);
+        int64_t n = 0;
+        for (auto& w : wb) n = std::max(n, w.off + (int64_t)w.rows * w.cols);
+        psi.ensure(n);
+        form_theta(c, i, psi.p, wb);
+        int its = 0;
+        E = davidson_twosite(c, i, psi.p, P, &its);
+        decimate(c, i, psi.p, wb, M, P.trunc_tol, dir, sh);
+        drop_plans(c);
+        if (dir > 0) {
+          c->R[i + 1].reset();
+          c->YR[i].reset();
+          renorm_left(c, i);
+        } else {
+          c->L[i + 1].reset();
+          c->XL[i + 1].reset();
+          renorm_right(c, i + 1);
+        }
+      }
+    }
+    if (sweep > 0 && sweep / std::max(1, P.sweeps_per_M) >= P.n_schedule - 1 && std::fabs(E - Eprev) < P.e_tol) {
+      ++sweep;
+      break;
+    }
+    Eprev = E;
+  }
+  if (nsw) *nsw = sweep;
+  return E;
+}
+
+}  // namespace lrt
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 using namespace lrt;
@@ -1569,6 +2010,47 @@ int heff_diag(lrt_t ctx, int site, int nsite, double* d_dev) {
     SigmaPlan& p = get_plan(ctx, site, nsite, 1);
     launch_diag(p.douts.p, p.dterms.p, p.ndiag, d_dev, ctx->st);
     CK(cudaGetLastError());
+  });
+}
+
+int sweep_gs(lrt_t ctx, const lrt_gs_params* p, double* e0) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "sweep_gs: op_build and mps_load first");
+    if (!p || !p->M_schedule || p->n_schedule <= 0 || p->max_sweeps <= 0 || !e0)
+      throw Error(LRT_EINVAL, "sweep_gs: bad parameters");
+    int nsw = 0;
+    *e0 = sweep_gs_impl(ctx, *p, &nsw);
+    ctx->last_sweeps = nsw;
+  });
+}
+
+int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps) throw Error(LRT_ESTATE, "mps_get_bonds: no MPS");
+    int tot = 0;
+    for (int b = 0; b <= ctx->k; ++b) {
+      if (bond_nsect) bond_nsect[b] = ctx->bonds[b].n();
+      for (int s = 0; s < ctx->bonds[b].n(); ++s, ++tot)
+        if (bond_sectors) {
+          bond_sectors[3 * tot] = ctx->bonds[b].a[s];
+          bond_sectors[3 * tot + 1] = ctx->bonds[b].b[s];
+          bond_sectors[3 * tot + 2] = ctx->bonds[b].d[s];
+        }
+    }
+    if (total_sectors) *total_sectors = tot;
+  });
+}
+
+int mps_get_site(lrt_t ctx, int site, double* host_out, int64_t* nelem) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps) throw Error(LRT_ESTATE, "mps_get_site: no MPS");
+    if (site < 0 || site >= ctx->k) throw Error(LRT_EINVAL, "mps_get_site: bad site");
+    const SiteTensor& T = ctx->sites[site];
+    if (nelem) *nelem = T.total;
+    if (host_out && T.total > 0) {
+      CK(cudaMemcpyAsync(host_out, T.d, (size_t)T.total * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+    }
   });
 }
 

@@ -9,6 +9,8 @@
 //  diag:      outer products of operator diagonals (preconditioner of Eq. error).
 #include "lrt_kernels.h"
 
+#include <algorithm>
+
 namespace lrt {
 
 // ---------------------------------------------------------------------------
@@ -171,6 +173,158 @@ void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* 
                  cudaStream_t st) {
   if (nouts <= 0) return;
   diag_kernel<<<nouts, 256, 0, st>>>(outs, terms, dbase);
+}
+
+}  // namespace lrt
+
+// ---------------------------------------------------------------------------
+// Davidson vector operations
+// ---------------------------------------------------------------------------
+namespace lrt {
+
+__global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ V, int64_t ld, int m,
+                                                   const double* __restrict__ w, int64_t n,
+                                                   double* __restrict__ out) {
+  __shared__ double red[256];
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(V[j * ld + e], w[e], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = red[0];
+}
+
+void launch_dots(const double* V, int64_t ld, int m, const double* w, int64_t n, double* out, cudaStream_t st) {
+  if (m <= 0) return;
+  dots_kernel<<<m, 256, 0, st>>>(V, ld, m, w, n, out);
+}
+
+__global__ void __launch_bounds__(256) lincomb_kernel(const double* __restrict__ V, int64_t ld, int m,
+                                                      const double* __restrict__ coef, int64_t n,
+                                                      double* __restrict__ out, double beta) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = beta == 0.0 ? 0.0 : beta * out[e];
+    for (int j = 0; j < m; ++j) acc = fma(coef[j], V[j * ld + e], acc);
+    out[e] = acc;
+  }
+}
+
+void launch_lincomb(const double* V, int64_t ld, int m, const double* coef, int64_t n, double* out, double beta,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  lincomb_kernel<<<grid, 256, 0, st>>>(V, ld, m, coef, n, out, beta);
+}
+
+__global__ void __launch_bounds__(256) precond_kernel(const double* __restrict__ r, const double* __restrict__ d,
+                                                      double theta, int64_t n, double* __restrict__ t) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double den = d[e] - theta;
+    if (fabs(den) < 1e-4) den = den < 0.0 ? -1e-4 : 1e-4;
+    t[e] = -r[e] / den;
+  }
+}
+
+void launch_precond(const double* r, const double* d, double theta, int64_t n, double* t, cudaStream_t st) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  precond_kernel<<<grid, 256, 0, st>>>(r, d, theta, n, t);
+}
+
+// Cyclic Jacobi eigenvalue iteration for a small symmetric matrix held in shared
+// memory (n <= JACOBI_MAXN = 48): each rotation zeroes A[p][q]; sweeps stop when the off-diagonal norm is
+// below 1e-15 of the Frobenius norm, or after a fixed number of sweeps.
+__global__ void __launch_bounds__(256) jacobi_kernel(double* __restrict__ Ag, int n, double* __restrict__ w,
+                                                     double* __restrict__ Zg) {
+  __shared__ double A[JACOBI_MAXN][JACOBI_MAXN + 1];
+  __shared__ double Z[JACOBI_MAXN][JACOBI_MAXN + 1];
+  __shared__ double cs[2];
+  __shared__ double off;
+  __shared__ int order[JACOBI_MAXN];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    A[i][j] = 0.5 * (Ag[i * n + j] + Ag[j * n + i]);
+    Z[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) {
+      double o = 0.0, f = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          f += A[i][j] * A[i][j];
+          if (i != j) o += A[i][j] * A[i][j];
+        }
+      off = (o <= 1e-30 * f) ? -1.0 : o;
+    }
+    __syncthreads();
+    if (off < 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (tid == 0) {
+          const double apq = A[p][q];
+          double c = 1.0, s = 0.0;
+          if (apq != 0.0) {
+            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+          cs[0] = c;
+          cs[1] = s;
+        }
+        __syncthreads();
+        const double c = cs[0], s = cs[1];
+        if (s != 0.0) {
+          // rotate columns p, q of A and Z
+          for (int i = tid; i < n; i += blockDim.x) {
+            const double aip = A[i][p], aiq = A[i][q];
+            A[i][p] = c * aip - s * aiq;
+            A[i][q] = s * aip + c * aiq;
+            const double zip = Z[i][p], ziq = Z[i][q];
+            Z[i][p] = c * zip - s * ziq;
+            Z[i][q] = s * zip + c * ziq;
+          }
+          __syncthreads();
+          // rotate rows p, q of A
+          for (int j = tid; j < n; j += blockDim.x) {
+            const double apj = A[p][j], aqj = A[q][j];
+            A[p][j] = c * apj - s * aqj;
+            A[q][j] = s * apj + c * aqj;
+          }
+        }
+        __syncthreads();
+      }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 1; i < n; ++i) {       // insertion sort by eigenvalue
+      const int v = order[i];
+      int j = i - 1;
+      while (j >= 0 && A[order[j]][order[j]] > A[v][v]) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    Zg[i * n + j] = Z[i][order[j]];
+  }
+  for (int i = tid; i < n; i += blockDim.x) w[i] = A[order[i]][order[i]];
+}
+
+void launch_jacobi_eigh(double* A, int n, double* w, double* Z, cudaStream_t st) {
+  if (n <= 0) return;
+  jacobi_kernel<<<1, 64, 0, st>>>(A, n, w, Z);
 }
 
 }  // namespace lrt

@@ -68,3 +68,16 @@ constexpr int GEMM_TM = 64;   // output tile rows
 constexpr int GEMM_TN = 32;   // output tile columns
 
 }  // namespace lrt
+
+namespace lrt {
+// Davidson vector operations (FP64): V holds m vectors of length n with stride ld.
+void launch_dots(const double* V, int64_t ld, int m, const double* w, int64_t n, double* out, cudaStream_t st);
+void launch_lincomb(const double* V, int64_t ld, int m, const double* coef, int64_t n, double* out, double beta,
+                    cudaStream_t st);
+void launch_precond(const double* r, const double* d, double theta, int64_t n, double* t, cudaStream_t st);
+// Eigen-decomposition of a small symmetric n x n matrix (n <= JACOBI_MAXN) by cyclic Jacobi
+// rotations in one CTA: A (row-major, overwritten) -> eigenvalues w (ascending) and
+// eigenvectors as the columns of Z (row-major n x n).
+void launch_jacobi_eigh(double* A, int n, double* w, double* Z, cudaStream_t st);
+constexpr int JACOBI_MAXN = 48;
+}  // namespace lrt
