@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblrt.so")
-SOURCES = ["lrt_host.cpp", "lrt_kernels.cu", "lrt_noalloc.cu"]
+SOURCES = ["lrt_host.cpp", "lrt_kernels.cu", "lrt_noalloc.cu", "lrt_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -588,11 +588,15 @@ struct GatherPlan {
 struct GemmPlan {
   DevArray<GemmOut> outs;
   DevArray<GemmSeg> segs;
-  DevArray<int3> tiles;
-  int ntiles = 0;
+  DevArray<int3> tiles;      // FP64 kernel tiles
+  DevArray<int3> tc_tiles;   // tensor-core kernel tiles
+  int ntiles = 0, tc_ntiles = 0;
   double flops = 0.0;
   void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr) const {
     launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st);
+  }
+  void run_tc(cudaStream_t st, const double* xb, double* yb, double* tb, int* err) const {
+    launch_gemm_tf32x3(outs.p, segs.p, tc_tiles.p, tc_ntiles, xb, yb, tb, err, st);
   }
 };
 
@@ -637,6 +641,16 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
   P.tiles.upload(tiles, st);
   P.ntiles = (int)tiles.size();
   P.flops = fl;
+  std::vector<int3> tct;
+  const int TM = tc_tile_m(), TN = tc_tile_n();
+  for (size_t i = 0; i < outs.size(); ++i) {
+    const int tm = (outs[i].m + TM - 1) / TM;
+    const int tn = (outs[i].n + TN - 1) / TN;
+    for (int a = 0; a < tm; ++a)
+      for (int b = 0; b < tn; ++b) tct.push_back(make_int3((int)i, a, b));
+  }
+  P.tc_tiles.upload(tct, st);
+  P.tc_ntiles = (int)tct.size();
 }
 
 }  // namespace lrt
@@ -737,6 +751,10 @@ struct lrt_ctx {
   std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
   lrt_sigma_stats last{};
   int last_sweeps = 0;
+  int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
+  ~lrt_ctx() {
+    if (derr) cudaFree(derr);
+  }
 };
 
 namespace lrt {
@@ -1990,8 +2008,25 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     SigmaPlan& p = get_plan(ctx, site, nsite, nvec);
     if ((const double*)y_dev < x_dev + p.nelem * nvec && x_dev < (const double*)y_dev + p.nelem * nvec)
       throw Error(LRT_EINVAL, "sigma: x and y overlap");
-    p.p1.run(ctx->st, x_dev, y_dev, p.tbuf);
-    p.p2.run(ctx->st, x_dev, y_dev, p.tbuf);
+    if (precision == LRT_MIXED) {
+      if (!ctx->derr) {
+        if (cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+        CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
+      }
+      p.p1.run_tc(ctx->st, x_dev, y_dev, p.tbuf, ctx->derr);
+      p.p2.run_tc(ctx->st, x_dev, y_dev, p.tbuf, ctx->derr);
+      CK(cudaGetLastError());
+      int flag = 0;
+      CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      if (flag) {
+        CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
+        throw Error(LRT_ETIMEOUT, "sigma: a tensor-core pipeline wait expired; results are invalid");
+      }
+    } else {
+      p.p1.run(ctx->st, x_dev, y_dev, p.tbuf);
+      p.p2.run(ctx->st, x_dev, y_dev, p.tbuf);
+    }
     CK(cudaGetLastError());
     ctx->last.flops = p.flops_alg;
     ctx->last.flops_issued = p.p1.flops + p.p2.flops;

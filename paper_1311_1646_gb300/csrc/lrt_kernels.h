@@ -63,6 +63,13 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
+// split-TF32 tensor-core variant of launch_gemm_fp64 (tiles of tc_tile_m() x tc_tile_n());
+// *err is set to 1 if a bounded wait expired
+void launch_gemm_tf32x3(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                        const double* xbase, double* ybase, double* tbase, int* err, cudaStream_t st);
+int tc_tile_m();
+int tc_tile_n();
+
 constexpr int GATHER_TILE = 32;
 constexpr int GEMM_TM = 64;   // output tile rows
 constexpr int GEMM_TN = 32;   // output tile columns
