@@ -140,6 +140,29 @@ typedef struct {
 } lrt_gs_params;
 int sweep_gs(lrt_t ctx, const lrt_gs_params* params, double* e0);
 
+/* DMRG-TDA (Fig. alg:dmrgtda).  The zeroth-order state must be loaded in its
+ * mixed-canonical gauge: mps_load with site_data = L0_i (left-orthonormal) and
+ * site_data_right = R0_i (right-orthonormal), then tda_load with C0[i] (left-fused
+ * layout, C0_i = L0_i Lambda_{i+1} = Lambda_i R0_i, Eq. gauge-shift) and lam[b], the
+ * singular values of bond b concatenated sector by sector in table order.
+ * sweep_tda runs the block Davidson of Fig. alg:david_gep through forward and backward
+ * sweeps: Ritz rotation of the right-block objects (Eq. ritzrot2), first-order gauge
+ * shifts (Eqs. gauge_fwd, gauge_bwd, left1st, right1st), site sigma (Eqs. sigv1, sigv2),
+ * residual (Eq. rnorm), diagonal preconditioner (Eq. error), projection (Eq. param),
+ * reduced matrices (Eqs. hleft2, sleft2) and first-order renormalization (Eqs. lopr1st,
+ * ropr1st).  Outputs omega[nroots] = theta - E0 (excitation energies, ascending),
+ * resid[nroots] = sum_i |r_i|^2 of the last sweep and *e0 = <Psi0|H|Psi0>.
+ * Returns LRT_ENOCONV (results written) when max_iter is reached first. */
+typedef struct {
+  int max_space;      /* N, maximum number of trial vectors (0: max(4 nroots, 16)); <= 48 */
+  int max_iter;
+  double eps;         /* converged when sum_i |r_i^mu|^2 < eps for every root */
+  double pinv_cut;    /* Lambda^-1: singular values below pinv_cut * largest are dropped */
+  uint64_t seed;      /* initial trial vectors: SplitMix64 Gaussians projected by Q^C */
+} lrt_tda_params;
+int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);
+int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0);
+
 /* Read back the loaded MPS: bond tables (bond_nsect[k+1], bond_sectors[3 * total])
  * and the left-fused data of one site (host_out may be NULL to query *nelem). */
 int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors);

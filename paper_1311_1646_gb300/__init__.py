@@ -20,7 +20,7 @@ LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site"]
+           "mps_get_bonds", "mps_get_site", "tda_load", "sweep_tda"]
 
 _lib = None
 
@@ -45,6 +45,11 @@ class GsParams(ctypes.Structure):
                 ("M_schedule", ctypes.POINTER(ctypes.c_int)), ("sweeps_per_M", ctypes.c_int),
                 ("e_tol", ctypes.c_double), ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int),
                 ("dav_max_space", ctypes.c_int), ("trunc_tol", ctypes.c_double)]
+
+
+class TdaParams(ctypes.Structure):
+    _fields_ = [("max_space", ctypes.c_int), ("max_iter", ctypes.c_int), ("eps", ctypes.c_double),
+                ("pinv_cut", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class LrtError(RuntimeError):
@@ -79,6 +84,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mps_get_bonds.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
     lib.mps_get_site.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_int64)]
+    ppd = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+    lib.tda_load.argtypes = [vp, ppd, ppd]
+    lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
     for name in EXPORTS:
         if name != "lrt_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -202,6 +210,26 @@ class Context:
         e = ctypes.c_double()
         self._check(self.lib.sweep_gs(self.h, ctypes.byref(p), ctypes.byref(e)), "sweep_gs")
         return e.value
+
+    def tda_load(self, C0: list, lam: list):
+        """Zeroth-order centre tensors C0_i (left-fused layout) and Schmidt values per bond."""
+        c0 = [np.ascontiguousarray(x, dtype=np.float64) for x in C0]
+        lm = [np.ascontiguousarray(x, dtype=np.float64) for x in lam]
+        pc = (ctypes.POINTER(ctypes.c_double) * len(c0))(*[_dptr(a) for a in c0])
+        pl = (ctypes.POINTER(ctypes.c_double) * len(lm))(*[_dptr(a) for a in lm])
+        self._check(self.lib.tda_load(self.h, pc, pl), "tda_load")
+
+    def sweep_tda(self, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
+                  pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False):
+        """DMRG-TDA roots: returns (omega, resid, e0); omega are excitation energies."""
+        om = np.zeros(nroots)
+        rs = np.zeros(nroots)
+        e0 = ctypes.c_double()
+        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed)
+        rc = self.lib.sweep_tda(self.h, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), ctypes.byref(e0))
+        if rc != 0 and not (allow_noconv and rc == -4):
+            self._check(rc, "sweep_tda")
+        return om, rs, e0.value
 
     def mps_get(self):
         """The loaded MPS as (bonds, sites): bond tables [(na, nb, dim)] and left-fused site arrays."""

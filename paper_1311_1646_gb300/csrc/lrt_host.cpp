@@ -577,6 +577,30 @@ struct DevArray {
   }
 };
 
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) {
+    o.p = nullptr;
+    o.n = 0;
+  }
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  double* ensure(size_t need) {
+    if (need <= n && p) return p;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (need == 0) need = 1;
+    if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation (sweep)");
+    n = need;
+    return p;
+  }
+};
+
 struct GatherPlan {
   DevArray<GatherTask> tasks;
   DevArray<GatherSrc> srcs;
@@ -718,6 +742,8 @@ static void site_layout(SiteTensor& S, const Sectors& L, const Sectors& R) {
   S.total = off;
 }
 
+struct TdaState;
+
 struct SigmaPlan {
   GemmPlan p1, p2;
   DevArray<DiagOut> douts;
@@ -752,6 +778,7 @@ struct lrt_ctx {
   lrt_sigma_stats last{};
   int last_sweeps = 0;
   int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
+  std::unique_ptr<lrt::TdaState> tda;
   ~lrt_ctx() {
     if (derr) cudaFree(derr);
   }
@@ -798,9 +825,11 @@ static void reset_env(lrt_ctx* c) {
 }
 
 // L[b] (+) site b  (right = false)   or   site b (+) R[b+1]  (right = true)
-static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
+// X (+) site b (right = false: X is a left block ending at bond b) or site b (+) X
+// (right = true: X is a right block starting at bond b+1).  For a first-order
+// (transition) set X, Xrev is its reverse set: a transposed reference reads it.
+static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, int b, bool right) {
   const Ints& I = c->I;
-  const OpSet& X = right ? *c->R[b + 1] : *c->L[b];
   const Site site(b);
   auto E = std::make_unique<OpSet>();
   E->right = right;
@@ -845,11 +874,12 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
       const int j = kv.first.first, tr = kv.first.second;
       const Mat4& e4 = kv.second;
       if (e4.zero()) continue;
+      const OpSet& XS = (tr && Xrev) ? *Xrev : X;
       for (int s = 0; s < X.ns(); ++s) {
         const int sb = X.bra_of(j, s);
-        if (sb < 0 || !X.block_nz(j, s)) continue;
+        if (sb < 0 || !XS.block_nz(j, s)) continue;
         const int be = tr ? s : sb, ke = tr ? sb : s;
-        const double* src = X.d + X.off_of(j, s);
+        const double* src = XS.d + X.off_of(j, s);
         const int ld = X.basis.d[s];
         for (int n1 = 0; n1 < 4; ++n1)
           for (int n0 = 0; n0 < 4; ++n0) {
@@ -902,6 +932,10 @@ static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
   return E;
 }
 
+static std::unique_ptr<OpSet> enlarge(lrt_ctx* c, int b, bool right) {
+  return enlarge_set(c, right ? *c->R[b + 1] : *c->L[b], nullptr, b, right);
+}
+
 static OpSet& enlarged(lrt_ctx* c, int b, bool right) {
   auto& slot = right ? c->YR[b] : c->XL[b];
   if (!slot) {
@@ -912,39 +946,60 @@ static OpSet& enlarged(lrt_ctx* c, int b, bool right) {
   return *slot;
 }
 
-static void renorm_left(lrt_ctx* c, int b) {
-  OpSet& E = enlarged(c, b, false);
-  const Fused& F = *E.fused;
-  const SiteTensor& T = c->sites[b];
+// One contribution bra^T [E] ket to a renormalized block: E is an enlarged operator
+// set, bra and ket are site tensors (the zeroth-order isometry, or a first-order
+// one for the second bracket of Eqs. lopr1st / ropr1st).
+struct RenTerm {
+  const OpSet* E;
+  const SiteTensor* bra;
+  const SiteTensor* ket;
+};
+
+// right-fused copy of a site tensor between bonds b and b+1 (per left sector q:
+// D_q x fused(q), sub-blocks n side by side); returns the per-sector offsets
+static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, DevBuf& buf, const Fused& F);
+
+// left block of bond b+1 = sum_t bra_t^T E_t ket_t over the enlarged left block of bond b
+static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms) {
+  const OpSet& E0 = *terms[0].E;
+  const Fused& F = *E0.fused;
   auto N = std::make_unique<OpSet>();
   N->right = false;
   N->basis = c->bonds[b + 1];
-  make_keys(*N, E.orbs, E.mode, c->I.nso);
+  make_keys(*N, E0.orbs, E0.mode, c->I.nso);
   layout_blocks(*N);
   alloc_zero(*N, c->st);
   std::vector<GemmOut> o1, o2;
   std::vector<GemmSeg> s1, s2;
   int64_t toff = 0;
-  std::vector<int64_t> tpos;
   for (size_t o = 0; o < N->keys.size(); ++o)
     for (int q = 0; q < N->ns(); ++q) {
       const int qb = N->bra_of((int)o, q);
       if (qb < 0) continue;
       const int fk = F.s.find(N->basis.a[q], N->basis.b[q]);
       const int fb = F.s.find(N->basis.a[qb], N->basis.b[qb]);
-      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
-      if (T.blk_off[q] < 0 || T.blk_off[qb] < 0) continue;
-      N->bnz[o * N->ns() + q] = 1;
+      if (fk < 0 || fb < 0) continue;
       const int Dq = N->basis.d[q], Dqb = N->basis.d[qb];
       const int rk = F.s.d[fk], rb = F.s.d[fb];
-      if (T.blk_rows[q] != rk || T.blk_rows[qb] != rb)
-        throw Error(LRT_EINVAL, "site tensor rows do not match the enlarged basis");
-      tpos.push_back(toff);
-      o1.push_back(GemmOut{nullptr, toff, Dq, rb, Dq, (int)s1.size(), 1, 0, 0});
-      s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), T.d + T.blk_off[q], 0, 0, rk, Dq, rk, 0, 0, 0, 0, 1.0});
-      o2.push_back(GemmOut{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 1, 0, 0});
-      s2.push_back(GemmSeg{T.d + T.blk_off[qb], nullptr, 0, toff, Dqb, Dq, rb, 1, 0, 0, 0, 1.0});
-      toff += (int64_t)rb * Dq;
+      GemmOut out{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 0, 0, 0};
+      for (const RenTerm& t : terms) {
+        const OpSet& E = *t.E;
+        if (E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
+        const SiteTensor& K = *t.ket;
+        const SiteTensor& Bt = *t.bra;
+        if (K.blk_off[q] < 0 || Bt.blk_off[qb] < 0) continue;
+        if (K.blk_rows[q] != rk || Bt.blk_rows[qb] != rb)
+          throw Error(LRT_EINVAL, "site tensor rows do not match the enlarged basis");
+        o1.push_back(GemmOut{nullptr, toff, Dq, rb, Dq, (int)s1.size(), 1, 0, 0});
+        s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), K.d + K.blk_off[q], 0, 0, rk, Dq, rk, 0, 0, 0, 0, 1.0});
+        s2.push_back(GemmSeg{Bt.d + Bt.blk_off[qb], nullptr, 0, toff, Dqb, Dq, rb, 1, 0, 0, 0, 1.0});
+        ++out.seg_count;
+        toff += (int64_t)rb * Dq;
+      }
+      if (out.seg_count > 0) {
+        o2.push_back(out);
+        N->bnz[o * N->ns() + q] = 1;
+      }
     }
   double* tmp = nullptr;
   if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
@@ -960,52 +1015,27 @@ static void renorm_left(lrt_ctx* c, int b) {
   CK(cudaStreamSynchronize(c->st));
   if (tmp) cudaFree(tmp);
   N->finish_nz();
-  c->L[b + 1] = std::move(N);
-  for (int x = b + 2; x <= c->k; ++x) c->L[x].reset();
-  for (int x = b + 1; x < c->k; ++x) c->XL[x].reset();
-  drop_plans(c);
+  return N;
 }
 
-static void renorm_right(lrt_ctx* c, int b) {
-  OpSet& E = enlarged(c, b, true);
-  const Fused& F = *E.fused;
-  const SiteTensor& T = c->sites_r.empty() ? c->sites[b] : c->sites_r[b];
+// right block of bond b = sum_t R_bra,t [E_t] R_ket,t^T over the enlarged right block site b (+) R
+static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms) {
+  const OpSet& E0 = *terms[0].E;
+  const Fused& F = *E0.fused;
   const Sectors& Lb = c->bonds[b];
-  // right-fused copy of the site tensor: per left sector q, D_q x fused(q), sub-blocks n side by side
-  std::vector<int64_t> rf_off(Lb.n(), -1);
-  int64_t rtot = 0;
-  for (int q = 0; q < Lb.n(); ++q) {
-    const int f = F.s.find(Lb.a[q], Lb.b[q]);
-    if (f < 0) continue;
-    rf_off[q] = rtot;
-    rtot += (int64_t)Lb.d[q] * F.s.d[f];
-  }
-  double* rf = nullptr;
-  if (rtot > 0 && cudaMalloc(&rf, (size_t)rtot * sizeof(double)) != cudaSuccess)
-    throw Error(LRT_ENOMEM, "renormalize workspace");
-  CK(cudaMemsetAsync(rf, 0, (size_t)rtot * sizeof(double), c->st));
-  {
-    std::vector<GatherTask> tasks;
-    std::vector<GatherSrc> srcs;
-    for (int q = 0; q < Lb.n(); ++q) {
-      if (rf_off[q] < 0) continue;
-      const int f = F.s.find(Lb.a[q], Lb.b[q]);
-      for (int n = 0; n < 4; ++n) {
-        if (T.sub_off[q][n] < 0) continue;
-        const int qr = T.sub_qr[q][n];
-        const int Dr = c->bonds[b + 1].d[qr];
-        tasks.push_back(GatherTask{rf + rf_off[q] + F.off[f][n], F.s.d[f], Lb.d[q], Dr, (int)srcs.size(), 1});
-        srcs.push_back(GatherSrc{T.d + T.sub_off[q][n], Dr, 0, 1.0});
+  // right-fused copies of every distinct site tensor
+  std::map<const SiteTensor*, std::pair<std::unique_ptr<DevBuf>, std::vector<int64_t>>> rf;
+  for (const RenTerm& t : terms)
+    for (const SiteTensor* T : {t.bra, t.ket})
+      if (!rf.count(T)) {
+        auto buf = std::make_unique<DevBuf>();
+        auto off = rfused_copy(c, b, *T, *buf, F);
+        rf[T] = {std::move(buf), std::move(off)};
       }
-    }
-    GatherPlan gp;
-    build_gather(gp, tasks, srcs, c->st);
-    gp.run(c->st);
-  }
   auto N = std::make_unique<OpSet>();
   N->right = true;
   N->basis = Lb;
-  make_keys(*N, E.orbs, E.mode, c->I.nso);
+  make_keys(*N, E0.orbs, E0.mode, c->I.nso);
   layout_blocks(*N);
   alloc_zero(*N, c->st);
   std::vector<GemmOut> o1, o2;
@@ -1014,24 +1044,33 @@ static void renorm_right(lrt_ctx* c, int b) {
   for (size_t o = 0; o < N->keys.size(); ++o)
     for (int q = 0; q < N->ns(); ++q) {
       const int qb = N->bra_of((int)o, q);
-      if (qb < 0 || rf_off[q] < 0 || rf_off[qb] < 0) continue;
+      if (qb < 0) continue;
       const int fk = F.s.find(Lb.a[q], Lb.b[q]);
       const int fb = F.s.find(Lb.a[qb], Lb.b[qb]);
-      if (fk < 0 || fb < 0 || E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
-      N->bnz[o * N->ns() + q] = 1;
+      if (fk < 0 || fb < 0) continue;
       const int Dq = Lb.d[q], Dqb = Lb.d[qb];
       const int ck = F.s.d[fk], cb = F.s.d[fb];
-      o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 0});
-      s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), rf + rf_off[q], 0, 0, ck, ck, ck, 0, 1, 0, 0, 1.0});
-      o2.push_back(GemmOut{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 1, 0, 0});
-      s2.push_back(GemmSeg{rf + rf_off[qb], nullptr, 0, toff, cb, Dq, cb, 0, 0, 0, 0, 1.0});
-      toff += (int64_t)cb * Dq;
+      GemmOut out{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 0, 0, 0};
+      for (const RenTerm& t : terms) {
+        const OpSet& E = *t.E;
+        if (E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
+        const auto& K = rf.at(t.ket);
+        const auto& Bt = rf.at(t.bra);
+        if (K.second[q] < 0 || Bt.second[qb] < 0) continue;
+        o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 0});
+        s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), K.first->p + K.second[q], 0, 0, ck, ck, ck, 0, 1, 0, 0, 1.0});
+        s2.push_back(GemmSeg{Bt.first->p + Bt.second[qb], nullptr, 0, toff, cb, Dq, cb, 0, 0, 0, 0, 1.0});
+        ++out.seg_count;
+        toff += (int64_t)cb * Dq;
+      }
+      if (out.seg_count > 0) {
+        o2.push_back(out);
+        N->bnz[o * N->ns() + q] = 1;
+      }
     }
   double* tmp = nullptr;
-  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess) {
-    cudaFree(rf);
+  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "renormalize workspace");
-  }
   for (auto& x : o1) x.C = tmp + x.c_off;
   for (auto& x : s2) x.B = tmp + x.b_off;
   GemmPlan p1, p2;
@@ -1042,9 +1081,22 @@ static void renorm_right(lrt_ctx* c, int b) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   if (tmp) cudaFree(tmp);
-  if (rf) cudaFree(rf);
   N->finish_nz();
-  c->R[b] = std::move(N);
+  return N;
+}
+
+static void renorm_left(lrt_ctx* c, int b) {
+  OpSet& E = enlarged(c, b, false);
+  c->L[b + 1] = renorm_left_terms(c, b, {RenTerm{&E, &c->sites[b], &c->sites[b]}});
+  for (int x = b + 2; x <= c->k; ++x) c->L[x].reset();
+  for (int x = b + 1; x < c->k; ++x) c->XL[x].reset();
+  drop_plans(c);
+}
+
+static void renorm_right(lrt_ctx* c, int b) {
+  OpSet& E = enlarged(c, b, true);
+  const SiteTensor& T = c->sites_r.empty() ? c->sites[b] : c->sites_r[b];
+  c->R[b] = renorm_right_terms(c, b, {RenTerm{&E, &T, &T}});
   for (int x = 0; x < b; ++x) c->R[x].reset();
   for (int x = 0; x < b; ++x) c->YR[x].reset();
   drop_plans(c);
@@ -1098,18 +1150,13 @@ static uint16_t transpose_mask(uint16_t m) {
 // enlarged operators are never multiplied:
 //   phase 1: T[t](rows n') = sum_{n : X_t(n',n) != 0} X_t(n',n) psi_Q(rows n)
 //   phase 2: y_Q'(rows n' [, cols m']) = sum_t sign_t T[t](rows n' [, cols m]) Y_t(m',m)^T
-static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec) {
+// X: enlarged left block (L (+) site `site`); Y: the right block of bond site+1
+// (nsite 1) or the enlarged right block site+1 (+) R (nsite 2).  Xrev / Yrev: reverse
+// sets of first-order (transition) operator sets, read by transposed references.
+static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, const OpSet& Y,
+                                                  const OpSet* Yrev, int site, int nsite, int nvec) {
   const Ints& I = c->I;
   const int k = c->k;
-  OpSet& X = enlarged(c, site, false);
-  OpSet* Yp;
-  if (nsite == 1) {
-    if (!c->R[site + 1]) throw Error(LRT_ESTATE, "right block of bond " + std::to_string(site + 1) + " not built");
-    Yp = c->R[site + 1].get();
-  } else {
-    Yp = &enlarged(c, site + 1, true);
-  }
-  OpSet& Y = *Yp;
   const Fused& XF = *X.fused;
   const Fused* YF = (nsite == 2) ? Y.fused.get() : nullptr;
   const std::vector<WfnBlock> wb = wfn_blocks(c, site, nsite);
@@ -1159,7 +1206,10 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   std::vector<Ref> rx, ry;
   double op_bytes = 0.0, falg = 0.0;
   int nprod = 0;
-  const int Ikey = X.find(Key{KI, -1, -1});
+  // The identity of a zeroth-order enlarged block is the unit matrix (orthonormal
+  // basis), so its products use psi directly; the identity of a first-order set is the
+  // transition overlap <l0|l1> and is multiplied like any other operator.
+  const int Ikey = Xrev ? -1 : X.find(Key{KI, -1, -1});
 
   for (const Term& t : terms) {
     rx.clear();
@@ -1169,9 +1219,11 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
     for (const Ref& a : rx)
       for (const Ref& bref : ry) {
         const double coef = t.c * a.c * bref.c;
+        const OpSet& XS = (a.t && Xrev) ? *Xrev : X;
+        const OpSet& YS = (bref.t && Yrev) ? *Yrev : Y;
         for (int f = 0; f < X.ns(); ++f) {
           const int fb0 = X.bra_of(a.op, f);
-          if (fb0 < 0 || !X.block_nz(a.op, f)) continue;
+          if (fb0 < 0 || !XS.block_nz(a.op, f)) continue;
           const int be = a.t ? f : fb0, ke = a.t ? fb0 : f;
           auto ik = blk_of.find(Sectors::key(X.basis.a[ke], X.basis.b[ke]));
           auto ib = blk_of.find(Sectors::key(X.basis.a[be], X.basis.b[be]));
@@ -1185,17 +1237,17 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
           int transB, ldb;
           uint16_t ymask = 1;   // stored blocks: one dense sub-block
           if (!bref.t) {
-            if (Y.bra_of(bref.op, yk) != ybb || !Y.block_nz(bref.op, yk)) continue;
-            Bp = Y.d + Y.off_of(bref.op, yk);
+            if (Y.bra_of(bref.op, yk) != ybb || !YS.block_nz(bref.op, yk)) continue;
+            Bp = YS.d + Y.off_of(bref.op, yk);
             transB = 1;
             ldb = Y.basis.d[yk];
-            if (YF) ymask = Y.mask[(size_t)bref.op * Y.ns() + yk];
+            if (YF) ymask = YS.mask[(size_t)bref.op * Y.ns() + yk];
           } else {
-            if (Y.bra_of(bref.op, ybb) != yk || !Y.block_nz(bref.op, ybb)) continue;
-            Bp = Y.d + Y.off_of(bref.op, ybb);
+            if (Y.bra_of(bref.op, ybb) != yk || !YS.block_nz(bref.op, ybb)) continue;
+            Bp = YS.d + Y.off_of(bref.op, ybb);
             transB = 0;
             ldb = Y.basis.d[ybb];
-            if (YF) ymask = transpose_mask(Y.mask[(size_t)bref.op * Y.ns() + ybb]);
+            if (YF) ymask = transpose_mask(YS.mask[(size_t)bref.op * Y.ns() + ybb]);
           }
           const int sign = (Y.par[bref.op] && ((wk.label_a + wk.label_b) & 1)) ? -1 : 1;
           const double sc = coef * sign;
@@ -1213,11 +1265,11 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
             const auto key = std::make_tuple(a.op, a.t, f);
             auto it = tcache.find(key);
             if (it == tcache.end()) {
-              uint16_t mx = X.mask[(size_t)a.op * X.ns() + f];
+              uint16_t mx = XS.mask[(size_t)a.op * X.ns() + f];
               if (a.t) mx = transpose_mask(mx);
               tp = toff;
               toff += (int64_t)wbb.rows * wk.cols;
-              const double* base = X.d + X.off_of(a.op, f);
+              const double* base = XS.d + X.off_of(a.op, f);
               const int ld = X.basis.d[f];
               op_bytes += 8.0 * ((double)wbb.rows * wk.rows);
               for (int r = 0; r < 4; ++r) {
@@ -1295,7 +1347,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
           // ---- diagonal contribution
           if (be == ke && yk == ybb) {
             DiagTerm d{};
-            d.x = ident ? nullptr : X.d + X.off_of(a.op, f);
+            d.x = ident ? nullptr : XS.d + X.off_of(a.op, f);
             d.xs = X.basis.d[f] + 1;
             d.y = Bp;
             d.ys = Y.basis.d[yk] + 1;
@@ -1367,6 +1419,18 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   return plan;
 }
 
+static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec) {
+  OpSet& X = enlarged(c, site, false);
+  OpSet* Yp;
+  if (nsite == 1) {
+    if (!c->R[site + 1]) throw Error(LRT_ESTATE, "right block of bond " + std::to_string(site + 1) + " not built");
+    Yp = c->R[site + 1].get();
+  } else {
+    Yp = &enlarged(c, site + 1, true);
+  }
+  return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
+}
+
 static SigmaPlan* find_plan(lrt_ctx* c, int site, int nsite, int nvec) {
   auto it = c->plans.find(std::make_tuple(site, nsite, nvec));
   return it == c->plans.end() ? nullptr : it->second.get();
@@ -1389,26 +1453,6 @@ static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
 // decimation with the gauge shift of Eq. gauge-shift
 // ===========================================================================
 namespace lrt {
-
-struct DevBuf {
-  double* p = nullptr;
-  size_t n = 0;
-  DevBuf() = default;
-  DevBuf(const DevBuf&) = delete;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-  double* ensure(size_t need) {
-    if (need <= n && p) return p;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-    if (need == 0) need = 1;
-    if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation (sweep)");
-    n = need;
-    return p;
-  }
-};
 
 struct SolverHandle {
   cusolverDnHandle_t h = nullptr;
@@ -1521,7 +1565,10 @@ static double davidson_twosite(lrt_ctx* c, int i, double* psi, const lrt_gs_para
 
 // right-fused copy (per left sector q: D_q x fused(q), sub-blocks n side by side) of site b
 static std::vector<int64_t> site_rfused(lrt_ctx* c, int b, DevBuf& buf, const Fused& F) {
-  const SiteTensor& T = c->sites[b];
+  return rfused_copy(c, b, c->sites[b], buf, F);
+}
+
+static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, DevBuf& buf, const Fused& F) {
   const Sectors& Lb = c->bonds[b];
   std::vector<int64_t> off(Lb.n(), -1);
   int64_t tot = 0;
@@ -1811,6 +1858,562 @@ static double sweep_gs_impl(lrt_ctx* c, const lrt_gs_params& P, int* nsw) {
 }  // namespace lrt
 
 // ===========================================================================
+// DMRG-TDA sweep (Fig. alg:dmrgtda): block Davidson through forward and backward
+// sweeps with first-order renormalized operators
+// ===========================================================================
+namespace lrt {
+
+struct TdaState {
+  std::vector<SiteTensor> C0;                 // C0_i, left-fused
+  std::vector<std::vector<double>> lam;       // Schmidt values per bond, concatenated by sector
+  bool loaded = false;
+};
+
+// dense bond matrices (one D x D block per sector of a bond)
+struct BondMat {
+  std::vector<int64_t> off;
+  DevBuf buf;
+};
+
+static void bond_layout(const Sectors& S, BondMat& M, cudaStream_t st) {
+  M.off.assign(S.n(), 0);
+  int64_t t = 0;
+  for (int q = 0; q < S.n(); ++q) {
+    M.off[q] = t;
+    t += (int64_t)S.d[q] * S.d[q];
+  }
+  M.buf.ensure(std::max<int64_t>(t, 1));
+  CK(cudaMemsetAsync(M.buf.p, 0, (size_t)std::max<int64_t>(t, 1) * sizeof(double), st));
+}
+
+static SiteTensor new_site(lrt_ctx* c, int i) {
+  SiteTensor T;
+  site_layout(T, c->bonds[i], c->bonds[i + 1]);
+  if (cudaMalloc(&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "site tensor");
+  CK(cudaMemsetAsync(T.d, 0, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double), c->st));
+  return T;
+}
+
+static void run_gemms(lrt_ctx* c, const std::vector<GemmOut>& o, const std::vector<GemmSeg>& g) {
+  if (o.empty()) return;
+  GemmPlan p;
+  build_gemm(p, o, g, c->st);
+  p.run(c->st, nullptr, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+}
+
+static double t_dot(lrt_ctx* c, const SiteTensor& A, const SiteTensor& B, DevBuf& tmp) {
+  tmp.ensure(4);
+  return dev_dot(A.d, B.d, A.total, tmp.p, c->st);
+}
+
+// Y = a X + b Y
+static void t_axpby(lrt_ctx* c, double a, const SiteTensor& X, double b, SiteTensor& Y, DevBuf& tmp) {
+  tmp.ensure(4);
+  CK(cudaMemcpyAsync(tmp.p, &a, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  launch_lincomb(X.d, X.total, 1, tmp.p, Y.total, Y.d, b, c->st);
+  CK(cudaStreamSynchronize(c->st));
+}
+
+// out_q = A_q^T B_q for every right sector q (bond i+1)
+static void t_lc(lrt_ctx* c, int i, const SiteTensor& A, const SiteTensor& B, BondMat& out) {
+  const Sectors& R = c->bonds[i + 1];
+  bond_layout(R, out, c->st);
+  std::vector<GemmOut> o;
+  std::vector<GemmSeg> g;
+  for (int q = 0; q < R.n(); ++q) {
+    if (A.blk_off[q] < 0) continue;
+    const int D = R.d[q];
+    o.push_back(GemmOut{out.buf.p + out.off[q], 0, D, D, D, (int)g.size(), 1, 0, 0});
+    g.push_back(GemmSeg{A.d + A.blk_off[q], B.d + B.blk_off[q], 0, 0, D, D, A.blk_rows[q], 1, 0, 0, 0, 1.0});
+  }
+  run_gemms(c, o, g);
+}
+
+// out = A X (X on the right bond i+1), or out += when acc
+static void t_rmul(lrt_ctx* c, int i, const SiteTensor& A, const BondMat& X, SiteTensor& out, bool acc) {
+  const Sectors& R = c->bonds[i + 1];
+  std::vector<GemmOut> o;
+  std::vector<GemmSeg> g;
+  for (int q = 0; q < R.n(); ++q) {
+    if (A.blk_off[q] < 0) continue;
+    const int D = R.d[q];
+    o.push_back(GemmOut{out.d + out.blk_off[q], 0, D, A.blk_rows[q], D, (int)g.size(), 1, acc ? 1 : 0, 0});
+    g.push_back(GemmSeg{A.d + A.blk_off[q], X.buf.p + X.off[q], 0, 0, D, D, D, 0, 0, 0, 0, 1.0});
+  }
+  run_gemms(c, o, g);
+}
+
+// out_ql = sum_n A(ql, n) B(ql, n)^T for every left sector ql (bond i)
+static void t_rc(lrt_ctx* c, int i, const SiteTensor& A, const SiteTensor& B, BondMat& out) {
+  const Sectors& L = c->bonds[i];
+  bond_layout(L, out, c->st);
+  std::vector<GemmOut> o;
+  std::vector<GemmSeg> g;
+  for (int q = 0; q < L.n(); ++q) {
+    const int D = L.d[q];
+    GemmOut x{out.buf.p + out.off[q], 0, D, D, D, (int)g.size(), 0, 0, 0};
+    for (int n = 0; n < 4; ++n) {
+      if (A.sub_off[q][n] < 0) continue;
+      const int Dr = c->bonds[i + 1].d[A.sub_qr[q][n]];
+      g.push_back(GemmSeg{A.d + A.sub_off[q][n], B.d + B.sub_off[q][n], 0, 0, Dr, Dr, Dr, 0, 1, 0, 0, 1.0});
+      ++x.seg_count;
+    }
+    if (x.seg_count) o.push_back(x);
+  }
+  run_gemms(c, o, g);
+}
+
+// out = X A (X on the left bond i), or out += when acc
+static void t_lmul(lrt_ctx* c, int i, const BondMat& X, const SiteTensor& A, SiteTensor& out, bool acc) {
+  const Sectors& L = c->bonds[i];
+  std::vector<GemmOut> o;
+  std::vector<GemmSeg> g;
+  for (int q = 0; q < L.n(); ++q)
+    for (int n = 0; n < 4; ++n) {
+      if (A.sub_off[q][n] < 0) continue;
+      const int D = L.d[q];
+      const int Dr = c->bonds[i + 1].d[A.sub_qr[q][n]];
+      o.push_back(GemmOut{out.d + A.sub_off[q][n], 0, Dr, D, Dr, (int)g.size(), 1, acc ? 1 : 0, 0});
+      g.push_back(GemmSeg{X.buf.p + X.off[q], A.d + A.sub_off[q][n], 0, 0, D, Dr, D, 0, 0, 0, 0, 1.0});
+    }
+  run_gemms(c, o, g);
+}
+
+static void lam_mats(lrt_ctx* c, int b, const std::vector<double>& lam, double cut, BondMat& L, BondMat& Li) {
+  const Sectors& S = c->bonds[b];
+  bond_layout(S, L, c->st);
+  bond_layout(S, Li, c->st);
+  double smax = 0.0;
+  for (double x : lam) smax = std::max(smax, x);
+  std::vector<double> hl(L.buf.n, 0.0), hi(L.buf.n, 0.0);
+  int64_t pos = 0;
+  for (int q = 0; q < S.n(); ++q) {
+    for (int a = 0; a < S.d[q]; ++a) {
+      const double x = lam[pos + a];
+      hl[L.off[q] + (int64_t)a * S.d[q] + a] = x;
+      hi[L.off[q] + (int64_t)a * S.d[q] + a] = (x > cut * smax) ? 1.0 / x : 0.0;
+    }
+    pos += S.d[q];
+  }
+  CK(cudaMemcpyAsync(L.buf.p, hl.data(), hl.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(Li.buf.p, hi.data(), hi.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+}
+
+// an operator set with the layout of `t` and zero data
+static std::unique_ptr<OpSet> clone_layout(lrt_ctx* c, const OpSet& t) {
+  auto S = std::make_unique<OpSet>();
+  S->basis = t.basis;
+  S->right = t.right;
+  S->orbs = t.orbs;
+  S->in = t.in;
+  S->mode = t.mode;
+  S->keys = t.keys;
+  S->index = t.index;
+  S->da = t.da;
+  S->db = t.db;
+  S->par = t.par;
+  S->bra = t.bra;
+  S->off = t.off;
+  S->total = t.total;
+  S->bnz = t.bnz;
+  S->onz = t.onz;
+  S->mask = t.mask;
+  if (t.fused) S->fused = std::make_unique<Fused>(*t.fused);
+  alloc_zero(*S, c->st);
+  return S;
+}
+
+struct FirstOrder {           // a first-order operator set and its reverse set
+  std::unique_ptr<OpSet> f, r;
+  bool empty() const { return !f; }
+};
+
+static double splitmix_normal(uint64_t seed, uint64_t idx) {
+  auto sm = [](uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const uint64_t g = 0x9E3779B97F4A7C15ull;
+  const uint64_t z1 = sm(seed + (2 * idx + 1) * g), z2 = sm(seed + (2 * idx + 2) * g);
+  const double u1 = ((double)(z1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((double)(z2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+struct TdaRunner {
+  lrt_ctx* c;
+  int k;
+  const lrt_tda_params& P;
+  std::vector<BondMat> lam, ilam;
+  std::vector<DevBuf> diag;
+  std::vector<std::unique_ptr<SigmaPlan>> h0plan;
+  DevBuf tmp;
+  double E0 = 0.0;
+
+  TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p) {}
+
+  const SiteTensor& L0(int i) { return c->sites[i]; }
+  const SiteTensor& R0(int i) { return c->sites_r[i]; }
+  const SiteTensor& C0(int i) { return c->tda->C0[i]; }
+
+  void setup() {
+    lam.resize(k + 1);
+    ilam.resize(k + 1);
+    for (int b = 0; b <= k; ++b) lam_mats(c, b, c->tda->lam[b], P.pinv_cut, lam[b], ilam[b]);
+    // zeroth-order environments: left blocks from L0, right blocks from R0
+    for (int b = 0; b + 1 < k; ++b) renorm_left(c, b);
+    for (int b = k - 1; b >= 1; --b) renorm_right(c, b);
+    for (int i = 0; i < k; ++i) {
+      enlarged(c, i, false);
+      if (i > 0) enlarged(c, i, true);
+    }
+    h0plan.resize(k);
+    diag.resize(k);
+    for (int i = 0; i < k; ++i) {
+      h0plan[i] = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, 1);
+      diag[i].ensure(std::max<int64_t>(h0plan[i]->nelem, 1));
+      launch_diag(h0plan[i]->douts.p, h0plan[i]->dterms.p, h0plan[i]->ndiag, diag[i].p, c->st);
+    }
+    SiteTensor y = new_site(c, 0);
+    h0(0, C0(0), y);
+    E0 = t_dot(c, C0(0), y, tmp);
+  }
+
+  // y = H_0^[i] C  (Eq. hzero_sb)
+  void h0(int i, const SiteTensor& C, SiteTensor& y) {
+    SigmaPlan& p = *h0plan[i];
+    p.p1.run(c->st, C.d, y.d, p.tbuf);
+    p.p2.run(c->st, C.d, y.d, p.tbuf);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+
+  // y = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i  (Eq. hleft_sb on C0)
+  void dh_left(int i, const FirstOrder& HL, SiteTensor& y) {
+    CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
+    if (HL.empty()) return;
+    auto Xf = enlarge_set(c, *HL.f, HL.r.get(), i, false);
+    auto Xr = enlarge_set(c, *HL.r, HL.f.get(), i, false);
+    auto plan = plan_sigma_sets(c, *Xf, Xr.get(), *c->R[i + 1], nullptr, i, 1, 1);
+    plan->p1.run(c->st, C0(i).d, y.d, plan->tbuf);
+    plan->p2.run(c->st, C0(i).d, y.d, plan->tbuf);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+
+  // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2)
+  void dh_right(int i, const FirstOrder& HR, SiteTensor& y) {
+    CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
+    if (HR.empty()) return;
+    auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1);
+    plan->p1.run(c->st, C0(i).d, y.d, plan->tbuf);
+    plan->p2.run(c->st, C0(i).d, y.d, plan->tbuf);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+
+  // Q^C C = C - C0 (C0 . C)
+  void proj_C(int i, SiteTensor& C) { t_axpby(c, -t_dot(c, C0(i), C, tmp), C0(i), 1.0, C, tmp); }
+  // Q^L C = C - L0 (L0^T C)
+  SiteTensor proj_L(int i, const SiteTensor& C) {
+    BondMat X;
+    t_lc(c, i, L0(i), C, X);
+    SiteTensor out = new_site(c, i);
+    t_axpby(c, 1.0, C, 0.0, out, tmp);
+    SiteTensor t = new_site(c, i);
+    t_rmul(c, i, L0(i), X, t, false);
+    t_axpby(c, -1.0, t, 1.0, out, tmp);
+    return out;
+  }
+  // C Q^R = C - (C R0^T) R0
+  SiteTensor proj_R(int i, const SiteTensor& C) {
+    BondMat X;
+    t_rc(c, i, C, R0(i), X);
+    SiteTensor out = new_site(c, i);
+    t_axpby(c, 1.0, C, 0.0, out, tmp);
+    SiteTensor t = new_site(c, i);
+    t_lmul(c, i, X, R0(i), t, false);
+    t_axpby(c, -1.0, t, 1.0, out, tmp);
+    return out;
+  }
+
+  // first-order left set at bond i+1 (Eq. lopr1st), both directions
+  FirstOrder grow_HL(int i, const FirstOrder& HL, const SiteTensor& L1) {
+    FirstOrder out;
+    const OpSet& XL = *c->XL[i];
+    if (HL.empty()) {
+      out.f = renorm_left_terms(c, i, {RenTerm{&XL, &L0(i), &L1}});
+      out.r = renorm_left_terms(c, i, {RenTerm{&XL, &L1, &L0(i)}});
+    } else {
+      auto Xf = enlarge_set(c, *HL.f, HL.r.get(), i, false);
+      auto Xr = enlarge_set(c, *HL.r, HL.f.get(), i, false);
+      out.f = renorm_left_terms(c, i, {RenTerm{Xf.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}});
+      out.r = renorm_left_terms(c, i, {RenTerm{Xr.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}});
+    }
+    return out;
+  }
+
+  // first-order right set at bond i (Eq. ropr1st), both directions
+  FirstOrder grow_HR(int i, const FirstOrder& HR, const SiteTensor& R1) {
+    FirstOrder out;
+    const OpSet& YR = *c->YR[i];
+    if (HR.empty()) {
+      out.f = renorm_right_terms(c, i, {RenTerm{&YR, &R0(i), &R1}});
+      out.r = renorm_right_terms(c, i, {RenTerm{&YR, &R1, &R0(i)}});
+    } else {
+      auto Yf = enlarge_set(c, *HR.f, HR.r.get(), i, true);
+      auto Yr = enlarge_set(c, *HR.r, HR.f.get(), i, true);
+      out.f = renorm_right_terms(c, i, {RenTerm{Yf.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R0(i), &R1}});
+      out.r = renorm_right_terms(c, i, {RenTerm{Yr.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R1, &R0(i)}});
+    }
+    return out;
+  }
+
+  // sum_j a_j S_j over operator sets of one layout (Eq. ritzrot2 on H^R)
+  std::unique_ptr<OpSet> combine(const std::vector<const OpSet*>& sets, const std::vector<double>& a) {
+    auto out = clone_layout(c, *sets[0]);
+    for (size_t j = 0; j < sets.size(); ++j) {
+      if (a[j] == 0.0 || sets[j]->total == 0) continue;
+      tmp.ensure(4);
+      CK(cudaMemcpyAsync(tmp.p, &a[j], sizeof(double), cudaMemcpyHostToDevice, c->st));
+      launch_lincomb(sets[j]->d, sets[j]->total, 1, tmp.p, out->total, out->d, 1.0, c->st);
+      CK(cudaStreamSynchronize(c->st));
+    }
+    return out;
+  }
+
+  SiteTensor random_site(int i, int mu) {
+    SiteTensor T = new_site(c, i);
+    std::vector<double> h(T.total);
+    const uint64_t seed = P.seed * 7919ull + 1000ull * (uint64_t)mu + (uint64_t)i;
+    for (int64_t e = 0; e < T.total; ++e) h[e] = splitmix_normal(seed, (uint64_t)e);
+    CK(cudaMemcpyAsync(T.d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    proj_C(i, T);
+    return T;
+  }
+
+  // small generalized eigenproblem H a = theta S a (S semi-definite), eigensolves on the GPU
+  void solve_gep(const std::vector<double>& H, const std::vector<double>& S, int l, std::vector<double>& w,
+                 std::vector<double>& U) {
+    if (l > JACOBI_MAXN) throw Error(LRT_EINVAL, "sweep_tda: subspace larger than the eigensolver limit");
+    DevBuf A, W, Z;
+    A.ensure((size_t)l * l);
+    W.ensure(l);
+    Z.ensure((size_t)l * l);
+    std::vector<double> s(l), Us((size_t)l * l);
+    CK(cudaMemcpyAsync(A.p, S.data(), (size_t)l * l * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_jacobi_eigh(A.p, l, W.p, Z.p, c->st);
+    CK(cudaMemcpyAsync(s.data(), W.p, l * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(Us.data(), Z.p, (size_t)l * l * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double smax = 0.0;
+    for (double x : s) smax = std::max(smax, x);
+    std::vector<int> keep;
+    for (int j = 0; j < l; ++j)
+      if (s[j] > 1e-12 * std::max(smax, 1e-300)) keep.push_back(j);
+    const int r = (int)keep.size();
+    std::vector<double> X((size_t)l * r);   // X = U_keep s^-1/2
+    for (int a = 0; a < l; ++a)
+      for (int j = 0; j < r; ++j) X[(size_t)a * r + j] = Us[(size_t)a * l + keep[j]] / std::sqrt(s[keep[j]]);
+    std::vector<double> Hp((size_t)r * r, 0.0);
+    for (int p = 0; p < r; ++p)
+      for (int q = 0; q < r; ++q) {
+        double acc = 0.0;
+        for (int a = 0; a < l; ++a)
+          for (int b2 = 0; b2 < l; ++b2)
+            acc += X[(size_t)a * r + p] * 0.5 * (H[(size_t)a * l + b2] + H[(size_t)b2 * l + a]) * X[(size_t)b2 * r + q];
+        Hp[(size_t)p * r + q] = acc;
+      }
+    std::vector<double> wr(r), Y((size_t)r * r);
+    CK(cudaMemcpyAsync(A.p, Hp.data(), (size_t)r * r * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_jacobi_eigh(A.p, r, W.p, Z.p, c->st);
+    CK(cudaMemcpyAsync(wr.data(), W.p, r * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(Y.data(), Z.p, (size_t)r * r * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    w = wr;
+    U.assign((size_t)l * r, 0.0);     // U = X Y  (l x r)
+    for (int a = 0; a < l; ++a)
+      for (int q = 0; q < r; ++q) {
+        double acc = 0.0;
+        for (int p2 = 0; p2 < r; ++p2) acc += X[(size_t)a * r + p2] * Y[(size_t)p2 * r + q];
+        U[(size_t)a * r + q] = acc;
+      }
+  }
+
+  struct Vec {
+    std::vector<SiteTensor> R1;
+    std::vector<FirstOrder> HR;   // index b = bond
+  };
+
+  void run(int n, double* theta_out, double* resid_out, int* iters_out) {
+    setup();
+    const int N = P.max_space > 0 ? P.max_space : std::max(4 * n, 16);
+    std::vector<Vec> old;
+    std::vector<double> alpha, theta, Hr, Sr, r2(n, 0.0);
+    int m = 0, it = 0, mcols = 0;
+    bool first = true;
+    for (;;) {
+      if (!first) {
+        std::vector<double> w, U;
+        const int lprev = (int)old.size();
+        solve_gep(Hr, Sr, lprev, w, U);
+        mcols = (int)w.size();
+        m = std::min(m, mcols);
+        alpha.assign((size_t)lprev * m, 0.0);
+        for (int a = 0; a < lprev; ++a)
+          for (int j = 0; j < m; ++j) alpha[(size_t)a * m + j] = U[(size_t)a * mcols + j];
+        theta.assign(w.begin(), w.begin() + m);
+      }
+      const int l = m + n;
+      Hr.assign((size_t)l * l, 0.0);
+      Sr.assign((size_t)l * l, 0.0);
+      std::fill(r2.begin(), r2.end(), 0.0);
+      // ---------------- forward sweep ----------------
+      std::vector<SiteTensor> Cprev(l);
+      std::vector<FirstOrder> HL(l);
+      std::vector<std::vector<SiteTensor>> L1(l);
+      for (auto& v : L1) v.resize(k);
+      for (int i = 0; i < k; ++i) {
+        std::vector<SiteTensor> C1(l);
+        std::vector<FirstOrder> HRrot(m);
+        for (int mu = 0; mu < m; ++mu) {
+          // Eq. ritzrot2 at this site
+          SiteTensor R1 = new_site(c, i);
+          std::vector<double> a(old.size());
+          for (size_t j = 0; j < old.size(); ++j) {
+            a[j] = alpha[j * m + mu];
+            t_axpby(c, a[j], old[j].R1[i], 1.0, R1, tmp);
+          }
+          if (i + 1 < k) {
+            std::vector<const OpSet*> fs, rs;
+            for (auto& v : old) {
+              fs.push_back(v.HR[i + 1].f.get());
+              rs.push_back(v.HR[i + 1].r.get());
+            }
+            HRrot[mu].f = combine(fs, a);
+            HRrot[mu].r = combine(rs, a);
+          }
+          // Eq. gauge_fwd
+          C1[mu] = new_site(c, i);
+          if (i == 0) {
+            t_lmul(c, i, lam[0], R1, C1[mu], false);
+          } else {
+            BondMat X;
+            t_lc(c, i - 1, L0(i - 1), Cprev[mu], X);
+            t_lmul(c, i, X, R0(i), C1[mu], false);
+            t_lmul(c, i, lam[i], R1, C1[mu], true);
+          }
+        }
+        // correction vectors (Eqs. sigv1, rnorm, error, param)
+        for (int mu = 0; mu < n; ++mu) {
+          if (first) {
+            C1[m + mu] = random_site(i, mu);
+            continue;
+          }
+          SiteTensor sig = new_site(c, i), t1 = new_site(c, i);
+          h0(i, C1[mu], sig);
+          dh_left(i, HL[mu], t1);
+          t_axpby(c, 1.0, t1, 1.0, sig, tmp);
+          dh_right(i, HRrot[mu], t1);
+          t_axpby(c, 1.0, t1, 1.0, sig, tmp);
+          t_axpby(c, -theta[mu], C1[mu], 1.0, sig, tmp);     // r = sigma - theta C
+          r2[mu] += t_dot(c, sig, sig, tmp);
+          SiteTensor z = new_site(c, i);
+          launch_precond(sig.d, diag[i].p, theta[mu], sig.total, z.d, c->st);   // -r / (d - theta)
+          t_axpby(c, 0.0, z, -1.0, z, tmp);                                       // r / (d - theta)
+          proj_C(i, z);
+          C1[m + mu] = std::move(z);
+        }
+        // projected coefficients (Eq. cwfn1st) and reduced matrices (Eqs. hleft2, sleft2)
+        std::vector<SiteTensor> Ct(l), H0Ct(l), dHC0(l);
+        for (int mu = 0; mu < l; ++mu) {
+          Ct[mu] = proj_L(i, C1[mu]);
+          H0Ct[mu] = new_site(c, i);
+          h0(i, Ct[mu], H0Ct[mu]);
+          dHC0[mu] = new_site(c, i);
+          dh_left(i, HL[mu], dHC0[mu]);
+        }
+        for (int a = 0; a < l; ++a)
+          for (int b2 = 0; b2 < l; ++b2) {
+            Hr[(size_t)a * l + b2] += t_dot(c, Ct[a], H0Ct[b2], tmp) + t_dot(c, Ct[a], dHC0[b2], tmp) +
+                                      t_dot(c, dHC0[a], Ct[b2], tmp);
+            Sr[(size_t)a * l + b2] += t_dot(c, Ct[a], Ct[b2], tmp);
+          }
+        // Eqs. left1st and lopr1st
+        for (int mu = 0; mu < l; ++mu) {
+          L1[mu][i] = new_site(c, i);
+          t_rmul(c, i, Ct[mu], ilam[i + 1], L1[mu][i], false);
+          if (i + 1 < k) HL[mu] = grow_HL(i, HL[mu], L1[mu][i]);
+        }
+        Cprev = std::move(C1);
+      }
+      // ---------------- backward sweep ----------------
+      std::vector<Vec> nv(l);
+      for (int mu = 0; mu < l; ++mu) {
+        nv[mu].R1.resize(k);
+        nv[mu].HR.resize(k + 1);
+        SiteTensor Cb = new_site(c, k - 1);
+        t_rmul(c, k - 1, L1[mu][k - 1], lam[k], Cb, false);
+        FirstOrder HR;
+        for (int i = k - 1; i >= 0; --i) {
+          if (i < k - 1) {
+            // Eq. gauge_bwd: C1_i = L1_i Lambda_{i+1} + L0_i (C1_{i+1} R0_{i+1}^T)
+            BondMat Y;
+            t_rc(c, i + 1, Cb, R0(i + 1), Y);
+            SiteTensor nb = new_site(c, i);
+            t_rmul(c, i, L1[mu][i], lam[i + 1], nb, false);
+            t_rmul(c, i, L0(i), Y, nb, true);
+            Cb = std::move(nb);
+          }
+          // Eq. right1st
+          SiteTensor pr = proj_R(i, Cb);
+          nv[mu].R1[i] = new_site(c, i);
+          t_lmul(c, i, ilam[i], pr, nv[mu].R1[i], false);
+          if (i > 0) {
+            HR = grow_HR(i, HR, nv[mu].R1[i]);
+            nv[mu].HR[i].f = clone_layout(c, *HR.f);
+            nv[mu].HR[i].r = clone_layout(c, *HR.r);
+            t_copy_set(*HR.f, *nv[mu].HR[i].f);
+            t_copy_set(*HR.r, *nv[mu].HR[i].r);
+          }
+        }
+      }
+      old = std::move(nv);
+      if (!first) {
+        ++it;
+        bool conv = true;
+        for (int mu = 0; mu < n; ++mu) conv = conv && (r2[mu] < P.eps);
+        if (conv || it >= P.max_iter) {
+          for (int mu = 0; mu < n; ++mu) {
+            theta_out[mu] = mu < (int)theta.size() ? theta[mu] : 0.0;
+            resid_out[mu] = r2[mu];
+          }
+          if (iters_out) *iters_out = it;
+          if (!conv) throw Error(LRT_ENOCONV, "sweep_tda: not converged within max_iter");
+          return;
+        }
+      }
+      first = false;
+      m = (l < N) ? l : n;
+    }
+  }
+
+  void t_copy_set(const OpSet& a, OpSet& b) {
+    if (a.total > 0)
+      CK(cudaMemcpyAsync(b.d, a.d, (size_t)a.total * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+};
+
+}  // namespace lrt
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 using namespace lrt;
@@ -2057,6 +2660,61 @@ int sweep_gs(lrt_t ctx, const lrt_gs_params* p, double* e0) {
     *e0 = sweep_gs_impl(ctx, *p, &nsw);
     ctx->last_sweeps = nsw;
   });
+}
+
+int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "tda_load: op_build and mps_load first");
+    if (ctx->sites_r.empty()) throw Error(LRT_ESTATE, "tda_load: the MPS must be loaded with its right-orthonormal form");
+    if (!C0 || !lam) throw Error(LRT_EINVAL, "tda_load: NULL arrays");
+    auto st = std::make_unique<TdaState>();
+    for (int i = 0; i < ctx->k; ++i) {
+      SiteTensor T;
+      site_layout(T, ctx->bonds[i], ctx->bonds[i + 1]);
+      if (cudaMalloc(&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
+        throw Error(LRT_ENOMEM, "tda_load");
+      if (!C0[i]) throw Error(LRT_EINVAL, "tda_load: missing C0");
+      CK(cudaMemcpyAsync(T.d, C0[i], (size_t)T.total * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+      st->C0.push_back(std::move(T));
+    }
+    for (int b = 0; b <= ctx->k; ++b) {
+      int64_t n = 0;
+      for (int q = 0; q < ctx->bonds[b].n(); ++q) n += ctx->bonds[b].d[q];
+      if (!lam[b]) throw Error(LRT_EINVAL, "tda_load: missing Lambda");
+      st->lam.emplace_back(lam[b], lam[b] + n);
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    st->loaded = true;
+    ctx->tda = std::move(st);
+  });
+}
+
+int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, double* resid, double* e0) {
+  int rc = LRT_OK;
+  std::vector<double> th(std::max(nroots, 1), 0.0), rs(std::max(nroots, 1), 0.0);
+  double E0 = 0.0;
+  const int r = guard(ctx, [&] {
+    if (!ctx->tda || !ctx->tda->loaded) throw Error(LRT_ESTATE, "sweep_tda: tda_load first");
+    if (!p || nroots <= 0 || !omega || !resid) throw Error(LRT_EINVAL, "sweep_tda: bad arguments");
+    TdaRunner R(ctx, *p);
+    int its = 0;
+    try {
+      R.run(nroots, th.data(), rs.data(), &its);
+    } catch (const Error& e) {
+      if (e.code != LRT_ENOCONV) throw;
+      rc = LRT_ENOCONV;
+    }
+    E0 = R.E0;
+    ctx->last_sweeps = its;
+  });
+  if (r != LRT_OK) return r;
+  for (int mu = 0; mu < nroots; ++mu) {
+    omega[mu] = th[mu] - E0;
+    resid[mu] = rs[mu];
+  }
+  if (e0) *e0 = E0;
+  if (rc != LRT_OK) ctx->err = "sweep_tda: not converged within max_iter (results written)";
+  return rc;
 }
 
 int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors) {

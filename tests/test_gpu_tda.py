@@ -1,0 +1,84 @@
+"""DMRG-TDA sweep on the GPU against the tangent-space definition, the oracle's sweep and FCI (GPU).
+
+The zeroth-order reference (two-site then one-site sweeps, mixed-canonical gauge)
+is produced by the CPU oracle from seeded inputs and handed to both sides.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dmrg, fock
+from oracle import mps as om
+from oracle import tda
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_1646_gb300 import build
+    build.build()
+    import paper_1311_1646_gb300 as p
+    p.load()
+    return p
+
+
+def _reference(k, na, nb, M, seed=7):
+    H = synth.ab_initio(k, na, nb, seed)
+    t, v = fock.spin_integrals(H.h, H.eri)
+    E, sites, _ = dmrg.ground_state(H, t, v, [M], synth.random_mps(k, na, nb, M, 3))
+    E, sites, _ = dmrg.onesite_sweeps(H, t, v, sites)
+    return H, t, v, om.mixed_canonical(sites)
+
+
+def _gpu_tda(pkg, H, ref, nroots, **kw):
+    L0, R0, C0, Lam, _ = ref
+    k = H.k
+    tables = [[(q[0], q[1], len(Lam[b][q])) for q in sorted(Lam[b])] for b in range(k + 1)]
+    L = [om.pack_site(L0[i], tables[i], tables[i + 1]) for i in range(k)]
+    R = [om.pack_site(R0[i], tables[i], tables[i + 1]) for i in range(k)]
+    C = [om.pack_site(C0[i], tables[i], tables[i + 1]) for i in range(k)]
+    lam = [np.concatenate([Lam[b][q] for q in sorted(Lam[b])]) for b in range(k + 1)]
+    ctx = pkg.Context(0)
+    ctx.op_build(k, H.h, H.eri, e_core=H.e_core)
+    ctx.mps_load(k, H.n_alpha, H.n_beta, tables, L, 0, sites_right=R)
+    ctx.tda_load(C, lam)
+    out = ctx.sweep_tda(nroots, **kw)
+    ctx.close()
+    return out
+
+
+def test_tda_matches_tangent_space_definition_and_oracle_sweep(pkg):
+    k, na, nb, M, n = 4, 2, 2, 8, 2
+    H, t, v, ref = _reference(k, na, nb, M)
+    L0, R0, C0, Lam, _ = ref
+    w, E0, dim = tda.tangent_rr(H, L0, R0, C0, Lam, n)
+    omega, resid, e0 = _gpu_tda(pkg, H, ref, n, max_iter=40, eps=1e-13, allow_noconv=True)
+    assert abs(e0 - E0) < 1e-10
+    assert np.abs(omega + e0 - w).max() < 1e-7
+    th, E0s, r2, it = tda.sweep_tda(H, t, v, L0, R0, C0, Lam, n, eps=1e-13, max_iter=40)
+    assert np.abs(omega + e0 - th).max() < 1e-7
+    assert np.all(resid < 1e-6)
+    ef = fock.fci_energies(H.h, H.eri, H.e_core, k, na, nb, n + 1)
+    assert np.all(omega + e0 >= ef[1:n + 1] - 1e-9)     # Rayleigh-Ritz in a subspace
+
+
+def test_tda_on_the_full_space_gives_fci_excitations(pkg):
+    k, na, nb, M, n = 4, 2, 2, 16, 3
+    H, t, v, ref = _reference(k, na, nb, M)
+    ef = fock.fci_energies(H.h, H.eri, H.e_core, k, na, nb, n + 1)
+    omega, resid, e0 = _gpu_tda(pkg, H, ref, n, max_iter=40, eps=1e-13, allow_noconv=True)
+    assert abs(e0 - ef[0]) < 1e-9
+    assert np.abs(omega - (ef[1:] - ef[0])).max() < 1e-7
+
+
+def test_tda_odd_electrons(pkg):
+    k, na, nb, M, n = 5, 3, 2, 10, 2
+    H, t, v, ref = _reference(k, na, nb, M)
+    L0, R0, C0, Lam, _ = ref
+    w, E0, dim = tda.tangent_rr(H, L0, R0, C0, Lam, n)
+    omega, resid, e0 = _gpu_tda(pkg, H, ref, n, max_iter=40, eps=1e-13, allow_noconv=True)
+    assert np.abs(omega + e0 - w).max() < 1e-6
