@@ -212,6 +212,15 @@ struct OpSet {
   std::vector<uint16_t> mask;     // enlarged sets: nonzero sub-blocks (bit 4*n_bra + n_ket) per block
   std::vector<char> bnz;          // per block: not identically zero (structural zeros are skipped)
   std::vector<char> onz;          // per operator: some block not identically zero
+  float* hi = nullptr;            // TF32 split of the data (mixed path), created on first use
+  float* lo = nullptr;
+  void ensure_shadow(cudaStream_t st) {
+    if (hi || total <= 0) return;
+    if (cudaMalloc(&hi, (size_t)total * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&lo, (size_t)total * sizeof(float)) != cudaSuccess)
+      throw Error(LRT_ENOMEM, "TF32 copy of an operator set");
+    launch_split_tf32(d, total, hi, lo, st);
+  }
   bool block_nz(int op, int ket) const { return bnz[(size_t)op * ns() + ket] != 0; }
   void finish_nz() {
     onz.assign(keys.size(), 0);
@@ -223,6 +232,8 @@ struct OpSet {
   OpSet(const OpSet&) = delete;
   ~OpSet() {
     if (d) cudaFree(d);
+    if (hi) cudaFree(hi);
+    if (lo) cudaFree(lo);
   }
   int ns() const { return basis.n(); }
   int find(const Key& k) const {
@@ -619,9 +630,6 @@ struct GemmPlan {
   void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr) const {
     launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st);
   }
-  void run_tc(cudaStream_t st, const double* xb, double* yb, double* tb, int* err) const {
-    launch_gemm_tf32x3(outs.p, segs.p, tc_tiles.p, tc_ntiles, xb, yb, tb, err, st);
-  }
 };
 
 static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vector<GatherSrc>& srcs,
@@ -755,8 +763,17 @@ struct SigmaPlan {
   int n_terms = 0, n_products = 0;
   double op_bytes = 0.0;
   double flops_alg = 0.0;   // products of non-zero sub-blocks only
+  // host copies of the segments and the operator set each absolute operand points into
+  std::vector<GemmSeg> S1, S2;
+  std::vector<const struct OpSet*> S1set, S2set;
+  // mixed path (split TF32): segments with TF32 operand pointers and hi/lo workspaces
+  bool tc_ready = false;
+  DevArray<TcSeg> tc1, tc2;
+  float *xhi = nullptr, *xlo = nullptr, *thi = nullptr, *tlo = nullptr;
   ~SigmaPlan() {
     if (tbuf) cudaFree(tbuf);
+    for (float* q : {xhi, xlo, thi, tlo})
+      if (q) cudaFree(q);
   }
 };
 
@@ -1197,8 +1214,10 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
     }
   }
   std::vector<std::vector<GemmSeg>> seg2(osub.size());
+  std::vector<std::vector<const OpSet*>> seg2set(osub.size());
   std::vector<GemmOut> o1;
   std::vector<GemmSeg> s1;
+  std::vector<const OpSet*> s1set;
   struct TEntry { int64_t tp; uint16_t rows; };
   std::map<std::tuple<int, int, int>, TEntry> tcache;   // (X op, trans, X ket fused) -> T
   int64_t toff = 0;
@@ -1297,6 +1316,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                   g.k = XF.dim[ke][cc];
                   g.scale = 1.0;
                   s1.push_back(g);
+                  s1set.push_back(&XS);
                   ++out.seg_count;
                   falg += 2.0 * XF.dim[be][r] * XF.dim[ke][cc] * wk.cols;
                 }
@@ -1324,6 +1344,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
               g.k = wk.cols;
               g.scale = sc;
               seg2[out_of.at({ib->second, r, 0})].push_back(g);
+              seg2set[out_of.at({ib->second, r, 0})].push_back(&YS);
               falg += 2.0 * XF.dim[be][r] * wk.cols * wbb.cols;
             } else {
               for (int mp = 0; mp < 4; ++mp)
@@ -1340,6 +1361,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                   g.k = YF->dim[yk][m];
                   g.scale = sc;
                   seg2[out_of.at({ib->second, r, mp})].push_back(g);
+                  seg2set[out_of.at({ib->second, r, mp})].push_back(&YS);
                   falg += 2.0 * XF.dim[be][r] * YF->dim[yk][m] * YF->dim[ybb][mp];
                 }
             }
@@ -1373,6 +1395,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
         GemmSeg g = s1[x.seg_begin + q];
         g.b_off += (int64_t)v * nelem;
         S1.push_back(g);
+        plan->S1set.push_back(s1set[x.seg_begin + q]);
       }
       O1.push_back(y);
     }
@@ -1389,7 +1412,8 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
       }
       GemmOut y{nullptr, coff + (int64_t)v * nelem, w.cols, XF.dim[fx][os.r], ncols, (int)S2.size(),
                 (int)seg2[u].size(), 0, 1};
-      for (GemmSeg g : seg2[u]) {
+      for (size_t q = 0; q < seg2[u].size(); ++q) {
+        GemmSeg g = seg2[u][q];
         if (g.a_rel) {
           g.a_off += (int64_t)v * nelem;
         } else {
@@ -1397,12 +1421,15 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
           g.a_off += (int64_t)v * toff;
         }
         S2.push_back(g);
+        plan->S2set.push_back(seg2set[u][q]);
       }
       O2.push_back(y);
     }
   }
   build_gemm(plan->p1, O1, S1, c->st);
   build_gemm(plan->p2, O2, S2, c->st);
+  plan->S1 = std::move(S1);
+  plan->S2 = std::move(S2);
   std::vector<DiagOut> dout;
   std::vector<DiagTerm> dts;
   for (size_t w = 0; w < wb.size(); ++w) {
@@ -1429,6 +1456,51 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
     Yp = &enlarged(c, site + 1, true);
   }
   return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
+}
+
+// TF32 segments and workspaces of a plan for the mixed path (once per plan)
+static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
+  if (p.tc_ready) return;
+  auto tc_of = [&](const GemmSeg& g, const OpSet* set, bool a_abs) {
+    TcSeg t{};
+    t.a_off = g.a_off;
+    t.b_off = g.b_off;
+    t.lda = g.lda;
+    t.ldb = g.ldb;
+    t.k = g.k;
+    t.transA = g.transA;
+    t.transB = g.transB;
+    t.a_rel = g.a_rel;
+    t.b_rel = g.b_rel;
+    t.scale = (float)g.scale;
+    if (a_abs) {
+      const int64_t off = g.A - set->d;
+      t.Ahi = set->hi + off;
+      t.Alo = set->lo + off;
+    } else {
+      const int64_t off = g.B - set->d;
+      t.Bhi = set->hi + off;
+      t.Blo = set->lo + off;
+    }
+    return t;
+  };
+  std::vector<TcSeg> t1, t2;
+  for (size_t i = 0; i < p.S1.size(); ++i) {
+    const_cast<OpSet*>(p.S1set[i])->ensure_shadow(c->st);
+    t1.push_back(tc_of(p.S1[i], p.S1set[i], true));
+  }
+  for (size_t i = 0; i < p.S2.size(); ++i) {
+    const_cast<OpSet*>(p.S2set[i])->ensure_shadow(c->st);
+    t2.push_back(tc_of(p.S2[i], p.S2set[i], false));
+  }
+  p.tc1.upload(t1, c->st);
+  p.tc2.upload(t2, c->st);
+  const size_t nx = (size_t)std::max<int64_t>(p.nelem * nvec, 1), nt = (size_t)std::max<int64_t>(p.tsize, 1);
+  if (cudaMalloc(&p.xhi, nx * sizeof(float)) != cudaSuccess || cudaMalloc(&p.xlo, nx * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p.thi, nt * sizeof(float)) != cudaSuccess || cudaMalloc(&p.tlo, nt * sizeof(float)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "mixed-precision workspace");
+  CK(cudaStreamSynchronize(c->st));
+  p.tc_ready = true;
 }
 
 static SigmaPlan* find_plan(lrt_ctx* c, int site, int nsite, int nvec) {
@@ -2616,8 +2688,11 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
         if (cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
         CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
       }
-      p.p1.run_tc(ctx->st, x_dev, y_dev, p.tbuf, ctx->derr);
-      p.p2.run_tc(ctx->st, x_dev, y_dev, p.tbuf, ctx->derr);
+      prepare_tc(ctx, p, nvec);
+      launch_split_tf32(x_dev, p.nelem * nvec, p.xhi, p.xlo, ctx->st);
+      const TcBases tb{p.xhi, p.xlo, p.thi, p.tlo, y_dev};
+      launch_gemm_tf32x3(p.p1.outs.p, p.tc1.p, p.p1.tc_tiles.p, p.p1.tc_ntiles, tb, ctx->derr, ctx->st);
+      launch_gemm_tf32x3(p.p2.outs.p, p.tc2.p, p.p2.tc_tiles.p, p.p2.tc_ntiles, tb, ctx->derr, ctx->st);
       CK(cudaGetLastError());
       int flag = 0;
       CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));

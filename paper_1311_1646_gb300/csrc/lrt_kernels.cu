@@ -79,12 +79,12 @@ constexpr int KC = 16;
 constexpr int GEMM_THREADS = 128;
 constexpr int GEMM_MAXE = GEMM_TM * GEMM_TN / GEMM_THREADS;   // outputs per thread
 
-__global__ void __launch_bounds__(GEMM_THREADS) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
-                                                                 const GemmSeg* __restrict__ segs,
-                                                                 const int3* __restrict__ tiles, int ntiles,
-                                                                 const double* __restrict__ xbase,
-                                                                 double* __restrict__ ybase,
-                                                                 double* __restrict__ tbase) {
+__global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
+                                                                    const GemmSeg* __restrict__ segs,
+                                                                    const int3* __restrict__ tiles, int ntiles,
+                                                                    const double* __restrict__ xbase,
+                                                                    double* __restrict__ ybase,
+                                                                    double* __restrict__ tbase) {
   __shared__ double As[GEMM_TM][KC + 1];
   __shared__ double Bs[KC][GEMM_TN + 1];
   const int w = blockIdx.x;
@@ -95,13 +95,12 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_fp64_kernel(const GemmOut* 
   const int mt = min(GEMM_TM, o.m - m0), nt = min(GEMM_TN, o.n - n0);
   const int ne = mt * nt;
   const int tid = threadIdx.x;
-  int ri[GEMM_MAXE], ci[GEMM_MAXE];
+  uint32_t rc[GEMM_MAXE];        // (row << 16) | col of each owned output element
   double acc[GEMM_MAXE];
 #pragma unroll
   for (int j = 0; j < GEMM_MAXE; ++j) {
     const int e = tid + GEMM_THREADS * j;
-    ri[j] = e < ne ? e / nt : 0;
-    ci[j] = e < ne ? e % nt : 0;
+    rc[j] = e < ne ? ((uint32_t)(e / nt) << 16) | (uint32_t)(e % nt) : 0u;
     acc[j] = 0.0;
   }
   const int cnt = ne > tid ? (ne - tid + GEMM_THREADS - 1) / GEMM_THREADS : 0;
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_fp64_kernel(const GemmOut* 
       for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
         for (int j = 0; j < GEMM_MAXE; ++j)
-          if (j < cnt) acc[j] = fma(As[ri[j]][kk], Bs[kk][ci[j]], acc[j]);
+          if (j < cnt) acc[j] = fma(As[rc[j] >> 16][kk], Bs[kk][rc[j] & 0xFFFFu], acc[j]);
       }
       __syncthreads();
     }
@@ -136,8 +135,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_fp64_kernel(const GemmOut* 
 #pragma unroll
   for (int j = 0; j < GEMM_MAXE; ++j) {
     if (j >= cnt) break;
-    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : tbase) + o.c_off : o.C) + (int64_t)(m0 + ri[j]) * o.ldc +
-                (n0 + ci[j]);
+    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : tbase) + o.c_off : o.C) +
+                (int64_t)(m0 + (int)(rc[j] >> 16)) * o.ldc + (n0 + (int)(rc[j] & 0xFFFFu));
     *c = o.accumulate ? (*c + acc[j]) : acc[j];
   }
 }
@@ -151,22 +150,54 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
 // ---------------------------------------------------------------------------
 // diagonal of H_eff
 // ---------------------------------------------------------------------------
+// One CTA per output block; term diagonals are staged through shared memory in
+// chunks so each element reads them from there instead of from global memory.
+constexpr int DIAG_CHUNK = 16;
+constexpr int DIAG_MAXD = 128;     // rows and columns of a block staged per chunk (32 KB of shared memory)
+
 __global__ void __launch_bounds__(256) diag_kernel(const DiagOut* __restrict__ outs,
                                                    const DiagTerm* __restrict__ terms,
                                                    double* __restrict__ dbase) {
+  __shared__ double xs[DIAG_CHUNK][DIAG_MAXD];
+  __shared__ double ys[DIAG_CHUNK][DIAG_MAXD];
+  __shared__ double sc[DIAG_CHUNK];
   const DiagOut o = outs[blockIdx.x];
-  const int n = o.rows * o.cols;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int i = e / o.cols, j = e % o.cols;
-    double acc = 0.0;
-    for (int t = 0; t < o.term_count; ++t) {
-      const DiagTerm d = terms[o.term_begin + t];
-      const double xv = d.x ? d.x[(int64_t)i * d.xs] : 1.0;
-      const double yv = d.y ? d.y[(int64_t)j * d.ys] : 1.0;
-      acc += d.scale * xv * yv;
+  for (int r0 = 0; r0 < o.rows; r0 += DIAG_MAXD)
+    for (int c0 = 0; c0 < o.cols; c0 += DIAG_MAXD) {
+      const int rt = min(DIAG_MAXD, o.rows - r0), ct = min(DIAG_MAXD, o.cols - c0);
+      const int n = rt * ct;
+      // each thread keeps up to 8 partial sums in registers, more are revisited below
+      for (int base = 0; base < n; base += 8 * blockDim.x) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int t0 = 0; t0 < o.term_count; t0 += DIAG_CHUNK) {
+          const int tc = min(DIAG_CHUNK, o.term_count - t0);
+          __syncthreads();
+          for (int e = threadIdx.x; e < tc * (rt + ct); e += blockDim.x) {
+            const int t = e / (rt + ct), u = e % (rt + ct);
+            const DiagTerm d = terms[o.term_begin + t0 + t];
+            if (u < rt) xs[t][u] = d.x ? d.x[(int64_t)(r0 + u) * d.xs] : 1.0;
+            else ys[t][u - rt] = d.y ? d.y[(int64_t)(c0 + u - rt) * d.ys] : 1.0;
+            if (u == 0) sc[t] = d.scale;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int e = base + threadIdx.x + j * blockDim.x;
+            if (e < n) {
+              const int i = e / ct, jj = e % ct;
+              double a = acc[j];
+              for (int t = 0; t < tc; ++t) a = fma(sc[t] * xs[t][i], ys[t][jj], a);
+              acc[j] = a;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = base + threadIdx.x + j * blockDim.x;
+          if (e < n) dbase[o.d_off + (int64_t)(r0 + e / ct) * o.cols + (c0 + e % ct)] = acc[j];
+        }
+      }
     }
-    dbase[o.d_off + e] = acc;
-  }
 }
 
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase,

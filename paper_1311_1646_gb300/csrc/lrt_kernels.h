@@ -63,10 +63,33 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
-// split-TF32 tensor-core variant of launch_gemm_fp64 (tiles of tc_tile_m() x tc_tile_n());
-// *err is set to 1 if a bounded wait expired
-void launch_gemm_tf32x3(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                        const double* xbase, double* ybase, double* tbase, int* err, cudaStream_t st);
+// Split-TF32 tensor-core variant of the grouped GEMM.  Operands are pre-split TF32
+// pairs (hi, lo) in FP32 storage: absolute pointers for operator data, or offsets from
+// the hi/lo copies of x (rel 1) or of the intermediates (rel 2).  Outputs with
+// c_rel == 2 are written as hi/lo pairs into the intermediates, others as FP64.
+struct TcSeg {
+  const float* Ahi;
+  const float* Alo;
+  const float* Bhi;
+  const float* Blo;
+  int64_t a_off, b_off;
+  int lda, ldb;
+  int k;
+  int transA, transB;
+  int a_rel, b_rel;
+  float scale;
+};
+struct TcBases {
+  const float* xhi;
+  const float* xlo;
+  float* thi;
+  float* tlo;
+  double* y;
+};
+void launch_gemm_tf32x3(const GemmOut* outs, const TcSeg* segs, const int3* tiles, int ntiles, TcBases b,
+                        int* err, cudaStream_t st);
+// hi = rna_tf32((float)x), lo = rna_tf32((float)x - hi) elementwise
+void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaStream_t st);
 int tc_tile_m();
 int tc_tile_n();
 

@@ -1,13 +1,15 @@
 // Split-TF32 tensor-core GEMM (tcgen05, sm_103a) for the mixed-precision path.
 //
-// Same task descriptors as gemm_fp64_kernel: every output tile (128 rows x 64
+// Same task structure as gemm_fp64_kernel: every output tile (128 rows x 64
 // columns) sums K-concatenated products scale_s * op(A_s) op(B_s).  Operands are
-// FP64 in memory; each element x is rounded to FP32 and split into TF32 parts
-// x = hi + lo (hi = rna(x), lo = rna(x - hi)), and the product is accumulated as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below FP32 resolution).
+// held as TF32 pairs x = hi + lo (hi = rna(x), lo = rna(x - hi) of the FP32-rounded
+// value), split once per operator set and once per input vector, and the product is
+// accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi (lo*lo is below FP32 resolution).
 // Each product (segment) accumulates in FP32 in tensor memory; the running sum over
-// the segments of a tile is carried in FP64 registers (one tensor-memory read per
-// finished segment), so FP32 accumulation spans only the K of one block product.
+// the segments of a tile is a compensated (two-sum) FP32 pair in registers, read
+// back once per finished segment, so plain FP32 accumulation spans only the K of one
+// block product.  No FP64 arithmetic runs in the loop: on this GPU the FP64 pipe is
+// the scarcest resource.
 //
 // Per K chunk of 32: all 128 threads convert and store the four operand tiles in
 // shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
@@ -70,8 +72,7 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_tf32(double v, uint32_t& hi, uint32_t& lo) {
-  const float x = (float)v;
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = to_tf32(x);
   lo = to_tf32(x - __uint_as_float(hi));
 }
@@ -126,12 +127,9 @@ __device__ __forceinline__ void ld_16cols(uint32_t taddr, float* v) {
 }  // namespace
 
 __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOut* __restrict__ outs,
-                                                                     const GemmSeg* __restrict__ segs,
+                                                                     const TcSeg* __restrict__ segs,
                                                                      const int3* __restrict__ tiles, int ntiles,
-                                                                     const double* __restrict__ xbase,
-                                                                     double* __restrict__ ybase,
-                                                                     double* __restrict__ tbase,
-                                                                     int* __restrict__ err) {
+                                                                     TcBases bases, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
@@ -168,14 +166,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
   constexpr uint32_t idesc = make_idesc();
   uint32_t phase = 0;
   const int row = warp * 32 + (tid & 31);
-  double acc[TC_N];
+  float sum[TC_N], cmp[TC_N];     // compensated running sum of the tile row
 #pragma unroll
-  for (int c = 0; c < TC_N; ++c) acc[c] = 0.0;
+  for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
 
   for (int s = 0; s < o.seg_count && !failed; ++s) {
-    GemmSeg g = segs[o.seg_begin + s];
-    if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : tbase) + g.a_off;
-    if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : tbase) + g.b_off;
+    const TcSeg g = segs[o.seg_begin + s];
+    const float* Ah = g.a_rel ? (g.a_rel == 1 ? bases.xhi : bases.thi) + g.a_off : g.Ahi;
+    const float* Al = g.a_rel ? (g.a_rel == 1 ? bases.xlo : bases.tlo) + g.a_off : g.Alo;
+    const float* Bh = g.b_rel ? (g.b_rel == 1 ? bases.xhi : bases.thi) + g.b_off : g.Bhi;
+    const float* Bl = g.b_rel ? (g.b_rel == 1 ? bases.xlo : bases.tlo) + g.b_off : g.Blo;
     bool issued = false;
     for (int k0 = 0; k0 < g.k && !failed; k0 += TC_K) {
       const int kc = min(TC_K, g.k - k0);
@@ -183,13 +183,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
       for (int e = tid; e < TC_M * TC_K; e += TC_THREADS) {
         int i, kk;
         if (!g.transA) { i = e / TC_K; kk = e % TC_K; } else { kk = e / TC_M; i = e % TC_M; }
-        double v = 0.0;
+        uint32_t hi = 0u, lo = 0u;
         if (i < mt && kk < kc) {
-          const int gi = m0 + i, gk = k0 + kk;
-          v = g.scale * (g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk]);
+          const int64_t idx = g.transA ? (int64_t)(k0 + kk) * g.lda + (m0 + i) : (int64_t)(m0 + i) * g.lda + (k0 + kk);
+          hi = __float_as_uint(Ah[idx]);
+          lo = __float_as_uint(Al[idx]);
         }
-        uint32_t hi, lo;
-        split_tf32(v, hi, lo);
         const uint32_t off = kmajor_offset(i, kk);
         *(uint32_t*)(sAh + off) = hi;
         *(uint32_t*)(sAl + off) = lo;
@@ -198,13 +197,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
       for (int e = tid; e < TC_N * TC_K; e += TC_THREADS) {
         int j, kk;
         if (!g.transB) { kk = e / TC_N; j = e % TC_N; } else { j = e / TC_K; kk = e % TC_K; }
-        double v = 0.0;
+        uint32_t hi = 0u, lo = 0u;
         if (j < nt && kk < kc) {
-          const int gj = n0 + j, gk = k0 + kk;
-          v = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
+          const int64_t idx = g.transB ? (int64_t)(n0 + j) * g.ldb + (k0 + kk) : (int64_t)(k0 + kk) * g.ldb + (n0 + j);
+          hi = __float_as_uint(Bh[idx]);
+          lo = __float_as_uint(Bl[idx]);
         }
-        uint32_t hi, lo;
-        split_tf32(v, hi, lo);
         const uint32_t off = kmajor_offset(j, kk);
         *(uint32_t*)(sBh + off) = hi;
         *(uint32_t*)(sBl + off) = lo;
@@ -235,14 +233,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
       __syncthreads();
     }
     if (issued && !failed) {
-      // fold this product into the FP64 running sum of the tile
+      // fold this product into the compensated running sum (two-sum in FP32)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int c0 = 0; c0 < TC_N; c0 += 16) {
         float v[16];
         ld_16cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] += (double)v[i];
+        for (int i = 0; i < 16; ++i) {
+          const float y = g.scale * v[i] - cmp[c0 + i];
+          const float t = sum[c0 + i] + y;
+          cmp[c0 + i] = (t - sum[c0 + i]) - y;
+          sum[c0 + i] = t;
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
@@ -250,12 +253,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
   }
 
   if (!failed && row < mt) {
-    double* C = (o.c_rel ? (o.c_rel == 1 ? ybase : tbase) + o.c_off : o.C);
+    if (o.c_rel == 2) {
+      // intermediate: keep it as a TF32 pair for the next phase
 #pragma unroll
-    for (int c = 0; c < TC_N; ++c) {
-      if (c < nt) {
-        double* p = C + (int64_t)(m0 + row) * o.ldc + (n0 + c);
-        *p = o.accumulate ? (*p + acc[c]) : acc[c];
+      for (int c = 0; c < TC_N; ++c) {
+        if (c < nt) {
+          const float v = sum[c] - cmp[c];
+          uint32_t hi, lo;
+          split_tf32(v, hi, lo);
+          const int64_t idx = o.c_off + (int64_t)(m0 + row) * o.ldc + (n0 + c);
+          bases.thi[idx] = __uint_as_float(hi);
+          bases.tlo[idx] = __uint_as_float(lo);
+        }
+      }
+    } else {
+      double* C = (o.c_rel == 1 ? bases.y + o.c_off : o.C);
+#pragma unroll
+      for (int c = 0; c < TC_N; ++c) {
+        if (c < nt) {
+          const double v = (double)sum[c] - (double)cmp[c];
+          double* p = C + (int64_t)(m0 + row) * o.ldc + (n0 + c);
+          *p = o.accumulate ? (*p + v) : v;
+        }
       }
     }
   }
@@ -266,18 +285,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
   }
 }
 
+__global__ void __launch_bounds__(256) split_tf32_kernel(const double* __restrict__ src, int64_t n,
+                                                         float* __restrict__ hi, float* __restrict__ lo) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h, l;
+    split_tf32((float)src[e], h, l);
+    hi[e] = __uint_as_float(h);
+    lo[e] = __uint_as_float(l);
+  }
+}
+
+void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaStream_t st) {
+  if (n <= 0) return;
+  const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+  split_tf32_kernel<<<grid, 256, 0, st>>>(src, n, hi, lo);
+}
+
 int tc_tile_m() { return TC_M; }
 int tc_tile_n() { return TC_N; }
 
-void launch_gemm_tf32x3(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                        const double* xbase, double* ybase, double* tbase, int* err, cudaStream_t st) {
+void launch_gemm_tf32x3(const GemmOut* outs, const TcSeg* segs, const int3* tiles, int ntiles, TcBases b,
+                        int* err, cudaStream_t st) {
   if (ntiles <= 0) return;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
-  gemm_tf32x3_kernel<<<ntiles, TC_THREADS, SMEM_BYTES, st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase, err);
+  gemm_tf32x3_kernel<<<ntiles, TC_THREADS, SMEM_BYTES, st>>>(outs, segs, tiles, ntiles, b, err);
 }
 
 }  // namespace lrt

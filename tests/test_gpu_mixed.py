@@ -8,7 +8,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 # 3xTF32 products of FP32-rounded operands, FP32 accumulation inside one block
-# product and FP64 across products: observed 3e-7..2e-6 of max|y| on these cases.
+# product and compensated FP32 sums across products: observed 3e-7..2e-6 of max|y|.
 MIXED_RTOL = 1e-5
 
 
