@@ -681,6 +681,11 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
     for (int a = 0; a < tm; ++a)
       for (int b = 0; b < tn; ++b) tct.push_back(make_int3((int)i, a, b));
   }
+  // the persistent tensor-core kernel deals tiles round-robin: longest first
+  std::vector<int64_t> ktot(outs.size(), 0);
+  for (size_t i = 0; i < outs.size(); ++i)
+    for (int s = 0; s < outs[i].seg_count; ++s) ktot[i] += segs[outs[i].seg_begin + s].k;
+  std::stable_sort(tct.begin(), tct.end(), [&](const int3& a, const int3& b) { return ktot[a.x] > ktot[b.x]; });
   P.tc_tiles.upload(tct, st);
   P.tc_ntiles = (int)tct.size();
 }

@@ -6,19 +6,37 @@
 // value), split once per operator set and once per input vector, and the product is
 // accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi (lo*lo is below FP32 resolution).
 // Each product (segment) accumulates in FP32 in tensor memory; the running sum over
-// the segments of a tile is a compensated (two-sum) FP32 pair in registers, read
-// back once per finished segment, so plain FP32 accumulation spans only the K of one
+// the segments of a tile is a compensated (two-sum) FP32 pair in registers, folded
+// in once per finished segment, so plain FP32 accumulation spans only the K of one
 // block product.  No FP64 arithmetic runs in the loop: on this GPU the FP64 pipe is
 // the scarcest resource.
 //
-// Per K chunk of 32: all 128 threads convert and store the four operand tiles in
-// shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices), one thread issues 3 x 4 tcgen05.mma (K = 8 each) and commits them to
-// an mbarrier, and every thread waits on that barrier before the tiles are
-// rewritten.  Every wait is bounded: on expiry the kernel records an error code,
-// stops issuing work, releases its tensor memory and returns.
+// Persistent, warp-specialised kernel (one CTA per SM, tiles dealt round-robin in
+// the host's longest-first order; 8 warps, so two per SM sub-partition and up to 255
+// registers a thread for the epilogue's 128 running-sum registers):
+//   warps 4-6  producers: copy K chunks of 32 of the four operand tiles from global
+//              memory into a 4-stage ring in shared memory, 128-byte-swizzled K-major
+//              (the layout tcgen05 reads with SWIZZLE_128B descriptors), zero-filling
+//              the K tail; arrive on full[stage].
+//   warp 7     one thread issues 3 x (K / 8) tcgen05.mma per chunk into one of two
+//              TMEM accumulators (64 columns each), commits the stage back to its
+//              producers and, after the last chunk of a product, commits the
+//              accumulator to the epilogue.
+//   warps 0-3  epilogue: thread = tile row = TMEM lane; folds each finished product
+//              into the compensated sum, releases the accumulator, stores the tile.
+// The block products are small (rows and columns of a few tens), so instead of TMA
+// (one tensor map per operand would be needed) the producers gather with coalesced
+// loads: along K for K-contiguous operands (one row of 32 per warp instruction, a
+// conflict-free 128-byte shared store) and along M/N for transposed ones (32 rows per
+// instruction, four K values per thread packed into one 16-byte store).
+//
+// Every wait is bounded by the global timer and also ends when another role has
+// failed: on expiry the kernel records an error code, stops issuing work, waits (with
+// a bound) for its own MMAs in flight, releases its tensor memory and returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "lrt_kernels.h"
 
@@ -28,33 +46,41 @@ namespace {
 
 constexpr int TC_M = 128;               // rows of an output tile (one TMEM lane per row)
 constexpr int TC_N = 64;                // columns of an output tile (TMEM columns)
-constexpr int TC_K = 32;                // K elements staged per chunk
-constexpr int TC_THREADS = 128;
-constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A
-constexpr int B_BYTES = TC_N * TC_K * 4;
-constexpr int SMEM_BYTES = 2 * A_BYTES + 2 * B_BYTES + 1024;
-constexpr uint32_t WAIT_LIMIT = 1u << 26;
+constexpr int TC_K = 32;                // K elements per stage (one 128-byte swizzle row)
+constexpr int STAGES = 4;
+constexpr int EPI_WARPS = 4, PROD_WARPS = 3;
+constexpr int TC_THREADS = 32 * (EPI_WARPS + PROD_WARPS + 1);
+constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A (16 KB)
+constexpr int B_BYTES = TC_N * TC_K * 4;    // 8 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 2 * TC_N;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+
+static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
+              "swizzle atoms must stay 1024-byte aligned");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// byte offset of element (row, k) of a K-major tile with TC_K columns:
-// core matrix (row / 8, k / 4) at ((row / 8) * (TC_K / 4) + k / 4) * 128, inside it
-// row (row % 8) at 16 bytes and element (k % 4) at 4 bytes.
-__device__ __forceinline__ uint32_t kmajor_offset(int row, int k) {
-  return (uint32_t)((((row >> 3) * (TC_K / 4) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+// byte offset of element (row, k) of a 128-byte-swizzled K-major tile with TC_K = 32
+// columns: row r occupies bytes [128 r, 128 r + 128); its 16-byte chunk c (elements
+// 4c..4c+3) sits at chunk position c XOR (r mod 8).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+  return (uint32_t)((row << 7) + ((((k >> 2) ^ row) & 7) << 4) + ((k & 3) << 2));
 }
 
-// shared-memory matrix descriptor, no swizzle, K-major:
-// LBO = 128 B (next core matrix along K), SBO = (TC_K / 4) * 128 B (next 8 rows)
+// shared-memory matrix descriptor, K-major, SWIZZLE_128B: 8-row groups 1024 bytes
+// apart (SBO), LBO unused for swizzled K-major layouts (set to 1)
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((((TC_K / 4) * 128u) >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;                 // descriptor version for this architecture
-  return d;                               // base offset 0, LBO mode 0, swizzle none (0)
+  d |= (uint64_t)2 << 61;                 // layout: 128-byte swizzle
+  return d;
 }
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TC_N
@@ -77,25 +103,49 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   lo = to_tf32(x - __uint_as_float(hi));
 }
 
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// bounded wait for the phase with the given parity; returns false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
+  (void)state;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait for the phase with the given parity; false on expiry or when another
+// role has already failed (then the caller stops)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* failed, int* err) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    if (mbar_try(a, parity)) return true;
+    if (*failed) return false;
+    if (now_ns() - t0 > WAIT_NS) {
+      *failed = 1;
+      if (err) atomicExch(err, 1);
+      return false;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -124,6 +174,57 @@ __device__ __forceinline__ void ld_16cols(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// One operand as the producers see it: tile row r (output row for A, output column
+// for B) against K.  A segment's transA matches `trans`; its transB is the opposite
+// (transB = 1 stores B as N x K, i.e. K-contiguous).
+struct Operand {
+  const float* hi;
+  const float* lo;
+  int64_t ld;
+  int trans;      // 0: element (r, k) at r * ld + k (K-contiguous); 1: at k * ld + r
+};
+
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero and reads nothing
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// Issue the copies of rows [0, nr) x K [k0, k0 + kc) of an operand into a swizzled
+// tile pair, zero-filling K in [kc, kpad).  Executed by the PROD_WARPS producer warps;
+// rows >= nr are left as they are (they only reach output rows/columns never stored).
+__device__ __forceinline__ void stage_operand(const Operand& op, int r0, int nr, int k0, int kc, int kpad,
+                                              uint32_t shi, uint32_t slo, int pw, int lane) {
+  if (!op.trans) {
+    // lane = k: one tile row per warp instruction, 128 contiguous bytes of the source
+    const int kk = lane;
+    if (kk >= kpad) return;
+    const uint32_t nb = kk < kc ? 4u : 0u;
+    const int ks = kk < kc ? kk : 0;
+    for (int r = pw; r < nr; r += PROD_WARPS) {
+      const int64_t idx = (int64_t)(r0 + r) * op.ld + (k0 + ks);
+      const uint32_t off = sw128_offset(r, kk);
+      cp_async4(shi + off, op.hi + idx, nb);
+      cp_async4(slo + off, op.lo + idx, nb);
+    }
+  } else {
+    // lane = (row mod 8, k mod 4): 8 rows x 4 K per warp instruction, four 32-byte
+    // source sectors and 32 distinct shared-memory banks
+    const int rr = lane & 7, q = lane >> 3;
+    const int ngroups = (nr + 7) >> 3;
+    const int nchunks = kpad >> 2;
+    for (int item = pw; item < ngroups * nchunks; item += PROD_WARPS) {
+      const int grp = item / nchunks, c = item - grp * nchunks;
+      const int r = grp * 8 + rr, kk = 4 * c + q;
+      if (r >= nr) continue;
+      const uint32_t nb = kk < kc ? 4u : 0u;
+      const int64_t idx = (int64_t)(k0 + (kk < kc ? kk : 0)) * op.ld + (r0 + r);
+      const uint32_t off = sw128_offset(r, kk);
+      cp_async4(shi + off, op.hi + idx, nb);
+      cp_async4(slo + off, op.lo + idx, nb);
+    }
+  }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOut* __restrict__ outs,
@@ -131,27 +232,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
                                                                      const int3* __restrict__ tiles, int ntiles,
                                                                      TcBases bases, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int failed;
-  const int w = blockIdx.x;
-  if (w >= ntiles) return;
+  __shared__ int failed_s;
+  volatile int* failed = &failed_s;
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sAh = sm;
-  uint8_t* sAl = sm + A_BYTES;
-  uint8_t* sBh = sm + 2 * A_BYTES;
-  uint8_t* sBl = sm + 2 * A_BYTES + B_BYTES;
   const int tid = threadIdx.x;
-  const int warp = tid >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TC_N));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
-    failed = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 32 * PROD_WARPS);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull_bar[a], 1);
+      mbar_init(&tempty_bar[a], 32 * EPI_WARPS);
+    }
+    mbar_init(&drain_bar, 1);
+    failed_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -159,129 +263,169 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  const int3 wi = tiles[w];
-  const GemmOut o = outs[wi.x];
-  const int m0 = wi.y * TC_M, n0 = wi.z * TC_N;
-  const int mt = min(TC_M, o.m - m0), nt = min(TC_N, o.n - n0);
-  constexpr uint32_t idesc = make_idesc();
-  uint32_t phase = 0;
-  const int row = warp * 32 + (tid & 31);
-  float sum[TC_N], cmp[TC_N];     // compensated running sum of the tile row
-#pragma unroll
-  for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
-
-  for (int s = 0; s < o.seg_count && !failed; ++s) {
-    const TcSeg g = segs[o.seg_begin + s];
-    const float* Ah = g.a_rel ? (g.a_rel == 1 ? bases.xhi : bases.thi) + g.a_off : g.Ahi;
-    const float* Al = g.a_rel ? (g.a_rel == 1 ? bases.xlo : bases.tlo) + g.a_off : g.Alo;
-    const float* Bh = g.b_rel ? (g.b_rel == 1 ? bases.xhi : bases.thi) + g.b_off : g.Bhi;
-    const float* Bl = g.b_rel ? (g.b_rel == 1 ? bases.xlo : bases.tlo) + g.b_off : g.Blo;
-    bool issued = false;
-    for (int k0 = 0; k0 < g.k && !failed; k0 += TC_K) {
-      const int kc = min(TC_K, g.k - k0);
-      // A tile: op(A)(m0 + i, k0 + kk), zero outside
-      for (int e = tid; e < TC_M * TC_K; e += TC_THREADS) {
-        int i, kk;
-        if (!g.transA) { i = e / TC_K; kk = e % TC_K; } else { kk = e / TC_M; i = e % TC_M; }
-        uint32_t hi = 0u, lo = 0u;
-        if (i < mt && kk < kc) {
-          const int64_t idx = g.transA ? (int64_t)(k0 + kk) * g.lda + (m0 + i) : (int64_t)(m0 + i) * g.lda + (k0 + kk);
-          hi = __float_as_uint(Ah[idx]);
-          lo = __float_as_uint(Al[idx]);
+  if (warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
+    // ---------------- producers
+    // Copies of chunk `it` are one cp.async group; the group LAG chunks older is
+    // waited for, fenced to the async proxy and announced on its full barrier, so
+    // LAG + 1 chunks of copies are in flight per thread.
+    constexpr int LAG = 2;
+    static_assert(LAG < STAGES, "the producer must not wait on a stage it has not announced");
+    const int pw = warp - EPI_WARPS;
+    uint32_t it = 0;
+    const uint32_t sbase = smem_u32(sm);
+    for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
+      const int3 wi = tiles[w];
+      const GemmOut o = outs[wi.x];
+      const int m0 = wi.y * TC_M, n0 = wi.z * TC_N;
+      const int mt = min(TC_M, o.m - m0), nt = min(TC_N, o.n - n0);
+      for (int s = 0; s < o.seg_count && !*failed; ++s) {
+        const TcSeg g = segs[o.seg_begin + s];
+        if (g.k <= 0) continue;
+        Operand A{g.a_rel ? (g.a_rel == 1 ? bases.xhi : bases.thi) + g.a_off : g.Ahi,
+                  g.a_rel ? (g.a_rel == 1 ? bases.xlo : bases.tlo) + g.a_off : g.Alo, g.lda, g.transA};
+        Operand B{g.b_rel ? (g.b_rel == 1 ? bases.xhi : bases.thi) + g.b_off : g.Bhi,
+                  g.b_rel ? (g.b_rel == 1 ? bases.xlo : bases.tlo) + g.b_off : g.Blo, g.ldb, !g.transB};
+        for (int k0 = 0; k0 < g.k; k0 += TC_K, ++it) {
+          const int kc = min(TC_K, g.k - k0), kpad = (kc + 7) & ~7;
+          const uint32_t stage = it % STAGES, round = it / STAGES;
+          if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err)) break;
+          const uint32_t st = sbase + stage * STAGE_BYTES;
+          stage_operand(A, m0, mt, k0, kc, kpad, st, st + A_BYTES, pw, lane);
+          stage_operand(B, n0, nt, k0, kc, kpad, st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, pw, lane);
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (it >= (uint32_t)LAG) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
+            // generic-proxy writes -> visible to the tensor core's async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full_bar[(it - LAG) % STAGES]);
+          }
         }
-        const uint32_t off = kmajor_offset(i, kk);
-        *(uint32_t*)(sAh + off) = hi;
-        *(uint32_t*)(sAl + off) = lo;
       }
-      // B tile stored N x K (K-major): element (j, kk) = op(B)(k0 + kk, n0 + j)
-      for (int e = tid; e < TC_N * TC_K; e += TC_THREADS) {
-        int j, kk;
-        if (!g.transB) { kk = e / TC_N; j = e % TC_N; } else { j = e / TC_K; kk = e % TC_K; }
-        uint32_t hi = 0u, lo = 0u;
-        if (j < nt && kk < kc) {
-          const int64_t idx = g.transB ? (int64_t)(n0 + j) * g.ldb + (k0 + kk) : (int64_t)(k0 + kk) * g.ldb + (n0 + j);
-          hi = __float_as_uint(Bh[idx]);
-          lo = __float_as_uint(Bl[idx]);
-        }
-        const uint32_t off = kmajor_offset(j, kk);
-        *(uint32_t*)(sBh + off) = hi;
-        *(uint32_t*)(sBl + off) = lo;
-      }
-      // make the generic-proxy stores visible to the tensor core (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (tid == 0) {
-        const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
-#pragma unroll
-        for (int ks = 0; ks < TC_K / 8; ++ks) {
-          const uint32_t step = (uint32_t)ks * 256u;   // two 16-byte core-matrix columns
-          const uint32_t acc0 = (issued || ks > 0) ? 1u : 0u;
-          mma_tf32(tmem, make_desc(ah + step), make_desc(bh + step), idesc, acc0);
-          mma_tf32(tmem, make_desc(ah + step), make_desc(bl + step), idesc, 1u);
-          mma_tf32(tmem, make_desc(al + step), make_desc(bh + step), idesc, 1u);
-        }
-        mma_commit(&bar);
-      }
-      issued = true;
-      if (!mbar_wait(&bar, phase)) {
-        failed = 1;
-        if (err) atomicExch(err, 1);
-      }
-      phase ^= 1u;
-      __syncthreads();
     }
-    if (issued && !failed) {
-      // fold this product into the compensated running sum (two-sum in FP32)
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int c0 = 0; c0 < TC_N; c0 += 16) {
-        float v[16];
-        ld_16cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float y = g.scale * v[i] - cmp[c0 + i];
-          const float t = sum[c0 + i] + y;
-          cmp[c0 + i] = (t - sum[c0 + i]) - y;
-          sum[c0 + i] = t;
+    // announce the chunks still in flight
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!*failed)
+      for (uint32_t j = (it > (uint32_t)LAG ? it - LAG : 0u); j < it; ++j) mbar_arrive(&full_bar[j % STAGES]);
+  } else if (warp == EPI_WARPS + PROD_WARPS) {
+    // ---------------- MMA issuer (one thread)
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc();
+      uint32_t it = 0, sg = 0;
+      bool any = false;
+      for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
+        const GemmOut o = outs[tiles[w].x];
+        for (int s = 0; s < o.seg_count && !*failed; ++s) {
+          const int k = segs[o.seg_begin + s].k;
+          if (k <= 0) continue;
+          const uint32_t a = sg & 1, u = sg >> 1;
+          if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dt = tmem + a * TC_N;
+          bool first = true;
+          for (int k0 = 0; k0 < k; k0 += TC_K, ++it) {
+            const int nks = (min(TC_K, k - k0) + 7) >> 3;
+            const uint32_t stage = it % STAGES, round = it / STAGES;
+            if (!mbar_wait(&full_bar[stage], round & 1, failed, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(sm + stage * STAGE_BYTES);
+            const uint32_t ah = base, al = base + A_BYTES, bh = base + 2 * A_BYTES, bl = bh + B_BYTES;
+            for (int ks = 0; ks < nks; ++ks) {
+              const uint32_t step = (uint32_t)ks * 32u;     // 8 TF32 = 32 bytes along K
+              mma_tf32(dt, make_desc(ah + step), make_desc(bh + step), idesc, first ? 0u : 1u);
+              mma_tf32(dt, make_desc(ah + step), make_desc(bl + step), idesc, 1u);
+              mma_tf32(dt, make_desc(al + step), make_desc(bh + step), idesc, 1u);
+              first = false;
+            }
+            mma_commit(&empty_bar[stage]);
+            any = true;
+          }
+          if (*failed) break;
+          mma_commit(&tfull_bar[a]);
+          ++sg;
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
+      if (*failed && any) {
+        // let the MMAs already issued finish before the tensor memory is released
+        mma_commit(&drain_bar);
+        const uint32_t da = smem_u32(&drain_bar);
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(da, 0) && now_ns() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: thread = tile row = TMEM lane
+    const int row = tid;
+    uint32_t sg = 0;
+    for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
+      const int3 wi = tiles[w];
+      const GemmOut o = outs[wi.x];
+      const int m0 = wi.y * TC_M, n0 = wi.z * TC_N;
+      const int mt = min(TC_M, o.m - m0), nt = min(TC_N, o.n - n0);
+      float sum[TC_N], cmp[TC_N];
+#pragma unroll
+      for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
+      for (int s = 0; s < o.seg_count; ++s) {
+        const TcSeg g = segs[o.seg_begin + s];
+        if (g.k <= 0) continue;
+        const uint32_t a = sg & 1, u = sg >> 1;
+        // the warp stays converged for the .sync.aligned tensor-memory loads
+        const bool ok = mbar_wait(&tfull_bar[a], u & 1, failed, err);
+        if (!__all_sync(0xffffffffu, ok)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + a * TC_N;
+#pragma unroll
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+          float v[16];
+          ld_16cols(taddr + (uint32_t)c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float y = g.scale * v[i] - cmp[c0 + i];
+            const float t = sum[c0 + i] + y;
+            cmp[c0 + i] = (t - sum[c0 + i]) - y;
+            sum[c0 + i] = t;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&tempty_bar[a]);
+        ++sg;
+      }
+      if (*failed) break;
+      if (row < mt) {
+        if (o.c_rel == 2) {
+          // intermediate: keep it as a TF32 pair for the next phase
+#pragma unroll
+          for (int c = 0; c < TC_N; ++c) {
+            if (c < nt) {
+              const float v = sum[c] - cmp[c];
+              uint32_t hi, lo;
+              split_tf32(v, hi, lo);
+              const int64_t idx = o.c_off + (int64_t)(m0 + row) * o.ldc + (n0 + c);
+              bases.thi[idx] = __uint_as_float(hi);
+              bases.tlo[idx] = __uint_as_float(lo);
+            }
+          }
+        } else {
+          double* C = (o.c_rel == 1 ? bases.y + o.c_off : o.C);
+#pragma unroll
+          for (int c = 0; c < TC_N; ++c) {
+            if (c < nt) {
+              const double v = (double)sum[c] - (double)cmp[c];
+              double* p = C + (int64_t)(m0 + row) * o.ldc + (n0 + c);
+              *p = o.accumulate ? (*p + v) : v;
+            }
+          }
+        }
+      }
     }
   }
 
-  if (!failed && row < mt) {
-    if (o.c_rel == 2) {
-      // intermediate: keep it as a TF32 pair for the next phase
-#pragma unroll
-      for (int c = 0; c < TC_N; ++c) {
-        if (c < nt) {
-          const float v = sum[c] - cmp[c];
-          uint32_t hi, lo;
-          split_tf32(v, hi, lo);
-          const int64_t idx = o.c_off + (int64_t)(m0 + row) * o.ldc + (n0 + c);
-          bases.thi[idx] = __uint_as_float(hi);
-          bases.tlo[idx] = __uint_as_float(lo);
-        }
-      }
-    } else {
-      double* C = (o.c_rel == 1 ? bases.y + o.c_off : o.C);
-#pragma unroll
-      for (int c = 0; c < TC_N; ++c) {
-        if (c < nt) {
-          const double v = (double)sum[c] - (double)cmp[c];
-          double* p = C + (int64_t)(m0 + row) * o.ldc + (n0 + c);
-          *p = o.accumulate ? (*p + v) : v;
-        }
-      }
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
 }
 
@@ -307,12 +451,16 @@ int tc_tile_n() { return TC_N; }
 void launch_gemm_tf32x3(const GemmOut* outs, const TcSeg* segs, const int3* tiles, int ntiles, TcBases b,
                         int* err, cudaStream_t st) {
   if (ntiles <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static int nsm = 0;
+  if (!nsm) {
     cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
   }
-  gemm_tf32x3_kernel<<<ntiles, TC_THREADS, SMEM_BYTES, st>>>(outs, segs, tiles, ntiles, b, err);
+  const int grid = std::min(ntiles, nsm);
+  gemm_tf32x3_kernel<<<grid, TC_THREADS, SMEM_BYTES, st>>>(outs, segs, tiles, ntiles, b, err);
 }
 
 }  // namespace lrt
