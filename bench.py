@@ -30,6 +30,16 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (152 SMs x 2 FMA/clk x 2 flop x ~2.06 GHz)
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 GEMM rate x the nominal TF32/BF16 ratio."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)["bf16_tflops"] * TF32_PER_BF16, "of measured (bf16 burst x 1.1/2.25)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * TF32_PER_BF16, "of fallback (1.9 PF bf16 x 1.1/2.25)"
 WORKLOAD = "ppp_polyene_k12_M256_twosite_6roots_fp64"
 
 
@@ -40,6 +50,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                   help="sigma arithmetic: FP64, or split-TF32 tensor-core products (LRT_MIXED)")
     return p.parse_args()
 
 
@@ -121,6 +133,7 @@ def run_ours(args):
     device = local
     torch.cuda.set_device(device)
     ctx, H, left, right, positions, sizes, nvec = build_workload(pkg, device)
+    prec = pkg.LRT_MIXED if args.precision == "mixed" else pkg.LRT_FP64
     stream = torch.cuda.current_stream(device)
     xs = {i: torch.tensor(synth.random_vector(nvec * sizes[i], 100 + i), dtype=torch.float64,
                           device=f"cuda:{device}") for i in positions}
@@ -132,7 +145,7 @@ def run_ours(args):
     flops_step, launches_step = 0.0, 0
     for i in positions:
         ctx.heff_diag(i, 2, ds[i])
-        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec)
+        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
         st = ctx.stats()
         flops_step += st["flops"]
         launches_step += st["launches"] + 1
@@ -143,7 +156,7 @@ def run_ours(args):
             ctx.heff_diag(i, 2, ds[i])
             if ev is not None:
                 ev[n][0].record(stream)
-            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec)
+            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
             if ev is not None:
                 ev[n][1].record(stream)
 
@@ -190,7 +203,7 @@ def run_ours(args):
         for i in positions:
             xs[i].copy_(hx[i], non_blocking=True)
             ctx.heff_diag(i, 2, ds[i])
-            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec)
+            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
             hy[i].copy_(ys[i], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -202,8 +215,22 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ctx, H, left, right, nvec, sizes)
     if rank == 0:
+        if args.precision == "mixed":
+            peak, peak_note = tf32_peak()
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "gemm_tf32x3_kernel (sigma phases 1+2)",
+                    "peak_note": peak_note + "; achieved counts each split-TF32 product once "
+                                 "(the tensor pipe issues it 3x)"}
+            metric, dtype = "H_eff sigma TFLOP/s (algorithmic, split-TF32 mixed)", "tf32x3"
+        else:
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "gemm_fp64_kernel (sigma phases 1+2)",
+                    "peak_note": "nominal FP64 of GB300; FMA probe measured 1.20 TFLOP/s"}
+            metric, dtype = "H_eff sigma TFLOP/s (algorithmic, FP64)", "f64"
         out = {
-            "metric": "H_eff sigma TFLOP/s (algorithmic, FP64)",
+            "metric": metric,
             "value": value,
             "unit": "TFLOP/s",
             "n_gpus": world,
@@ -213,15 +240,13 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": dtype,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "k": 12, "electrons": 12, "M": 256, "nsite": 2,
+            "config": {"workload": WORKLOAD if args.precision == "fp64" else WORKLOAD.replace("fp64", "mixed"),
+                       "k": 12, "electrons": 12, "M": 256, "nsite": 2,
                        "nvec": nvec, "positions": len(positions), "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "gemm_fp64_kernel (sigma phases 1+2)",
-                         "peak_note": "nominal FP64 of GB300; FMA probe measured 1.20 TFLOP/s"},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

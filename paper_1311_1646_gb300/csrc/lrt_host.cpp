@@ -624,8 +624,7 @@ struct GemmPlan {
   DevArray<GemmOut> outs;
   DevArray<GemmSeg> segs;
   DevArray<int3> tiles;      // FP64 kernel tiles
-  DevArray<int3> tc_tiles;   // tensor-core kernel tiles
-  int ntiles = 0, tc_ntiles = 0;
+  int ntiles = 0;
   double flops = 0.0;
   void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr) const {
     launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st);
@@ -673,21 +672,6 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
   P.tiles.upload(tiles, st);
   P.ntiles = (int)tiles.size();
   P.flops = fl;
-  std::vector<int3> tct;
-  const int TM = tc_tile_m(), TN = tc_tile_n();
-  for (size_t i = 0; i < outs.size(); ++i) {
-    const int tm = (outs[i].m + TM - 1) / TM;
-    const int tn = (outs[i].n + TN - 1) / TN;
-    for (int a = 0; a < tm; ++a)
-      for (int b = 0; b < tn; ++b) tct.push_back(make_int3((int)i, a, b));
-  }
-  // the persistent tensor-core kernel deals tiles round-robin: longest first
-  std::vector<int64_t> ktot(outs.size(), 0);
-  for (size_t i = 0; i < outs.size(); ++i)
-    for (int s = 0; s < outs[i].seg_count; ++s) ktot[i] += segs[outs[i].seg_begin + s].k;
-  std::stable_sort(tct.begin(), tct.end(), [&](const int3& a, const int3& b) { return ktot[a.x] > ktot[b.x]; });
-  P.tc_tiles.upload(tct, st);
-  P.tc_ntiles = (int)tct.size();
 }
 
 }  // namespace lrt
@@ -768,12 +752,16 @@ struct SigmaPlan {
   int n_terms = 0, n_products = 0;
   double op_bytes = 0.0;
   double flops_alg = 0.0;   // products of non-zero sub-blocks only
-  // host copies of the segments and the operator set each absolute operand points into
-  std::vector<GemmSeg> S1, S2;
-  std::vector<const struct OpSet*> S1set, S2set;
+  // block-level twin of the two phases for the tensor-core path (host only), with the
+  // operator set each absolute operand points into
+  std::vector<GemmOut> B1, B2;
+  std::vector<GemmSeg> BS1, BS2;
+  std::vector<const struct OpSet*> BS1set, BS2set;
   // mixed path (split TF32): segments with TF32 operand pointers and hi/lo workspaces
   bool tc_ready = false;
-  DevArray<TcSeg> tc1, tc2;
+  DevArray<TcItem> tci1, tci2;    // per-CTA work streams of the two phases
+  DevArray<int> tcb1, tcb2;
+  int tcn1 = 0, tcn2 = 0;
   float *xhi = nullptr, *xlo = nullptr, *thi = nullptr, *tlo = nullptr;
   ~SigmaPlan() {
     if (tbuf) cudaFree(tbuf);
@@ -1223,6 +1211,31 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   std::vector<GemmOut> o1;
   std::vector<GemmSeg> s1;
   std::vector<const OpSet*> s1set;
+  // Block-level twin of the plan for the tensor-core path: whole fused blocks instead
+  // of 4 x 4 sub-blocks (structurally zero sub-blocks are stored zeros), so that the
+  // products fill the 128-row tensor-core tiles.  Phase 1: one product per T block;
+  // phase 2: one output per (y block, column sub-block), A = all rows of T.
+  struct BlkOut { int blk, mcol; };
+  std::vector<BlkOut> bsub;
+  std::map<std::pair<int, int>, int> bout_of;
+  for (size_t w = 0; w < wb.size(); ++w) {
+    if (nsite == 1) {
+      bout_of[{(int)w, 0}] = (int)bsub.size();
+      bsub.push_back({(int)w, 0});
+    } else {
+      const int fy = YF->s.find(wb[w].label_a, wb[w].label_b);
+      for (int m = 0; m < 4; ++m) {
+        if (YF->dim[fy][m] == 0) continue;
+        bout_of[{(int)w, m}] = (int)bsub.size();
+        bsub.push_back({(int)w, m});
+      }
+    }
+  }
+  std::vector<std::vector<GemmSeg>> bseg2(bsub.size());
+  std::vector<std::vector<const OpSet*>> bseg2set(bsub.size());
+  std::vector<GemmOut> bo1;
+  std::vector<GemmSeg> bs1;
+  std::vector<const OpSet*> bs1set;
   struct TEntry { int64_t tp; uint16_t rows; };
   std::map<std::tuple<int, int, int>, TEntry> tcache;   // (X op, trans, X ket fused) -> T
   int64_t toff = 0;
@@ -1327,6 +1340,21 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                 }
                 o1.push_back(out);
               }
+              if (rows) {
+                GemmOut bo{nullptr, tp, wk.cols, wbb.rows, wk.cols, (int)bs1.size(), 1, 0, 0};
+                GemmSeg g{};
+                g.A = base;
+                g.transA = a.t ? 1 : 0;
+                g.lda = ld;
+                g.b_rel = 1;
+                g.b_off = wk.off;
+                g.ldb = wk.cols;
+                g.k = wk.rows;
+                g.scale = 1.0;
+                bs1.push_back(g);
+                bs1set.push_back(&XS);
+                bo1.push_back(bo);
+              }
               tcache[key] = TEntry{tp, rows};
             } else {
               tp = it->second.tp;
@@ -1371,6 +1399,39 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                 }
             }
           }
+          if (rows) {
+            const int64_t abase = ident ? wk.off : tp;
+            if (nsite == 1) {
+              GemmSeg g{};
+              g.a_rel = ident ? 1 : 0;
+              g.a_off = abase;
+              g.lda = wk.cols;
+              g.B = Bp;
+              g.ldb = ldb;
+              g.transB = transB;
+              g.k = wk.cols;
+              g.scale = sc;
+              bseg2[bout_of.at({ib->second, 0})].push_back(g);
+              bseg2set[bout_of.at({ib->second, 0})].push_back(&YS);
+            } else {
+              for (int mp = 0; mp < 4; ++mp)
+                for (int m = 0; m < 4; ++m) {
+                  if (!(ymask & (1u << (4 * mp + m)))) continue;
+                  GemmSeg g{};
+                  g.a_rel = ident ? 1 : 0;
+                  g.a_off = abase + YF->off[yk][m];
+                  g.lda = wk.cols;
+                  if (!bref.t) g.B = Bp + (int64_t)YF->off[ybb][mp] * ldb + YF->off[yk][m];
+                  else g.B = Bp + (int64_t)YF->off[yk][m] * ldb + YF->off[ybb][mp];
+                  g.ldb = ldb;
+                  g.transB = transB;
+                  g.k = YF->dim[yk][m];
+                  g.scale = sc;
+                  bseg2[bout_of.at({ib->second, mp})].push_back(g);
+                  bseg2set[bout_of.at({ib->second, mp})].push_back(&YS);
+                }
+            }
+          }
           // ---- diagonal contribution
           if (be == ke && yk == ybb) {
             DiagTerm d{};
@@ -1400,7 +1461,6 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
         GemmSeg g = s1[x.seg_begin + q];
         g.b_off += (int64_t)v * nelem;
         S1.push_back(g);
-        plan->S1set.push_back(s1set[x.seg_begin + q]);
       }
       O1.push_back(y);
     }
@@ -1426,15 +1486,52 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
           g.a_off += (int64_t)v * toff;
         }
         S2.push_back(g);
-        plan->S2set.push_back(seg2set[u][q]);
       }
       O2.push_back(y);
     }
   }
   build_gemm(plan->p1, O1, S1, c->st);
   build_gemm(plan->p2, O2, S2, c->st);
-  plan->S1 = std::move(S1);
-  plan->S2 = std::move(S2);
+  // block-level twin, expanded over the vectors the same way
+  for (int v = 0; v < nvec; ++v) {
+    for (const GemmOut& x : bo1) {
+      GemmOut y = x;
+      y.c_off = x.c_off + (int64_t)v * toff;
+      y.c_rel = 2;
+      y.seg_begin = (int)plan->BS1.size();
+      for (int q = 0; q < x.seg_count; ++q) {
+        GemmSeg g = bs1[x.seg_begin + q];
+        g.b_off += (int64_t)v * nelem;
+        plan->BS1.push_back(g);
+        plan->BS1set.push_back(bs1set[x.seg_begin + q]);
+      }
+      plan->B1.push_back(y);
+    }
+    for (size_t u = 0; u < bsub.size(); ++u) {
+      const WfnBlock& w = wb[bsub[u].blk];
+      int64_t coff = w.off;
+      int ncols = w.cols;
+      if (nsite == 2) {
+        const int fy = YF->s.find(w.label_a, w.label_b);
+        coff += YF->off[fy][bsub[u].mcol];
+        ncols = YF->dim[fy][bsub[u].mcol];
+      }
+      GemmOut y{nullptr, coff + (int64_t)v * nelem, w.cols, w.rows, ncols, (int)plan->BS2.size(),
+                (int)bseg2[u].size(), 0, 1};
+      for (size_t q = 0; q < bseg2[u].size(); ++q) {
+        GemmSeg g = bseg2[u][q];
+        if (g.a_rel) {
+          g.a_off += (int64_t)v * nelem;
+        } else {
+          g.a_rel = 2;
+          g.a_off += (int64_t)v * toff;
+        }
+        plan->BS2.push_back(g);
+        plan->BS2set.push_back(bseg2set[u][q]);
+      }
+      plan->B2.push_back(y);
+    }
+  }
   std::vector<DiagOut> dout;
   std::vector<DiagTerm> dts;
   for (size_t w = 0; w < wb.size(); ++w) {
@@ -1463,47 +1560,90 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
 }
 
-// TF32 segments and workspaces of a plan for the mixed path (once per plan)
+// Work stream of one tensor-core launch: tiles of 128 x 64 in longest-first order,
+// CTA b takes the tiles b, b + n, b + 2n, ...; each tile is a header followed by its
+// block products with operands resolved to the TF32 copies (operator shadows, x, T).
+static void build_tc_stream(const std::vector<GemmOut>& outs, const std::vector<GemmSeg>& S,
+                            const std::vector<const OpSet*>& Sset, const float* xhi, const float* xlo,
+                            const float* thi, const float* tlo, DevArray<TcItem>& items, DevArray<int>& begins,
+                            int& nctas, cudaStream_t st) {
+  const int TM = tc_tile_m(), TN = tc_tile_n();
+  std::vector<int3> tiles;
+  std::vector<int64_t> ktot(outs.size(), 0);
+  for (size_t i = 0; i < outs.size(); ++i) {
+    for (int s = 0; s < outs[i].seg_count; ++s) ktot[i] += S[outs[i].seg_begin + s].k;
+    for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
+      for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b) tiles.push_back(make_int3((int)i, a, b));
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) { return ktot[a.x] > ktot[b.x]; });
+  const int nt = (int)tiles.size();
+  nctas = nt > 0 ? tc_num_ctas(nt) : 0;
+  std::vector<TcItem> it;
+  std::vector<int> beg;
+  auto resolve = [&](int rel, int64_t off, const double* abs, const OpSet* set, const float*& hi,
+                     const float*& lo) {
+    if (rel == 1) {
+      hi = xhi + off;
+      lo = xlo + off;
+    } else if (rel == 2) {
+      hi = thi + off;
+      lo = tlo + off;
+    } else {
+      if (!set || !set->hi || abs < set->d || abs >= set->d + set->total)
+        throw Error(LRT_EINVAL, "tensor-core stream: operand outside its operator set");
+      hi = set->hi + (abs - set->d);
+      lo = set->lo + (abs - set->d);
+    }
+  };
+  for (int b = 0; b < nctas; ++b) {
+    beg.push_back((int)it.size());
+    for (int w = b; w < nt; w += nctas) {
+      const int3 t = tiles[w];
+      const GemmOut& o = outs[t.x];
+      TcItem h{};
+      h.type = TC_ITEM_TILE;
+      h.t.C = o.C;
+      h.t.c_off = o.c_off;
+      h.t.ldc = o.ldc;
+      h.t.m0 = t.y * TM;
+      h.t.n0 = t.z * TN;
+      h.t.mt = std::min(TM, o.m - h.t.m0);
+      h.t.nt = std::min(TN, o.n - h.t.n0);
+      h.t.c_rel = o.c_rel;
+      h.t.accumulate = o.accumulate;
+      it.push_back(h);
+      for (int q = 0; q < o.seg_count; ++q) {
+        const GemmSeg& g = S[o.seg_begin + q];
+        if (g.k <= 0) continue;
+        TcItem r{};
+        r.type = TC_ITEM_SEG;
+        resolve(g.a_rel, g.a_off, g.A, Sset[o.seg_begin + q], r.s.a_hi, r.s.a_lo);
+        resolve(g.b_rel, g.b_off, g.B, Sset[o.seg_begin + q], r.s.b_hi, r.s.b_lo);
+        r.s.lda = g.lda;
+        r.s.ldb = g.ldb;
+        r.s.k = g.k;
+        r.s.trans = (g.transA ? TC_TRANS_A : 0) | (g.transB ? 0 : TC_TRANS_B);
+        r.s.scale = (float)g.scale;
+        it.push_back(r);
+      }
+    }
+  }
+  beg.push_back((int)it.size());
+  items.upload(it, st);
+  begins.upload(beg, st);
+}
+
+// TF32 copies, work streams and workspaces of a plan for the mixed path (once per plan)
 static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   if (p.tc_ready) return;
-  auto tc_of = [&](const GemmSeg& g, const OpSet* set, bool a_abs) {
-    TcSeg t{};
-    t.a_off = g.a_off;
-    t.b_off = g.b_off;
-    t.lda = g.lda;
-    t.ldb = g.ldb;
-    t.k = g.k;
-    t.transA = g.transA;
-    t.transB = g.transB;
-    t.a_rel = g.a_rel;
-    t.b_rel = g.b_rel;
-    t.scale = (float)g.scale;
-    if (a_abs) {
-      const int64_t off = g.A - set->d;
-      t.Ahi = set->hi + off;
-      t.Alo = set->lo + off;
-    } else {
-      const int64_t off = g.B - set->d;
-      t.Bhi = set->hi + off;
-      t.Blo = set->lo + off;
-    }
-    return t;
-  };
-  std::vector<TcSeg> t1, t2;
-  for (size_t i = 0; i < p.S1.size(); ++i) {
-    const_cast<OpSet*>(p.S1set[i])->ensure_shadow(c->st);
-    t1.push_back(tc_of(p.S1[i], p.S1set[i], true));
-  }
-  for (size_t i = 0; i < p.S2.size(); ++i) {
-    const_cast<OpSet*>(p.S2set[i])->ensure_shadow(c->st);
-    t2.push_back(tc_of(p.S2[i], p.S2set[i], false));
-  }
-  p.tc1.upload(t1, c->st);
-  p.tc2.upload(t2, c->st);
+  for (const OpSet* s : p.BS1set) const_cast<OpSet*>(s)->ensure_shadow(c->st);
+  for (const OpSet* s : p.BS2set) const_cast<OpSet*>(s)->ensure_shadow(c->st);
   const size_t nx = (size_t)std::max<int64_t>(p.nelem * nvec, 1), nt = (size_t)std::max<int64_t>(p.tsize, 1);
   if (cudaMalloc(&p.xhi, nx * sizeof(float)) != cudaSuccess || cudaMalloc(&p.xlo, nx * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&p.thi, nt * sizeof(float)) != cudaSuccess || cudaMalloc(&p.tlo, nt * sizeof(float)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "mixed-precision workspace");
+  build_tc_stream(p.B1, p.BS1, p.BS1set, p.xhi, p.xlo, p.thi, p.tlo, p.tci1, p.tcb1, p.tcn1, c->st);
+  build_tc_stream(p.B2, p.BS2, p.BS2set, p.xhi, p.xlo, p.thi, p.tlo, p.tci2, p.tcb2, p.tcn2, c->st);
   CK(cudaStreamSynchronize(c->st));
   p.tc_ready = true;
 }
@@ -2695,9 +2835,9 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
       }
       prepare_tc(ctx, p, nvec);
       launch_split_tf32(x_dev, p.nelem * nvec, p.xhi, p.xlo, ctx->st);
-      const TcBases tb{p.xhi, p.xlo, p.thi, p.tlo, y_dev};
-      launch_gemm_tf32x3(p.p1.outs.p, p.tc1.p, p.p1.tc_tiles.p, p.p1.tc_ntiles, tb, ctx->derr, ctx->st);
-      launch_gemm_tf32x3(p.p2.outs.p, p.tc2.p, p.p2.tc_tiles.p, p.p2.tc_ntiles, tb, ctx->derr, ctx->st);
+      const TcOut to{p.thi, p.tlo, y_dev};
+      launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, to, ctx->derr, ctx->st);
+      launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, to, ctx->derr, ctx->st);
       CK(cudaGetLastError());
       int flag = 0;
       CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));

@@ -64,30 +64,47 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
 // Split-TF32 tensor-core variant of the grouped GEMM.  Operands are pre-split TF32
-// pairs (hi, lo) in FP32 storage: absolute pointers for operator data, or offsets from
-// the hi/lo copies of x (rel 1) or of the intermediates (rel 2).  Outputs with
-// c_rel == 2 are written as hi/lo pairs into the intermediates, others as FP64.
-struct TcSeg {
-  const float* Ahi;
-  const float* Alo;
-  const float* Bhi;
-  const float* Blo;
-  int64_t a_off, b_off;
-  int lda, ldb;
-  int k;
-  int transA, transB;
-  int a_rel, b_rel;
-  float scale;
+// pairs (hi, lo) in FP32 storage.  The host lays out, for every CTA of the
+// persistent launch, the work it will do as one linear stream of items: a tile
+// header, then the tile's block products (segments) with operand pointers resolved.
+// Outputs with c_rel == 2 are written as hi/lo pairs into the intermediates (thi,
+// tlo at c_off), c_rel == 1 as FP64 into y at c_off, c_rel == 0 as FP64 into C.
+struct TcTileHdr {
+  double* C;
+  int64_t c_off;
+  int ldc, m0, n0, mt, nt, c_rel, accumulate, pad;
 };
-struct TcBases {
-  const float* xhi;
-  const float* xlo;
+constexpr int TC_TRANS_A = 1;   // A element (i, k) at k * lda + i (else i * lda + k)
+constexpr int TC_TRANS_B = 2;   // B element (k, j) at k * ldb + j (else j * ldb + k)
+struct TcSegRec {
+  const float* a_hi;
+  const float* a_lo;
+  const float* b_hi;
+  const float* b_lo;
+  int lda, ldb, k, trans;
+  float scale;
+  int pad;
+};
+constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2;
+struct TcItem {
+  int type;
+  int pad;
+  union {
+    TcTileHdr t;
+    TcSegRec s;
+  };
+};
+struct TcOut {
   float* thi;
   float* tlo;
   double* y;
 };
-void launch_gemm_tf32x3(const GemmOut* outs, const TcSeg* segs, const int3* tiles, int ntiles, TcBases b,
-                        int* err, cudaStream_t st);
+// number of CTAs (one per SM) the tensor-core launch uses for ntiles tiles; CTA b
+// takes tiles b, b + n, b + 2n, ... of the host's order
+int tc_num_ctas(int ntiles);
+// items[cta_begin[b] .. cta_begin[b + 1]) is the stream of CTA b, b < nctas
+void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err,
+                        cudaStream_t st);
 // hi = rna_tf32((float)x), lo = rna_tf32((float)x - hi) elementwise
 void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaStream_t st);
 int tc_tile_m();

@@ -11,24 +11,29 @@
 // block product.  No FP64 arithmetic runs in the loop: on this GPU the FP64 pipe is
 // the scarcest resource.
 //
-// Persistent, warp-specialised kernel (one CTA per SM, tiles dealt round-robin in
-// the host's longest-first order; 8 warps, so two per SM sub-partition and up to 255
-// registers a thread for the epilogue's 128 running-sum registers):
+// Persistent, warp-specialised kernel (one CTA per SM; 8 warps, so two per SM
+// sub-partition and up to 255 registers a thread for the epilogue's 128 running-sum
+// registers).  The host hands every CTA a linear stream of items (tile header, then
+// the tile's block products), so only the producers touch global metadata, a few
+// items ahead; the other roles get theirs through shared memory:
 //   warps 4-6  producers: copy K chunks of 32 of the four operand tiles from global
-//              memory into a 4-stage ring in shared memory, 128-byte-swizzled K-major
+//              memory into a 3-stage ring in shared memory, 128-byte-swizzled K-major
 //              (the layout tcgen05 reads with SWIZZLE_128B descriptors), zero-filling
-//              the K tail; arrive on full[stage].
+//              the K tail, with cp.async so that three chunks are in flight; each
+//              chunk carries a small record (K steps, first/last of its product), and
+//              each product and tile end a record for the epilogue in a ring.
 //   warp 7     one thread issues 3 x (K / 8) tcgen05.mma per chunk into one of two
 //              TMEM accumulators (64 columns each), commits the stage back to its
 //              producers and, after the last chunk of a product, commits the
 //              accumulator to the epilogue.
 //   warps 0-3  epilogue: thread = tile row = TMEM lane; folds each finished product
-//              into the compensated sum, releases the accumulator, stores the tile.
+//              into the compensated sum, releases the accumulator, and at a tile end
+//              stages the tile in shared memory so that a warp stores whole rows
+//              (coalesced) instead of one row per thread.
 // The block products are small (rows and columns of a few tens), so instead of TMA
-// (one tensor map per operand would be needed) the producers gather with coalesced
-// loads: along K for K-contiguous operands (one row of 32 per warp instruction, a
-// conflict-free 128-byte shared store) and along M/N for transposed ones (32 rows per
-// instruction, four K values per thread packed into one 16-byte store).
+// (one tensor map per operand would be needed) the producers gather: along K for
+// K-contiguous operands (one 128-byte source row per warp instruction) and 8 rows x 4
+// K for transposed ones (four 32-byte source sectors), both bank-conflict free.
 //
 // Every wait is bounded by the global timer and also ends when another role has
 // failed: on expiry the kernel records an error code, stops issuing work, waits (with
@@ -47,14 +52,18 @@ namespace {
 constexpr int TC_M = 128;               // rows of an output tile (one TMEM lane per row)
 constexpr int TC_N = 64;                // columns of an output tile (TMEM columns)
 constexpr int TC_K = 32;                // K elements per stage (one 128-byte swizzle row)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
+constexpr int NINFO = 16;               // epilogue record ring
 constexpr int EPI_WARPS = 4, PROD_WARPS = 3;
 constexpr int TC_THREADS = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A (16 KB)
 constexpr int B_BYTES = TC_N * TC_K * 4;    // 8 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr uint32_t TMEM_COLS = 2 * TC_N;
+constexpr int STG_LD = TC_N + 1;        // 8-byte words per staged output row (padded)
+constexpr int STG_WARP_BYTES = 32 * STG_LD * 8;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * STG_WARP_BYTES + 1024;
+constexpr int NACC = 4;                 // TMEM accumulators (product ring to the epilogue)
+constexpr uint32_t TMEM_COLS = NACC * TC_N;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 
 static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
@@ -114,9 +123,7 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  uint64_t state;
-  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
-  (void)state;
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
@@ -137,13 +144,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   const uint32_t a = smem_u32(bar);
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = now_ns();
-  for (;;) {
+  for (uint32_t n = 1;; ++n) {
     if (mbar_try(a, parity)) return true;
-    if (*failed) return false;
-    if (now_ns() - t0 > WAIT_NS) {
-      *failed = 1;
-      if (err) atomicExch(err, 1);
-      return false;
+    if ((n & 255u) == 0u) {
+      if (*failed) return false;
+      if (now_ns() - t0 > WAIT_NS) {
+        *failed = 1;
+        if (err) atomicExch(err, 1);
+        return false;
+      }
     }
   }
 }
@@ -162,16 +171,13 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void ld_16cols(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive TMEM columns of this warp's 32 lanes; completes at tcgen05.wait::ld
+__device__ __forceinline__ void ld_16cols_async(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // One operand as the producers see it: tile row r (output row for A, output column
@@ -225,14 +231,41 @@ __device__ __forceinline__ void stage_operand(const Operand& op, int r0, int nr,
   }
 }
 
+// per-stage record from the producers to the MMA thread
+constexpr int META_FIRST = 1, META_LAST = 2, META_END = 4;
+struct StageMeta {
+  int nks;     // K steps of 8
+  int flags;
+};
+// ring record from the producers to the epilogue
+constexpr int INFO_MMA = 1, INFO_TILE_END = 2, INFO_END = 4;
+struct EpiInfo {
+  int flags;
+  float scale;
+  TcTileHdr t;
+};
+
+__device__ __forceinline__ TcItem load_item(const TcItem* p) {
+  TcItem r;
+  const int4* q = reinterpret_cast<const int4*>(p);
+  int4* d = reinterpret_cast<int4*>(&r);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(TcItem) / 16); ++i) d[i] = __ldg(q + i);
+  return r;
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOut* __restrict__ outs,
-                                                                     const TcSeg* __restrict__ segs,
-                                                                     const int3* __restrict__ tiles, int ntiles,
-                                                                     TcBases bases, int* __restrict__ err) {
+static_assert(sizeof(TcItem) % 16 == 0, "items are read as 16-byte vectors");
+
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem* __restrict__ items,
+                                                                     const int* __restrict__ cta_begin,
+                                                                     TcOut out, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[NACC], tempty_bar[NACC], drain_bar;
+  __shared__ uint64_t info_full[NINFO], info_empty[NINFO];
+  __shared__ StageMeta meta[STAGES];
+  __shared__ EpiInfo info[NINFO];
   __shared__ uint32_t tmem_base;
   __shared__ int failed_s;
   volatile int* failed = &failed_s;
@@ -247,12 +280,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
   }
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 32 * PROD_WARPS);
+      mbar_init(&full_bar[s], 32 * PROD_WARPS + 1);   // copies of every producer thread + the record
       mbar_init(&empty_bar[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mbar_init(&tfull_bar[a], 1);
       mbar_init(&tempty_bar[a], 32 * EPI_WARPS);
+    }
+    for (int q = 0; q < NINFO; ++q) {
+      mbar_init(&info_full[q], 1);
+      mbar_init(&info_empty[q], 32 * EPI_WARPS);
     }
     mbar_init(&drain_bar, 1);
     failed_s = 0;
@@ -265,82 +302,113 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
 
   if (warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
     // ---------------- producers
-    // Copies of chunk `it` are one cp.async group; the group LAG chunks older is
-    // waited for, fenced to the async proxy and announced on its full barrier, so
-    // LAG + 1 chunks of copies are in flight per thread.
-    constexpr int LAG = 2;
-    static_assert(LAG < STAGES, "the producer must not wait on a stage it has not announced");
+    // Each thread's copies of a chunk arrive on the stage's full barrier when they
+    // land (cp.async.mbarrier.arrive.noinc); the leader adds one ordinary arrive that
+    // publishes the stage record.  The MMA thread fences to the async proxy after
+    // its wait, before the tensor core reads the stage.
     const int pw = warp - EPI_WARPS;
-    uint32_t it = 0;
+    const bool leader = (pw == 0 && lane == 0);
     const uint32_t sbase = smem_u32(sm);
-    for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
-      const int3 wi = tiles[w];
-      const GemmOut o = outs[wi.x];
-      const int m0 = wi.y * TC_M, n0 = wi.z * TC_N;
-      const int mt = min(TC_M, o.m - m0), nt = min(TC_N, o.n - n0);
-      for (int s = 0; s < o.seg_count && !*failed; ++s) {
-        const TcSeg g = segs[o.seg_begin + s];
-        if (g.k <= 0) continue;
-        Operand A{g.a_rel ? (g.a_rel == 1 ? bases.xhi : bases.thi) + g.a_off : g.Ahi,
-                  g.a_rel ? (g.a_rel == 1 ? bases.xlo : bases.tlo) + g.a_off : g.Alo, g.lda, g.transA};
-        Operand B{g.b_rel ? (g.b_rel == 1 ? bases.xhi : bases.thi) + g.b_off : g.Bhi,
-                  g.b_rel ? (g.b_rel == 1 ? bases.xlo : bases.tlo) + g.b_off : g.Blo, g.ldb, !g.transB};
-        for (int k0 = 0; k0 < g.k; k0 += TC_K, ++it) {
+    uint32_t it = 0, ei = 0;
+    // the epilogue record ring: only the leader writes it
+    auto post = [&](const EpiInfo& rec) -> bool {
+      const uint32_t slot = ei % NINFO, use = ei / NINFO;
+      if (use > 0 && !mbar_wait(&info_empty[slot], (use - 1) & 1, failed, err)) return false;
+      info[slot] = rec;
+      mbar_arrive(&info_full[slot]);
+      ++ei;
+      return true;
+    };
+    auto next_stage = [&](bool& ok) -> uint32_t {
+      const uint32_t stage = it % STAGES, round = it / STAGES;
+      ok = !(round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err));
+      return stage;
+    };
+    auto close_stage = [&](uint32_t stage) {
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_bar[stage]))
+                   : "memory");
+      if (leader) mbar_arrive(&full_bar[stage]);
+      ++it;
+    };
+
+    const int p0 = cta_begin[blockIdx.x], p1 = cta_begin[blockIdx.x + 1];
+    bool have_tile = false, ok = true;
+    TcTileHdr hdr{};
+    TcItem cur, nx1, nx2;
+    if (p0 < p1) cur = load_item(items + p0);
+    if (p0 + 1 < p1) nx1 = load_item(items + p0 + 1);
+    for (int p = p0; p < p1 && ok && !*failed; ++p) {
+      if (p + 2 < p1) nx2 = load_item(items + p + 2);
+      if (cur.type == TC_ITEM_TILE) {
+        if (have_tile && leader) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
+        hdr = cur.t;
+        have_tile = true;
+      } else if (cur.s.k > 0) {
+        const TcSegRec& g = cur.s;
+        if (leader) ok = post(EpiInfo{INFO_MMA, g.scale, hdr});
+        Operand A{g.a_hi, g.a_lo, g.lda, (g.trans & TC_TRANS_A) ? 1 : 0};
+        Operand B{g.b_hi, g.b_lo, g.ldb, (g.trans & TC_TRANS_B) ? 1 : 0};
+        for (int k0 = 0; k0 < g.k && ok; k0 += TC_K) {
           const int kc = min(TC_K, g.k - k0), kpad = (kc + 7) & ~7;
-          const uint32_t stage = it % STAGES, round = it / STAGES;
-          if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err)) break;
+          const uint32_t stage = next_stage(ok);
+          if (!ok) break;
           const uint32_t st = sbase + stage * STAGE_BYTES;
-          stage_operand(A, m0, mt, k0, kc, kpad, st, st + A_BYTES, pw, lane);
-          stage_operand(B, n0, nt, k0, kc, kpad, st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, pw, lane);
-          asm volatile("cp.async.commit_group;" ::: "memory");
-          if (it >= (uint32_t)LAG) {
-            asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
-            // generic-proxy writes -> visible to the tensor core's async proxy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&full_bar[(it - LAG) % STAGES]);
-          }
+          stage_operand(A, hdr.m0, hdr.mt, k0, kc, kpad, st, st + A_BYTES, pw, lane);
+          stage_operand(B, hdr.n0, hdr.nt, k0, kc, kpad, st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, pw, lane);
+          if (leader)
+            meta[stage] = StageMeta{kpad >> 3, (k0 == 0 ? META_FIRST : 0) | (k0 + TC_K >= g.k ? META_LAST : 0)};
+          close_stage(stage);
         }
       }
+      cur = nx1;
+      nx1 = nx2;
     }
-    // announce the chunks still in flight
+    if (ok && !*failed) {
+      if (have_tile && leader) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
+      if (leader) ok = ok && post(EpiInfo{INFO_END, 0.0f, hdr});
+      // end-of-stream record for the MMA thread, in a stage of its own
+      bool sok = true;
+      const uint32_t stage = next_stage(sok);
+      if (sok) {
+        if (leader) meta[stage] = StageMeta{0, META_END};
+        close_stage(stage);
+      }
+    }
+    // no copy may still be in flight when the CTA exits
     asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (!*failed)
-      for (uint32_t j = (it > (uint32_t)LAG ? it - LAG : 0u); j < it; ++j) mbar_arrive(&full_bar[j % STAGES]);
   } else if (warp == EPI_WARPS + PROD_WARPS) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
       constexpr uint32_t idesc = make_idesc();
-      uint32_t it = 0, sg = 0;
+      uint32_t sg = 0;
       bool any = false;
-      for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
-        const GemmOut o = outs[tiles[w].x];
-        for (int s = 0; s < o.seg_count && !*failed; ++s) {
-          const int k = segs[o.seg_begin + s].k;
-          if (k <= 0) continue;
-          const uint32_t a = sg & 1, u = sg >> 1;
+      for (uint32_t it = 0; !*failed; ++it) {
+        const uint32_t stage = it % STAGES, round = it / STAGES;
+        if (!mbar_wait(&full_bar[stage], round & 1, failed, err)) break;
+        const StageMeta m = meta[stage];
+        if (m.flags & META_END) break;
+        const uint32_t a = sg % NACC;
+        if (m.flags & META_FIRST) {
+          const uint32_t u = sg / NACC;
           if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err)) break;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dt = tmem + a * TC_N;
-          bool first = true;
-          for (int k0 = 0; k0 < k; k0 += TC_K, ++it) {
-            const int nks = (min(TC_K, k - k0) + 7) >> 3;
-            const uint32_t stage = it % STAGES, round = it / STAGES;
-            if (!mbar_wait(&full_bar[stage], round & 1, failed, err)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(sm + stage * STAGE_BYTES);
-            const uint32_t ah = base, al = base + A_BYTES, bh = base + 2 * A_BYTES, bl = bh + B_BYTES;
-            for (int ks = 0; ks < nks; ++ks) {
-              const uint32_t step = (uint32_t)ks * 32u;     // 8 TF32 = 32 bytes along K
-              mma_tf32(dt, make_desc(ah + step), make_desc(bh + step), idesc, first ? 0u : 1u);
-              mma_tf32(dt, make_desc(ah + step), make_desc(bl + step), idesc, 1u);
-              mma_tf32(dt, make_desc(al + step), make_desc(bh + step), idesc, 1u);
-              first = false;
-            }
-            mma_commit(&empty_bar[stage]);
-            any = true;
-          }
-          if (*failed) break;
+        }
+        // the stage was written through the generic proxy (cp.async); the tensor core
+        // reads it through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dt = tmem + a * TC_N;
+        const uint32_t base = smem_u32(sm + stage * STAGE_BYTES);
+        const uint32_t ah = base, al = base + A_BYTES, bh = base + 2 * A_BYTES, bl = bh + B_BYTES;
+        for (int ks = 0; ks < m.nks; ++ks) {
+          const uint32_t step = (uint32_t)ks * 32u;     // 8 TF32 = 32 bytes along K
+          const uint32_t acc = ((m.flags & META_FIRST) && ks == 0) ? 0u : 1u;
+          mma_tf32(dt, make_desc(ah + step), make_desc(bh + step), idesc, acc);
+          mma_tf32(dt, make_desc(ah + step), make_desc(bl + step), idesc, 1u);
+          mma_tf32(dt, make_desc(al + step), make_desc(bh + step), idesc, 1u);
+        }
+        mma_commit(&empty_bar[stage]);
+        any = true;
+        if (m.flags & META_LAST) {
           mma_commit(&tfull_bar[a]);
           ++sg;
         }
@@ -356,32 +424,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
     }
   } else {
     // ---------------- epilogue: thread = tile row = TMEM lane
-    const int row = tid;
+    uint8_t* stg = sm + STAGES * STAGE_BYTES + warp * STG_WARP_BYTES;   // this warp's 32 rows
     uint32_t sg = 0;
-    for (int w = blockIdx.x; w < ntiles && !*failed; w += gridDim.x) {
-      const int3 wi = tiles[w];
-      const GemmOut o = outs[wi.x];
-      const int m0 = wi.y * TC_M, n0 = wi.z * TC_N;
-      const int mt = min(TC_M, o.m - m0), nt = min(TC_N, o.n - n0);
-      float sum[TC_N], cmp[TC_N];
+    float sum[TC_N], cmp[TC_N];
 #pragma unroll
-      for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
-      for (int s = 0; s < o.seg_count; ++s) {
-        const TcSeg g = segs[o.seg_begin + s];
-        if (g.k <= 0) continue;
-        const uint32_t a = sg & 1, u = sg >> 1;
-        // the warp stays converged for the .sync.aligned tensor-memory loads
+    for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
+    for (uint32_t ei = 0;; ++ei) {
+      const uint32_t slot = ei % NINFO;
+      // the warp stays converged for the .sync.aligned tensor-memory loads
+      const bool got = mbar_wait(&info_full[slot], (ei / NINFO) & 1, failed, err);
+      if (!__all_sync(0xffffffffu, got)) break;
+      const EpiInfo rec = info[slot];
+      mbar_arrive(&info_empty[slot]);
+      if (rec.flags & INFO_END) break;
+      if (rec.flags & INFO_MMA) {
+        const uint32_t a = sg % NACC, u = sg / NACC;
         const bool ok = mbar_wait(&tfull_bar[a], u & 1, failed, err);
         if (!__all_sync(0xffffffffu, ok)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + a * TC_N;
 #pragma unroll
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
-          float v[16];
-          ld_16cols(taddr + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < TC_N; c0 += 32) {
+          uint32_t v[32];
+          ld_16cols_async(taddr + (uint32_t)c0, v);
+          ld_16cols_async(taddr + (uint32_t)c0 + 16u, v + 16);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float y = g.scale * v[i] - cmp[c0 + i];
+          for (int i = 0; i < 32; ++i) {
+            const float y = rec.scale * __uint_as_float(v[i]) - cmp[c0 + i];
             const float t = sum[c0 + i] + y;
             cmp[c0 + i] = (t - sum[c0 + i]) - y;
             sum[c0 + i] = t;
@@ -391,32 +461,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const GemmOu
         mbar_arrive(&tempty_bar[a]);
         ++sg;
       }
-      if (*failed) break;
-      if (row < mt) {
-        if (o.c_rel == 2) {
-          // intermediate: keep it as a TF32 pair for the next phase
+      if (rec.flags & INFO_TILE_END) {
+        const TcTileHdr& t = rec.t;
+        // stage: thread `lane` writes its row, then the warp stores row by row
+        const int rr = lane;
+        if (t.c_rel == 2) {
 #pragma unroll
           for (int c = 0; c < TC_N; ++c) {
-            if (c < nt) {
-              const float v = sum[c] - cmp[c];
-              uint32_t hi, lo;
-              split_tf32(v, hi, lo);
-              const int64_t idx = o.c_off + (int64_t)(m0 + row) * o.ldc + (n0 + c);
-              bases.thi[idx] = __uint_as_float(hi);
-              bases.tlo[idx] = __uint_as_float(lo);
+            uint32_t hi, lo;
+            split_tf32(sum[c] - cmp[c], hi, lo);
+            *(uint2*)(stg + (rr * STG_LD + c) * 8) = make_uint2(hi, lo);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < TC_N; ++c)
+            *(double*)(stg + (rr * STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
+        }
+        __syncwarp();
+        const int rbase = warp * 32;
+        const int nrows = min(32, t.mt - rbase);
+        if (t.c_rel == 2) {
+          for (int r = 0; r < nrows; ++r) {
+            const int64_t o = t.c_off + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
+            for (int c = lane; c < t.nt; c += 32) {
+              const uint2 v = *(const uint2*)(stg + (r * STG_LD + c) * 8);
+              out.thi[o + c] = __uint_as_float(v.x);
+              out.tlo[o + c] = __uint_as_float(v.y);
             }
           }
         } else {
-          double* C = (o.c_rel == 1 ? bases.y + o.c_off : o.C);
-#pragma unroll
-          for (int c = 0; c < TC_N; ++c) {
-            if (c < nt) {
-              const double v = (double)sum[c] - (double)cmp[c];
-              double* p = C + (int64_t)(m0 + row) * o.ldc + (n0 + c);
-              *p = o.accumulate ? (*p + v) : v;
+          double* C = (t.c_rel == 1 ? out.y + t.c_off : t.C);
+          for (int r = 0; r < nrows; ++r) {
+            double* dst = C + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
+            for (int c = lane; c < t.nt; c += 32) {
+              const double v = *(const double*)(stg + (r * STG_LD + c) * 8);
+              dst[c] = t.accumulate ? dst[c] + v : v;
             }
           }
         }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
       }
     }
   }
@@ -448,19 +533,28 @@ void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaS
 int tc_tile_m() { return TC_M; }
 int tc_tile_n() { return TC_N; }
 
-void launch_gemm_tf32x3(const GemmOut* outs, const TcSeg* segs, const int3* tiles, int ntiles, TcBases b,
-                        int* err, cudaStream_t st) {
-  if (ntiles <= 0) return;
+static int sm_count() {
   static int nsm = 0;
   if (!nsm) {
-    cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
   }
-  const int grid = std::min(ntiles, nsm);
-  gemm_tf32x3_kernel<<<grid, TC_THREADS, SMEM_BYTES, st>>>(outs, segs, tiles, ntiles, b, err);
+  return nsm;
+}
+
+int tc_num_ctas(int ntiles) { return std::max(1, std::min(ntiles, sm_count())); }
+
+void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err,
+                        cudaStream_t st) {
+  if (nctas <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = true;
+  }
+  gemm_tf32x3_kernel<<<nctas, TC_THREADS, SMEM_BYTES, st>>>(items, cta_begin, out, err);
 }
 
 }  // namespace lrt
