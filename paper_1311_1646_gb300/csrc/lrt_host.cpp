@@ -212,15 +212,7 @@ struct OpSet {
   std::vector<uint16_t> mask;     // enlarged sets: nonzero sub-blocks (bit 4*n_bra + n_ket) per block
   std::vector<char> bnz;          // per block: not identically zero (structural zeros are skipped)
   std::vector<char> onz;          // per operator: some block not identically zero
-  float* hi = nullptr;            // TF32 split of the data (mixed path), created on first use
-  float* lo = nullptr;
-  void ensure_shadow(cudaStream_t st) {
-    if (hi || total <= 0) return;
-    if (cudaMalloc(&hi, (size_t)total * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&lo, (size_t)total * sizeof(float)) != cudaSuccess)
-      throw Error(LRT_ENOMEM, "TF32 copy of an operator set");
-    launch_split_tf32(d, total, hi, lo, st);
-  }
+
   bool block_nz(int op, int ket) const { return bnz[(size_t)op * ns() + ket] != 0; }
   void finish_nz() {
     onz.assign(keys.size(), 0);
@@ -232,8 +224,6 @@ struct OpSet {
   OpSet(const OpSet&) = delete;
   ~OpSet() {
     if (d) cudaFree(d);
-    if (hi) cudaFree(hi);
-    if (lo) cudaFree(lo);
   }
   int ns() const { return basis.n(); }
   int find(const Key& k) const {
@@ -741,6 +731,64 @@ static void site_layout(SiteTensor& S, const Sectors& L, const Sectors& R) {
 
 struct TdaState;
 
+// Tensor-core twin of a sigma plan.  A TC matrix is R x K (R = output rows or
+// columns of the product, K = contracted index), packed as ceil(K / 32) chunks of
+// Rp = roundup(R, 8) rows of 32 TF32 pairs (see TcPack).
+struct TcMat {
+  int pool;
+  int64_t off;     // float offset inside its pool (inside one vector's part for pools 1, 2)
+  int R, Rp, K;
+};
+struct TcPlanSeg {
+  int a, b;        // TC matrices
+  int k;
+  float scale;
+};
+struct TcPlanOut {
+  int tmat;        // output TC matrix (intermediate), or -1 for an FP64 output in y
+  int64_t c_off;   // y output: offset and row stride
+  int ldc;
+  int m, n;
+  int seg_begin, seg_count;
+};
+struct TcPlan {
+  std::vector<TcMat> mats;
+  int64_t pool_size[3] = {0, 0, 0};     // floats (per vector for pools 1, 2)
+  std::vector<TcPack> pack0;            // operator sub-matrices (absolute sources)
+  std::vector<TcPack> pack1;            // x-derived (sources relative to x)
+  std::map<std::tuple<const double*, int64_t, int, int, int>, int> op_of;
+  std::map<std::tuple<int64_t, int64_t, int, int, int>, int> x_of;
+  std::vector<TcPlanOut> out1, out2;
+  std::vector<TcPlanSeg> segs;
+  static int64_t words(int Rp, int K) { return (int64_t)((K + 31) / 32) * Rp * 32; }
+  int add(int pool, int R, int K) {
+    TcMat m{pool, pool_size[pool], R, (R + 7) & ~7, K};
+    pool_size[pool] += words(m.Rp, K);
+    mats.push_back(m);
+    return (int)mats.size() - 1;
+  }
+  // operator sub-matrix: element (r, k) = src[r * ld + k] (or src[k * ld + r] when trans)
+  int op(const double* src, int64_t ld, int trans, int R, int K) {
+    auto key = std::make_tuple(src, ld, trans, R, K);
+    auto it = op_of.find(key);
+    if (it != op_of.end()) return it->second;
+    const int id = add(0, R, K);
+    pack0.push_back(TcPack{src, 0, ld, mats[id].off, R, K, mats[id].Rp, trans});
+    op_of[key] = id;
+    return id;
+  }
+  // sub-matrix of x, source offset relative to the vector's start
+  int x(int64_t src_off, int64_t ld, int trans, int R, int K) {
+    auto key = std::make_tuple(src_off, ld, trans, R, K);
+    auto it = x_of.find(key);
+    if (it != x_of.end()) return it->second;
+    const int id = add(1, R, K);
+    pack1.push_back(TcPack{nullptr, src_off, ld, mats[id].off, R, K, mats[id].Rp, trans});
+    x_of[key] = id;
+    return id;
+  }
+};
+
 struct SigmaPlan {
   GemmPlan p1, p2;
   DevArray<DiagOut> douts;
@@ -752,21 +800,24 @@ struct SigmaPlan {
   int n_terms = 0, n_products = 0;
   double op_bytes = 0.0;
   double flops_alg = 0.0;   // products of non-zero sub-blocks only
-  // block-level twin of the two phases for the tensor-core path (host only), with the
-  // operator set each absolute operand points into
-  std::vector<GemmOut> B1, B2;
-  std::vector<GemmSeg> BS1, BS2;
-  std::vector<const struct OpSet*> BS1set, BS2set;
+  // tensor-core twin of the two phases (host description; device streams built on
+  // first mixed use): whole fused blocks, operands as TC matrices in three pools
+  // (0: operator sub-matrices, 1: x-derived, per vector, 2: intermediates T, per vector)
+  TcPlan tc;
   // mixed path (split TF32): segments with TF32 operand pointers and hi/lo workspaces
   bool tc_ready = false;
   DevArray<TcItem> tci1, tci2;    // per-CTA work streams of the two phases
   DevArray<int> tcb1, tcb2;
   int tcn1 = 0, tcn2 = 0;
-  float *xhi = nullptr, *xlo = nullptr, *thi = nullptr, *tlo = nullptr;
+  DevArray<TcPack> xpack;         // packing of x into pool 1 (every call)
+  float* pool_hi[3] = {nullptr, nullptr, nullptr};
+  float* pool_lo[3] = {nullptr, nullptr, nullptr};
   ~SigmaPlan() {
     if (tbuf) cudaFree(tbuf);
-    for (float* q : {xhi, xlo, thi, tlo})
-      if (q) cudaFree(q);
+    for (int q = 0; q < 3; ++q) {
+      if (pool_hi[q]) cudaFree(pool_hi[q]);
+      if (pool_lo[q]) cudaFree(pool_lo[q]);
+    }
   }
 };
 
@@ -1211,31 +1262,13 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   std::vector<GemmOut> o1;
   std::vector<GemmSeg> s1;
   std::vector<const OpSet*> s1set;
-  // Block-level twin of the plan for the tensor-core path: whole fused blocks instead
-  // of 4 x 4 sub-blocks (structurally zero sub-blocks are stored zeros), so that the
-  // products fill the 128-row tensor-core tiles.  Phase 1: one product per T block;
-  // phase 2: one output per (y block, column sub-block), A = all rows of T.
-  struct BlkOut { int blk, mcol; };
-  std::vector<BlkOut> bsub;
-  std::map<std::pair<int, int>, int> bout_of;
-  for (size_t w = 0; w < wb.size(); ++w) {
-    if (nsite == 1) {
-      bout_of[{(int)w, 0}] = (int)bsub.size();
-      bsub.push_back({(int)w, 0});
-    } else {
-      const int fy = YF->s.find(wb[w].label_a, wb[w].label_b);
-      for (int m = 0; m < 4; ++m) {
-        if (YF->dim[fy][m] == 0) continue;
-        bout_of[{(int)w, m}] = (int)bsub.size();
-        bsub.push_back({(int)w, m});
-      }
-    }
-  }
-  std::vector<std::vector<GemmSeg>> bseg2(bsub.size());
-  std::vector<std::vector<const OpSet*>> bseg2set(bsub.size());
-  std::vector<GemmOut> bo1;
-  std::vector<GemmSeg> bs1;
-  std::vector<const OpSet*> bs1set;
+  // Tensor-core twin: whole fused blocks instead of 4 x 4 sub-blocks (structurally
+  // zero sub-blocks are stored zeros), so that the products fill the 128-row tiles.
+  // Phase 1: per T block and right column group m, T_m = op(O_X) x_m; phase 2: per
+  // (y block, column group), sum of T_m (or x_m) times the Y sub-matrix.
+  TcPlan& tcp = plan->tc;
+  std::map<std::tuple<int, int, int>, std::array<int, 4>> tc_T;   // T key -> TC matrix per m
+  std::map<std::pair<int, int>, std::vector<TcPlanSeg>> tc_y;     // (y block, column group) -> products
   struct TEntry { int64_t tp; uint16_t rows; };
   std::map<std::tuple<int, int, int>, TEntry> tcache;   // (X op, trans, X ket fused) -> T
   int64_t toff = 0;
@@ -1341,19 +1374,18 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                 o1.push_back(out);
               }
               if (rows) {
-                GemmOut bo{nullptr, tp, wk.cols, wbb.rows, wk.cols, (int)bs1.size(), 1, 0, 0};
-                GemmSeg g{};
-                g.A = base;
-                g.transA = a.t ? 1 : 0;
-                g.lda = ld;
-                g.b_rel = 1;
-                g.b_off = wk.off;
-                g.ldb = wk.cols;
-                g.k = wk.rows;
-                g.scale = 1.0;
-                bs1.push_back(g);
-                bs1set.push_back(&XS);
-                bo1.push_back(bo);
+                const int A = tcp.op(base, ld, a.t ? 1 : 0, wbb.rows, wk.rows);
+                std::array<int, 4> tm{-1, -1, -1, -1};
+                for (int m = 0; m < (nsite == 1 ? 1 : 4); ++m) {
+                  const int dim = nsite == 1 ? wk.cols : YF->dim[yk][m];
+                  const int64_t coff = nsite == 1 ? 0 : YF->off[yk][m];
+                  if (dim == 0) continue;
+                  const int B = tcp.x(wk.off + coff, wk.cols, 1, dim, wk.rows);
+                  tm[m] = tcp.add(2, wbb.rows, dim);
+                  tcp.out1.push_back(TcPlanOut{tm[m], 0, 0, wbb.rows, dim, (int)tcp.segs.size(), 1});
+                  tcp.segs.push_back(TcPlanSeg{A, B, wk.rows, 1.0f});
+                }
+                tc_T[key] = tm;
               }
               tcache[key] = TEntry{tp, rows};
             } else {
@@ -1400,35 +1432,21 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
             }
           }
           if (rows) {
-            const int64_t abase = ident ? wk.off : tp;
+            const std::array<int, 4>* tm = ident ? nullptr : &tc_T.at(std::make_tuple(a.op, a.t, f));
             if (nsite == 1) {
-              GemmSeg g{};
-              g.a_rel = ident ? 1 : 0;
-              g.a_off = abase;
-              g.lda = wk.cols;
-              g.B = Bp;
-              g.ldb = ldb;
-              g.transB = transB;
-              g.k = wk.cols;
-              g.scale = sc;
-              bseg2[bout_of.at({ib->second, 0})].push_back(g);
-              bseg2set[bout_of.at({ib->second, 0})].push_back(&YS);
+              const int A = ident ? tcp.x(wk.off, wk.cols, 0, wk.rows, wk.cols) : (*tm)[0];
+              const int B = tcp.op(Bp, ldb, bref.t ? 1 : 0, Y.basis.d[ybb], Y.basis.d[yk]);
+              tc_y[{ib->second, 0}].push_back(TcPlanSeg{A, B, wk.cols, (float)sc});
             } else {
               for (int mp = 0; mp < 4; ++mp)
                 for (int m = 0; m < 4; ++m) {
                   if (!(ymask & (1u << (4 * mp + m)))) continue;
-                  GemmSeg g{};
-                  g.a_rel = ident ? 1 : 0;
-                  g.a_off = abase + YF->off[yk][m];
-                  g.lda = wk.cols;
-                  if (!bref.t) g.B = Bp + (int64_t)YF->off[ybb][mp] * ldb + YF->off[yk][m];
-                  else g.B = Bp + (int64_t)YF->off[yk][m] * ldb + YF->off[ybb][mp];
-                  g.ldb = ldb;
-                  g.transB = transB;
-                  g.k = YF->dim[yk][m];
-                  g.scale = sc;
-                  bseg2[bout_of.at({ib->second, mp})].push_back(g);
-                  bseg2set[bout_of.at({ib->second, mp})].push_back(&YS);
+                  const int A = ident ? tcp.x(wk.off + YF->off[yk][m], wk.cols, 0, wk.rows, YF->dim[yk][m]) : (*tm)[m];
+                  if (A < 0) throw Error(LRT_EINVAL, "tensor-core plan: missing intermediate");
+                  const double* src = !bref.t ? Bp + (int64_t)YF->off[ybb][mp] * ldb + YF->off[yk][m]
+                                              : Bp + (int64_t)YF->off[yk][m] * ldb + YF->off[ybb][mp];
+                  const int B = tcp.op(src, ldb, bref.t ? 1 : 0, YF->dim[ybb][mp], YF->dim[yk][m]);
+                  tc_y[{ib->second, mp}].push_back(TcPlanSeg{A, B, YF->dim[yk][m], (float)sc});
                 }
             }
           }
@@ -1492,46 +1510,23 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   }
   build_gemm(plan->p1, O1, S1, c->st);
   build_gemm(plan->p2, O2, S2, c->st);
-  // block-level twin, expanded over the vectors the same way
-  for (int v = 0; v < nvec; ++v) {
-    for (const GemmOut& x : bo1) {
-      GemmOut y = x;
-      y.c_off = x.c_off + (int64_t)v * toff;
-      y.c_rel = 2;
-      y.seg_begin = (int)plan->BS1.size();
-      for (int q = 0; q < x.seg_count; ++q) {
-        GemmSeg g = bs1[x.seg_begin + q];
-        g.b_off += (int64_t)v * nelem;
-        plan->BS1.push_back(g);
-        plan->BS1set.push_back(bs1set[x.seg_begin + q]);
-      }
-      plan->B1.push_back(y);
-    }
-    for (size_t u = 0; u < bsub.size(); ++u) {
-      const WfnBlock& w = wb[bsub[u].blk];
-      int64_t coff = w.off;
-      int ncols = w.cols;
+  // tensor-core twin: phase-2 outputs, one per (y block, column group)
+  for (size_t w = 0; w < wb.size(); ++w)
+    for (int m = 0; m < (nsite == 1 ? 1 : 4); ++m) {
+      const WfnBlock& wbk = wb[w];
+      int64_t coff = wbk.off;
+      int ncols = wbk.cols;
       if (nsite == 2) {
-        const int fy = YF->s.find(w.label_a, w.label_b);
-        coff += YF->off[fy][bsub[u].mcol];
-        ncols = YF->dim[fy][bsub[u].mcol];
+        const int fy = YF->s.find(wbk.label_a, wbk.label_b);
+        if (YF->dim[fy][m] == 0) continue;
+        coff += YF->off[fy][m];
+        ncols = YF->dim[fy][m];
       }
-      GemmOut y{nullptr, coff + (int64_t)v * nelem, w.cols, w.rows, ncols, (int)plan->BS2.size(),
-                (int)bseg2[u].size(), 0, 1};
-      for (size_t q = 0; q < bseg2[u].size(); ++q) {
-        GemmSeg g = bseg2[u][q];
-        if (g.a_rel) {
-          g.a_off += (int64_t)v * nelem;
-        } else {
-          g.a_rel = 2;
-          g.a_off += (int64_t)v * toff;
-        }
-        plan->BS2.push_back(g);
-        plan->BS2set.push_back(bseg2set[u][q]);
-      }
-      plan->B2.push_back(y);
+      auto it = tc_y.find({(int)w, m});
+      const int sb = (int)tcp.segs.size();
+      if (it != tc_y.end()) tcp.segs.insert(tcp.segs.end(), it->second.begin(), it->second.end());
+      tcp.out2.push_back(TcPlanOut{-1, coff, wbk.cols, wbk.rows, ncols, sb, (int)tcp.segs.size() - sb});
     }
-  }
   std::vector<DiagOut> dout;
   std::vector<DiagTerm> dts;
   for (size_t w = 0; w < wb.size(); ++w) {
@@ -1560,70 +1555,73 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
 }
 
-// Work stream of one tensor-core launch: tiles of 128 x 64 in longest-first order,
-// CTA b takes the tiles b, b + n, b + 2n, ...; each tile is a header followed by its
-// block products with operands resolved to the TF32 copies (operator shadows, x, T).
-static void build_tc_stream(const std::vector<GemmOut>& outs, const std::vector<GemmSeg>& S,
-                            const std::vector<const OpSet*>& Sset, const float* xhi, const float* xlo,
-                            const float* thi, const float* tlo, DevArray<TcItem>& items, DevArray<int>& begins,
+// Work stream of one tensor-core launch: tiles of 128 x 64 of every output and
+// vector in longest-first order, CTA b takes the tiles b, b + n, b + 2n, ...; each
+// tile is a header followed by its block products with TC-matrix operands resolved.
+static void build_tc_stream(const TcPlan& tp, const std::vector<TcPlanOut>& outs, int nvec, int64_t nelem,
+                            float* const* phi, float* const* plo, DevArray<TcItem>& items, DevArray<int>& begins,
                             int& nctas, cudaStream_t st) {
   const int TM = tc_tile_m(), TN = tc_tile_n();
-  std::vector<int3> tiles;
-  std::vector<int64_t> ktot(outs.size(), 0);
-  for (size_t i = 0; i < outs.size(); ++i) {
-    for (int s = 0; s < outs[i].seg_count; ++s) ktot[i] += S[outs[i].seg_begin + s].k;
-    for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
-      for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b) tiles.push_back(make_int3((int)i, a, b));
-  }
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) { return ktot[a.x] > ktot[b.x]; });
+  struct Tile { int v, o, a, b; int64_t k; };
+  std::vector<Tile> tiles;
+  for (int v = 0; v < nvec; ++v)
+    for (size_t i = 0; i < outs.size(); ++i) {
+      int64_t kt = 0;
+      for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
+      for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
+        for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b) tiles.push_back(Tile{v, (int)i, a, b, kt});
+    }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& x, const Tile& y) { return x.k > y.k; });
   const int nt = (int)tiles.size();
   nctas = nt > 0 ? tc_num_ctas(nt) : 0;
+  auto base = [&](const TcMat& m, int v, bool hi) -> float* {
+    float* p = (hi ? phi : plo)[m.pool];
+    return p + (m.pool ? (int64_t)v * tp.pool_size[m.pool] : 0) + m.off;
+  };
   std::vector<TcItem> it;
   std::vector<int> beg;
-  auto resolve = [&](int rel, int64_t off, const double* abs, const OpSet* set, const float*& hi,
-                     const float*& lo) {
-    if (rel == 1) {
-      hi = xhi + off;
-      lo = xlo + off;
-    } else if (rel == 2) {
-      hi = thi + off;
-      lo = tlo + off;
-    } else {
-      if (!set || !set->hi || abs < set->d || abs >= set->d + set->total)
-        throw Error(LRT_EINVAL, "tensor-core stream: operand outside its operator set");
-      hi = set->hi + (abs - set->d);
-      lo = set->lo + (abs - set->d);
-    }
-  };
   for (int b = 0; b < nctas; ++b) {
     beg.push_back((int)it.size());
     for (int w = b; w < nt; w += nctas) {
-      const int3 t = tiles[w];
-      const GemmOut& o = outs[t.x];
+      const Tile& t = tiles[w];
+      const TcPlanOut& o = outs[t.o];
       TcItem h{};
       h.type = TC_ITEM_TILE;
-      h.t.C = o.C;
-      h.t.c_off = o.c_off;
-      h.t.ldc = o.ldc;
-      h.t.m0 = t.y * TM;
-      h.t.n0 = t.z * TN;
+      h.t.m0 = t.a * TM;
+      h.t.n0 = t.b * TN;
       h.t.mt = std::min(TM, o.m - h.t.m0);
       h.t.nt = std::min(TN, o.n - h.t.n0);
-      h.t.c_rel = o.c_rel;
-      h.t.accumulate = o.accumulate;
+      if (o.tmat >= 0) {
+        const TcMat& m = tp.mats[o.tmat];
+        h.t.c_rel = 2;
+        h.t.t_hi = base(m, t.v, true);
+        h.t.t_lo = base(m, t.v, false);
+        h.t.t_rp = m.Rp;
+        h.t.t_k = m.K;
+      } else {
+        h.t.c_rel = 1;
+        h.t.c_off = o.c_off + (int64_t)t.v * nelem;
+        h.t.ldc = o.ldc;
+      }
       it.push_back(h);
       for (int q = 0; q < o.seg_count; ++q) {
-        const GemmSeg& g = S[o.seg_begin + q];
+        const TcPlanSeg& g = tp.segs[o.seg_begin + q];
         if (g.k <= 0) continue;
+        const TcMat& A = tp.mats[g.a];
+        const TcMat& B = tp.mats[g.b];
+        // the kernel copies rows [m0, m0 + 128) of A and [n0, n0 + 64) of B, clipped to Rp
+        if (A.R < o.m || B.R < o.n || A.K < g.k || B.K < g.k)
+          throw Error(LRT_EINVAL, "tensor-core plan: operand smaller than its product");
         TcItem r{};
         r.type = TC_ITEM_SEG;
-        resolve(g.a_rel, g.a_off, g.A, Sset[o.seg_begin + q], r.s.a_hi, r.s.a_lo);
-        resolve(g.b_rel, g.b_off, g.B, Sset[o.seg_begin + q], r.s.b_hi, r.s.b_lo);
-        r.s.lda = g.lda;
-        r.s.ldb = g.ldb;
+        r.s.a_hi = base(A, t.v, true);
+        r.s.a_lo = base(A, t.v, false);
+        r.s.b_hi = base(B, t.v, true);
+        r.s.b_lo = base(B, t.v, false);
+        r.s.a_rp = A.Rp;
+        r.s.b_rp = B.Rp;
         r.s.k = g.k;
-        r.s.trans = (g.transA ? TC_TRANS_A : 0) | (g.transB ? 0 : TC_TRANS_B);
-        r.s.scale = (float)g.scale;
+        r.s.scale = g.scale;
         it.push_back(r);
       }
     }
@@ -1633,17 +1631,30 @@ static void build_tc_stream(const std::vector<GemmOut>& outs, const std::vector<
   begins.upload(beg, st);
 }
 
-// TF32 copies, work streams and workspaces of a plan for the mixed path (once per plan)
+// TC-matrix pools, packed operators and work streams of a plan (once per plan)
 static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   if (p.tc_ready) return;
-  for (const OpSet* s : p.BS1set) const_cast<OpSet*>(s)->ensure_shadow(c->st);
-  for (const OpSet* s : p.BS2set) const_cast<OpSet*>(s)->ensure_shadow(c->st);
-  const size_t nx = (size_t)std::max<int64_t>(p.nelem * nvec, 1), nt = (size_t)std::max<int64_t>(p.tsize, 1);
-  if (cudaMalloc(&p.xhi, nx * sizeof(float)) != cudaSuccess || cudaMalloc(&p.xlo, nx * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&p.thi, nt * sizeof(float)) != cudaSuccess || cudaMalloc(&p.tlo, nt * sizeof(float)) != cudaSuccess)
-    throw Error(LRT_ENOMEM, "mixed-precision workspace");
-  build_tc_stream(p.B1, p.BS1, p.BS1set, p.xhi, p.xlo, p.thi, p.tlo, p.tci1, p.tcb1, p.tcn1, c->st);
-  build_tc_stream(p.B2, p.BS2, p.BS2set, p.xhi, p.xlo, p.thi, p.tlo, p.tci2, p.tcb2, p.tcn2, c->st);
+  TcPlan& tp = p.tc;
+  for (int q = 0; q < 3; ++q) {
+    const size_t n = (size_t)std::max<int64_t>(tp.pool_size[q] * (q ? nvec : 1), 1);
+    if (cudaMalloc(&p.pool_hi[q], n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p.pool_lo[q], n * sizeof(float)) != cudaSuccess)
+      throw Error(LRT_ENOMEM, "tensor-core operand pools");
+    if (q == 2) {
+      CK(cudaMemsetAsync(p.pool_hi[q], 0, n * sizeof(float), c->st));
+      CK(cudaMemsetAsync(p.pool_lo[q], 0, n * sizeof(float), c->st));
+    }
+  }
+  {
+    DevArray<TcPack> d0;
+    d0.upload(tp.pack0, c->st);
+    launch_tc_pack(d0.p, (int)tp.pack0.size(), nullptr, 0, p.pool_hi[0], p.pool_lo[0], 0, 1, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+  }
+  p.xpack.upload(tp.pack1, c->st);
+  build_tc_stream(tp, tp.out1, nvec, p.nelem, p.pool_hi, p.pool_lo, p.tci1, p.tcb1, p.tcn1, c->st);
+  build_tc_stream(tp, tp.out2, nvec, p.nelem, p.pool_hi, p.pool_lo, p.tci2, p.tcb2, p.tcn2, c->st);
   CK(cudaStreamSynchronize(c->st));
   p.tc_ready = true;
 }
@@ -2834,8 +2845,9 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
         CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
       }
       prepare_tc(ctx, p, nvec);
-      launch_split_tf32(x_dev, p.nelem * nvec, p.xhi, p.xlo, ctx->st);
-      const TcOut to{p.thi, p.tlo, y_dev};
+      launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1],
+                     p.tc.pool_size[1], nvec, ctx->st);
+      const TcOut to{y_dev};
       launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, to, ctx->derr, ctx->st);
       launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, to, ctx->derr, ctx->st);
       CK(cudaGetLastError());

@@ -63,27 +63,37 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
-// Split-TF32 tensor-core variant of the grouped GEMM.  Operands are pre-split TF32
-// pairs (hi, lo) in FP32 storage.  The host lays out, for every CTA of the
-// persistent launch, the work it will do as one linear stream of items: a tile
-// header, then the tile's block products (segments) with operand pointers resolved.
-// Outputs with c_rel == 2 are written as hi/lo pairs into the intermediates (thi,
-// tlo at c_off), c_rel == 1 as FP64 into y at c_off, c_rel == 0 as FP64 into C.
+// Split-TF32 tensor-core variant of the grouped GEMM.
+//
+// Operands live in "TC matrices": an R x K matrix (R = output rows or columns of
+// the product, K = the contracted index) stored as TF32 pairs in two planes (hi, lo),
+// each plane ceil(K / 32) chunks of Rp = roundup(R, 8) rows of 32 values, 128 bytes
+// a row, the 16-byte groups of row r permuted by XOR (r mod 8): the image tcgen05
+// reads with a 128-byte-swizzled K-major descriptor, so one bulk copy moves rows
+// [r0, r0 + n) of a chunk.  Padding (K beyond the matrix, rows R..Rp) is zero.
+//
+// The host lays out, for every CTA of the persistent launch, the work it will do as
+// one linear stream of items: a tile header, then the tile's block products.
 struct TcTileHdr {
-  double* C;
+  double* C;          // FP64 output (c_rel 0); y + c_off when c_rel == 1
+  float* t_hi;        // TC-matrix output (c_rel 2): planes of the intermediate
+  float* t_lo;
   int64_t c_off;
-  int ldc, m0, n0, mt, nt, c_rel, accumulate, pad;
+  int ldc;
+  int m0, n0, mt, nt; // tile origin and extent inside the output
+  int c_rel;
+  int accumulate;
+  int t_rp, t_k;      // TC-matrix output: padded rows, valid K (= output columns)
+  int pad;
 };
-constexpr int TC_TRANS_A = 1;   // A element (i, k) at k * lda + i (else i * lda + k)
-constexpr int TC_TRANS_B = 2;   // B element (k, j) at k * ldb + j (else j * ldb + k)
 struct TcSegRec {
-  const float* a_hi;
+  const float* a_hi;  // TC matrix A (rows = output rows) and B (rows = output columns)
   const float* a_lo;
   const float* b_hi;
   const float* b_lo;
-  int lda, ldb, k, trans;
+  int a_rp, b_rp;     // padded rows of the two matrices
+  int k;              // valid K
   float scale;
-  int pad;
 };
 constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2;
 struct TcItem {
@@ -95,8 +105,6 @@ struct TcItem {
   };
 };
 struct TcOut {
-  float* thi;
-  float* tlo;
   double* y;
 };
 // number of CTAs (one per SM) the tensor-core launch uses for ntiles tiles; CTA b
@@ -105,8 +113,20 @@ int tc_num_ctas(int ntiles);
 // items[cta_begin[b] .. cta_begin[b + 1]) is the stream of CTA b, b < nctas
 void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err,
                         cudaStream_t st);
-// hi = rna_tf32((float)x), lo = rna_tf32((float)x - hi) elementwise
-void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaStream_t st);
+
+// Packing into TC matrices: element (r, k) of the source is src[r * ld + k], or
+// src[k * ld + r] when trans; source = base + src_off when base is given at launch.
+struct TcPack {
+  const double* src;
+  int64_t src_off;
+  int64_t ld;
+  int64_t dst_off;    // float offset of the matrix in the destination planes
+  int R, K, Rp, trans;
+};
+// packs descriptors [0, n) for each of nvec vectors: vector v reads base + v * src_stride
+// (or src when base is null) and writes at dst + v * dst_stride
+void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stride, float* dst_hi, float* dst_lo,
+                    int64_t dst_stride, int nvec, cudaStream_t st);
 int tc_tile_m();
 int tc_tile_n();
 

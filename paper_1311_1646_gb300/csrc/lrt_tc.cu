@@ -11,33 +11,30 @@
 // block product.  No FP64 arithmetic runs in the loop: on this GPU the FP64 pipe is
 // the scarcest resource.
 //
-// Persistent, warp-specialised kernel (one CTA per SM; 8 warps, so two per SM
-// sub-partition and up to 255 registers a thread for the epilogue's 128 running-sum
-// registers).  The host hands every CTA a linear stream of items (tile header, then
-// the tile's block products), so only the producers touch global metadata, a few
-// items ahead; the other roles get theirs through shared memory:
-//   warps 4-6  producers: copy K chunks of 32 of the four operand tiles from global
-//              memory into a 3-stage ring in shared memory, 128-byte-swizzled K-major
-//              (the layout tcgen05 reads with SWIZZLE_128B descriptors), zero-filling
-//              the K tail, with cp.async so that three chunks are in flight; each
-//              chunk carries a small record (K steps, first/last of its product), and
-//              each product and tile end a record for the epilogue in a ring.
-//   warp 7     one thread issues 3 x (K / 8) tcgen05.mma per chunk into one of two
-//              TMEM accumulators (64 columns each), commits the stage back to its
-//              producers and, after the last chunk of a product, commits the
+// Persistent, warp-specialised kernel (one CTA per SM, 6 warps).  The host hands
+// every CTA a linear stream of items (tile header, then the tile's block products),
+// so only the producer touches global metadata, a few items ahead; the other roles
+// get theirs through shared memory:
+//   warp 4     producer (one thread): per K chunk of 32, four bulk copies
+//              (cp.async.bulk, completion counted in bytes on the stage's mbarrier)
+//              of the A and B TC-matrix rows of the tile, hi and lo planes, into a
+//              3-stage ring; the packed layout already is the 128-byte-swizzled
+//              K-major image with zero K padding.  Each chunk carries a record (K
+//              steps, first/last of its product); each product and each tile end a
+//              record for the epilogue in a ring.
+//   warp 5     one thread issues 3 x (K / 8) tcgen05.mma per chunk into one of four
+//              TMEM accumulators (64 columns each), commits the stage back to the
+//              producer and, after the last chunk of a product, commits the
 //              accumulator to the epilogue.
 //   warps 0-3  epilogue: thread = tile row = TMEM lane; folds each finished product
 //              into the compensated sum, releases the accumulator, and at a tile end
-//              stages the tile in shared memory so that a warp stores whole rows
-//              (coalesced) instead of one row per thread.
-// The block products are small (rows and columns of a few tens), so instead of TMA
-// (one tensor map per operand would be needed) the producers gather: along K for
-// K-contiguous operands (one 128-byte source row per warp instruction) and 8 rows x 4
-// K for transposed ones (four 32-byte source sectors), both bank-conflict free.
+//              stages the tile in shared memory so that a warp stores whole rows:
+//              FP64 into y, or TF32 pairs into the TC matrix of an intermediate.
 //
 // Every wait is bounded by the global timer and also ends when another role has
 // failed: on expiry the kernel records an error code, stops issuing work, waits (with
-// a bound) for its own MMAs in flight, releases its tensor memory and returns.
+// a bound) for its own MMAs and copies in flight, releases its tensor memory and
+// returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,7 +51,7 @@ constexpr int TC_N = 64;                // columns of an output tile (TMEM colum
 constexpr int TC_K = 32;                // K elements per stage (one 128-byte swizzle row)
 constexpr int STAGES = 3;
 constexpr int NINFO = 16;               // epilogue record ring
-constexpr int EPI_WARPS = 4, PROD_WARPS = 3;
+constexpr int EPI_WARPS = 4, PROD_WARPS = 1;
 constexpr int TC_THREADS = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A (16 KB)
 constexpr int B_BYTES = TC_N * TC_K * 4;    // 8 KB
@@ -71,13 +68,6 @@ static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0 && B_BYTES % 1024 =
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (row, k) of a 128-byte-swizzled K-major tile with TC_K = 32
-// columns: row r occupies bytes [128 r, 128 r + 128); its 16-byte chunk c (elements
-// 4c..4c+3) sits at chunk position c XOR (r mod 8).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-  return (uint32_t)((row << 7) + ((((k >> 2) ^ row) & 7) << 4) + ((k & 3) << 2));
 }
 
 // shared-memory matrix descriptor, K-major, SWIZZLE_128B: 8-row groups 1024 bytes
@@ -180,55 +170,18 @@ __device__ __forceinline__ void ld_16cols_async(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// One operand as the producers see it: tile row r (output row for A, output column
-// for B) against K.  A segment's transA matches `trans`; its transB is the opposite
-// (transB = 1 stores B as N x K, i.e. K-contiguous).
-struct Operand {
-  const float* hi;
-  const float* lo;
-  int64_t ld;
-  int trans;      // 0: element (r, k) at r * ld + k (K-contiguous); 1: at k * ld + r
-};
-
-// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero and reads nothing
-__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
 
-// Issue the copies of rows [0, nr) x K [k0, k0 + kc) of an operand into a swizzled
-// tile pair, zero-filling K in [kc, kpad).  Executed by the PROD_WARPS producer warps;
-// rows >= nr are left as they are (they only reach output rows/columns never stored).
-__device__ __forceinline__ void stage_operand(const Operand& op, int r0, int nr, int k0, int kc, int kpad,
-                                              uint32_t shi, uint32_t slo, int pw, int lane) {
-  if (!op.trans) {
-    // lane = k: one tile row per warp instruction, 128 contiguous bytes of the source
-    const int kk = lane;
-    if (kk >= kpad) return;
-    const uint32_t nb = kk < kc ? 4u : 0u;
-    const int ks = kk < kc ? kk : 0;
-    for (int r = pw; r < nr; r += PROD_WARPS) {
-      const int64_t idx = (int64_t)(r0 + r) * op.ld + (k0 + ks);
-      const uint32_t off = sw128_offset(r, kk);
-      cp_async4(shi + off, op.hi + idx, nb);
-      cp_async4(slo + off, op.lo + idx, nb);
-    }
-  } else {
-    // lane = (row mod 8, k mod 4): 8 rows x 4 K per warp instruction, four 32-byte
-    // source sectors and 32 distinct shared-memory banks
-    const int rr = lane & 7, q = lane >> 3;
-    const int ngroups = (nr + 7) >> 3;
-    const int nchunks = kpad >> 2;
-    for (int item = pw; item < ngroups * nchunks; item += PROD_WARPS) {
-      const int grp = item / nchunks, c = item - grp * nchunks;
-      const int r = grp * 8 + rr, kk = 4 * c + q;
-      if (r >= nr) continue;
-      const uint32_t nb = kk < kc ? 4u : 0u;
-      const int64_t idx = (int64_t)(k0 + (kk < kc ? kk : 0)) * op.ld + (r0 + r);
-      const uint32_t off = sw128_offset(r, kk);
-      cp_async4(shi + off, op.hi + idx, nb);
-      cp_async4(slo + off, op.lo + idx, nb);
-    }
-  }
+// global -> shared bulk copy whose completion is counted (in bytes) on an mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // per-stage record from the producers to the MMA thread
@@ -280,7 +233,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   }
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 32 * PROD_WARPS + 1);   // copies of every producer thread + the record
+      mbar_init(&full_bar[s], 1);   // the producer's arrive (with the expected bytes)
       mbar_init(&empty_bar[s], 1);
     }
     for (int a = 0; a < NACC; ++a) {
@@ -300,82 +253,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
-    // ---------------- producers
-    // Each thread's copies of a chunk arrive on the stage's full barrier when they
-    // land (cp.async.mbarrier.arrive.noinc); the leader adds one ordinary arrive that
-    // publishes the stage record.  The MMA thread fences to the async proxy after
-    // its wait, before the tensor core reads the stage.
-    const int pw = warp - EPI_WARPS;
-    const bool leader = (pw == 0 && lane == 0);
-    const uint32_t sbase = smem_u32(sm);
-    uint32_t it = 0, ei = 0;
-    // the epilogue record ring: only the leader writes it
-    auto post = [&](const EpiInfo& rec) -> bool {
-      const uint32_t slot = ei % NINFO, use = ei / NINFO;
-      if (use > 0 && !mbar_wait(&info_empty[slot], (use - 1) & 1, failed, err)) return false;
-      info[slot] = rec;
-      mbar_arrive(&info_full[slot]);
-      ++ei;
-      return true;
-    };
-    auto next_stage = [&](bool& ok) -> uint32_t {
-      const uint32_t stage = it % STAGES, round = it / STAGES;
-      ok = !(round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err));
-      return stage;
-    };
-    auto close_stage = [&](uint32_t stage) {
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_bar[stage]))
-                   : "memory");
-      if (leader) mbar_arrive(&full_bar[stage]);
-      ++it;
-    };
-
-    const int p0 = cta_begin[blockIdx.x], p1 = cta_begin[blockIdx.x + 1];
-    bool have_tile = false, ok = true;
-    TcTileHdr hdr{};
-    TcItem cur, nx1, nx2;
-    if (p0 < p1) cur = load_item(items + p0);
-    if (p0 + 1 < p1) nx1 = load_item(items + p0 + 1);
-    for (int p = p0; p < p1 && ok && !*failed; ++p) {
-      if (p + 2 < p1) nx2 = load_item(items + p + 2);
-      if (cur.type == TC_ITEM_TILE) {
-        if (have_tile && leader) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
-        hdr = cur.t;
-        have_tile = true;
-      } else if (cur.s.k > 0) {
-        const TcSegRec& g = cur.s;
-        if (leader) ok = post(EpiInfo{INFO_MMA, g.scale, hdr});
-        Operand A{g.a_hi, g.a_lo, g.lda, (g.trans & TC_TRANS_A) ? 1 : 0};
-        Operand B{g.b_hi, g.b_lo, g.ldb, (g.trans & TC_TRANS_B) ? 1 : 0};
-        for (int k0 = 0; k0 < g.k && ok; k0 += TC_K) {
-          const int kc = min(TC_K, g.k - k0), kpad = (kc + 7) & ~7;
-          const uint32_t stage = next_stage(ok);
-          if (!ok) break;
-          const uint32_t st = sbase + stage * STAGE_BYTES;
-          stage_operand(A, hdr.m0, hdr.mt, k0, kc, kpad, st, st + A_BYTES, pw, lane);
-          stage_operand(B, hdr.n0, hdr.nt, k0, kc, kpad, st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, pw, lane);
-          if (leader)
-            meta[stage] = StageMeta{kpad >> 3, (k0 == 0 ? META_FIRST : 0) | (k0 + TC_K >= g.k ? META_LAST : 0)};
-          close_stage(stage);
+  if (warp == EPI_WARPS) {
+    // ---------------- producer (one thread)
+    if (lane == 0) {
+      const uint32_t sbase = smem_u32(sm);
+      uint32_t it = 0, ei = 0;
+      bool ok = true;
+      // the epilogue record ring
+      auto post = [&](const EpiInfo& rec) -> bool {
+        const uint32_t slot = ei % NINFO, use = ei / NINFO;
+        if (use > 0 && !mbar_wait(&info_empty[slot], (use - 1) & 1, failed, err)) return false;
+        info[slot] = rec;
+        mbar_arrive(&info_full[slot]);
+        ++ei;
+        return true;
+      };
+      const int p0 = cta_begin[blockIdx.x], p1 = cta_begin[blockIdx.x + 1];
+      bool have_tile = false;
+      TcTileHdr hdr{};
+      TcItem cur, nx1, nx2;
+      if (p0 < p1) cur = load_item(items + p0);
+      if (p0 + 1 < p1) nx1 = load_item(items + p0 + 1);
+      for (int p = p0; p < p1 && ok && !*failed; ++p) {
+        if (p + 2 < p1) nx2 = load_item(items + p + 2);
+        if (cur.type == TC_ITEM_TILE) {
+          if (have_tile) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
+          hdr = cur.t;
+          have_tile = true;
+        } else if (cur.s.k > 0) {
+          const TcSegRec& g = cur.s;
+          ok = post(EpiInfo{INFO_MMA, g.scale, hdr});
+          // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
+          const uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0), rb = (uint32_t)min(TC_N, g.b_rp - hdr.n0);
+          const uint32_t bytes = 2u * 128u * (ra + rb);
+          for (int k0 = 0, q = 0; k0 < g.k && ok; k0 += TC_K, ++q, ++it) {
+            const uint32_t stage = it % STAGES, round = it / STAGES;
+            if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err)) {
+              ok = false;
+              break;
+            }
+            const int kc = min(TC_K, g.k - k0);
+            meta[stage] = StageMeta{(kc + 7) >> 3, (k0 == 0 ? META_FIRST : 0) | (k0 + TC_K >= g.k ? META_LAST : 0)};
+            const uint32_t st = sbase + stage * STAGE_BYTES;
+            const int64_t ao = ((int64_t)q * g.a_rp + hdr.m0) * TC_K, bo = ((int64_t)q * g.b_rp + hdr.n0) * TC_K;
+            mbar_arrive_tx(&full_bar[stage], bytes);
+            bulk_g2s(st, g.a_hi + ao, 128u * ra, &full_bar[stage]);
+            bulk_g2s(st + A_BYTES, g.a_lo + ao, 128u * ra, &full_bar[stage]);
+            bulk_g2s(st + 2 * A_BYTES, g.b_hi + bo, 128u * rb, &full_bar[stage]);
+            bulk_g2s(st + 2 * A_BYTES + B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
+          }
+        }
+        cur = nx1;
+        nx1 = nx2;
+      }
+      if (ok && !*failed) {
+        if (have_tile) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
+        ok = ok && post(EpiInfo{INFO_END, 0.0f, hdr});
+        // end-of-stream record for the MMA thread, in a stage of its own
+        const uint32_t stage = it % STAGES, round = it / STAGES;
+        if (ok && !(round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err))) {
+          meta[stage] = StageMeta{0, META_END};
+          mbar_arrive(&full_bar[stage]);
         }
       }
-      cur = nx1;
-      nx1 = nx2;
-    }
-    if (ok && !*failed) {
-      if (have_tile && leader) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
-      if (leader) ok = ok && post(EpiInfo{INFO_END, 0.0f, hdr});
-      // end-of-stream record for the MMA thread, in a stage of its own
-      bool sok = true;
-      const uint32_t stage = next_stage(sok);
-      if (sok) {
-        if (leader) meta[stage] = StageMeta{0, META_END};
-        close_stage(stage);
+      if (*failed) {
+        // copies already issued must land before the CTA's shared memory goes away:
+        // wait (bounded) for every stage that was filled after its last release
+        for (uint32_t j = (it > (uint32_t)STAGES ? it - STAGES : 0u); j < it; ++j) {
+          const uint32_t fa = smem_u32(&full_bar[j % STAGES]);
+          const uint64_t t0 = now_ns();
+          while (!mbar_try(fa, (j / STAGES) & 1) && now_ns() - t0 < WAIT_NS) {
+          }
+        }
       }
     }
-    // no copy may still be in flight when the CTA exits
-    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == EPI_WARPS + PROD_WARPS) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
@@ -392,9 +343,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           const uint32_t u = sg / NACC;
           if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err)) break;
         }
-        // the stage was written through the generic proxy (cp.async); the tensor core
-        // reads it through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dt = tmem + a * TC_N;
         const uint32_t base = smem_u32(sm + stage * STAGE_BYTES);
@@ -481,12 +429,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         const int rbase = warp * 32;
         const int nrows = min(32, t.mt - rbase);
         if (t.c_rel == 2) {
-          for (int r = 0; r < nrows; ++r) {
-            const int64_t o = t.c_off + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
-            for (int c = lane; c < t.nt; c += 32) {
-              const uint2 v = *(const uint2*)(stg + (r * STG_LD + c) * 8);
-              out.thi[o + c] = __uint_as_float(v.x);
-              out.tlo[o + c] = __uint_as_float(v.y);
+          // TC matrix: chunk q holds columns 32q..32q+31; row r's 16-byte groups are
+          // permuted by XOR (r mod 8); columns beyond the output are written as zero
+          const int pos = lane;
+          for (int q = 0; q < TC_N / 32; ++q) {
+            const int cq = t.n0 + 32 * q;          // first column of the chunk
+            if (cq >= t.t_k) break;
+            const bool live = (32 * q + pos < t.nt) && (cq + pos < t.t_k);
+            for (int r = 0; r < nrows; ++r) {
+              const int gr = t.m0 + rbase + r;
+              const uint2 v = live ? *(const uint2*)(stg + (r * STG_LD + 32 * q + pos) * 8) : make_uint2(0u, 0u);
+              const int64_t o = ((int64_t)(cq >> 5) * t.t_rp + gr) * 32 + ((((pos >> 2) ^ gr) & 7) << 2) + (pos & 3);
+              t.t_hi[o] = __uint_as_float(v.x);
+              t.t_lo[o] = __uint_as_float(v.y);
             }
           }
         } else {
@@ -514,20 +469,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   }
 }
 
-__global__ void __launch_bounds__(256) split_tf32_kernel(const double* __restrict__ src, int64_t n,
-                                                         float* __restrict__ hi, float* __restrict__ lo) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+// Packing into TC matrices: block x = descriptor, block y = vector; a warp writes one
+// 128-byte row of a chunk (lane = position in the chunk), rows and chunks strided
+// over the block's warps.
+__global__ void __launch_bounds__(256) tc_pack_kernel(const TcPack* __restrict__ d, const double* base,
+                                                      int64_t src_stride, float* __restrict__ hi,
+                                                      float* __restrict__ lo, int64_t dst_stride) {
+  const TcPack p = d[blockIdx.x];
+  const double* src = (base ? base + (int64_t)blockIdx.y * src_stride + p.src_off : p.src);
+  const int64_t dst = p.dst_off + (int64_t)blockIdx.y * dst_stride;
+  const int nch = (p.K + 31) >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = warp; w < nch * p.Rp; w += blockDim.x >> 5) {
+    const int q = w / p.Rp, r = w - q * p.Rp;
+    const int k = 32 * q + lane;
+    float v = 0.0f;
+    if (r < p.R && k < p.K) v = (float)(p.trans ? src[(int64_t)k * p.ld + r] : src[(int64_t)r * p.ld + k]);
     uint32_t h, l;
-    split_tf32((float)src[e], h, l);
-    hi[e] = __uint_as_float(h);
-    lo[e] = __uint_as_float(l);
+    split_tf32(v, h, l);
+    const int64_t o = dst + ((int64_t)q * p.Rp + r) * 32 + ((((lane >> 2) ^ r) & 7) << 2) + (lane & 3);
+    hi[o] = __uint_as_float(h);
+    lo[o] = __uint_as_float(l);
   }
 }
 
-void launch_split_tf32(const double* src, int64_t n, float* hi, float* lo, cudaStream_t st) {
-  if (n <= 0) return;
-  const int grid = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
-  split_tf32_kernel<<<grid, 256, 0, st>>>(src, n, hi, lo);
+void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stride, float* dst_hi, float* dst_lo,
+                    int64_t dst_stride, int nvec, cudaStream_t st) {
+  if (n <= 0 || nvec <= 0) return;
+  tc_pack_kernel<<<dim3((unsigned)n, (unsigned)nvec), 256, 0, st>>>(d, base, src_stride, dst_hi, dst_lo, dst_stride);
 }
 
 int tc_tile_m() { return TC_M; }
