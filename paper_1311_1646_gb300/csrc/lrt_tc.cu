@@ -191,7 +191,7 @@ struct StageMeta {
   int flags;
 };
 // ring record from the producers to the epilogue
-constexpr int INFO_MMA = 1, INFO_TILE_END = 2, INFO_END = 4;
+constexpr int INFO_MMA = 1, INFO_TILE_END = 2, INFO_END = 4, INFO_FIRST = 8;
 struct EpiInfo {
   int flags;
   float scale;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         return true;
       };
       const int p0 = cta_begin[blockIdx.x], p1 = cta_begin[blockIdx.x + 1];
-      bool have_tile = false;
+      bool have_tile = false, first_seg = true;
       TcTileHdr hdr{};
       TcItem cur, nx1, nx2;
       if (p0 < p1) cur = load_item(items + p0);
@@ -280,9 +280,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           if (have_tile) ok = post(EpiInfo{INFO_TILE_END, 0.0f, hdr});
           hdr = cur.t;
           have_tile = true;
+          first_seg = true;
         } else if (cur.s.k > 0) {
           const TcSegRec& g = cur.s;
-          ok = post(EpiInfo{INFO_MMA, g.scale, hdr});
+          ok = post(EpiInfo{INFO_MMA | (first_seg ? INFO_FIRST : 0), g.scale, hdr});
+          first_seg = false;
           // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
           const uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0), rb = (uint32_t)min(TC_N, g.b_rp - hdr.n0);
           const uint32_t bytes = 2u * 128u * (ra + rb);
@@ -374,6 +376,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
     // ---------------- epilogue: thread = tile row = TMEM lane
     uint8_t* stg = sm + STAGES * STAGE_BYTES + warp * STG_WARP_BYTES;   // this warp's 32 rows
     uint32_t sg = 0;
+    bool tile_has_mma = false;
     float sum[TC_N], cmp[TC_N];
 #pragma unroll
     for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
@@ -397,54 +400,83 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           ld_16cols_async(taddr + (uint32_t)c0, v);
           ld_16cols_async(taddr + (uint32_t)c0 + 16u, v + 16);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (rec.flags & INFO_FIRST) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float y = rec.scale * __uint_as_float(v[i]) - cmp[c0 + i];
-            const float t = sum[c0 + i] + y;
-            cmp[c0 + i] = (t - sum[c0 + i]) - y;
-            sum[c0 + i] = t;
+            for (int i = 0; i < 32; ++i) {
+              sum[c0 + i] = rec.scale * __uint_as_float(v[i]);
+              cmp[c0 + i] = 0.0f;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float y = rec.scale * __uint_as_float(v[i]) - cmp[c0 + i];
+              const float t = sum[c0 + i] + y;
+              cmp[c0 + i] = (t - sum[c0 + i]) - y;
+              sum[c0 + i] = t;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&tempty_bar[a]);
         ++sg;
+        tile_has_mma = true;
       }
       if (rec.flags & INFO_TILE_END) {
         const TcTileHdr& t = rec.t;
-        // stage: thread `lane` writes its row, then the warp stores row by row
-        const int rr = lane;
-        if (t.c_rel == 2) {
+        if (!tile_has_mma) {
 #pragma unroll
-          for (int c = 0; c < TC_N; ++c) {
-            uint32_t hi, lo;
-            split_tf32(sum[c] - cmp[c], hi, lo);
-            *(uint2*)(stg + (rr * STG_LD + c) * 8) = make_uint2(hi, lo);
+          for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
+        }
+        tile_has_mma = false;
+        const int rr = lane;
+        const int rbase = warp * 32;
+        const int nrows = min(32, t.mt - rbase);
+        // the staging buffer may still be read by this warp's previous bulk stores
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
+        if (t.c_rel == 2) {
+          // Intermediate: this warp's rows as a TC-matrix image (two chunks of 32
+          // columns, hi and lo planes; row r's 16-byte groups permuted by r mod 8),
+          // then one bulk store per chunk and plane: rows [m0 + 32 w, + nrows) of a
+          // chunk are contiguous in the matrix.  Columns past the output are zeros.
+#pragma unroll
+          for (int q = 0; q < TC_N / 32; ++q)
+#pragma unroll
+            for (int g4 = 0; g4 < 8; ++g4) {
+              uint32_t h[4], l[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int c = 32 * q + 4 * g4 + e;
+                h[e] = l[e] = 0u;
+                if (c < t.nt) split_tf32(sum[c] - cmp[c], h[e], l[e]);
+              }
+              const uint32_t o = (uint32_t)(((q * 32 + rr) << 7) + (((g4 ^ rr) & 7) << 4));
+              *(uint4*)(stg + o) = make_uint4(h[0], h[1], h[2], h[3]);
+              *(uint4*)(stg + 2 * 32 * 128 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0 && nrows > 0) {
+            for (int q = 0; q < TC_N / 32; ++q) {
+              const int cq = t.n0 + 32 * q;
+              if (cq >= t.t_k) break;
+              const int64_t go = ((int64_t)(cq >> 5) * t.t_rp + t.m0 + rbase) * 32;
+              const uint32_t so = smem_u32(stg) + (uint32_t)(q * 32 * 128);
+              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(t.t_hi + go), "r"(so),
+                           "r"((uint32_t)nrows * 128u)
+                           : "memory");
+              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(t.t_lo + go),
+                           "r"(so + 2u * 32u * 128u), "r"((uint32_t)nrows * 128u)
+                           : "memory");
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
         } else {
+          // FP64 output: stage the rows, then the warp stores row by row (coalesced)
 #pragma unroll
           for (int c = 0; c < TC_N; ++c)
             *(double*)(stg + (rr * STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
-        }
-        __syncwarp();
-        const int rbase = warp * 32;
-        const int nrows = min(32, t.mt - rbase);
-        if (t.c_rel == 2) {
-          // TC matrix: chunk q holds columns 32q..32q+31; row r's 16-byte groups are
-          // permuted by XOR (r mod 8); columns beyond the output are written as zero
-          const int pos = lane;
-          for (int q = 0; q < TC_N / 32; ++q) {
-            const int cq = t.n0 + 32 * q;          // first column of the chunk
-            if (cq >= t.t_k) break;
-            const bool live = (32 * q + pos < t.nt) && (cq + pos < t.t_k);
-            for (int r = 0; r < nrows; ++r) {
-              const int gr = t.m0 + rbase + r;
-              const uint2 v = live ? *(const uint2*)(stg + (r * STG_LD + 32 * q + pos) * 8) : make_uint2(0u, 0u);
-              const int64_t o = ((int64_t)(cq >> 5) * t.t_rp + gr) * 32 + ((((pos >> 2) ^ gr) & 7) << 2) + (pos & 3);
-              t.t_hi[o] = __uint_as_float(v.x);
-              t.t_lo[o] = __uint_as_float(v.y);
-            }
-          }
-        } else {
+          __syncwarp();
           double* C = (t.c_rel == 1 ? out.y + t.c_off : t.C);
           for (int r = 0; r < nrows; ++r) {
             double* dst = C + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
@@ -455,12 +487,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           }
         }
         __syncwarp();
-#pragma unroll
-        for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
       }
     }
   }
 
+  if (warp < EPI_WARPS && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
