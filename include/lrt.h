@@ -159,8 +159,23 @@ typedef struct {
   double eps;         /* converged when sum_i |r_i^mu|^2 < eps for every root */
   double pinv_cut;    /* Lambda^-1: singular values below pinv_cut * largest are dropped */
   uint64_t seed;      /* initial trial vectors: SplitMix64 Gaussians projected by Q^C */
+  int precision;      /* LRT_FP64, or LRT_MIXED: the site products H_0 C and dH C0 run as
+                         split-TF32 tensor-core products until every root's sum |r|^2 is
+                         below refine_tol, then the sweeps continue in FP64 to eps (the
+                         FP64 residual correction); the results always come from FP64
+                         sweeps */
+  double refine_tol;  /* LRT_MIXED: switch to FP64 below this sum |r|^2 (<= 0: 1e-6) */
 } lrt_tda_params;
 int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);
+/* tda_prepare: the mixed-canonical gauge on the GPU instead of tda_load.  Takes the
+ * loaded MPS with sites 1..k-1 right-orthonormal and the centre on site 0 (the state
+ * sweep_gs leaves, or an MPS loaded that way), normalizes it (*norm = its norm before,
+ * may be NULL) and puts every bond in its Schmidt basis by a left-to-right pass of
+ * per-sector SVDs: the loaded sites become L0_i, the right-orthonormal sites R0_i,
+ * and the centres C0_i and Schmidt values Lambda_b are stored as tda_load would.
+ * Bond dimensions do not change; a sector with fewer fused rows than states gets
+ * zero Schmidt values (dropped by pinv_cut in sweep_tda). */
+int tda_prepare(lrt_t ctx, double* norm);
 int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0);
 
 /* Read back the loaded MPS: bond tables (bond_nsect[k+1], bond_sectors[3 * total])

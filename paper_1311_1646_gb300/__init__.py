@@ -20,7 +20,7 @@ LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site", "tda_load", "sweep_tda"]
+           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda"]
 
 _lib = None
 
@@ -49,7 +49,8 @@ class GsParams(ctypes.Structure):
 
 class TdaParams(ctypes.Structure):
     _fields_ = [("max_space", ctypes.c_int), ("max_iter", ctypes.c_int), ("eps", ctypes.c_double),
-                ("pinv_cut", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("pinv_cut", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
 
 
 class LrtError(RuntimeError):
@@ -86,6 +87,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mps_get_site.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_int64)]
     ppd = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
     lib.tda_load.argtypes = [vp, ppd, ppd]
+    lib.tda_prepare.argtypes = [vp, dp]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
     for name in EXPORTS:
         if name != "lrt_last_error":
@@ -219,13 +221,22 @@ class Context:
         pl = (ctypes.POINTER(ctypes.c_double) * len(lm))(*[_dptr(a) for a in lm])
         self._check(self.lib.tda_load(self.h, pc, pl), "tda_load")
 
+    def tda_prepare(self) -> float:
+        """Mixed-canonical gauge of the loaded MPS on the GPU (instead of tda_load); returns its norm."""
+        nrm = ctypes.c_double()
+        self._check(self.lib.tda_prepare(self.h, ctypes.byref(nrm)), "tda_prepare")
+        return nrm.value
+
     def sweep_tda(self, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
-                  pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False):
-        """DMRG-TDA roots: returns (omega, resid, e0); omega are excitation energies."""
+                  pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
+                  precision: int = LRT_FP64, refine_tol: float = 0.0):
+        """DMRG-TDA roots: returns (omega, resid, e0); omega are excitation energies.  With
+        precision=LRT_MIXED the site products run on the tensor cores until the residuals
+        fall below refine_tol, then the sweeps finish in FP64."""
         om = np.zeros(nroots)
         rs = np.zeros(nroots)
         e0 = ctypes.c_double()
-        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed)
+        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol)
         rc = self.lib.sweep_tda(self.h, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), ctypes.byref(e0))
         if rc != 0 and not (allow_noconv and rc == -4):
             self._check(rc, "sweep_tda")

@@ -1659,6 +1659,29 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   p.tc_ready = true;
 }
 
+// y = H_eff x through the split-TF32 tensor-core kernels (both phases), then a check
+// of the kernels' error flag (a bounded pipeline wait that expired)
+static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec) {
+  if (!ctx->derr) {
+    if (cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+    CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
+  }
+  prepare_tc(ctx, p, nvec);
+  launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1], p.tc.pool_size[1],
+                 nvec, ctx->st);
+  const TcOut to{y_dev};
+  launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, to, ctx->derr, ctx->st);
+  launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, to, ctx->derr, ctx->st);
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (flag) {
+    CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
+    throw Error(LRT_ETIMEOUT, "sigma: a tensor-core pipeline wait expired; results are invalid");
+  }
+}
+
 static SigmaPlan* find_plan(lrt_ctx* c, int site, int nsite, int nvec) {
   auto it = c->plans.find(std::make_tuple(site, nsite, nvec));
   return it == c->plans.end() ? nullptr : it->second.get();
@@ -2282,8 +2305,21 @@ struct TdaRunner {
   std::vector<std::unique_ptr<SigmaPlan>> h0plan;
   DevBuf tmp;
   double E0 = 0.0;
+  bool mixed = false;   // site products on the tensor cores (until the FP64 refinement)
 
-  TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p) {}
+  TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p), mixed(p.precision == LRT_MIXED) {}
+
+  // y = (plan) x for one vector, in the current precision
+  void apply(SigmaPlan& p, const double* x, double* y) {
+    if (mixed) {
+      run_tc(c, p, x, y, 1);
+    } else {
+      p.p1.run(c->st, x, y, p.tbuf);
+      p.p2.run(c->st, x, y, p.tbuf);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(c->st));
+    }
+  }
 
   const SiteTensor& L0(int i) { return c->sites[i]; }
   const SiteTensor& R0(int i) { return c->sites_r[i]; }
@@ -2308,17 +2344,16 @@ struct TdaRunner {
       launch_diag(h0plan[i]->douts.p, h0plan[i]->dterms.p, h0plan[i]->ndiag, diag[i].p, c->st);
     }
     SiteTensor y = new_site(c, 0);
+    const bool m = mixed;
+    mixed = false;            // the reference energy is FP64
     h0(0, C0(0), y);
+    mixed = m;
     E0 = t_dot(c, C0(0), y, tmp);
   }
 
   // y = H_0^[i] C  (Eq. hzero_sb)
   void h0(int i, const SiteTensor& C, SiteTensor& y) {
-    SigmaPlan& p = *h0plan[i];
-    p.p1.run(c->st, C.d, y.d, p.tbuf);
-    p.p2.run(c->st, C.d, y.d, p.tbuf);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    apply(*h0plan[i], C.d, y.d);
   }
 
   // y = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i  (Eq. hleft_sb on C0)
@@ -2328,10 +2363,7 @@ struct TdaRunner {
     auto Xf = enlarge_set(c, *HL.f, HL.r.get(), i, false);
     auto Xr = enlarge_set(c, *HL.r, HL.f.get(), i, false);
     auto plan = plan_sigma_sets(c, *Xf, Xr.get(), *c->R[i + 1], nullptr, i, 1, 1);
-    plan->p1.run(c->st, C0(i).d, y.d, plan->tbuf);
-    plan->p2.run(c->st, C0(i).d, y.d, plan->tbuf);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    apply(*plan, C0(i).d, y.d);
   }
 
   // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2)
@@ -2339,10 +2371,7 @@ struct TdaRunner {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (HR.empty()) return;
     auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1);
-    plan->p1.run(c->st, C0(i).d, y.d, plan->tbuf);
-    plan->p2.run(c->st, C0(i).d, y.d, plan->tbuf);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(c->st));
+    apply(*plan, C0(i).d, y.d);
   }
 
   // Q^C C = C - C0 (C0 . C)
@@ -2617,6 +2646,15 @@ struct TdaRunner {
         ++it;
         bool conv = true;
         for (int mu = 0; mu < n; ++mu) conv = conv && (r2[mu] < P.eps);
+        if (mixed) {
+          // FP64 residual correction: once the tensor-core sweeps have brought every
+          // residual below refine_tol, the remaining sweeps (and the results) are FP64
+          const double rt = P.refine_tol > 0.0 ? P.refine_tol : 1e-6;
+          bool low = true;
+          for (int mu = 0; mu < n; ++mu) low = low && (r2[mu] < std::max(rt, P.eps));
+          if (low) mixed = false;
+          conv = false;
+        }
         if (conv || it >= P.max_iter) {
           for (int mu = 0; mu < n; ++mu) {
             theta_out[mu] = mu < (int)theta.size() ? theta[mu] : 0.0;
@@ -2638,6 +2676,188 @@ struct TdaRunner {
     CK(cudaStreamSynchronize(c->st));
   }
 };
+
+// Mixed-canonical gauge of the whole MPS (the form the TDA sweep works in): on every
+// bond the Schmidt basis, with C0_i = L0_i Lambda_{i+1} = Lambda_i R0_i.  Input: the
+// MPS in c->sites with sites 1..k-1 right-orthonormal and the centre at site 0 (the
+// state sweep_gs leaves).  A left-to-right pass, per right sector of every site, takes
+// the SVD of the left-fused C_i = Lambda_i V_prev^T R_i = L S Vn^T (cuSOLVER Jacobi SVD,
+// FP64 on the GPU): L0_i = L, Lambda_{i+1} = S, R0_i = V_prev^T R_i Vn, C0_i = C_i Vn.
+// Bond dimensions are kept: when a sector has fewer fused rows than states, the
+// missing singular values are zero and the matching columns of L0 are zero.
+static void tda_prepare_impl(lrt_ctx* c, double* norm_out) {
+  const int k = c->k;
+  cudaStream_t st = c->st;
+  SolverHandle sh;
+  if (cusolverDnCreate(&sh.h) != CUSOLVER_STATUS_SUCCESS) throw Error(LRT_ECUDA, "cusolverDnCreate failed");
+  cusolverDnSetStream(sh.h, st);
+  gesvdjInfo_t params = nullptr;
+  if (cusolverDnCreateGesvdjInfo(&params) != CUSOLVER_STATUS_SUCCESS) throw Error(LRT_ECUDA, "gesvdj info");
+  struct ParamsGuard {
+    gesvdjInfo_t p;
+    ~ParamsGuard() {
+      if (p) cusolverDnDestroyGesvdjInfo(p);
+    }
+  } pg{params};
+  DevBuf tmp, work, A, U, V, S;
+  tmp.ensure(4);
+  int* dinfo = nullptr;
+  if (cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
+  struct InfoGuard {
+    int* p;
+    ~InfoGuard() { cudaFree(p); }
+  } ig{dinfo};
+
+  // normalize the centre
+  SiteTensor& S0 = c->sites[0];
+  const double nrm = std::sqrt(std::max(0.0, dev_dot(S0.d, S0.d, S0.total, tmp.p, st)));
+  if (!(nrm > 0.0)) throw Error(LRT_EINVAL, "tda_prepare: zero wavefunction");
+  t_axpby(c, 1.0 / nrm, S0, 0.0, S0, tmp);
+  if (norm_out) *norm_out = nrm;
+
+  auto tda = std::make_unique<TdaState>();
+  tda->C0.resize(k);
+  tda->lam.resize(k + 1);
+  tda->lam[0].assign(1, 1.0);
+  std::vector<SiteTensor> L0(k), R0(k);
+  // X = Lambda_i V_prev^T and V_prev^T on bond i (identity on bond 0)
+  BondMat X, VT;
+  bond_layout(c->bonds[0], X, st);
+  bond_layout(c->bonds[0], VT, st);
+  {
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(X.buf.p, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(VT.buf.p, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  for (int i = 0; i < k; ++i) {
+    const Sectors& Rb = c->bonds[i + 1];
+    const SiteTensor& Ri = c->sites[i];
+    SiteTensor Ci = new_site(c, i), Rt = new_site(c, i);
+    t_lmul(c, i, X, Ri, Ci, false);
+    t_lmul(c, i, VT, Ri, Rt, false);
+    SiteTensor Li = new_site(c, i);
+    BondMat Vn;
+    bond_layout(Rb, Vn, st);
+    std::vector<double> lam;
+    std::vector<GatherTask> tasks;
+    std::vector<GatherSrc> srcs;
+    // SVD results of all sectors live in U/V buffers until the gathers below
+    std::vector<int64_t> uoff(Rb.n(), -1), voff(Rb.n(), -1);
+    int64_t ut = 0, vt = 0, at = 0;
+    for (int q = 0; q < Rb.n(); ++q) {
+      const int D = Rb.d[q], rows = Ci.blk_off[q] >= 0 ? Ci.blk_rows[q] : 0;
+      if (rows == 0 || D == 0) continue;
+      uoff[q] = ut;
+      voff[q] = vt;
+      ut += (int64_t)D * D;
+      vt += (int64_t)rows * rows;
+      at = std::max<int64_t>(at, (int64_t)D * rows);
+    }
+    U.ensure(std::max<int64_t>(ut, 1));
+    V.ensure(std::max<int64_t>(vt, 1));
+    A.ensure(std::max<int64_t>(at, 1));
+    S.ensure(1);
+    std::vector<double> sv;
+    for (int q = 0; q < Rb.n(); ++q) {
+      const int D = Rb.d[q];
+      if (uoff[q] < 0) {
+        // no fused rows: Schmidt values zero, rotation the identity
+        std::vector<double> I((size_t)D * D, 0.0);
+        for (int a = 0; a < D; ++a) I[(size_t)a * D + a] = 1.0;
+        if (D > 0)
+          CK(cudaMemcpyAsync(Vn.buf.p + Vn.off[q], I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        lam.insert(lam.end(), D, 0.0);
+        CK(cudaStreamSynchronize(st));
+        continue;
+      }
+      const int rows = Ci.blk_rows[q];
+      const int p = std::min(D, rows);
+      // the row-major block (rows x D) is the column-major D x rows matrix A = M^T;
+      // A = U_a S V_a^T gives M = V_a S U_a^T
+      CK(cudaMemcpyAsync(A.p, Ci.d + Ci.blk_off[q], (size_t)D * rows * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      S.ensure(std::max(1, p));
+      int lwork = 0;
+      if (cusolverDnDgesvdj_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, 0, D, rows, A.p, D, S.p, U.p + uoff[q], D,
+                                       V.p + voff[q], rows, &lwork, params) != CUSOLVER_STATUS_SUCCESS)
+        throw Error(LRT_ECUDA, "gesvdj buffer size");
+      work.ensure(std::max(lwork, 1));
+      if (cusolverDnDgesvdj(sh.h, CUSOLVER_EIG_MODE_VECTOR, 0, D, rows, A.p, D, S.p, U.p + uoff[q], D, V.p + voff[q],
+                            rows, work.p, lwork, dinfo, params) != CUSOLVER_STATUS_SUCCESS)
+        throw Error(LRT_ECUDA, "gesvdj");
+      int info = 0;
+      sv.resize(p);
+      CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(sv.data(), S.p, p * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (info < 0) throw Error(LRT_ECUDA, "gesvdj: invalid argument " + std::to_string(-info));
+      for (int a = 0; a < D; ++a) lam.push_back(a < p ? sv[a] : 0.0);
+      // L block (rows x D, row-major): columns j < p are V_a's columns (column-major,
+      // ld rows); Vn (D x D, row-major) = U_a (column-major, ld D)
+      tasks.push_back(GatherTask{Li.d + Li.blk_off[q], D, rows, p, (int)srcs.size(), 1});
+      srcs.push_back(GatherSrc{V.p + voff[q], rows, 1, 1.0});
+      tasks.push_back(GatherTask{Vn.buf.p + Vn.off[q], D, D, D, (int)srcs.size(), 1});
+      srcs.push_back(GatherSrc{U.p + uoff[q], D, 1, 1.0});
+    }
+    if (!tasks.empty()) {
+      GatherPlan gp;
+      build_gather(gp, tasks, srcs, st);
+      gp.run(st);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(st));
+    }
+    SiteTensor C0 = new_site(c, i), R0i = new_site(c, i);
+    t_rmul(c, i, Ci, Vn, C0, false);
+    t_rmul(c, i, Rt, Vn, R0i, false);
+    L0[i] = std::move(Li);
+    R0[i] = std::move(R0i);
+    tda->C0[i] = std::move(C0);
+    tda->lam[i + 1] = lam;
+    if (i + 1 < k) {
+      // next bond: X = Lambda Vn^T, VT = Vn^T
+      bond_layout(Rb, X, st);
+      bond_layout(Rb, VT, st);
+      std::vector<GatherTask> t2;
+      std::vector<GatherSrc> s2;
+      for (int q = 0; q < Rb.n(); ++q) {
+        const int D = Rb.d[q];
+        if (D == 0) continue;
+        t2.push_back(GatherTask{VT.buf.p + VT.off[q], D, D, D, (int)s2.size(), 1});
+        s2.push_back(GatherSrc{Vn.buf.p + Vn.off[q], D, 1, 1.0});
+      }
+      if (!t2.empty()) {
+        GatherPlan gp;
+        build_gather(gp, t2, s2, st);
+        gp.run(st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+      }
+      // X_q = diag(lambda_q) VT_q
+      std::vector<GemmOut> o;
+      std::vector<GemmSeg> g;
+      BondMat Lm, Lmi;
+      lam_mats(c, i + 1, lam, 0.0, Lm, Lmi);
+      for (int q = 0; q < Rb.n(); ++q) {
+        const int D = Rb.d[q];
+        if (D == 0) continue;
+        o.push_back(GemmOut{X.buf.p + X.off[q], 0, D, D, D, (int)g.size(), 1, 0, 0});
+        g.push_back(GemmSeg{Lm.buf.p + Lm.off[q], VT.buf.p + VT.off[q], 0, 0, D, D, D, 0, 0, 0, 0, 1.0});
+      }
+      run_gemms(c, o, g);
+    }
+  }
+  c->sites = std::move(L0);
+  c->sites_r = std::move(R0);
+  tda->loaded = true;
+  c->tda = std::move(tda);
+  // environments and plans belong to the old gauge
+  drop_plans(c);
+  for (int b = 0; b < k; ++b) {
+    c->XL[b].reset();
+    c->YR[b].reset();
+  }
+  for (int b = 1; b < k; ++b) c->L[b].reset();
+  for (int b = 0; b < k; ++b) c->R[b].reset();
+}
 
 }  // namespace lrt
 
@@ -2840,24 +3060,7 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     if ((const double*)y_dev < x_dev + p.nelem * nvec && x_dev < (const double*)y_dev + p.nelem * nvec)
       throw Error(LRT_EINVAL, "sigma: x and y overlap");
     if (precision == LRT_MIXED) {
-      if (!ctx->derr) {
-        if (cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
-        CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
-      }
-      prepare_tc(ctx, p, nvec);
-      launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1],
-                     p.tc.pool_size[1], nvec, ctx->st);
-      const TcOut to{y_dev};
-      launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, to, ctx->derr, ctx->st);
-      launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, to, ctx->derr, ctx->st);
-      CK(cudaGetLastError());
-      int flag = 0;
-      CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-      CK(cudaStreamSynchronize(ctx->st));
-      if (flag) {
-        CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
-        throw Error(LRT_ETIMEOUT, "sigma: a tensor-core pipeline wait expired; results are invalid");
-      }
+      run_tc(ctx, p, x_dev, y_dev, nvec);
     } else {
       p.p1.run(ctx->st, x_dev, y_dev, p.tbuf);
       p.p2.run(ctx->st, x_dev, y_dev, p.tbuf);
@@ -2918,6 +3121,14 @@ int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam) {
     CK(cudaStreamSynchronize(ctx->st));
     st->loaded = true;
     ctx->tda = std::move(st);
+  });
+}
+
+int tda_prepare(lrt_t ctx, double* norm) {
+  return guard(ctx, [&] {
+    if (!ctx->have_mps || !ctx->have_ham) throw Error(LRT_ESTATE, "tda_prepare: op_build and mps_load first");
+    if (ctx->k < 1) throw Error(LRT_EINVAL, "tda_prepare: empty MPS");
+    tda_prepare_impl(ctx, norm);
   });
 }
 
