@@ -32,6 +32,26 @@ import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (152 SMs x 2 FMA/clk x 2 flop x ~2.06 GHz)
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the two
+# sigma launches of the middle position (profiles/gemm_*_ppp_k12_M256_twosite.md), valid only
+# for the kernel source it was taken on (sha256 prefix); otherwise the bench reports null.
+TRAFFIC = {
+    "fp64": {"source": "lrt_kernels.cu", "sha256": "751ff19ee3994d57", "bytes": (57.139e6 + 14.172e6) / 2},
+    "mixed": {"source": "lrt_tc.cu", "sha256": "bd44adc66b77d94a", "bytes": (96.711e6 + 150.526e6) / 2},
+}
+
+
+def traffic(precision):
+    import hashlib
+    t = TRAFFIC[precision]
+    path = os.path.join(ROOT, "paper_1311_1646_gb300", "csrc", t["source"])
+    try:
+        with open(path, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return t["bytes"] if h == t["sha256"] else None
+
 
 def tf32_peak():
     """Dense TF32 tensor peak: the measured BF16 GEMM rate x the nominal TF32/BF16 ratio."""
@@ -52,6 +72,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="sigma arithmetic: FP64, or split-TF32 tensor-core products (LRT_MIXED)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the side measurements (mixed sigma, water-shaped sigma, TDA s/root)")
     return p.parse_args()
 
 
@@ -214,18 +236,21 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ctx, H, left, right, nvec, sizes)
+    side = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        side = extras(pkg, ctx, device, xs, ys, positions, nvec, stream)
     if rank == 0:
         if args.precision == "mixed":
             peak, peak_note = tf32_peak()
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic("mixed"),
                     "kernel": "gemm_tf32x3_kernel (sigma phases 1+2)",
                     "peak_note": peak_note + "; achieved counts each split-TF32 product once "
                                  "(the tensor pipe issues it 3x)"}
             metric, dtype = "H_eff sigma TFLOP/s (algorithmic, split-TF32 mixed)", "tf32x3"
         else:
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic("fp64"),
                     "kernel": "gemm_fp64_kernel (sigma phases 1+2)",
                     "peak_note": "nominal FP64 of GB300; FMA probe measured 1.20 TFLOP/s"}
             metric, dtype = "H_eff sigma TFLOP/s (algorithmic, FP64)", "f64"
@@ -253,11 +278,95 @@ def run_ours(args):
             "gpu_launches": launches_step * args.steps,
             "flops_per_step": flops_step,
             "sigma_ms_per_step": sum(sigma_ms) / args.steps,
+            "extras": side,
         }
         print(json.dumps(out))
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
+    """Side measurements, outside the timed steps: the mixed path on this workload, the
+    water-shaped workload where it matters most, and TDA seconds per root."""
+    import torch
+    out = {}
+    # (1) mixed sigma on the polyene workload, error against the FP64 result
+    flops, t64, tmx, err = 0.0, 0.0, 0.0, 0.0
+    for i in positions:
+        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec)
+        y64 = ys[i].clone()
+        flops += ctx.stats()["flops"]
+        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=pkg.LRT_MIXED)
+        err = max(err, float((ys[i] - y64).abs().max() / y64.abs().max()))
+        t64 += _timed(lambda: ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec), 3, stream)
+        tmx += _timed(lambda: ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=pkg.LRT_MIXED), 3, stream)
+    out["mixed_same_workload"] = {"fp64_tflops": flops / t64 / 1e9, "mixed_tflops": flops / tmx / 1e9,
+                                  "speedup": t64 / tmx, "max_rel_err_vs_fp64": err}
+    # (2) water-shaped k=24, M=500, one-site sigma at the middle, 6 vectors
+    cfg = synth.config(3)
+    H = cfg["ham"]
+    i, nv = H.k // 2 - 1, 6
+    m = synth.mixed_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 5, center=i)
+    w = pkg.Context(device)
+    w.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    w.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, i)
+    for b in range(i):
+        w.renormalize(b, +1)
+    for b in range(H.k - 1, i, -1):
+        w.renormalize(b, -1)
+    n, _ = w.wfn_layout(i, 1)
+    x = torch.tensor(synth.random_vector(n * nv, 77), dtype=torch.float64, device=f"cuda:{device}")
+    y = torch.empty_like(x)
+    w.sigma(i, 1, x, y, nvec=nv)
+    y64 = y.clone()
+    fl = w.stats()["flops"]
+    w.sigma(i, 1, x, y, nvec=nv, precision=pkg.LRT_MIXED)
+    err = float((y - y64).abs().max() / y64.abs().max())
+    t64 = _timed(lambda: w.sigma(i, 1, x, y, nvec=nv), 3, stream)
+    tmx = _timed(lambda: w.sigma(i, 1, x, y, nvec=nv, precision=pkg.LRT_MIXED), 5, stream)
+    out["water_k24_M500_onesite"] = {"site": i, "nvec": nv, "gflop": fl / 1e9, "fp64_ms": t64, "mixed_ms": tmx,
+                                     "fp64_tflops": fl / t64 / 1e9, "mixed_tflops": fl / tmx / 1e9,
+                                     "speedup": t64 / tmx, "max_rel_err_vs_fp64": err}
+    w.close()
+    # (3) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU
+    cfg = synth.config(1)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    res = {}
+    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
+        t = pkg.Context(device)
+        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+        t.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+        e_gs = t.sweep_gs([32, cfg["M"]], max_sweeps=8)
+        t.tda_prepare()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, rs, e0 = t.sweep_tda(nr, max_iter=30, eps=1e-10, allow_noconv=True, precision=prec)
+        torch.cuda.synchronize()
+        res[prec] = (time.perf_counter() - t0, om, rs, e0, e_gs)
+        t.close()
+    (s64, w64, r64, e64, g64), (smx, wmx, rmx, emx, gmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
+    out["tda_abinitio_k8_M64_4roots"] = {
+        "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "e0_gs": g64,
+        "omega_fp64": list(w64), "omega_mixed": list(wmx),
+        "max_abs_domega_Eh": float(np.abs(w64 - wmx).max()),
+        "resid_fp64": list(r64), "resid_mixed": list(rmx), "converged_eps": 1e-10,
+        "note": "wall time of sweep_tda (max 30 sweeps) / roots; reference from sweep_gs + tda_prepare on the GPU"}
+    return out
 
 
 def _oracle_setup(H, left, right, i):
