@@ -355,7 +355,8 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
         t.tda_prepare()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        om, rs, e0 = t.sweep_tda(nr, max_iter=30, eps=1e-10, allow_noconv=True, precision=prec)
+        om, rs, e0 = t.sweep_tda(nr, max_iter=20, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
+                                 refine_tol=1e-2)
         torch.cuda.synchronize()
         res[prec] = (time.perf_counter() - t0, om, rs, e0, e_gs)
         t.close()
@@ -364,8 +365,11 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
         "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "e0_gs": g64,
         "omega_fp64": list(w64), "omega_mixed": list(wmx),
         "max_abs_domega_Eh": float(np.abs(w64 - wmx).max()),
-        "resid_fp64": list(r64), "resid_mixed": list(rmx), "converged_eps": 1e-10,
-        "note": "wall time of sweep_tda (max 30 sweeps) / roots; reference from sweep_gs + tda_prepare on the GPU"}
+        "resid_fp64": list(r64), "resid_mixed": list(rmx), "eps": 1e-8,
+        "converged_fp64": bool(np.all(r64 < 1e-8)), "converged_mixed": bool(np.all(rmx < 1e-8)),
+        "note": "wall time of sweep_tda (20 sweeps at most, diagonal start; mixed: tensor-core site "
+                "products until sum |r|^2 < 1e-2, then FP64) / roots; reference from sweep_gs + "
+                "tda_prepare on the GPU; this loop is host-bound at this size"}
     return out
 
 

@@ -158,7 +158,9 @@ typedef struct {
   int max_iter;
   double eps;         /* converged when sum_i |r_i^mu|^2 < eps for every root */
   double pinv_cut;    /* Lambda^-1: singular values below pinv_cut * largest are dropped */
-  uint64_t seed;      /* initial trial vectors: SplitMix64 Gaussians projected by Q^C */
+  uint64_t seed;      /* initial trial vectors projected by Q^C: SplitMix64 Gaussians of this
+                         seed, or (seed 0) at every site the unit vector on the root's rank
+                         among the lowest diagonal elements of H_0 where |C0| < 1/2 */
   int precision;      /* LRT_FP64, or LRT_MIXED: the site products H_0 C and dH C0 run as
                          split-TF32 tensor-core products until every root's sum |r|^2 is
                          below refine_tol, then the sweeps continue in FP64 to eps (the

@@ -45,6 +45,75 @@ struct Error : std::runtime_error {
   Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+// Caching device allocator for the library's small buffers (plans, site tensors, bond
+// matrices, work vectors): blocks of up to 8 MiB are rounded up to a power of two and
+// kept for reuse by the context that freed them, so the TDA sweep's thousands of small
+// temporaries cost neither a cudaMalloc nor the device synchronization of a cudaFree.
+// Every ABI call makes its context's pool current for the calling thread; a context
+// launches on one stream, so a reused block is ordered after the work that last used
+// it.  Larger blocks go straight to the driver.
+struct DevPool {
+  std::unordered_map<void*, size_t> live;      // pointer -> size class
+  std::map<size_t, std::vector<void*>> cached; // size class -> free blocks
+  void release() {
+    for (auto& kv : cached)
+      for (void* p : kv.second) cudaFree(p);
+    cached.clear();
+  }
+  ~DevPool() { release(); }
+};
+static thread_local DevPool* t_pool = nullptr;
+constexpr size_t POOL_MAX_BYTES = (size_t)8 << 20;
+
+struct PoolScope {
+  DevPool* prev;
+  explicit PoolScope(DevPool* p) : prev(t_pool) { t_pool = p; }
+  ~PoolScope() { t_pool = prev; }
+};
+
+static cudaError_t dev_alloc(void** p, size_t bytes) {
+  DevPool* pool = t_pool;
+  if (pool && bytes <= POOL_MAX_BYTES) {
+    size_t c = 256;
+    while (c < bytes) c <<= 1;
+    auto& fl = pool->cached[c];
+    if (!fl.empty()) {
+      *p = fl.back();
+      fl.pop_back();
+      pool->live[*p] = c;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(p, c);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      pool->release();
+      e = cudaMalloc(p, c);
+    }
+    if (e == cudaSuccess) pool->live[*p] = c;
+    return e;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess && pool) {
+    cudaGetLastError();
+    pool->release();
+    e = cudaMalloc(p, bytes);
+  }
+  return e;
+}
+
+static void dev_free(void* p) {
+  if (!p) return;
+  if (DevPool* pool = t_pool) {
+    auto it = pool->live.find(p);
+    if (it != pool->live.end()) {
+      pool->cached[it->second].push_back(p);
+      pool->live.erase(it);
+      return;
+    }
+  }
+  cudaFree(p);
+}
+
 #define CK(call)                                                                      \
   do {                                                                                \
     cudaError_t e_ = (call);                                                          \
@@ -223,7 +292,7 @@ struct OpSet {
   OpSet() = default;
   OpSet(const OpSet&) = delete;
   ~OpSet() {
-    if (d) cudaFree(d);
+    if (d) dev_free(d);
   }
   int ns() const { return basis.n(); }
   int find(const Key& k) const {
@@ -286,7 +355,7 @@ static void layout_blocks(OpSet& S) {
 
 static void alloc_zero(OpSet& S, cudaStream_t st) {
   if (S.total <= 0) return;
-  cudaError_t e = cudaMalloc(&S.d, (size_t)S.total * sizeof(double));
+  cudaError_t e = dev_alloc((void**)&S.d, (size_t)S.total * sizeof(double));
   if (e != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation of an operator set failed");
   CK(cudaMemsetAsync(S.d, 0, (size_t)S.total * sizeof(double), st));
 }
@@ -564,16 +633,16 @@ struct DevArray {
   DevArray() = default;
   DevArray(const DevArray&) = delete;
   ~DevArray() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   }
   void upload(const std::vector<T>& v, cudaStream_t st) {
     if (p) {
-      cudaFree(p);
+      dev_free(p);
       p = nullptr;
     }
     n = v.size();
     if (n == 0) return;
-    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation failed");
+    if (dev_alloc((void**)&p, n * sizeof(T)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation failed");
     CK(cudaMemcpyAsync(p, v.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
   }
 };
@@ -588,15 +657,15 @@ struct DevBuf {
     o.n = 0;
   }
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   }
   double* ensure(size_t need) {
     if (need <= n && p) return p;
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
     p = nullptr;
     n = 0;
     if (need == 0) need = 1;
-    if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation (sweep)");
+    if (dev_alloc((void**)&p, need * sizeof(double)) != cudaSuccess) throw Error(LRT_ENOMEM, "device allocation (sweep)");
     n = need;
     return p;
   }
@@ -688,7 +757,7 @@ struct SiteTensor {
   SiteTensor(const SiteTensor&) = delete;
   SiteTensor& operator=(SiteTensor&& o) noexcept {
     if (this != &o) {
-      if (d) cudaFree(d);
+      if (d) dev_free(d);
       blk_off = std::move(o.blk_off);
       blk_rows = std::move(o.blk_rows);
       sub_off = std::move(o.sub_off);
@@ -700,7 +769,7 @@ struct SiteTensor {
     return *this;
   }
   ~SiteTensor() {
-    if (d) cudaFree(d);
+    if (d) dev_free(d);
   }
 };
 
@@ -813,10 +882,10 @@ struct SigmaPlan {
   float* pool_hi[3] = {nullptr, nullptr, nullptr};
   float* pool_lo[3] = {nullptr, nullptr, nullptr};
   ~SigmaPlan() {
-    if (tbuf) cudaFree(tbuf);
+    if (tbuf) dev_free(tbuf);
     for (int q = 0; q < 3; ++q) {
-      if (pool_hi[q]) cudaFree(pool_hi[q]);
-      if (pool_lo[q]) cudaFree(pool_lo[q]);
+      if (pool_hi[q]) dev_free(pool_hi[q]);
+      if (pool_lo[q]) dev_free(pool_lo[q]);
     }
   }
 };
@@ -824,6 +893,7 @@ struct SigmaPlan {
 }  // namespace lrt
 
 struct lrt_ctx {
+  lrt::DevPool pool;     // first member: destroyed last, after every buffer returned to it
   int dev = 0;
   cudaStream_t st = nullptr;
   std::string err;
@@ -841,7 +911,7 @@ struct lrt_ctx {
   int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
   std::unique_ptr<lrt::TdaState> tda;
   ~lrt_ctx() {
-    if (derr) cudaFree(derr);
+    if (derr) lrt::dev_free(derr);
   }
 };
 
@@ -1063,7 +1133,7 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
       }
     }
   double* tmp = nullptr;
-  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
+  if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "renormalize workspace");
   for (auto& x : o1) x.C = tmp + x.c_off;
   for (auto& x : s2) x.B = tmp + x.b_off;
@@ -1074,7 +1144,7 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
   p2.run(c->st, nullptr, nullptr);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
-  if (tmp) cudaFree(tmp);
+  if (tmp) dev_free(tmp);
   N->finish_nz();
   return N;
 }
@@ -1130,7 +1200,7 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
       }
     }
   double* tmp = nullptr;
-  if (toff > 0 && cudaMalloc(&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
+  if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "renormalize workspace");
   for (auto& x : o1) x.C = tmp + x.c_off;
   for (auto& x : s2) x.B = tmp + x.b_off;
@@ -1141,7 +1211,7 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
   p2.run(c->st, nullptr, nullptr);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
-  if (tmp) cudaFree(tmp);
+  if (tmp) dev_free(tmp);
   N->finish_nz();
   return N;
 }
@@ -1463,7 +1533,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
         }
       }
   }
-  if (toff > 0 && cudaMalloc(&plan->tbuf, (size_t)toff * nvec * sizeof(double)) != cudaSuccess)
+  if (toff > 0 && dev_alloc((void**)&plan->tbuf, (size_t)toff * nvec * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "sigma workspace");
   std::vector<GemmOut> O1, O2;
   std::vector<GemmSeg> S1, S2;
@@ -1637,8 +1707,8 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   TcPlan& tp = p.tc;
   for (int q = 0; q < 3; ++q) {
     const size_t n = (size_t)std::max<int64_t>(tp.pool_size[q] * (q ? nvec : 1), 1);
-    if (cudaMalloc(&p.pool_hi[q], n * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&p.pool_lo[q], n * sizeof(float)) != cudaSuccess)
+    if (dev_alloc((void**)&p.pool_hi[q], n * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void**)&p.pool_lo[q], n * sizeof(float)) != cudaSuccess)
       throw Error(LRT_ENOMEM, "tensor-core operand pools");
     if (q == 2) {
       CK(cudaMemsetAsync(p.pool_hi[q], 0, n * sizeof(float), c->st));
@@ -1663,7 +1733,7 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
 // of the kernels' error flag (a bounded pipeline wait that expired)
 static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec) {
   if (!ctx->derr) {
-    if (cudaMalloc(&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+    if (dev_alloc((void**)&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
     CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
   }
   prepare_tc(ctx, p, nvec);
@@ -1920,7 +1990,7 @@ static double decimate(lrt_ctx* c, int i, const double* psi, const std::vector<W
   }
   // eigen-decomposition per sector (cuSOLVER, FP64 on the device)
   int* dinfo = nullptr;
-  if (cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
+  if (dev_alloc((void**)&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
   DevBuf work;
   std::vector<int64_t> eoff(wb.size());
   int64_t eo = 0;
@@ -1943,7 +2013,7 @@ static double decimate(lrt_ctx* c, int i, const double* psi, const std::vector<W
   int info = 0;
   CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  cudaFree(dinfo);
+  dev_free(dinfo);
   if (info != 0) throw Error(LRT_ECUDA, "syevd reported info " + std::to_string(info));
   // keep the M largest weights over all sectors (ties: sector order, then index)
   struct W { double v; int w; int j; };
@@ -1980,8 +2050,8 @@ static double decimate(lrt_ctx* c, int i, const double* psi, const std::vector<W
   SiteTensor Ti, Tj;
   site_layout(Ti, c->bonds[i], c->bonds[i + 1]);
   site_layout(Tj, c->bonds[i + 1], c->bonds[i + 2]);
-  if (cudaMalloc(&Ti.d, (size_t)std::max<int64_t>(Ti.total, 1) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&Tj.d, (size_t)std::max<int64_t>(Tj.total, 1) * sizeof(double)) != cudaSuccess)
+  if (dev_alloc((void**)&Ti.d, (size_t)std::max<int64_t>(Ti.total, 1) * sizeof(double)) != cudaSuccess ||
+      dev_alloc((void**)&Tj.d, (size_t)std::max<int64_t>(Tj.total, 1) * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "site tensors");
   CK(cudaMemsetAsync(Ti.d, 0, (size_t)std::max<int64_t>(Ti.total, 1) * sizeof(double), st));
   CK(cudaMemsetAsync(Tj.d, 0, (size_t)std::max<int64_t>(Tj.total, 1) * sizeof(double), st));
@@ -2140,7 +2210,7 @@ static void bond_layout(const Sectors& S, BondMat& M, cudaStream_t st) {
 static SiteTensor new_site(lrt_ctx* c, int i) {
   SiteTensor T;
   site_layout(T, c->bonds[i], c->bonds[i + 1]);
-  if (cudaMalloc(&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
+  if (dev_alloc((void**)&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "site tensor");
   CK(cudaMemsetAsync(T.d, 0, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double), c->st));
   return T;
@@ -2444,6 +2514,29 @@ struct TdaRunner {
     return out;
   }
 
+  // Initial trial vector mu at site i.  seed != 0: SplitMix64 Gaussians; seed == 0: the
+  // unit vector on the mu-th lowest diagonal element of H_0^[i] among the components where
+  // the reference is small (|C0| < 1/2), a single-site excitation.  Both projected by Q^C.
+  SiteTensor start_site(int i, int mu) {
+    if (P.seed != 0) return random_site(i, mu);
+    SiteTensor T = new_site(c, i);
+    std::vector<double> d(T.total), c0(T.total);
+    CK(cudaMemcpyAsync(d.data(), diag[i].p, d.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c0.data(), C0(i).d, c0.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    std::vector<int64_t> idx;
+    for (int64_t e = 0; e < T.total; ++e)
+      if (std::fabs(c0[e]) < 0.5) idx.push_back(e);
+    if (idx.empty()) return random_site(i, mu);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return d[a] < d[b]; });
+    const int64_t e = idx[std::min<int64_t>(mu, (int64_t)idx.size() - 1)];
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(T.d + e, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    proj_C(i, T);
+    return T;
+  }
+
   SiteTensor random_site(int i, int mu) {
     SiteTensor T = new_site(c, i);
     std::vector<double> h(T.total);
@@ -2567,16 +2660,22 @@ struct TdaRunner {
             t_lmul(c, i, lam[i], R1, C1[mu], true);
           }
         }
+        // [H_mu^{L} x h x H_0^{R}] C0 for every vector (Eq. sigv2, first line); it enters
+        // both the site sigma of the corrections and the reduced matrices below
+        std::vector<SiteTensor> dHC0(l);
+        for (int mu = 0; mu < l; ++mu) {
+          dHC0[mu] = new_site(c, i);
+          dh_left(i, HL[mu], dHC0[mu]);
+        }
         // correction vectors (Eqs. sigv1, rnorm, error, param)
         for (int mu = 0; mu < n; ++mu) {
           if (first) {
-            C1[m + mu] = random_site(i, mu);
+            C1[m + mu] = start_site(i, mu);
             continue;
           }
           SiteTensor sig = new_site(c, i), t1 = new_site(c, i);
           h0(i, C1[mu], sig);
-          dh_left(i, HL[mu], t1);
-          t_axpby(c, 1.0, t1, 1.0, sig, tmp);
+          t_axpby(c, 1.0, dHC0[mu], 1.0, sig, tmp);
           dh_right(i, HRrot[mu], t1);
           t_axpby(c, 1.0, t1, 1.0, sig, tmp);
           t_axpby(c, -theta[mu], C1[mu], 1.0, sig, tmp);     // r = sigma - theta C
@@ -2588,20 +2687,43 @@ struct TdaRunner {
           C1[m + mu] = std::move(z);
         }
         // projected coefficients (Eq. cwfn1st) and reduced matrices (Eqs. hleft2, sleft2)
-        std::vector<SiteTensor> Ct(l), H0Ct(l), dHC0(l);
+        std::vector<SiteTensor> Ct(l), H0Ct(l);
         for (int mu = 0; mu < l; ++mu) {
           Ct[mu] = proj_L(i, C1[mu]);
           H0Ct[mu] = new_site(c, i);
           h0(i, Ct[mu], H0Ct[mu]);
-          dHC0[mu] = new_site(c, i);
-          dh_left(i, HL[mu], dHC0[mu]);
         }
-        for (int a = 0; a < l; ++a)
-          for (int b2 = 0; b2 < l; ++b2) {
-            Hr[(size_t)a * l + b2] += t_dot(c, Ct[a], H0Ct[b2], tmp) + t_dot(c, Ct[a], dHC0[b2], tmp) +
-                                      t_dot(c, dHC0[a], Ct[b2], tmp);
-            Sr[(size_t)a * l + b2] += t_dot(c, Ct[a], Ct[b2], tmp);
+        {
+          // all l x l products of the site at once: <Ct|H0 Ct>, <Ct|dH C0>, <Ct|Ct>
+          std::vector<const double*> pc(l), ph(l), pd(l);
+          for (int a = 0; a < l; ++a) {
+            pc[a] = Ct[a].d;
+            ph[a] = H0Ct[a].d;
+            pd[a] = dHC0[a].d;
           }
+          DevArray<const double*> dc, dh, dd;
+          dc.upload(pc, c->st);
+          dh.upload(ph, c->st);
+          dd.upload(pd, c->st);
+          DevBuf prod;
+          prod.ensure((size_t)3 * l * l);
+          const int64_t nel = Ct[0].total;
+          launch_pair_dots(dc.p, dh.p, l, l, nel, prod.p, c->st);
+          launch_pair_dots(dc.p, dd.p, l, l, nel, prod.p + (size_t)l * l, c->st);
+          launch_pair_dots(dc.p, dc.p, l, l, nel, prod.p + (size_t)2 * l * l, c->st);
+          std::vector<double> hp((size_t)3 * l * l);
+          CK(cudaGetLastError());
+          CK(cudaMemcpyAsync(hp.data(), prod.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+          CK(cudaStreamSynchronize(c->st));
+          const double* D1 = hp.data();
+          const double* D2 = D1 + (size_t)l * l;
+          const double* D3 = D2 + (size_t)l * l;
+          for (int a = 0; a < l; ++a)
+            for (int b2 = 0; b2 < l; ++b2) {
+              Hr[(size_t)a * l + b2] += D1[(size_t)a * l + b2] + D2[(size_t)a * l + b2] + D2[(size_t)b2 * l + a];
+              Sr[(size_t)a * l + b2] += D3[(size_t)a * l + b2];
+            }
+        }
         // Eqs. left1st and lopr1st
         for (int mu = 0; mu < l; ++mu) {
           L1[mu][i] = new_site(c, i);
@@ -2702,10 +2824,10 @@ static void tda_prepare_impl(lrt_ctx* c, double* norm_out) {
   DevBuf tmp, work, A, U, V, S;
   tmp.ensure(4);
   int* dinfo = nullptr;
-  if (cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
+  if (dev_alloc((void**)&dinfo, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
   struct InfoGuard {
     int* p;
-    ~InfoGuard() { cudaFree(p); }
+    ~InfoGuard() { dev_free(p); }
   } ig{dinfo};
 
   // normalize the centre
@@ -2912,6 +3034,7 @@ static int guard(lrt_ctx* c, F&& f) {
   if (!c) return LRT_EINVAL;
   try {
     CK(cudaSetDevice(c->dev));
+    PoolScope ps(&c->pool);
     f();
     c->err.clear();
     return LRT_OK;
@@ -2953,7 +3076,10 @@ int lrt_destroy(lrt_t ctx) {
   if (!ctx) return LRT_EINVAL;
   cudaSetDevice(ctx->dev);
   cudaStreamSynchronize(ctx->st);
-  delete ctx;
+  {
+    PoolScope ps(&ctx->pool);
+    delete ctx;
+  }
   return LRT_OK;
 }
 
@@ -2998,7 +3124,7 @@ int mps_load(lrt_t ctx, const lrt_mps_desc* m) {
         site_layout(out[i], bonds[i], bonds[i + 1]);
         if (out[i].total > 0) {
           if (!data[i]) throw Error(LRT_EINVAL, "mps_load: missing site data");
-          if (cudaMalloc(&out[i].d, (size_t)out[i].total * sizeof(double)) != cudaSuccess)
+          if (dev_alloc((void**)&out[i].d, (size_t)out[i].total * sizeof(double)) != cudaSuccess)
             throw Error(LRT_ENOMEM, "mps_load: device allocation");
           CK(cudaMemcpyAsync(out[i].d, data[i], (size_t)out[i].total * sizeof(double),
                              cudaMemcpyHostToDevice, ctx->st));
@@ -3106,7 +3232,7 @@ int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam) {
     for (int i = 0; i < ctx->k; ++i) {
       SiteTensor T;
       site_layout(T, ctx->bonds[i], ctx->bonds[i + 1]);
-      if (cudaMalloc(&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
+      if (dev_alloc((void**)&T.d, (size_t)std::max<int64_t>(T.total, 1) * sizeof(double)) != cudaSuccess)
         throw Error(LRT_ENOMEM, "tda_load");
       if (!C0[i]) throw Error(LRT_EINVAL, "tda_load: missing C0");
       CK(cudaMemcpyAsync(T.d, C0[i], (size_t)T.total * sizeof(double), cudaMemcpyHostToDevice, ctx->st));

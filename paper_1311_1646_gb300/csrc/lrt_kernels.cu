@@ -235,6 +235,31 @@ void launch_dots(const double* V, int64_t ld, int m, const double* w, int64_t n,
   dots_kernel<<<m, 256, 0, st>>>(V, ld, m, w, n, out);
 }
 
+// out[a * nb + b] = A[a] . B[b] for vectors given by pointer arrays (one block per pair)
+__global__ void __launch_bounds__(256) pair_dots_kernel(const double* const* __restrict__ A,
+                                                        const double* const* __restrict__ B, int nb, int64_t n,
+                                                        double* __restrict__ out) {
+  __shared__ double red[256];
+  const int a = blockIdx.x / nb, b = blockIdx.x % nb;
+  const double* x = A[a];
+  const double* y = B[b];
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(x[e], y[e], acc);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+void launch_pair_dots(const double* const* A, const double* const* B, int na, int nb, int64_t n, double* out,
+                      cudaStream_t st) {
+  if (na <= 0 || nb <= 0) return;
+  pair_dots_kernel<<<na * nb, 256, 0, st>>>(A, B, nb, n, out);
+}
+
 __global__ void __launch_bounds__(256) lincomb_kernel(const double* __restrict__ V, int64_t ld, int m,
                                                       const double* __restrict__ coef, int64_t n,
                                                       double* __restrict__ out, double beta) {

@@ -139,6 +139,9 @@ constexpr int GEMM_TN = 32;   // output tile columns
 namespace lrt {
 // Davidson vector operations (FP64): V holds m vectors of length n with stride ld.
 void launch_dots(const double* V, int64_t ld, int m, const double* w, int64_t n, double* out, cudaStream_t st);
+// out[a * nb + b] = A[a] . B[b], a < na, b < nb (device arrays of device pointers, length n each)
+void launch_pair_dots(const double* const* A, const double* const* B, int na, int nb, int64_t n, double* out,
+                      cudaStream_t st);
 void launch_lincomb(const double* V, int64_t ld, int m, const double* coef, int64_t n, double* out, double beta,
                     cudaStream_t st);
 void launch_precond(const double* r, const double* d, double theta, int64_t n, double* t, cudaStream_t st);
