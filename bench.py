@@ -341,7 +341,45 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
                                      "fp64_tflops": fl / t64 / 1e9, "mixed_tflops": fl / tmx / 1e9,
                                      "speedup": t64 / tmx, "max_rel_err_vs_fp64": err}
     w.close()
-    # (3) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU
+    # (3) 32 independent instances (config 4 shapes), one-site sigma with 4 vectors at the
+    # middle site of each: one grouped launch per phase (sigma_batched, CUDA graph replay)
+    # against the same instances called one after another
+    insts = []
+    for b in range(32):
+        cfg = synth.config(4, batch_index=b)
+        H = cfg["ham"]
+        i = H.k // 2 - 1
+        m = synth.mixed_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 900 + b, center=i)
+        c = pkg.Context(device)
+        c.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        c.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, i)
+        for bb in range(i):
+            c.renormalize(bb, +1)
+        for bb in range(H.k - 1, i, -1):
+            c.renormalize(bb, -1)
+        n, _ = c.wfn_layout(i, 1)
+        x = torch.tensor(synth.random_vector(n * 4, 3 + b), dtype=torch.float64, device=f"cuda:{device}")
+        insts.append((c, i, x, torch.empty_like(x)))
+    bctx = [a[0] for a in insts]
+    bsite = [a[1] for a in insts]
+    bx = [a[2] for a in insts]
+    by = [a[3] for a in insts]
+    batch = {"instances": 32, "nvec": 4, "nsite": 1}
+    for name, prec in (("fp64", pkg.LRT_FP64), ("mixed", pkg.LRT_MIXED)):
+        fl = 0.0
+        for c, i, x, y in insts:
+            c.sigma(i, 1, x, y, nvec=4, precision=prec)
+            fl += c.stats()["flops"]
+        pkg.sigma_batched(bctx, bsite, 1, bx, by, nvec=4, precision=prec)
+        pkg.sigma_batched(bctx, bsite, 1, bx, by, nvec=4, precision=prec)
+        seq = _timed(lambda: [c.sigma(i, 1, x, y, nvec=4, precision=prec) for c, i, x, y in insts], 3, stream)
+        bat = _timed(lambda: pkg.sigma_batched(bctx, bsite, 1, bx, by, nvec=4, precision=prec), 5, stream)
+        batch[name] = {"gflop": fl / 1e9, "sequential_ms": seq, "batched_ms": bat,
+                       "sequential_tflops": fl / seq / 1e9, "batched_tflops": fl / bat / 1e9}
+    for c in bctx:
+        c.close()
+    out["batch32_config4_onesite"] = batch
+    # (4) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU
     cfg = synth.config(1)
     H = cfg["ham"]
     nr = cfg["nroots"]

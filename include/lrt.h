@@ -185,6 +185,19 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega
 int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors);
 int mps_get_site(lrt_t ctx, int site, double* host_out, int64_t* nelem);
 
+/* sigma_batched: y_j = H_eff^(j) x_j for n_inst independent instances, each its own
+ * context (its own Hamiltonian and MPS, on the same device), in one grouped launch per
+ * phase: the instances' block products are merged into one task list (FP64) or one
+ * persistent tensor-core work stream (LRT_MIXED) with tiles dealt longest-first over
+ * the SMs.  Instance j uses (sites[j], nsite, nvec) like sigma() and x_dev[j], y_dev[j]
+ * in its wfn_layout.  The launch runs on ctxs[0]'s stream; the other contexts must be
+ * idle (or use the same stream).  The merged plan is cached in ctxs[0] and rebuilt when
+ * an instance's plan changes (after renormalize); from the second call with the same
+ * x/y pointers on, the whole call is replayed from a captured CUDA graph.  Errors are
+ * reported on ctxs[0]. */
+int sigma_batched(const lrt_t* ctxs, int n_inst, const int* sites, int nsite, int nvec, const double* const* x_dev,
+                  double* const* y_dev, int precision);
+
 /* Statistics of the last sigma call: algorithmic FLOPs (2mnk summed over the
  * products of non-zero sub-blocks of the operators, zero padding excluded),
  * FLOPs issued by the kernels (fused blocks, zero sub-blocks included), bytes

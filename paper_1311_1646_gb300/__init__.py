@@ -20,7 +20,7 @@ LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda"]
+           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda", "sigma_batched"]
 
 _lib = None
 
@@ -88,6 +88,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     ppd = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
     lib.tda_load.argtypes = [vp, ppd, ppd]
     lib.tda_prepare.argtypes = [vp, dp]
+    lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
+                                  ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
     for name in EXPORTS:
         if name != "lrt_last_error":
@@ -268,3 +270,19 @@ class Context:
         self._check(self.lib.sigma_stats(self.h, ctypes.byref(s)), "sigma_stats")
         return {"flops": s.flops, "flops_issued": s.flops_issued, "op_bytes": s.op_bytes, "launches": s.launches,
                 "n_terms": s.n_terms, "n_products": s.n_products}
+
+
+def sigma_batched(ctxs: list, sites: list, nsite: int, xs: list, ys: list, nvec: int = 1,
+                  precision: int = LRT_FP64):
+    """y_j = H_eff^(j) x_j for several independent instances (one Context each) in one grouped
+    launch per phase; the first context's stream runs it."""
+    n = len(ctxs)
+    if not (len(sites) == len(xs) == len(ys) == n) or n == 0:
+        raise LrtError("sigma_batched: ctxs, sites, xs and ys must have the same non-zero length")
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
+    st = (ctypes.c_int * n)(*sites)
+    px = (ctypes.c_void_p * n)(*[_tensor_ptr(x, ctxs[j].wfn_layout(sites[j], nsite)[0] * nvec)
+                                 for j, x in enumerate(xs)])
+    py = (ctypes.c_void_p * n)(*[_tensor_ptr(y, ctxs[j].wfn_layout(sites[j], nsite)[0] * nvec)
+                                 for j, y in enumerate(ys)])
+    ctxs[0]._check(ctxs[0].lib.sigma_batched(hs, n, st, nsite, nvec, px, py, precision), "sigma_batched")

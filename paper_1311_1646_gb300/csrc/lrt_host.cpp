@@ -859,6 +859,7 @@ struct TcPlan {
 };
 
 struct SigmaPlan {
+  uint64_t serial = 0;      // unique per plan (batched launches detect rebuilt plans by it)
   GemmPlan p1, p2;
   DevArray<DiagOut> douts;
   DevArray<DiagTerm> dterms;
@@ -892,8 +893,13 @@ struct SigmaPlan {
 
 }  // namespace lrt
 
+namespace lrt {
+struct BatchPlan;
+}
 struct lrt_ctx {
   lrt::DevPool pool;     // first member: destroyed last, after every buffer returned to it
+  uint64_t id = 0;       // unique per context (batched launches identify instances by it)
+  std::map<std::string, std::unique_ptr<lrt::BatchPlan>> batches;   // batched sigma led by this context
   int dev = 0;
   cudaStream_t st = nullptr;
   std::string err;
@@ -1303,6 +1309,8 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   if (I.e_core != 0.0) terms.push_back({I.e_core, {KI, -1, -1, 0}, {KI, -1, -1, 0}});
 
   auto plan = std::make_unique<SigmaPlan>();
+  static uint64_t next_serial = 0;
+  plan->serial = ++next_serial;
   plan->nelem = nelem;
   plan->n_terms = (int)terms.size();
 
@@ -1625,28 +1633,41 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
 }
 
-// Work stream of one tensor-core launch: tiles of 128 x 64 of every output and
-// vector in longest-first order, CTA b takes the tiles b, b + n, b + 2n, ...; each
-// tile is a header followed by its block products with TC-matrix operands resolved.
-static void build_tc_stream(const TcPlan& tp, const std::vector<TcPlanOut>& outs, int nvec, int64_t nelem,
-                            float* const* phi, float* const* plo, DevArray<TcItem>& items, DevArray<int>& begins,
-                            int& nctas, cudaStream_t st) {
+// Work stream of one tensor-core launch over one or several plans (instances): tiles
+// of 128 x 64 of every output, vector and instance in longest-first order, CTA b takes
+// the tiles b, b + n, b + 2n, ...; each tile is a header followed by its block products
+// with TC-matrix operands resolved.
+struct TcSource {
+  const TcPlan* tp;
+  const std::vector<TcPlanOut>* outs;
+  float* const* phi;
+  float* const* plo;
+  int64_t nelem;
+  int inst;
+};
+static void build_tc_stream(const std::vector<TcSource>& src, int nvec, DevArray<TcItem>& items,
+                            DevArray<int>& begins, int& nctas, cudaStream_t st) {
   const int TM = tc_tile_m(), TN = tc_tile_n();
-  struct Tile { int v, o, a, b; int64_t k; };
+  struct Tile { int s, v, o, a, b; int64_t k; };
   std::vector<Tile> tiles;
-  for (int v = 0; v < nvec; ++v)
-    for (size_t i = 0; i < outs.size(); ++i) {
-      int64_t kt = 0;
-      for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
-      for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
-        for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b) tiles.push_back(Tile{v, (int)i, a, b, kt});
-    }
+  for (size_t si = 0; si < src.size(); ++si) {
+    const TcPlan& tp = *src[si].tp;
+    const std::vector<TcPlanOut>& outs = *src[si].outs;
+    for (int v = 0; v < nvec; ++v)
+      for (size_t i = 0; i < outs.size(); ++i) {
+        int64_t kt = 0;
+        for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
+        for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
+          for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b)
+            tiles.push_back(Tile{(int)si, v, (int)i, a, b, kt});
+      }
+  }
   std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& x, const Tile& y) { return x.k > y.k; });
   const int nt = (int)tiles.size();
   nctas = nt > 0 ? tc_num_ctas(nt) : 0;
-  auto base = [&](const TcMat& m, int v, bool hi) -> float* {
-    float* p = (hi ? phi : plo)[m.pool];
-    return p + (m.pool ? (int64_t)v * tp.pool_size[m.pool] : 0) + m.off;
+  auto base = [&](const TcSource& sc, const TcMat& m, int v, bool hi) -> float* {
+    float* p = (hi ? sc.phi : sc.plo)[m.pool];
+    return p + (m.pool ? (int64_t)v * sc.tp->pool_size[m.pool] : 0) + m.off;
   };
   std::vector<TcItem> it;
   std::vector<int> beg;
@@ -1654,23 +1675,26 @@ static void build_tc_stream(const TcPlan& tp, const std::vector<TcPlanOut>& outs
     beg.push_back((int)it.size());
     for (int w = b; w < nt; w += nctas) {
       const Tile& t = tiles[w];
-      const TcPlanOut& o = outs[t.o];
+      const TcSource& sc = src[t.s];
+      const TcPlan& tp = *sc.tp;
+      const TcPlanOut& o = (*sc.outs)[t.o];
       TcItem h{};
       h.type = TC_ITEM_TILE;
       h.t.m0 = t.a * TM;
       h.t.n0 = t.b * TN;
       h.t.mt = std::min(TM, o.m - h.t.m0);
       h.t.nt = std::min(TN, o.n - h.t.n0);
+      h.t.inst = sc.inst;
       if (o.tmat >= 0) {
         const TcMat& m = tp.mats[o.tmat];
         h.t.c_rel = 2;
-        h.t.t_hi = base(m, t.v, true);
-        h.t.t_lo = base(m, t.v, false);
+        h.t.t_hi = base(sc, m, t.v, true);
+        h.t.t_lo = base(sc, m, t.v, false);
         h.t.t_rp = m.Rp;
         h.t.t_k = m.K;
       } else {
         h.t.c_rel = 1;
-        h.t.c_off = o.c_off + (int64_t)t.v * nelem;
+        h.t.c_off = o.c_off + (int64_t)t.v * sc.nelem;
         h.t.ldc = o.ldc;
       }
       it.push_back(h);
@@ -1684,10 +1708,10 @@ static void build_tc_stream(const TcPlan& tp, const std::vector<TcPlanOut>& outs
           throw Error(LRT_EINVAL, "tensor-core plan: operand smaller than its product");
         TcItem r{};
         r.type = TC_ITEM_SEG;
-        r.s.a_hi = base(A, t.v, true);
-        r.s.a_lo = base(A, t.v, false);
-        r.s.b_hi = base(B, t.v, true);
-        r.s.b_lo = base(B, t.v, false);
+        r.s.a_hi = base(sc, A, t.v, true);
+        r.s.a_lo = base(sc, A, t.v, false);
+        r.s.b_hi = base(sc, B, t.v, true);
+        r.s.b_lo = base(sc, B, t.v, false);
         r.s.a_rp = A.Rp;
         r.s.b_rp = B.Rp;
         r.s.k = g.k;
@@ -1723,8 +1747,8 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
     CK(cudaStreamSynchronize(c->st));
   }
   p.xpack.upload(tp.pack1, c->st);
-  build_tc_stream(tp, tp.out1, nvec, p.nelem, p.pool_hi, p.pool_lo, p.tci1, p.tcb1, p.tcn1, c->st);
-  build_tc_stream(tp, tp.out2, nvec, p.nelem, p.pool_hi, p.pool_lo, p.tci2, p.tcb2, p.tcn2, c->st);
+  build_tc_stream({TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, p.tci1, p.tcb1, p.tcn1, c->st);
+  build_tc_stream({TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, p.tci2, p.tcb2, p.tcn2, c->st);
   CK(cudaStreamSynchronize(c->st));
   p.tc_ready = true;
 }
@@ -2984,6 +3008,203 @@ static void tda_prepare_impl(lrt_ctx* c, double* norm_out) {
 }  // namespace lrt
 
 // ===========================================================================
+// batched sigma: several independent instances (contexts) in one grouped launch per
+// phase, replayed from a CUDA graph while the caller's buffers stay the same
+// ===========================================================================
+namespace lrt {
+
+struct BatchPlan {
+  std::vector<uint64_t> ids, serials;   // instances and the plans this batch was built from
+  int precision = LRT_FP64;
+  double flops = 0.0;
+  // FP64: merged task lists, bases (x, y, T) per instance
+  GemmPlan p1, p2;
+  DevArray<GemmBases> bases;
+  std::vector<GemmBases> hbases;
+  // split-TF32: merged work streams, y per instance
+  DevArray<TcItem> tci1, tci2;
+  DevArray<int> tcb1, tcb2;
+  int tcn1 = 0, tcn2 = 0;
+  DevArray<double*> ys;
+  std::vector<double*> hys;
+  // one call captured as a CUDA graph
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const double*> gx;
+  std::vector<double*> gy;
+  bool ran = false;
+  cudaStream_t cap = nullptr;   // private stream the call is captured on (the caller's may be the legacy one)
+  ~BatchPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+template <class T>
+static std::vector<T> download(const DevArray<T>& a, cudaStream_t st) {
+  std::vector<T> h(a.n);
+  if (a.n) CK(cudaMemcpyAsync(h.data(), a.p, a.n * sizeof(T), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return h;
+}
+
+static void merge_fp64(GemmPlan& out, const std::vector<SigmaPlan*>& plans, bool phase2, cudaStream_t st) {
+  std::vector<GemmOut> O;
+  std::vector<GemmSeg> S;
+  for (size_t j = 0; j < plans.size(); ++j) {
+    const GemmPlan& g = phase2 ? plans[j]->p2 : plans[j]->p1;
+    std::vector<GemmOut> o = download(g.outs, st);
+    std::vector<GemmSeg> sg = download(g.segs, st);
+    const int sb = (int)S.size();
+    for (GemmOut x : o) {
+      x.seg_begin += sb;
+      x.inst = (int)j;
+      O.push_back(x);
+    }
+    S.insert(S.end(), sg.begin(), sg.end());
+  }
+  build_gemm(out, O, S, st);
+}
+
+// one batched call (the graph body): no host synchronization inside
+static void batch_issue(lrt_ctx* c0, BatchPlan& B, const std::vector<SigmaPlan*>& plans,
+                        const std::vector<const double*>& x, int nvec, cudaStream_t st) {
+  if (B.precision == LRT_MIXED) {
+    for (size_t j = 0; j < plans.size(); ++j) {
+      SigmaPlan& p = *plans[j];
+      launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x[j], p.nelem, p.pool_hi[1], p.pool_lo[1],
+                     p.tc.pool_size[1], nvec, st);
+    }
+    const TcOut to{nullptr, B.ys.p};
+    launch_gemm_tf32x3(B.tci1.p, B.tcb1.p, B.tcn1, to, c0->derr, st);
+    launch_gemm_tf32x3(B.tci2.p, B.tcb2.p, B.tcn2, to, c0->derr, st);
+  } else {
+    launch_gemm_fp64_multi(B.p1.outs.p, B.p1.segs.p, B.p1.tiles.p, B.p1.ntiles, B.bases.p, st);
+    launch_gemm_fp64_multi(B.p2.outs.p, B.p2.segs.p, B.p2.tiles.p, B.p2.ntiles, B.bases.p, st);
+  }
+}
+
+static void sigma_batched_impl(lrt_ctx* const* ctxs, int n, const int* sites, int nsite, int nvec,
+                               const double* const* x, double* const* y, int precision) {
+  lrt_ctx* c0 = ctxs[0];
+  std::vector<SigmaPlan*> plans(n);
+  std::string key = std::to_string(nsite) + ":" + std::to_string(nvec) + ":" + std::to_string(precision);
+  for (int j = 0; j < n; ++j) {
+    lrt_ctx* c = ctxs[j];
+    if (!c) throw Error(LRT_EINVAL, "sigma_batched: NULL context");
+    if (c->dev != c0->dev) throw Error(LRT_EINVAL, "sigma_batched: contexts on different devices");
+    if (!c->have_mps || !c->have_ham) throw Error(LRT_ESTATE, "sigma_batched: op_build and mps_load first");
+    if (sites[j] < 0 || sites[j] + nsite > c->k || !c->L[sites[j]])
+      throw Error(LRT_ESTATE, "sigma_batched: environment of instance " + std::to_string(j) + " missing");
+    if (!x[j] || !y[j]) throw Error(LRT_EINVAL, "sigma_batched: NULL vector");
+    PoolScope ps(&c->pool);
+    plans[j] = &get_plan(c, sites[j], nsite, nvec);
+    key += ":" + std::to_string(c->id) + "/" + std::to_string(sites[j]);
+  }
+  auto& slot = c0->batches[key];
+  bool fresh = false;
+  if (slot) {
+    for (int j = 0; j < n && !fresh; ++j) fresh = slot->serials[j] != plans[j]->serial;
+  }
+  if (!slot || fresh) {
+    auto B = std::make_unique<BatchPlan>();
+    B->precision = precision;
+    for (int j = 0; j < n; ++j) {
+      B->ids.push_back(ctxs[j]->id);
+      B->serials.push_back(plans[j]->serial);
+      B->flops += plans[j]->flops_alg;
+    }
+    if (precision == LRT_MIXED) {
+      std::vector<TcSource> s1, s2;
+      for (int j = 0; j < n; ++j) {
+        PoolScope ps(&ctxs[j]->pool);
+        prepare_tc(ctxs[j], *plans[j], nvec);
+        SigmaPlan& p = *plans[j];
+        s1.push_back(TcSource{&p.tc, &p.tc.out1, p.pool_hi, p.pool_lo, p.nelem, j});
+        s2.push_back(TcSource{&p.tc, &p.tc.out2, p.pool_hi, p.pool_lo, p.nelem, j});
+      }
+      build_tc_stream(s1, nvec, B->tci1, B->tcb1, B->tcn1, c0->st);
+      build_tc_stream(s2, nvec, B->tci2, B->tcb2, B->tcn2, c0->st);
+    } else {
+      merge_fp64(B->p1, plans, false, c0->st);
+      merge_fp64(B->p2, plans, true, c0->st);
+    }
+    CK(cudaStreamSynchronize(c0->st));
+    slot = std::move(B);
+  }
+  BatchPlan& B = *slot;
+  if (precision == LRT_MIXED && !c0->derr) {
+    if (dev_alloc((void**)&c0->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+    CK(cudaMemsetAsync(c0->derr, 0, sizeof(int), c0->st));
+  }
+  // per-call buffers: re-upload the base tables when they change (invalidates the graph)
+  std::vector<const double*> xv(x, x + n);
+  std::vector<double*> yv(y, y + n);
+  for (int j = 0; j < n; ++j) {
+    const double* lo = x[j];
+    const double* hi = x[j] + plans[j]->nelem * nvec;
+    for (int q = 0; q < n; ++q)
+      if ((const double*)y[q] < hi && lo < (const double*)y[q] + plans[q]->nelem * nvec)
+        throw Error(LRT_EINVAL, "sigma_batched: an x overlaps a y");
+  }
+  const bool same = B.ran && xv == B.gx && yv == B.gy;
+  if (!same) {
+    if (precision == LRT_MIXED) {
+      B.hys = yv;
+      B.ys.upload(B.hys, c0->st);
+    } else {
+      B.hbases.resize(n);
+      for (int j = 0; j < n; ++j) B.hbases[j] = GemmBases{x[j], y[j], plans[j]->tbuf};
+      B.bases.upload(B.hbases, c0->st);
+    }
+    if (B.exec) {
+      cudaGraphExecDestroy(B.exec);
+      B.exec = nullptr;
+    }
+  }
+  if (same && !B.exec) {
+    // second call with the same buffers: capture the call once, replay it from now on
+    cudaGraph_t g = nullptr;
+    if (!B.cap) CK(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal));
+    batch_issue(c0, B, plans, xv, nvec, B.cap);
+    const cudaError_t ce = cudaStreamEndCapture(B.cap, &g);
+    if (ce != cudaSuccess || !g) throw Error(LRT_ECUDA, "sigma_batched: graph capture failed");
+    const cudaError_t ie = cudaGraphInstantiate(&B.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      B.exec = nullptr;
+      throw Error(LRT_ECUDA, "sigma_batched: graph instantiation failed");
+    }
+  }
+  if (B.exec) {
+    CK(cudaGraphLaunch(B.exec, c0->st));
+  } else {
+    batch_issue(c0, B, plans, xv, nvec, c0->st);
+  }
+  CK(cudaGetLastError());
+  B.gx = xv;
+  B.gy = yv;
+  B.ran = true;
+  if (precision == LRT_MIXED) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c0->derr, sizeof(int), cudaMemcpyDeviceToHost, c0->st));
+    CK(cudaStreamSynchronize(c0->st));
+    if (flag) {
+      CK(cudaMemsetAsync(c0->derr, 0, sizeof(int), c0->st));
+      throw Error(LRT_ETIMEOUT, "sigma_batched: a tensor-core pipeline wait expired; results are invalid");
+    }
+  }
+  c0->last.flops = B.flops;
+  c0->last.flops_issued = 0.0;
+  c0->last.launches = 2;
+  c0->last.n_terms = 0;
+  c0->last.n_products = 0;
+  c0->last.op_bytes = 0.0;
+}
+
+}  // namespace lrt
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 using namespace lrt;
@@ -3066,6 +3287,8 @@ int lrt_create(lrt_t* out, int device, void* cuda_stream) {
   }
   auto* c = new (std::nothrow) lrt_ctx();
   if (!c) return LRT_ENOMEM;
+  static uint64_t next_id = 0;
+  c->id = ++next_id;
   c->dev = device;
   c->st = (cudaStream_t)cuda_stream;
   *out = c;
@@ -3198,6 +3421,17 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     ctx->last.n_terms = p.n_terms;
     ctx->last.n_products = p.n_products;
     ctx->last.op_bytes = p.op_bytes;
+  });
+}
+
+int sigma_batched(const lrt_t* ctxs, int n_inst, const int* sites, int nsite, int nvec, const double* const* x_dev,
+                  double* const* y_dev, int precision) {
+  if (!ctxs || n_inst <= 0 || !ctxs[0]) return LRT_EINVAL;
+  return guard(ctxs[0], [&] {
+    if (!sites || !x_dev || !y_dev || nsite < 1 || nsite > 2 || nvec <= 0)
+      throw Error(LRT_EINVAL, "sigma_batched: bad arguments");
+    if (precision != LRT_FP64 && precision != LRT_MIXED) throw Error(LRT_EINVAL, "sigma_batched: bad precision");
+    sigma_batched_impl(ctxs, n_inst, sites, nsite, nvec, x_dev, y_dev, precision);
   });
 }
 

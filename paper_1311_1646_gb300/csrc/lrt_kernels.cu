@@ -84,13 +84,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOu
                                                                     const int3* __restrict__ tiles, int ntiles,
                                                                     const double* __restrict__ xbase,
                                                                     double* __restrict__ ybase,
-                                                                    double* __restrict__ tbase) {
+                                                                    double* __restrict__ tbase,
+                                                                    const GemmBases* __restrict__ multi) {
   __shared__ double As[GEMM_TM][KC + 1];
   __shared__ double Bs[KC][GEMM_TN + 1];
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
   const GemmOut o = outs[wi.x];
+  if (multi) {
+    const GemmBases b = multi[o.inst];
+    xbase = b.x;
+    ybase = b.y;
+    tbase = b.t;
+  }
   const int m0 = wi.y * GEMM_TM, n0 = wi.z * GEMM_TN;
   const int mt = min(GEMM_TM, o.m - m0), nt = min(GEMM_TN, o.n - n0);
   const int ne = mt * nt;
@@ -144,7 +151,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOu
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st) {
   if (ntiles <= 0) return;
-  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase);
+  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase, nullptr);
+}
+
+void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                            const GemmBases* bases, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, nullptr, nullptr, nullptr, bases);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,6 +31,7 @@ struct GemmOut {
   int seg_begin, seg_count;
   int accumulate;
   int c_rel;
+  int inst;      // batched launches: index of the instance whose bases the rel pointers use
 };
 struct GemmSeg {
   const double* A;
@@ -61,6 +62,14 @@ void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* t
                    cudaStream_t st);
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st);
+// batched form: the bases of output o are bases[o.inst] (device array)
+struct GemmBases {
+  const double* x;
+  double* y;
+  double* t;
+};
+void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                            const GemmBases* bases, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
 // Split-TF32 tensor-core variant of the grouped GEMM.
@@ -84,7 +93,7 @@ struct TcTileHdr {
   int c_rel;
   int accumulate;
   int t_rp, t_k;      // TC-matrix output: padded rows, valid K (= output columns)
-  int pad;
+  int inst;           // batched launches: instance whose y receives a c_rel == 1 output
 };
 struct TcSegRec {
   const float* a_hi;  // TC matrix A (rows = output rows) and B (rows = output columns)
@@ -105,7 +114,8 @@ struct TcItem {
   };
 };
 struct TcOut {
-  double* y;
+  double* y;                // y of a single-instance launch
+  double* const* ys;        // batched launches: y of instance i is ys[i] (device array), else NULL
 };
 // number of CTAs (one per SM) the tensor-core launch uses for ntiles tiles; CTA b
 // takes tiles b, b + n, b + 2n, ... of the host's order

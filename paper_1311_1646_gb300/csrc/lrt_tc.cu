@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           for (int c = 0; c < TC_N; ++c)
             *(double*)(stg + (rr * STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
           __syncwarp();
-          double* C = (t.c_rel == 1 ? out.y + t.c_off : t.C);
+          double* C = (t.c_rel == 1 ? (out.ys ? out.ys[t.inst] : out.y) + t.c_off : t.C);
           for (int r = 0; r < nrows; ++r) {
             double* dst = C + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
             for (int c = lane; c < t.nt; c += 32) {
