@@ -635,6 +635,10 @@ struct DevArray {
   ~DevArray() {
     if (p) dev_free(p);
   }
+  void swap(DevArray& o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+  }
   void upload(const std::vector<T>& v, cudaStream_t st) {
     if (p) {
       dev_free(p);
@@ -879,6 +883,7 @@ struct SigmaPlan {
   DevArray<TcItem> tci1, tci2;    // per-CTA work streams of the two phases
   DevArray<int> tcb1, tcb2;
   int tcn1 = 0, tcn2 = 0;
+  int tn1 = 64, tn2 = 64;         // tile widths chosen by the autotuner
   DevArray<TcPack> xpack;         // packing of x into pool 1 (every call)
   float* pool_hi[3] = {nullptr, nullptr, nullptr};
   float* pool_lo[3] = {nullptr, nullptr, nullptr};
@@ -1645,9 +1650,9 @@ struct TcSource {
   int64_t nelem;
   int inst;
 };
-static void build_tc_stream(const std::vector<TcSource>& src, int nvec, DevArray<TcItem>& items,
+static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, DevArray<TcItem>& items,
                             DevArray<int>& begins, int& nctas, cudaStream_t st) {
-  const int TM = tc_tile_m(), TN = tc_tile_n();
+  const int TM = tc_tile_m();
   struct Tile { int s, v, o, a, b; int64_t k; };
   std::vector<Tile> tiles;
   for (size_t si = 0; si < src.size(); ++si) {
@@ -1725,6 +1730,72 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, DevArray
   begins.upload(beg, st);
 }
 
+// Autotuner of the tensor-core tile width (128 x 32 or 128 x 64) for one launch.
+// Launches with enough tiles to occupy the GPU several times are timed once with each
+// width (second of two runs, CUDA events, outputs into scratch buffers); smaller ones
+// take 32 when the work-weighted output width is at most 32.  Returns the width, with
+// the matching stream in items/begins/nctas.
+static int tune_tc_stream(lrt_ctx* c, const std::vector<TcSource>& src, int nvec, TcOut scratch,
+                          DevArray<TcItem>& items, DevArray<int>& begins, int& nctas) {
+  cudaStream_t st = c->st;
+  build_tc_stream(src, nvec, 64, items, begins, nctas, st);
+  double wn = 0.0, w = 0.0;
+  int64_t ntiles = 0;
+  for (const TcSource& sc : src)
+    for (const TcPlanOut& o : *sc.outs) {
+      int64_t kt = 0;
+      for (int q = 0; q < o.seg_count; ++q) kt += sc.tp->segs[o.seg_begin + q].k;
+      wn += (double)kt * o.m * std::min(o.n, 64);
+      w += (double)kt * o.m;
+      ntiles += (int64_t)((o.m + 127) / 128) * ((o.n + 63) / 64) * nvec;
+    }
+  const int heuristic = (w > 0.0 && wn / w <= 32.0) ? 32 : 64;
+  if (ntiles < 4 * (int64_t)tc_num_ctas(1 << 30)) {
+    if (heuristic == 32) build_tc_stream(src, nvec, 32, items, begins, nctas, st);
+    return heuristic;
+  }
+  if (!c->derr) {
+    if (dev_alloc((void**)&c->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+  }
+  DevArray<TcItem> it32;
+  DevArray<int> b32;
+  int n32 = 0;
+  build_tc_stream(src, nvec, 32, it32, b32, n32, st);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float t[2] = {0.0f, 0.0f};
+  for (int v = 0; v < 2; ++v) {
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(e0, st));
+      if (v == 0)
+        launch_gemm_tf32x3(items.p, begins.p, nctas, 64, scratch, c->derr, st);
+      else
+        launch_gemm_tf32x3(it32.p, b32.p, n32, 32, scratch, c->derr, st);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&t[v], e0, e1));
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) {
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), st));
+    throw Error(LRT_ETIMEOUT, "tensor-core autotuning: a pipeline wait expired");
+  }
+  if (t[1] < t[0]) {
+    items.swap(it32);
+    begins.swap(b32);
+    nctas = n32;
+    return 32;
+  }
+  return 64;
+}
+
 // TC-matrix pools, packed operators and work streams of a plan (once per plan)
 static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   if (p.tc_ready) return;
@@ -1747,8 +1818,20 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
     CK(cudaStreamSynchronize(c->st));
   }
   p.xpack.upload(tp.pack1, c->st);
-  build_tc_stream({TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, p.tci1, p.tcb1, p.tcn1, c->st);
-  build_tc_stream({TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, p.tci2, p.tcb2, p.tcn2, c->st);
+  {
+    // tile widths chosen on this plan's own data (x pool zeroed, outputs into scratch)
+    const size_t nx = (size_t)std::max<int64_t>(tp.pool_size[1] * nvec, 1);
+    CK(cudaMemsetAsync(p.pool_hi[1], 0, nx * sizeof(float), c->st));
+    CK(cudaMemsetAsync(p.pool_lo[1], 0, nx * sizeof(float), c->st));
+    DevBuf ys;
+    ys.ensure((size_t)std::max<int64_t>(p.nelem * nvec, 1));
+    const TcOut scratch{ys.p, nullptr};
+    p.tn1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci1,
+                           p.tcb1, p.tcn1);
+    p.tn2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci2,
+                           p.tcb2, p.tcn2);
+    CK(cudaStreamSynchronize(c->st));
+  }
   CK(cudaStreamSynchronize(c->st));
   p.tc_ready = true;
 }
@@ -1764,8 +1847,8 @@ static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_de
   launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1], p.tc.pool_size[1],
                  nvec, ctx->st);
   const TcOut to{y_dev};
-  launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, to, ctx->derr, ctx->st);
-  launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, to, ctx->derr, ctx->st);
+  launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, p.tn1, to, ctx->derr, ctx->st);
+  launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, p.tn2, to, ctx->derr, ctx->st);
   CK(cudaGetLastError());
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -3024,7 +3107,7 @@ struct BatchPlan {
   // split-TF32: merged work streams, y per instance
   DevArray<TcItem> tci1, tci2;
   DevArray<int> tcb1, tcb2;
-  int tcn1 = 0, tcn2 = 0;
+  int tcn1 = 0, tcn2 = 0, tn1 = 64, tn2 = 64;
   DevArray<double*> ys;
   std::vector<double*> hys;
   // one call captured as a CUDA graph
@@ -3075,8 +3158,8 @@ static void batch_issue(lrt_ctx* c0, BatchPlan& B, const std::vector<SigmaPlan*>
                      p.tc.pool_size[1], nvec, st);
     }
     const TcOut to{nullptr, B.ys.p};
-    launch_gemm_tf32x3(B.tci1.p, B.tcb1.p, B.tcn1, to, c0->derr, st);
-    launch_gemm_tf32x3(B.tci2.p, B.tcb2.p, B.tcn2, to, c0->derr, st);
+    launch_gemm_tf32x3(B.tci1.p, B.tcb1.p, B.tcn1, B.tn1, to, c0->derr, st);
+    launch_gemm_tf32x3(B.tci2.p, B.tcb2.p, B.tcn2, B.tn2, to, c0->derr, st);
   } else {
     launch_gemm_fp64_multi(B.p1.outs.p, B.p1.segs.p, B.p1.tiles.p, B.p1.ntiles, B.bases.p, st);
     launch_gemm_fp64_multi(B.p2.outs.p, B.p2.segs.p, B.p2.tiles.p, B.p2.ntiles, B.bases.p, st);
@@ -3122,8 +3205,16 @@ static void sigma_batched_impl(lrt_ctx* const* ctxs, int n, const int* sites, in
         s1.push_back(TcSource{&p.tc, &p.tc.out1, p.pool_hi, p.pool_lo, p.nelem, j});
         s2.push_back(TcSource{&p.tc, &p.tc.out2, p.pool_hi, p.pool_lo, p.nelem, j});
       }
-      build_tc_stream(s1, nvec, B->tci1, B->tcb1, B->tcn1, c0->st);
-      build_tc_stream(s2, nvec, B->tci2, B->tcb2, B->tcn2, c0->st);
+      // tile widths tuned on the merged streams, outputs into per-instance scratch
+      std::vector<DevBuf> scr(n);
+      std::vector<double*> sp(n);
+      for (int j = 0; j < n; ++j) sp[j] = scr[j].ensure((size_t)std::max<int64_t>(plans[j]->nelem * nvec, 1));
+      DevArray<double*> sys;
+      sys.upload(sp, c0->st);
+      const TcOut scratch{nullptr, sys.p};
+      B->tn1 = tune_tc_stream(c0, s1, nvec, scratch, B->tci1, B->tcb1, B->tcn1);
+      B->tn2 = tune_tc_stream(c0, s2, nvec, scratch, B->tci2, B->tcb2, B->tcn2);
+      CK(cudaStreamSynchronize(c0->st));
     } else {
       merge_fp64(B->p1, plans, false, c0->st);
       merge_fp64(B->p2, plans, true, c0->st);

@@ -120,8 +120,9 @@ struct TcOut {
 // number of CTAs (one per SM) the tensor-core launch uses for ntiles tiles; CTA b
 // takes tiles b, b + n, b + 2n, ... of the host's order
 int tc_num_ctas(int ntiles);
-// items[cta_begin[b] .. cta_begin[b + 1]) is the stream of CTA b, b < nctas
-void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err,
+// items[cta_begin[b] .. cta_begin[b + 1]) is the stream of CTA b, b < nctas; tiles are
+// 128 x tile_n (tile_n = 32 or 64, the value the stream was built for)
+void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, int tile_n, TcOut out, int* err,
                         cudaStream_t st);
 
 // Packing into TC matrices: element (r, k) of the source is src[r * ld + k], or
@@ -138,7 +139,6 @@ struct TcPack {
 void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stride, float* dst_hi, float* dst_lo,
                     int64_t dst_stride, int nvec, cudaStream_t st);
 int tc_tile_m();
-int tc_tile_n();
 
 constexpr int GATHER_TILE = 32;
 constexpr int GEMM_TM = 64;   // output tile rows

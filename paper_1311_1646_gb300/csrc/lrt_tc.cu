@@ -47,24 +47,30 @@ namespace lrt {
 namespace {
 
 constexpr int TC_M = 128;               // rows of an output tile (one TMEM lane per row)
-constexpr int TC_N = 64;                // columns of an output tile (TMEM columns)
 constexpr int TC_K = 32;                // K elements per stage (one 128-byte swizzle row)
 constexpr int STAGES = 3;
 constexpr int NINFO = 16;               // epilogue record ring
 constexpr int EPI_WARPS = 4, PROD_WARPS = 1;
 constexpr int TC_THREADS = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A (16 KB)
-constexpr int B_BYTES = TC_N * TC_K * 4;    // 8 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int STG_LD = TC_N + 1;        // 8-byte words per staged output row (padded)
-constexpr int STG_WARP_BYTES = 32 * STG_LD * 8;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * STG_WARP_BYTES + 1024;
 constexpr int NACC = 4;                 // TMEM accumulators (product ring to the epilogue)
-constexpr uint32_t TMEM_COLS = NACC * TC_N;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 
-static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
-              "swizzle atoms must stay 1024-byte aligned");
+// Sizes that follow from the tile width TN (output columns = TMEM columns of one
+// accumulator): 32 or 64, chosen per launch by the host's autotuner.
+template <int TN>
+struct Tile {
+  static constexpr int B_BYTES = TN * TC_K * 4;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STG_LD = TN + 1;                  // 8-byte words per staged output row (padded)
+  static constexpr int STG_WARP_BYTES = 32 * STG_LD * 8;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * STG_WARP_BYTES + 1024;
+  static constexpr uint32_t TMEM_COLS = NACC * TN;
+  static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0,
+                "swizzle atoms must stay 1024-byte aligned");
+  static_assert(2 * (TN / 32) * 32 * 128 <= STG_WARP_BYTES, "TC-matrix staging fits the warp's buffer");
+  static_assert(TMEM_COLS >= 32 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation: power of two >= 32");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -82,12 +88,13 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TC_N
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TN
+template <int TN>
 __host__ __device__ constexpr uint32_t make_idesc() {
   return (1u << 4)                        // D format F32
          | (2u << 7)                      // A format TF32
          | (2u << 10)                     // B format TF32
-         | ((uint32_t)(TC_N >> 3) << 17)  // N / 8
+         | ((uint32_t)(TN >> 3) << 17)    // N / 8
          | ((uint32_t)(TC_M >> 4) << 24); // M / 16
 }
 
@@ -211,6 +218,7 @@ __device__ __forceinline__ TcItem load_item(const TcItem* p) {
 
 static_assert(sizeof(TcItem) % 16 == 0, "items are read as 16-byte vectors");
 
+template <int TN>
 __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem* __restrict__ items,
                                                                      const int* __restrict__ cta_begin,
                                                                      TcOut out, int* __restrict__ err) {
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TMEM_COLS));
+                 "r"(Tile<TN>::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           ok = post(EpiInfo{INFO_MMA | (first_seg ? INFO_FIRST : 0), g.scale, hdr});
           first_seg = false;
           // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
-          const uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0), rb = (uint32_t)min(TC_N, g.b_rp - hdr.n0);
+          const uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0), rb = (uint32_t)min(TN, g.b_rp - hdr.n0);
           const uint32_t bytes = 2u * 128u * (ra + rb);
           for (int k0 = 0, q = 0; k0 < g.k && ok; k0 += TC_K, ++q, ++it) {
             const uint32_t stage = it % STAGES, round = it / STAGES;
@@ -296,13 +304,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
             }
             const int kc = min(TC_K, g.k - k0);
             meta[stage] = StageMeta{(kc + 7) >> 3, (k0 == 0 ? META_FIRST : 0) | (k0 + TC_K >= g.k ? META_LAST : 0)};
-            const uint32_t st = sbase + stage * STAGE_BYTES;
+            const uint32_t st = sbase + stage * Tile<TN>::STAGE_BYTES;
             const int64_t ao = ((int64_t)q * g.a_rp + hdr.m0) * TC_K, bo = ((int64_t)q * g.b_rp + hdr.n0) * TC_K;
             mbar_arrive_tx(&full_bar[stage], bytes);
             bulk_g2s(st, g.a_hi + ao, 128u * ra, &full_bar[stage]);
             bulk_g2s(st + A_BYTES, g.a_lo + ao, 128u * ra, &full_bar[stage]);
             bulk_g2s(st + 2 * A_BYTES, g.b_hi + bo, 128u * rb, &full_bar[stage]);
-            bulk_g2s(st + 2 * A_BYTES + B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
+            bulk_g2s(st + 2 * A_BYTES + Tile<TN>::B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
           }
         }
         cur = nx1;
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   } else if (warp == EPI_WARPS + PROD_WARPS) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc();
+      constexpr uint32_t idesc = make_idesc<TN>();
       uint32_t sg = 0;
       bool any = false;
       for (uint32_t it = 0; !*failed; ++it) {
@@ -346,9 +354,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err)) break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dt = tmem + a * TC_N;
-        const uint32_t base = smem_u32(sm + stage * STAGE_BYTES);
-        const uint32_t ah = base, al = base + A_BYTES, bh = base + 2 * A_BYTES, bl = bh + B_BYTES;
+        const uint32_t dt = tmem + a * TN;
+        const uint32_t base = smem_u32(sm + stage * Tile<TN>::STAGE_BYTES);
+        const uint32_t ah = base, al = base + A_BYTES, bh = base + 2 * A_BYTES, bl = bh + Tile<TN>::B_BYTES;
         for (int ks = 0; ks < m.nks; ++ks) {
           const uint32_t step = (uint32_t)ks * 32u;     // 8 TF32 = 32 bytes along K
           const uint32_t acc = ((m.flags & META_FIRST) && ks == 0) ? 0u : 1u;
@@ -374,12 +382,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
     }
   } else {
     // ---------------- epilogue: thread = tile row = TMEM lane
-    uint8_t* stg = sm + STAGES * STAGE_BYTES + warp * STG_WARP_BYTES;   // this warp's 32 rows
+    uint8_t* stg = sm + STAGES * Tile<TN>::STAGE_BYTES + warp * Tile<TN>::STG_WARP_BYTES;   // this warp's 32 rows
     uint32_t sg = 0;
     bool tile_has_mma = false;
-    float sum[TC_N], cmp[TC_N];
+    float sum[TN], cmp[TN];
 #pragma unroll
-    for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
+    for (int c = 0; c < TN; ++c) sum[c] = cmp[c] = 0.0f;
     for (uint32_t ei = 0;; ++ei) {
       const uint32_t slot = ei % NINFO;
       // the warp stays converged for the .sync.aligned tensor-memory loads
@@ -393,9 +401,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         const bool ok = mbar_wait(&tfull_bar[a], u & 1, failed, err);
         if (!__all_sync(0xffffffffu, ok)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + a * TC_N;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + a * TN;
 #pragma unroll
-        for (int c0 = 0; c0 < TC_N; c0 += 32) {
+        for (int c0 = 0; c0 < TN; c0 += 32) {
           uint32_t v[32];
           ld_16cols_async(taddr + (uint32_t)c0, v);
           ld_16cols_async(taddr + (uint32_t)c0 + 16u, v + 16);
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         const TcTileHdr& t = rec.t;
         if (!tile_has_mma) {
 #pragma unroll
-          for (int c = 0; c < TC_N; ++c) sum[c] = cmp[c] = 0.0f;
+          for (int c = 0; c < TN; ++c) sum[c] = cmp[c] = 0.0f;
         }
         tile_has_mma = false;
         const int rr = lane;
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           // then one bulk store per chunk and plane: rows [m0 + 32 w, + nrows) of a
           // chunk are contiguous in the matrix.  Columns past the output are zeros.
 #pragma unroll
-          for (int q = 0; q < TC_N / 32; ++q)
+          for (int q = 0; q < TN / 32; ++q)
 #pragma unroll
             for (int g4 = 0; g4 < 8; ++g4) {
               uint32_t h[4], l[4];
@@ -452,12 +460,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
               }
               const uint32_t o = (uint32_t)(((q * 32 + rr) << 7) + (((g4 ^ rr) & 7) << 4));
               *(uint4*)(stg + o) = make_uint4(h[0], h[1], h[2], h[3]);
-              *(uint4*)(stg + 2 * 32 * 128 + o) = make_uint4(l[0], l[1], l[2], l[3]);
+              *(uint4*)(stg + (TN / 32) * 32 * 128 + o) = make_uint4(l[0], l[1], l[2], l[3]);
             }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0 && nrows > 0) {
-            for (int q = 0; q < TC_N / 32; ++q) {
+            for (int q = 0; q < TN / 32; ++q) {
               const int cq = t.n0 + 32 * q;
               if (cq >= t.t_k) break;
               const int64_t go = ((int64_t)(cq >> 5) * t.t_rp + t.m0 + rbase) * 32;
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
                            "r"((uint32_t)nrows * 128u)
                            : "memory");
               asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(t.t_lo + go),
-                           "r"(so + 2u * 32u * 128u), "r"((uint32_t)nrows * 128u)
+                           "r"(so + (uint32_t)(TN / 32) * 32u * 128u), "r"((uint32_t)nrows * 128u)
                            : "memory");
             }
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -474,14 +482,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         } else {
           // FP64 output: stage the rows, then the warp stores row by row (coalesced)
 #pragma unroll
-          for (int c = 0; c < TC_N; ++c)
-            *(double*)(stg + (rr * STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
+          for (int c = 0; c < TN; ++c)
+            *(double*)(stg + (rr * Tile<TN>::STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
           __syncwarp();
           double* C = (t.c_rel == 1 ? (out.ys ? out.ys[t.inst] : out.y) + t.c_off : t.C);
           for (int r = 0; r < nrows; ++r) {
             double* dst = C + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
             for (int c = lane; c < t.nt; c += 32) {
-              const double v = *(const double*)(stg + (r * STG_LD + c) * 8);
+              const double v = *(const double*)(stg + (r * Tile<TN>::STG_LD + c) * 8);
               dst[c] = t.accumulate ? dst[c] + v : v;
             }
           }
@@ -496,7 +504,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Tile<TN>::TMEM_COLS));
   }
 }
 
@@ -531,7 +539,6 @@ void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stri
 }
 
 int tc_tile_m() { return TC_M; }
-int tc_tile_n() { return TC_N; }
 
 static int sm_count() {
   static int nsm = 0;
@@ -546,15 +553,23 @@ static int sm_count() {
 
 int tc_num_ctas(int ntiles) { return std::max(1, std::min(ntiles, sm_count())); }
 
-void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err,
-                        cudaStream_t st) {
-  if (nctas <= 0) return;
+template <int TN>
+static void launch_tn(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(gemm_tf32x3_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<TN>::SMEM_BYTES);
     attr = true;
   }
-  gemm_tf32x3_kernel<<<nctas, TC_THREADS, SMEM_BYTES, st>>>(items, cta_begin, out, err);
+  gemm_tf32x3_kernel<TN><<<nctas, TC_THREADS, Tile<TN>::SMEM_BYTES, st>>>(items, cta_begin, out, err);
+}
+
+void launch_gemm_tf32x3(const TcItem* items, const int* cta_begin, int nctas, int tile_n, TcOut out, int* err,
+                        cudaStream_t st) {
+  if (nctas <= 0) return;
+  if (tile_n == 32)
+    launch_tn<32>(items, cta_begin, nctas, out, err, st);
+  else
+    launch_tn<64>(items, cta_begin, nctas, out, err, st);
 }
 
 }  // namespace lrt
