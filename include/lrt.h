@@ -103,7 +103,10 @@ int wfn_layout(lrt_t ctx, int site, int nsite, int64_t* nelem, int* nblocks, int
  * dir = +1 builds the left block of bond site+1 from the left block of bond site and
  * the (left-orthonormal) tensor of `site`; dir = -1 builds the right block of bond
  * `site` from the right block of bond site+1 and the (right-orthonormal) tensor of
- * `site`.  Left block 0 and right block k are the vacuum and always exist. */
+ * `site`.  Left block 0 and right block k are the vacuum and always exist.
+ * precision LRT_FP64, or LRT_MIXED: the enlarged operators are formed in FP64 and the
+ * two grouped contractions O' = L^T (E L) run as split-TF32 tensor-core products with
+ * FP32 accumulation per block product (the new operators are stored in FP64). */
 int renormalize(lrt_t ctx, int site, int dir, int precision);
 
 /* sigma = H_eff x (Eq. dmrg) for `nvec` wavefunctions stored back to back in the

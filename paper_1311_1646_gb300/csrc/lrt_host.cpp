@@ -818,11 +818,12 @@ struct TcPlanSeg {
   float scale;
 };
 struct TcPlanOut {
-  int tmat;        // output TC matrix (intermediate), or -1 for an FP64 output in y
-  int64_t c_off;   // y output: offset and row stride
+  int tmat;        // output TC matrix (intermediate), or -1 for an FP64 output
+  int64_t c_off;   // FP64 output in y: offset and row stride
   int ldc;
   int m, n;
   int seg_begin, seg_count;
+  double* C = nullptr;   // FP64 output at an absolute address instead of y (row stride ldc)
 };
 struct TcPlan {
   std::vector<TcMat> mats;
@@ -1101,8 +1102,13 @@ struct RenTerm {
 // D_q x fused(q), sub-blocks n side by side); returns the per-sector offsets
 static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, DevBuf& buf, const Fused& F);
 
+static void run_two_phase_tc(lrt_ctx* c, const std::vector<GemmOut>& o1, const std::vector<GemmSeg>& s1,
+                             const std::vector<GemmOut>& o2, const std::vector<GemmSeg>& s2);
+
 // left block of bond b+1 = sum_t bra_t^T E_t ket_t over the enlarged left block of bond b
-static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms) {
+// (prec LRT_MIXED: the two grouped GEMMs as split-TF32 tensor-core products)
+static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms,
+                                                int prec = LRT_FP64) {
   const OpSet& E0 = *terms[0].E;
   const Fused& F = *E0.fused;
   auto N = std::make_unique<OpSet>();
@@ -1143,6 +1149,11 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
         N->bnz[o * N->ns() + q] = 1;
       }
     }
+  if (prec == LRT_MIXED) {
+    run_two_phase_tc(c, o1, s1, o2, s2);
+    N->finish_nz();
+    return N;
+  }
   double* tmp = nullptr;
   if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "renormalize workspace");
@@ -1161,7 +1172,8 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
 }
 
 // right block of bond b = sum_t R_bra,t [E_t] R_ket,t^T over the enlarged right block site b (+) R
-static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms) {
+static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms,
+                                                 int prec = LRT_FP64) {
   const OpSet& E0 = *terms[0].E;
   const Fused& F = *E0.fused;
   const Sectors& Lb = c->bonds[b];
@@ -1210,6 +1222,11 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
         N->bnz[o * N->ns() + q] = 1;
       }
     }
+  if (prec == LRT_MIXED) {
+    run_two_phase_tc(c, o1, s1, o2, s2);
+    N->finish_nz();
+    return N;
+  }
   double* tmp = nullptr;
   if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
     throw Error(LRT_ENOMEM, "renormalize workspace");
@@ -1227,18 +1244,18 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
   return N;
 }
 
-static void renorm_left(lrt_ctx* c, int b) {
+static void renorm_left(lrt_ctx* c, int b, int prec = LRT_FP64) {
   OpSet& E = enlarged(c, b, false);
-  c->L[b + 1] = renorm_left_terms(c, b, {RenTerm{&E, &c->sites[b], &c->sites[b]}});
+  c->L[b + 1] = renorm_left_terms(c, b, {RenTerm{&E, &c->sites[b], &c->sites[b]}}, prec);
   for (int x = b + 2; x <= c->k; ++x) c->L[x].reset();
   for (int x = b + 1; x < c->k; ++x) c->XL[x].reset();
   drop_plans(c);
 }
 
-static void renorm_right(lrt_ctx* c, int b) {
+static void renorm_right(lrt_ctx* c, int b, int prec = LRT_FP64) {
   OpSet& E = enlarged(c, b, true);
   const SiteTensor& T = c->sites_r.empty() ? c->sites[b] : c->sites_r[b];
-  c->R[b] = renorm_right_terms(c, b, {RenTerm{&E, &T, &T}});
+  c->R[b] = renorm_right_terms(c, b, {RenTerm{&E, &T, &T}}, prec);
   for (int x = 0; x < b; ++x) c->R[x].reset();
   for (int x = 0; x < b; ++x) c->YR[x].reset();
   drop_plans(c);
@@ -1697,6 +1714,10 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
         h.t.t_lo = base(sc, m, t.v, false);
         h.t.t_rp = m.Rp;
         h.t.t_k = m.K;
+      } else if (o.C) {
+        h.t.c_rel = 0;
+        h.t.C = o.C;
+        h.t.ldc = o.ldc;
       } else {
         h.t.c_rel = 1;
         h.t.c_off = o.c_off + (int64_t)t.v * sc.nelem;
@@ -1736,7 +1757,7 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
 // take 32 when the work-weighted output width is at most 32.  Returns the width, with
 // the matching stream in items/begins/nctas.
 static int tune_tc_stream(lrt_ctx* c, const std::vector<TcSource>& src, int nvec, TcOut scratch,
-                          DevArray<TcItem>& items, DevArray<int>& begins, int& nctas) {
+                          DevArray<TcItem>& items, DevArray<int>& begins, int& nctas, bool timed = true) {
   cudaStream_t st = c->st;
   build_tc_stream(src, nvec, 64, items, begins, nctas, st);
   double wn = 0.0, w = 0.0;
@@ -1750,7 +1771,7 @@ static int tune_tc_stream(lrt_ctx* c, const std::vector<TcSource>& src, int nvec
       ntiles += (int64_t)((o.m + 127) / 128) * ((o.n + 63) / 64) * nvec;
     }
   const int heuristic = (w > 0.0 && wn / w <= 32.0) ? 32 : 64;
-  if (ntiles < 4 * (int64_t)tc_num_ctas(1 << 30)) {
+  if (!timed || ntiles < 4 * (int64_t)tc_num_ctas(1 << 30)) {
     if (heuristic == 32) build_tc_stream(src, nvec, 32, items, begins, nctas, st);
     return heuristic;
   }
@@ -1856,6 +1877,83 @@ static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_de
   if (flag) {
     CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
     throw Error(LRT_ETIMEOUT, "sigma: a tensor-core pipeline wait expired; results are invalid");
+  }
+}
+
+// The renormalization's two grouped GEMMs (phase 1: T_i = op(A) op(B), one product per
+// output, into a workspace; phase 2: C = sum op(A) T_s with T_s read as B, no
+// transpose) on the tensor cores: phase 1 computes T_i^T = op(B)^T op(A)^T straight into
+// a TC matrix (rows = columns of T), which is the operand image phase 2 needs; phase 2
+// writes the FP64 blocks of C.  Operands are packed once; tile widths by the heuristic.
+static void run_two_phase_tc(lrt_ctx* c, const std::vector<GemmOut>& o1, const std::vector<GemmSeg>& s1,
+                             const std::vector<GemmOut>& o2, const std::vector<GemmSeg>& s2) {
+  TcPlan tp;
+  std::map<int64_t, int> tmat_of;   // workspace offset of T_i -> TC matrix of T_i^T
+  auto a_role = [&](const GemmSeg& g, int m) { return tp.op(g.A, g.lda, g.transA ? 1 : 0, m, g.k); };
+  auto b_role = [&](const GemmSeg& g, int n) { return tp.op(g.B, g.ldb, g.transB ? 0 : 1, n, g.k); };
+  for (const GemmOut& o : o1) {
+    if (o.seg_count != 1) throw Error(LRT_EINVAL, "mixed renormalize: one product per intermediate expected");
+    const GemmSeg& g = s1[o.seg_begin];
+    const int A = b_role(g, o.n);       // rows = columns of T
+    const int B = a_role(g, o.m);       // rows = rows of T
+    const int t = tp.add(2, o.n, o.m);
+    tmat_of[o.c_off] = t;
+    tp.out1.push_back(TcPlanOut{t, 0, 0, o.n, o.m, (int)tp.segs.size(), 1});
+    tp.segs.push_back(TcPlanSeg{A, B, g.k, (float)g.scale});
+  }
+  for (const GemmOut& o : o2) {
+    const int sb = (int)tp.segs.size();
+    for (int q = 0; q < o.seg_count; ++q) {
+      const GemmSeg& g = s2[o.seg_begin + q];
+      if (g.transB) throw Error(LRT_EINVAL, "mixed renormalize: transposed intermediate");
+      auto it = tmat_of.find(g.b_off);
+      if (it == tmat_of.end()) throw Error(LRT_EINVAL, "mixed renormalize: unknown intermediate");
+      tp.segs.push_back(TcPlanSeg{a_role(g, o.m), it->second, g.k, (float)g.scale});
+    }
+    TcPlanOut out{-1, 0, o.ldc, o.m, o.n, sb, (int)tp.segs.size() - sb};
+    out.C = o.C;
+    tp.out2.push_back(out);
+  }
+  float* phi[3] = {nullptr, nullptr, nullptr};
+  float* plo[3] = {nullptr, nullptr, nullptr};
+  struct Pools {
+    float** h;
+    float** l;
+    ~Pools() {
+      for (int q = 0; q < 3; ++q) {
+        dev_free(h[q]);
+        dev_free(l[q]);
+      }
+    }
+  } guard_pools{phi, plo};
+  for (int q : {0, 2}) {
+    const size_t nw = (size_t)std::max<int64_t>(tp.pool_size[q], 1);
+    if (dev_alloc((void**)&phi[q], nw * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void**)&plo[q], nw * sizeof(float)) != cudaSuccess)
+      throw Error(LRT_ENOMEM, "mixed renormalize: operand pools");
+  }
+  DevArray<TcPack> d0;
+  d0.upload(tp.pack0, c->st);
+  launch_tc_pack(d0.p, (int)tp.pack0.size(), nullptr, 0, phi[0], plo[0], 0, 1, c->st);
+  if (!c->derr) {
+    if (dev_alloc((void**)&c->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+  }
+  DevArray<TcItem> i1, i2;
+  DevArray<int> b1, b2;
+  int n1 = 0, n2 = 0;
+  const TcOut none{nullptr, nullptr};
+  const int t1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, phi, plo, 0, 0}}, 1, none, i1, b1, n1, false);
+  const int t2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, phi, plo, 0, 0}}, 1, none, i2, b2, n2, false);
+  launch_gemm_tf32x3(i1.p, b1.p, n1, t1, none, c->derr, c->st);
+  launch_gemm_tf32x3(i2.p, b2.p, n2, t2, none, c->derr, c->st);
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (flag) {
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->st));
+    throw Error(LRT_ETIMEOUT, "renormalize: a tensor-core pipeline wait expired; results are invalid");
   }
 }
 
@@ -3481,10 +3579,10 @@ int renormalize(lrt_t ctx, int site, int dir, int precision) {
     if (precision != LRT_FP64 && precision != LRT_MIXED) throw Error(LRT_EINVAL, "renormalize: bad precision");
     if (dir == 1) {
       if (!ctx->L[site]) throw Error(LRT_ESTATE, "renormalize: left block of bond " + std::to_string(site) + " missing");
-      renorm_left(ctx, site);
+      renorm_left(ctx, site, precision);
     } else {
       if (!ctx->R[site + 1]) throw Error(LRT_ESTATE, "renormalize: right block of bond " + std::to_string(site + 1) + " missing");
-      renorm_right(ctx, site);
+      renorm_right(ctx, site, precision);
     }
   });
 }

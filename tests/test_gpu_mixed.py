@@ -67,3 +67,31 @@ def test_mixed_sigma_workloads(pkg, cfg, i, nsite, nvec):
     print(f"mixed sigma config {cfg}: max-abs relative error {err:.2e}")
     assert err <= MIXED_RTOL, err
     ctx.close()
+
+
+@pytest.mark.parametrize("cfg,i,nsite", [(1, 3, 2), (2, 5, 2)])
+def test_mixed_renormalize(pkg, cfg, i, nsite):
+    """Every block renormalized with split-TF32 products (LRT_MIXED); the FP64 sigma on
+    those blocks against the all-FP64 one.  Each renormalization adds its own rounding,
+    so the bound is looser than for one sigma call."""
+    c = synth.config(cfg)
+    H = c["ham"]
+    m = synth.mixed_mps(H.k, H.n_alpha, H.n_beta, c["M"], 400 + cfg, center=i)
+    out = []
+    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
+        ctx = pkg.Context(0)
+        ctx.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        ctx.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, i)
+        for b in range(i):
+            ctx.renormalize(b, +1, prec)
+        for b in range(H.k - 1, i + nsite - 1, -1):
+            ctx.renormalize(b, -1, prec)
+        n, _ = ctx.wfn_layout(i, nsite)
+        x = torch.tensor(synth.random_vector(n, 8), dtype=torch.float64, device="cuda:0")
+        y = torch.empty_like(x)
+        ctx.sigma(i, nsite, x, y)
+        out.append(y.cpu().numpy())
+        ctx.close()
+    err = np.abs(out[0] - out[1]).max() / np.abs(out[0]).max()
+    print(f"mixed renormalize config {cfg}: max-abs relative error of sigma {err:.2e}")
+    assert err <= 5e-5, err
