@@ -140,6 +140,10 @@ typedef struct {
   int dav_max_iter;
   int dav_max_space;     /* <= 48 */
   double trunc_tol;      /* density-matrix weights below trunc_tol * largest are dropped */
+  int onesite_sweeps;    /* then this many one-site sweeps (Eq. dmrg at one site, bond
+                            dimensions fixed, gauge shifts by per-sector SVDs), which make
+                            the state stationary on the one-site manifold (the reference
+                            the TDA assumes); the MPS is left in the same form */
 } lrt_gs_params;
 int sweep_gs(lrt_t ctx, const lrt_gs_params* params, double* e0);
 
@@ -157,7 +161,7 @@ int sweep_gs(lrt_t ctx, const lrt_gs_params* params, double* e0);
  * resid[nroots] = sum_i |r_i|^2 of the last sweep and *e0 = <Psi0|H|Psi0>.
  * Returns LRT_ENOCONV (results written) when max_iter is reached first. */
 typedef struct {
-  int max_space;      /* N, maximum number of trial vectors (0: max(4 nroots, 16)); <= 48 */
+  int max_space;      /* N, maximum number of trial vectors (0: min(48, max(8 nroots, 24))); <= 48 */
   int max_iter;
   double eps;         /* converged when sum_i |r_i^mu|^2 < eps for every root */
   double pinv_cut;    /* Lambda^-1: singular values below pinv_cut * largest are dropped */

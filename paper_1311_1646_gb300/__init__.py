@@ -44,7 +44,7 @@ class GsParams(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int), ("n_schedule", ctypes.c_int),
                 ("M_schedule", ctypes.POINTER(ctypes.c_int)), ("sweeps_per_M", ctypes.c_int),
                 ("e_tol", ctypes.c_double), ("dav_tol", ctypes.c_double), ("dav_max_iter", ctypes.c_int),
-                ("dav_max_space", ctypes.c_int), ("trunc_tol", ctypes.c_double)]
+                ("dav_max_space", ctypes.c_int), ("trunc_tol", ctypes.c_double), ("onesite_sweeps", ctypes.c_int)]
 
 
 class TdaParams(ctypes.Structure):
@@ -206,11 +206,12 @@ class Context:
 
     def sweep_gs(self, M_schedule, max_sweeps: int = 20, sweeps_per_M: int = 2, e_tol: float = 1e-10,
                  dav_tol: float = 1e-8, dav_max_iter: int = 200, dav_max_space: int = 24,
-                 trunc_tol: float = 1e-14) -> float:
-        """Two-site ground-state sweeps on the loaded (right-orthonormal) MPS; returns E0."""
+                 trunc_tol: float = 1e-14, onesite_sweeps: int = 0) -> float:
+        """Two-site ground-state sweeps on the loaded (right-orthonormal) MPS, then
+        `onesite_sweeps` one-site sweeps; returns E0."""
         ms = (ctypes.c_int * len(M_schedule))(*M_schedule)
         p = GsParams(max_sweeps, len(M_schedule), ms, sweeps_per_M, e_tol, dav_tol, dav_max_iter,
-                     dav_max_space, trunc_tol)
+                     dav_max_space, trunc_tol, onesite_sweeps)
         e = ctypes.c_double()
         self._check(self.lib.sweep_gs(self.h, ctypes.byref(p), ctypes.byref(e)), "sweep_gs")
         return e.value

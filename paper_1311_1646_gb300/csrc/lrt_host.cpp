@@ -2001,8 +2001,8 @@ static void upload_coef(double* dcoef, const std::vector<double>& c, cudaStream_
 
 // Lowest eigenpair of H_eff at a two-site position; psi (device) is the start vector
 // and receives the eigenvector.  Returns the eigenvalue.
-static double davidson_twosite(lrt_ctx* c, int i, double* psi, const lrt_gs_params& P, int* iters_out) {
-  SigmaPlan& plan = get_plan(c, i, 2, 1);
+static double davidson_site(lrt_ctx* c, int i, int nsite, double* psi, const lrt_gs_params& P, int* iters_out) {
+  SigmaPlan& plan = get_plan(c, i, nsite, 1);
   const int64_t n = plan.nelem;
   const int maxs = std::max(2, std::min(P.dav_max_space, JACOBI_MAXN));
   DevBuf V, AV, diag, r, t, u, au, small, coef, Hd, Wd, Zd;
@@ -2357,7 +2357,7 @@ static double sweep_gs_impl(lrt_ctx* c, const lrt_gs_params& P, int* nsw) {
         psi.ensure(n);
         form_theta(c, i, psi.p, wb);
         int its = 0;
-        E = davidson_twosite(c, i, psi.p, P, &its);
+        E = davidson_site(c, i, 2, psi.p, P, &its);
         decimate(c, i, psi.p, wb, M, P.trunc_tol, dir, sh);
         drop_plans(c);
         if (dir > 0) {
@@ -2569,6 +2569,266 @@ static double splitmix_normal(uint64_t seed, uint64_t idx) {
   const double u1 = ((double)(z1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
   const double u2 = ((double)(z2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
   return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// ---------------------------------------------------------------------------
+// One-site ground-state sweeps (Eq. dmrg at one site, bond dimensions fixed), which
+// make the reference a stationary point of the one-site manifold as the TDA assumes.
+// Gauge shifts by per-sector SVDs (cuSOLVER Jacobi SVD): left to right
+// C_i = L S V^T per right sector, L_i = L, C_{i+1} = (S V^T) R_{i+1}; right to left
+// C_i = U S R per left sector (right-fused rows), R_i = R, C_{i-1} = L_{i-1} (U S).
+// A sector with fewer fused states than bond states keeps zero singular values.
+// ---------------------------------------------------------------------------
+struct SvdWork {
+  SolverHandle sh;
+  gesvdjInfo_t params = nullptr;
+  int* info = nullptr;
+  DevBuf work, A, U, V, S;
+  explicit SvdWork(cudaStream_t st) {
+    if (cusolverDnCreate(&sh.h) != CUSOLVER_STATUS_SUCCESS) throw Error(LRT_ECUDA, "cusolverDnCreate failed");
+    cusolverDnSetStream(sh.h, st);
+    if (cusolverDnCreateGesvdjInfo(&params) != CUSOLVER_STATUS_SUCCESS) throw Error(LRT_ECUDA, "gesvdj info");
+    if (dev_alloc((void**)&info, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "cusolver info");
+  }
+  ~SvdWork() {
+    if (params) cusolverDnDestroyGesvdjInfo(params);
+    dev_free(info);
+  }
+  // full SVD of the column-major m x n matrix at src (copied first): U (m x m), V (n x n)
+  // left in U, V; returns the min(m, n) singular values (descending)
+  std::vector<double> svd(const double* src, int m, int n, cudaStream_t st) {
+    const int p = std::min(m, n);
+    A.ensure((size_t)m * n);
+    U.ensure((size_t)m * m);
+    V.ensure((size_t)n * n);
+    S.ensure(std::max(1, p));
+    CK(cudaMemcpyAsync(A.p, src, (size_t)m * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int lwork = 0;
+    if (cusolverDnDgesvdj_bufferSize(sh.h, CUSOLVER_EIG_MODE_VECTOR, 0, m, n, A.p, m, S.p, U.p, m, V.p, n, &lwork,
+                                     params) != CUSOLVER_STATUS_SUCCESS)
+      throw Error(LRT_ECUDA, "gesvdj buffer size");
+    work.ensure(std::max(lwork, 1));
+    if (cusolverDnDgesvdj(sh.h, CUSOLVER_EIG_MODE_VECTOR, 0, m, n, A.p, m, S.p, U.p, m, V.p, n, work.p, lwork, info,
+                          params) != CUSOLVER_STATUS_SUCCESS)
+      throw Error(LRT_ECUDA, "gesvdj");
+    std::vector<double> s(p);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s.data(), S.p, p * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h < 0) throw Error(LRT_ECUDA, "gesvdj: invalid argument " + std::to_string(-h));
+    return s;
+  }
+};
+
+static void run_gathers(lrt_ctx* c, std::vector<GatherTask>& t, std::vector<GatherSrc>& s) {
+  if (t.empty()) return;
+  GatherPlan gp;
+  build_gather(gp, t, s, c->st);
+  gp.run(c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+}
+
+// M = X diag(w) (X: D x D bond blocks; per sector the weights w in sector order)
+static void scale_cols(lrt_ctx* c, int b, const BondMat& X, const std::vector<double>& w, BondMat& out) {
+  BondMat Lm, Lmi;
+  lam_mats(c, b, w, 0.0, Lm, Lmi);
+  const Sectors& S = c->bonds[b];
+  bond_layout(S, out, c->st);
+  std::vector<GemmOut> o;
+  std::vector<GemmSeg> g;
+  for (int q = 0; q < S.n(); ++q) {
+    const int D = S.d[q];
+    if (D == 0) continue;
+    o.push_back(GemmOut{out.buf.p + out.off[q], 0, D, D, D, (int)g.size(), 1, 0, 0});
+    g.push_back(GemmSeg{X.buf.p + X.off[q], Lm.buf.p + Lm.off[q], 0, 0, D, D, D, 0, 0, 0, 0, 1.0});
+  }
+  run_gemms(c, o, g);
+}
+
+// centre psi at site i -> L_i and the new centre at site i+1
+static void gauge_shift_right(lrt_ctx* c, int i, const double* psi, SvdWork& W) {
+  const Sectors& Rb = c->bonds[i + 1];
+  const SiteTensor& T = c->sites[i];
+  SiteTensor L = new_site(c, i);
+  BondMat UT;               // per sector: U_a^T (row a = right singular vector a), D x D
+  bond_layout(Rb, UT, c->st);
+  std::vector<double> lam;
+  std::vector<GatherTask> tasks;
+  std::vector<GatherSrc> srcs;
+  std::vector<DevBuf> keepU, keepV;
+  for (int q = 0; q < Rb.n(); ++q) {
+    const int D = Rb.d[q];
+    const int rows = T.blk_off[q] >= 0 ? T.blk_rows[q] : 0;
+    if (D == 0) continue;
+    if (rows == 0) {
+      std::vector<double> I((size_t)D * D, 0.0);
+      for (int a = 0; a < D; ++a) I[(size_t)a * D + a] = 1.0;
+      CK(cudaMemcpyAsync(UT.buf.p + UT.off[q], I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      lam.insert(lam.end(), D, 0.0);
+      continue;
+    }
+    // the row-major block M (rows x D) is the column-major D x rows matrix M^T = U_a S V_a^T
+    const std::vector<double> sv = W.svd(psi + T.blk_off[q], D, rows, c->st);
+    const int p = (int)sv.size();
+    for (int a = 0; a < D; ++a) lam.push_back(a < p ? sv[a] : 0.0);
+    keepU.emplace_back();
+    keepV.emplace_back();
+    DevBuf& u = keepU.back();
+    DevBuf& v = keepV.back();
+    u.ensure((size_t)D * D);
+    v.ensure((size_t)rows * rows);
+    CK(cudaMemcpyAsync(u.p, W.U.p, (size_t)D * D * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(v.p, W.V.p, (size_t)rows * rows * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    // L block (rows x D): columns a < p = V_a's columns; U_a^T row-major = U_a's memory
+    tasks.push_back(GatherTask{L.d + L.blk_off[q], D, rows, p, (int)srcs.size(), 1});
+    srcs.push_back(GatherSrc{v.p, rows, 1, 1.0});
+    tasks.push_back(GatherTask{UT.buf.p + UT.off[q], D, D, D, (int)srcs.size(), 1});
+    srcs.push_back(GatherSrc{u.p, D, 0, 1.0});
+  }
+  run_gathers(c, tasks, srcs);
+  // S V^T of the block = diag(lam) U_a^T; the next centre = (diag(lam) U_a^T) R_{i+1}
+  BondMat UTt, X;
+  bond_layout(Rb, UTt, c->st);
+  {
+    std::vector<GatherTask> t2;
+    std::vector<GatherSrc> s2;
+    for (int q = 0; q < Rb.n(); ++q) {
+      const int D = Rb.d[q];
+      if (D == 0) continue;
+      t2.push_back(GatherTask{UTt.buf.p + UTt.off[q], D, D, D, (int)s2.size(), 1});
+      s2.push_back(GatherSrc{UT.buf.p + UT.off[q], D, 1, 1.0});
+    }
+    run_gathers(c, t2, s2);
+  }
+  scale_cols(c, i + 1, UTt, lam, X);          // X^T = U_a diag(lam)  ->  X = diag(lam) U_a^T
+  BondMat Xs;
+  bond_layout(Rb, Xs, c->st);
+  {
+    std::vector<GatherTask> t3;
+    std::vector<GatherSrc> s3;
+    for (int q = 0; q < Rb.n(); ++q) {
+      const int D = Rb.d[q];
+      if (D == 0) continue;
+      t3.push_back(GatherTask{Xs.buf.p + Xs.off[q], D, D, D, (int)s3.size(), 1});
+      s3.push_back(GatherSrc{X.buf.p + X.off[q], D, 1, 1.0});
+    }
+    run_gathers(c, t3, s3);
+  }
+  SiteTensor next = new_site(c, i + 1);
+  t_lmul(c, i + 1, Xs, c->sites[i + 1], next, false);
+  c->sites[i] = std::move(L);
+  c->sites[i + 1] = std::move(next);
+}
+
+// centre psi at site i -> R_i and the new centre at site i-1
+static void gauge_shift_left(lrt_ctx* c, int i, const double* psi, SvdWork& W) {
+  const Sectors& Lb = c->bonds[i];
+  const Sectors& Rb = c->bonds[i + 1];
+  const SiteTensor& T = c->sites[i];
+  SiteTensor R = new_site(c, i);
+  BondMat Y;                 // per left sector: V_a (row-major), scaled by the singular values below
+  bond_layout(Lb, Y, c->st);
+  std::vector<double> lam;
+  std::vector<DevBuf> keep;
+  for (int q = 0; q < Lb.n(); ++q) {
+    const int D = Lb.d[q];
+    if (D == 0) continue;
+    // right-fused block (D x Wd): the sub-blocks (q, n) side by side
+    int Wd = 0;
+    std::array<int, 4> coff{-1, -1, -1, -1};
+    for (int n = 0; n < 4; ++n)
+      if (T.sub_off[q][n] >= 0) {
+        coff[n] = Wd;
+        Wd += Rb.d[T.sub_qr[q][n]];
+      }
+    if (Wd == 0) {
+      std::vector<double> I((size_t)D * D, 0.0);
+      for (int a = 0; a < D; ++a) I[(size_t)a * D + a] = 1.0;
+      CK(cudaMemcpyAsync(Y.buf.p + Y.off[q], I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      lam.insert(lam.end(), D, 0.0);
+      continue;
+    }
+    DevBuf rf;
+    rf.ensure((size_t)D * Wd);
+    CK(cudaMemsetAsync(rf.p, 0, (size_t)D * Wd * sizeof(double), c->st));
+    std::vector<GatherTask> tg;
+    std::vector<GatherSrc> sg;
+    for (int n = 0; n < 4; ++n)
+      if (coff[n] >= 0) {
+        const int Dr = Rb.d[T.sub_qr[q][n]];
+        tg.push_back(GatherTask{rf.p + coff[n], Wd, D, Dr, (int)sg.size(), 1});
+        sg.push_back(GatherSrc{psi + T.sub_off[q][n], Dr, 0, 1.0});
+      }
+    run_gathers(c, tg, sg);
+    // row-major RF (D x Wd) = column-major Wd x D matrix RF^T = U_a S V_a^T, so RF = V_a S U_a^T
+    const std::vector<double> sv = W.svd(rf.p, Wd, D, c->st);
+    const int p = (int)sv.size();
+    for (int a = 0; a < D; ++a) lam.push_back(a < p ? sv[a] : 0.0);
+    // R rows a < p: U_a^T (row-major = U_a's memory, ld Wd), scattered back to the sub-blocks
+    DevBuf rr;
+    rr.ensure((size_t)D * Wd);
+    CK(cudaMemsetAsync(rr.p, 0, (size_t)D * Wd * sizeof(double), c->st));
+    std::vector<GatherTask> t1;
+    std::vector<GatherSrc> s1;
+    t1.push_back(GatherTask{rr.p, Wd, p, Wd, 0, 1});
+    s1.push_back(GatherSrc{W.U.p, Wd, 0, 1.0});
+    t1.push_back(GatherTask{Y.buf.p + Y.off[q], D, D, p, 1, 1});       // V_a (D x D), columns a < p
+    s1.push_back(GatherSrc{W.V.p, D, 1, 1.0});
+    run_gathers(c, t1, s1);
+    std::vector<GatherTask> t2;
+    std::vector<GatherSrc> s2;
+    for (int n = 0; n < 4; ++n)
+      if (coff[n] >= 0) {
+        const int Dr = Rb.d[T.sub_qr[q][n]];
+        t2.push_back(GatherTask{R.d + T.sub_off[q][n], Dr, D, Dr, (int)s2.size(), 1});
+        s2.push_back(GatherSrc{rr.p + coff[n], Wd, 0, 1.0});
+      }
+    run_gathers(c, t2, s2);
+  }
+  BondMat US;
+  scale_cols(c, i, Y, lam, US);                 // U S of the right-fused SVD
+  SiteTensor prev = new_site(c, i - 1);
+  t_rmul(c, i - 1, c->sites[i - 1], US, prev, false);
+  c->sites[i] = std::move(R);
+  c->sites[i - 1] = std::move(prev);
+}
+
+static double sweep_onesite_impl(lrt_ctx* c, const lrt_gs_params& P, int nsweeps) {
+  const int k = c->k;
+  SvdWork W(c->st);
+  DevBuf psi;
+  double E = 0.0;
+  for (int sweep = 0; sweep < nsweeps; ++sweep) {
+    for (int i = 0; i + 1 < k; ++i) {
+      const SiteTensor& C = c->sites[i];
+      psi.ensure((size_t)std::max<int64_t>(C.total, 1));
+      CK(cudaMemcpyAsync(psi.p, C.d, (size_t)C.total * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      int its = 0;
+      E = davidson_site(c, i, 1, psi.p, P, &its);
+      gauge_shift_right(c, i, psi.p, W);
+      drop_plans(c);
+      c->R[i + 1].reset();
+      c->YR[i].reset();
+      renorm_left(c, i);
+    }
+    for (int i = k - 1; i >= 1; --i) {
+      const SiteTensor& C = c->sites[i];
+      psi.ensure((size_t)std::max<int64_t>(C.total, 1));
+      CK(cudaMemcpyAsync(psi.p, C.d, (size_t)C.total * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      int its = 0;
+      E = davidson_site(c, i, 1, psi.p, P, &its);
+      gauge_shift_left(c, i, psi.p, W);
+      drop_plans(c);
+      c->L[i].reset();
+      c->XL[i].reset();
+      renorm_right(c, i);
+    }
+  }
+  return E;
 }
 
 struct TdaRunner {
@@ -2808,7 +3068,7 @@ struct TdaRunner {
 
   void run(int n, double* theta_out, double* resid_out, int* iters_out) {
     setup();
-    const int N = P.max_space > 0 ? P.max_space : std::max(4 * n, 16);
+    const int N = P.max_space > 0 ? P.max_space : std::min(JACOBI_MAXN, std::max(8 * n, 24));
     std::vector<Vec> old;
     std::vector<double> alpha, theta, Hr, Sr, r2(n, 0.0);
     int m = 0, it = 0, mcols = 0;
@@ -3642,6 +3902,7 @@ int sweep_gs(lrt_t ctx, const lrt_gs_params* p, double* e0) {
       throw Error(LRT_EINVAL, "sweep_gs: bad parameters");
     int nsw = 0;
     *e0 = sweep_gs_impl(ctx, *p, &nsw);
+    if (p->onesite_sweeps > 0) *e0 = sweep_onesite_impl(ctx, *p, p->onesite_sweeps);
     ctx->last_sweeps = nsw;
   });
 }

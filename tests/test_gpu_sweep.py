@@ -68,3 +68,24 @@ def test_abinitio_k8_exact_at_M256(pkg):
     ef = fock.fci_energies(H.h, H.eri, H.e_core, H.k, H.n_alpha, H.n_beta, 1)[0]
     assert abs(E - ef) < 1e-8
     assert abs(_oracle_energy(H, bonds, sites) - E) < 1e-8
+
+
+def test_onesite_sweeps_lower_the_energy_and_keep_the_form(pkg):
+    """Two-site sweeps at a truncated bond dimension, then one-site sweeps: the energy does
+    not rise, it is the energy of the MPS left on the device (evaluated by the oracle), and
+    the sites 1..k-1 stay right-orthonormal."""
+    k, na, nb, M = 6, 3, 3, 12
+    H = synth.ab_initio(k, na, nb, 7)
+    E2, m, _, _ = _gs(pkg, H, 8, [M], max_sweeps=6)
+    E1, m1, bonds, sites = _gs(pkg, H, 8, [M], max_sweeps=6, onesite_sweeps=3)
+    assert E1 <= E2 + 1e-10
+    assert abs(_oracle_energy(H, bonds, sites) - E1) < 1e-9
+    for i in range(1, k):
+        blocks = om.unpack_site(sites[i], bonds[i], bonds[i + 1])
+        acc = {}
+        for (ql, _n, _qr), a in blocks.items():
+            acc[ql] = acc.get(ql, 0) + a @ a.T
+        for g in acc.values():
+            # rank-deficient sectors keep zero rows; the others are orthonormal
+            d = np.diag(g)
+            assert np.all((np.abs(d - 1.0) < 1e-10) | (np.abs(d) < 1e-10))
