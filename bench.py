@@ -36,8 +36,8 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 # sigma launches of the middle position (profiles/gemm_*_ppp_k12_M256_twosite.md), valid only
 # for the kernel source it was taken on (sha256 prefix); otherwise the bench reports null.
 TRAFFIC = {
-    "fp64": {"source": "lrt_kernels.cu", "sha256": "751ff19ee3994d57", "bytes": (57.139e6 + 14.172e6) / 2},
-    "mixed": {"source": "lrt_tc.cu", "sha256": "bd44adc66b77d94a", "bytes": (96.711e6 + 150.526e6) / 2},
+    "fp64": {"source": "lrt_kernels.cu", "sha256": "868172539334ceed", "bytes": (57.510e6 + 14.172e6) / 2},
+    "mixed": {"source": "lrt_tc.cu", "sha256": "af7f23206d56d09b", "bytes": (96.993e6 + 150.568e6) / 2},
 }
 
 
