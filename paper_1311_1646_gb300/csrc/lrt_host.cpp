@@ -865,6 +865,7 @@ struct TcPlan {
 
 struct SigmaPlan {
   uint64_t serial = 0;      // unique per plan (batched launches detect rebuilt plans by it)
+  bool has_tc = false;      // the tensor-core twin was planned
   GemmPlan p1, p2;
   DevArray<DiagOut> douts;
   DevArray<DiagTerm> dterms;
@@ -971,7 +972,60 @@ static void reset_env(lrt_ctx* c) {
 // X (+) site b (right = false: X is a left block ending at bond b) or site b (+) X
 // (right = true: X is a right block starting at bond b+1).  For a first-order
 // (transition) set X, Xrev is its reverse set: a transposed reference reads it.
-static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, int b, bool right) {
+// The plan of one enlargement (layout of the enlarged set and its gather tasks, with
+// addresses as offsets), reusable for any input set of the same layout and structure:
+// the TDA enlarges the first-order sets of every trial vector at a site, all alike.
+struct EnlTemplate {
+  std::unique_ptr<OpSet> proto;        // layout of the enlarged set, no data
+  std::vector<GatherTask> tasks;       // dst_off[i] replaces tasks[i].dst
+  std::vector<int64_t> dst_off;
+  std::vector<GatherSrc> srcs;         // src_off[i] from X (or Xrev when src_rev[i])
+  std::vector<int64_t> src_off;
+  std::vector<char> src_rev;
+  uint64_t sig = 0;
+};
+
+// layout and structure signature of an input (X, Xrev) pair
+static uint64_t set_signature(const OpSet& X, const OpSet* Xr) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (const OpSet* S : {&X, Xr}) {
+    if (!S) {
+      mix(0x9E3779B97F4A7C15ull);
+      continue;
+    }
+    mix((uint64_t)S->keys.size());
+    mix((uint64_t)S->ns());
+    mix((uint64_t)S->total);
+    for (char b : S->bnz) mix((uint64_t)(unsigned char)b);
+  }
+  return h;
+}
+
+static std::unique_ptr<OpSet> layout_copy(const OpSet& t) {
+  auto S = std::make_unique<OpSet>();
+  S->basis = t.basis;
+  S->right = t.right;
+  S->orbs = t.orbs;
+  S->in = t.in;
+  S->mode = t.mode;
+  S->keys = t.keys;
+  S->index = t.index;
+  S->da = t.da;
+  S->db = t.db;
+  S->par = t.par;
+  S->bra = t.bra;
+  S->off = t.off;
+  S->total = t.total;
+  S->bnz = t.bnz;
+  S->onz = t.onz;
+  S->mask = t.mask;
+  if (t.fused) S->fused = std::make_unique<Fused>(*t.fused);
+  return S;
+}
+
+static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, int b, bool right,
+                                          EnlTemplate* tpl = nullptr) {
   const Ints& I = c->I;
   const Site site(b);
   auto E = std::make_unique<OpSet>();
@@ -996,6 +1050,7 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
 
   std::vector<GatherTask> tasks;
   std::vector<std::vector<GatherSrc>> tsrc;
+  std::vector<std::vector<std::pair<int64_t, char>>> tsrc_off;   // template: source offsets
   std::unordered_map<const double*, int> task_of;
   std::vector<Ref> refs;
   for (size_t o = 0; o < E->keys.size(); ++o) {
@@ -1054,6 +1109,10 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
               ti = it->second;
             }
             tsrc[ti].push_back(GatherSrc{src, ld, tr, sign * e});
+            if (tpl) {
+              tsrc_off.resize(tsrc.size());
+              tsrc_off[ti].push_back({src - XS.d, (tr && Xrev) ? 1 : 0});
+            }
             E->mask[(size_t)o * E->ns() + fk] |= (uint16_t)(1u << (4 * n1 + n0));
             E->bnz[(size_t)o * E->ns() + fk] = 1;
           }
@@ -1066,12 +1125,43 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
     tasks[i].src_count = (int)tsrc[i].size();
     srcs.insert(srcs.end(), tsrc[i].begin(), tsrc[i].end());
   }
+  E->finish_nz();
+  if (tpl) {
+    tpl->proto = layout_copy(*E);
+    tpl->tasks = tasks;
+    tpl->srcs = srcs;
+    tpl->dst_off.clear();
+    for (const GatherTask& t : tasks) tpl->dst_off.push_back(t.dst - E->d);
+    tpl->src_off.clear();
+    tpl->src_rev.clear();
+    tsrc_off.resize(tsrc.size());
+    for (size_t i = 0; i < tasks.size(); ++i)
+      for (const auto& so : tsrc_off[i]) {
+        tpl->src_off.push_back(so.first);
+        tpl->src_rev.push_back(so.second);
+      }
+  }
   GatherPlan gp;
   build_gather(gp, tasks, srcs, c->st);
   gp.run(c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
-  E->finish_nz();
+  return E;
+}
+
+// an enlargement replayed from its template for new input data of the same layout
+static std::unique_ptr<OpSet> enlarge_from(lrt_ctx* c, const EnlTemplate& t, const OpSet& X, const OpSet* Xrev) {
+  auto E = layout_copy(*t.proto);
+  alloc_zero(*E, c->st);
+  std::vector<GatherTask> tasks = t.tasks;
+  std::vector<GatherSrc> srcs = t.srcs;
+  for (size_t i = 0; i < tasks.size(); ++i) tasks[i].dst = E->d + t.dst_off[i];
+  for (size_t i = 0; i < srcs.size(); ++i) srcs[i].src = (t.src_rev[i] ? Xrev->d : X.d) + t.src_off[i];
+  GatherPlan gp;
+  build_gather(gp, tasks, srcs, c->st);
+  gp.run(c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
   return E;
 }
 
@@ -1313,7 +1403,7 @@ static uint16_t transpose_mask(uint16_t m) {
 // (nsite 1) or the enlarged right block site+1 (+) R (nsite 2).  Xrev / Yrev: reverse
 // sets of first-order (transition) operator sets, read by transposed references.
 static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, const OpSet& Y,
-                                                  const OpSet* Yrev, int site, int nsite, int nvec) {
+                                                  const OpSet* Yrev, int site, int nsite, int nvec, bool tc = true) {
   const Ints& I = c->I;
   const int k = c->k;
   const Fused& XF = *X.fused;
@@ -1473,7 +1563,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                 }
                 o1.push_back(out);
               }
-              if (rows) {
+              if (tc && rows) {
                 const int A = tcp.op(base, ld, a.t ? 1 : 0, wbb.rows, wk.rows);
                 std::array<int, 4> tm{-1, -1, -1, -1};
                 for (int m = 0; m < (nsite == 1 ? 1 : 4); ++m) {
@@ -1531,7 +1621,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
                 }
             }
           }
-          if (rows) {
+          if (tc && rows) {
             const std::array<int, 4>* tm = ident ? nullptr : &tc_T.at(std::make_tuple(a.op, a.t, f));
             if (nsite == 1) {
               const int A = ident ? tcp.x(wk.off, wk.cols, 0, wk.rows, wk.cols) : (*tm)[0];
@@ -1611,7 +1701,8 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   build_gemm(plan->p1, O1, S1, c->st);
   build_gemm(plan->p2, O2, S2, c->st);
   // tensor-core twin: phase-2 outputs, one per (y block, column group)
-  for (size_t w = 0; w < wb.size(); ++w)
+  plan->has_tc = tc;
+  for (size_t w = 0; w < wb.size() && tc; ++w)
     for (int m = 0; m < (nsite == 1 ? 1 : 4); ++m) {
       const WfnBlock& wbk = wb[w];
       int64_t coff = wbk.off;
@@ -1643,7 +1734,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   return plan;
 }
 
-static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec) {
+static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, int nvec, bool tc) {
   OpSet& X = enlarged(c, site, false);
   OpSet* Yp;
   if (nsite == 1) {
@@ -1652,7 +1743,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma(lrt_ctx* c, int site, int nsite, in
   } else {
     Yp = &enlarged(c, site + 1, true);
   }
-  return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec);
+  return plan_sigma_sets(c, X, nullptr, *Yp, nullptr, site, nsite, nvec, tc);
 }
 
 // Work stream of one tensor-core launch over one or several plans (instances): tiles
@@ -1962,11 +2053,12 @@ static SigmaPlan* find_plan(lrt_ctx* c, int site, int nsite, int nvec) {
   return it == c->plans.end() ? nullptr : it->second.get();
 }
 
-static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec) {
+// the plan of (site, nsite, nvec); tc: with the tensor-core twin (replanned if missing)
+static SigmaPlan& get_plan(lrt_ctx* c, int site, int nsite, int nvec, bool tc = false) {
   auto key = std::make_tuple(site, nsite, nvec);
   auto it = c->plans.find(key);
-  if (it != c->plans.end()) return *it->second;
-  auto p = plan_sigma(c, site, nsite, nvec);
+  if (it != c->plans.end() && (!tc || it->second->has_tc)) return *it->second;
+  auto p = plan_sigma(c, site, nsite, nvec, tc);
   SigmaPlan& ref = *p;
   c->plans[key] = std::move(p);
   return ref;
@@ -2874,7 +2966,7 @@ struct TdaRunner {
     h0plan.resize(k);
     diag.resize(k);
     for (int i = 0; i < k; ++i) {
-      h0plan[i] = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, 1);
+      h0plan[i] = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, 1, mixed);
       diag[i].ensure(std::max<int64_t>(h0plan[i]->nelem, 1));
       launch_diag(h0plan[i]->douts.p, h0plan[i]->dterms.p, h0plan[i]->ndiag, diag[i].p, c->st);
     }
@@ -2892,12 +2984,31 @@ struct TdaRunner {
   }
 
   // y = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i  (Eq. hleft_sb on C0)
-  void dh_left(int i, const FirstOrder& HL, SiteTensor& y) {
+  // the first-order left sets of one vector enlarged by site i (both directions), shared
+  // by the site product below and the first-order renormalization of grow_HL
+  struct Enl {
+    std::unique_ptr<OpSet> f, r;
+  };
+  std::map<std::tuple<int, int, int>, EnlTemplate> enl_tpl;   // (site, right, reverse) -> template
+  std::unique_ptr<OpSet> enl(int i, bool right, int rev, const OpSet& X, const OpSet* Xr) {
+    EnlTemplate& t = enl_tpl[std::make_tuple(i, right ? 1 : 0, rev)];
+    const uint64_t sig = set_signature(X, Xr);
+    if (t.proto && t.sig == sig) return enlarge_from(c, t, X, Xr);
+    t = EnlTemplate();
+    t.sig = sig;
+    return enlarge_set(c, X, Xr, i, right, &t);
+  }
+  Enl enlarge_left(int i, const FirstOrder& HL) {
+    Enl e;
+    if (HL.empty()) return e;
+    e.f = enl(i, false, 0, *HL.f, HL.r.get());
+    e.r = enl(i, false, 1, *HL.r, HL.f.get());
+    return e;
+  }
+  void dh_left(int i, const Enl& XE, SiteTensor& y) {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
-    if (HL.empty()) return;
-    auto Xf = enlarge_set(c, *HL.f, HL.r.get(), i, false);
-    auto Xr = enlarge_set(c, *HL.r, HL.f.get(), i, false);
-    auto plan = plan_sigma_sets(c, *Xf, Xr.get(), *c->R[i + 1], nullptr, i, 1, 1);
+    if (!XE.f) return;
+    auto plan = plan_sigma_sets(c, *XE.f, XE.r.get(), *c->R[i + 1], nullptr, i, 1, 1, mixed);
     apply(*plan, C0(i).d, y.d);
   }
 
@@ -2905,7 +3016,7 @@ struct TdaRunner {
   void dh_right(int i, const FirstOrder& HR, SiteTensor& y) {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (HR.empty()) return;
-    auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1);
+    auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1, mixed);
     apply(*plan, C0(i).d, y.d);
   }
 
@@ -2935,17 +3046,15 @@ struct TdaRunner {
   }
 
   // first-order left set at bond i+1 (Eq. lopr1st), both directions
-  FirstOrder grow_HL(int i, const FirstOrder& HL, const SiteTensor& L1) {
+  FirstOrder grow_HL(int i, const Enl& XE, const SiteTensor& L1) {
     FirstOrder out;
     const OpSet& XL = *c->XL[i];
-    if (HL.empty()) {
+    if (!XE.f) {
       out.f = renorm_left_terms(c, i, {RenTerm{&XL, &L0(i), &L1}});
       out.r = renorm_left_terms(c, i, {RenTerm{&XL, &L1, &L0(i)}});
     } else {
-      auto Xf = enlarge_set(c, *HL.f, HL.r.get(), i, false);
-      auto Xr = enlarge_set(c, *HL.r, HL.f.get(), i, false);
-      out.f = renorm_left_terms(c, i, {RenTerm{Xf.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}});
-      out.r = renorm_left_terms(c, i, {RenTerm{Xr.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}});
+      out.f = renorm_left_terms(c, i, {RenTerm{XE.f.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}});
+      out.r = renorm_left_terms(c, i, {RenTerm{XE.r.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}});
     }
     return out;
   }
@@ -2958,8 +3067,8 @@ struct TdaRunner {
       out.f = renorm_right_terms(c, i, {RenTerm{&YR, &R0(i), &R1}});
       out.r = renorm_right_terms(c, i, {RenTerm{&YR, &R1, &R0(i)}});
     } else {
-      auto Yf = enlarge_set(c, *HR.f, HR.r.get(), i, true);
-      auto Yr = enlarge_set(c, *HR.r, HR.f.get(), i, true);
+      auto Yf = enl(i, true, 0, *HR.f, HR.r.get());
+      auto Yr = enl(i, true, 1, *HR.r, HR.f.get());
       out.f = renorm_right_terms(c, i, {RenTerm{Yf.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R0(i), &R1}});
       out.r = renorm_right_terms(c, i, {RenTerm{Yr.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R1, &R0(i)}});
     }
@@ -3127,10 +3236,12 @@ struct TdaRunner {
         }
         // [H_mu^{L} x h x H_0^{R}] C0 for every vector (Eq. sigv2, first line); it enters
         // both the site sigma of the corrections and the reduced matrices below
+        std::vector<Enl> XE(l);
         std::vector<SiteTensor> dHC0(l);
         for (int mu = 0; mu < l; ++mu) {
+          XE[mu] = enlarge_left(i, HL[mu]);
           dHC0[mu] = new_site(c, i);
-          dh_left(i, HL[mu], dHC0[mu]);
+          dh_left(i, XE[mu], dHC0[mu]);
         }
         // correction vectors (Eqs. sigv1, rnorm, error, param)
         for (int mu = 0; mu < n; ++mu) {
@@ -3193,7 +3304,7 @@ struct TdaRunner {
         for (int mu = 0; mu < l; ++mu) {
           L1[mu][i] = new_site(c, i);
           t_rmul(c, i, Ct[mu], ilam[i + 1], L1[mu][i], false);
-          if (i + 1 < k) HL[mu] = grow_HL(i, HL[mu], L1[mu][i]);
+          if (i + 1 < k) HL[mu] = grow_HL(i, XE[mu], L1[mu][i]);
         }
         Cprev = std::move(C1);
       }
@@ -3538,7 +3649,7 @@ static void sigma_batched_impl(lrt_ctx* const* ctxs, int n, const int* sites, in
       throw Error(LRT_ESTATE, "sigma_batched: environment of instance " + std::to_string(j) + " missing");
     if (!x[j] || !y[j]) throw Error(LRT_EINVAL, "sigma_batched: NULL vector");
     PoolScope ps(&c->pool);
-    plans[j] = &get_plan(c, sites[j], nsite, nvec);
+    plans[j] = &get_plan(c, sites[j], nsite, nvec, precision == LRT_MIXED);
     key += ":" + std::to_string(c->id) + "/" + std::to_string(sites[j]);
   }
   auto& slot = c0->batches[key];
@@ -3854,7 +3965,7 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
       throw Error(LRT_EINVAL, "sigma: bad arguments");
     if (precision != LRT_FP64 && precision != LRT_MIXED) throw Error(LRT_EINVAL, "sigma: bad precision");
     if (!ctx->L[site]) throw Error(LRT_ESTATE, "sigma: left block of bond " + std::to_string(site) + " missing");
-    SigmaPlan& p = get_plan(ctx, site, nsite, nvec);
+    SigmaPlan& p = get_plan(ctx, site, nsite, nvec, precision == LRT_MIXED);
     if ((const double*)y_dev < x_dev + p.nelem * nvec && x_dev < (const double*)y_dev + p.nelem * nvec)
       throw Error(LRT_EINVAL, "sigma: x and y overlap");
     if (precision == LRT_MIXED) {
