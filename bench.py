@@ -390,36 +390,42 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
     for c in bctx:
         c.close()
     out["batch32_config4_onesite"] = batch
-    # (4) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU
+    # (4) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU: two-site
+    # and one-site ground-state sweeps once, then tda_prepare + sweep_tda in each precision
     cfg = synth.config(1)
     H = cfg["ham"]
     nr = cfg["nroots"]
+    g = pkg.Context(device)
+    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+    e_gs = g.sweep_gs([32, cfg["M"]], max_sweeps=8, onesite_sweeps=4)
+    bonds, sites = g.mps_get()
+    g.close()
     res = {}
     for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
         t = pkg.Context(device)
         t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-        m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
-        t.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
-        e_gs = t.sweep_gs([32, cfg["M"]], max_sweeps=8, onesite_sweeps=4)
+        t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
         t.tda_prepare()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        om, rs, e0 = t.sweep_tda(nr, max_iter=30, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
-                                 refine_tol=1e-3)
+        om, rs, e0 = t.sweep_tda(nr, max_iter=60, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
+                                 refine_tol=1e-4)
         torch.cuda.synchronize()
-        res[prec] = (time.perf_counter() - t0, om, rs, e0, e_gs)
+        res[prec] = (time.perf_counter() - t0, om, rs, e0)
         t.close()
-    (s64, w64, r64, e64, g64), (smx, wmx, rmx, emx, gmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
+    (s64, w64, r64, e64), (smx, wmx, rmx, emx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
     out["tda_abinitio_k8_M64_4roots"] = {
-        "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "e0_gs": g64,
+        "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "e0": e64,
         "omega_fp64": list(w64), "omega_mixed": list(wmx),
-        "max_abs_domega_Eh": float(np.abs(w64 - wmx).max()),
+        "abs_domega_Eh": list(np.abs(w64 - wmx)),
         "resid_fp64": list(r64), "resid_mixed": list(rmx), "eps": 1e-8,
-        "converged_fp64": bool(np.all(r64 < 1e-8)), "converged_mixed": bool(np.all(rmx < 1e-8)),
-        "note": "wall time of sweep_tda (30 sweeps at most, diagonal start, subspace 32; mixed: "
-                "tensor-core site products until sum |r|^2 < 1e-3, then FP64) / roots; reference from "
-                "two-site + 4 one-site sweep_gs sweeps and tda_prepare on the GPU; the TDA loop is "
-                "host-bound at this size"}
+        "note": "wall time of sweep_tda (60 sweeps at most, diagonal start, subspace 32; mixed: "
+                "tensor-core site products until sum |r|^2 < 1e-4, then FP64) / roots; reference: "
+                "two-site + 4 one-site sweep_gs sweeps and tda_prepare on the GPU; resid = sum of "
+                "the site residuals^2 per root (roots with resid near 1e-4 stall there); the TDA "
+                "loop is host-bound at this size"}
     return out
 
 
