@@ -77,6 +77,20 @@ def parse():
     return p.parse_args()
 
 
+def replica_throughput(total_ms, steps, flops_step, world, device="cpu"):
+    """Replicas (one independent copy of the step per rank): the slowest rank's time over
+    the timed steps decides, and the whole job did world x flops_step per step.
+    Returns (ms_per_step, TFLOP/s of the whole job)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * flops_step / (ms_per_step * 1e-3) / 1e12
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -202,13 +216,8 @@ def run_ours(args):
         step_ms.append(e0.elapsed_time(e1))
         sigma_ms.append(sum(a.elapsed_time(b) for a, b in ev))
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{device}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * flops_step / (ms_per_step * 1e-3) / 1e12
+    ms_per_step, value = replica_throughput(sum(step_ms), args.steps, flops_step, world,
+                                            f"cuda:{device}" if world > 1 else "cpu")
     achieved = flops_step / (sum(sigma_ms) / args.steps * 1e-3) / 1e12
 
     # end to end through the public API: pinned host inputs -> device -> sigma -> host
