@@ -3350,7 +3350,8 @@ struct TdaRunner {
           const double rt = P.refine_tol > 0.0 ? P.refine_tol : 1e-6;
           bool low = true;
           for (int mu = 0; mu < n; ++mu) low = low && (r2[mu] < std::max(rt, P.eps));
-          if (low) mixed = false;
+          // at the latest after two thirds of the sweeps, so that the last ones are FP64
+          if (low || it >= (2 * P.max_iter) / 3) mixed = false;
           conv = false;
         }
         if (conv || it >= P.max_iter) {
