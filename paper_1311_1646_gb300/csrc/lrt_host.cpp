@@ -1761,19 +1761,59 @@ struct TcSource {
 static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, DevArray<TcItem>& items,
                             DevArray<int>& begins, int& nctas, cudaStream_t st) {
   const int TM = tc_tile_m();
-  struct Tile { int s, v, o, a, b; int64_t k; };
+  // Stacking: single-product outputs into intermediates (phase 1) that share their B
+  // operand, K and width have their last (partial) 128-row block packed with others into
+  // one tile, rows rounded up to 8 (first fit, decreasing).
+  struct Piece { int o, row0, nrows, srow; };
+  struct Stack { int s, v, n, k, b; std::vector<Piece> pc; };
+  std::vector<Stack> stacks;
+  struct Tile { int s, v, o, a, b; int64_t k; int stack; };
   std::vector<Tile> tiles;
   for (size_t si = 0; si < src.size(); ++si) {
     const TcPlan& tp = *src[si].tp;
     const std::vector<TcPlanOut>& outs = *src[si].outs;
-    for (int v = 0; v < nvec; ++v)
+    for (int v = 0; v < nvec; ++v) {
+      std::map<std::tuple<int, int, int>, std::vector<Piece>> groups;   // (B matrix, n, k) -> pieces
       for (size_t i = 0; i < outs.size(); ++i) {
         int64_t kt = 0;
         for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
-        for (int a = 0; a < (outs[i].m + TM - 1) / TM; ++a)
+        const bool stackable = outs[i].tmat >= 0 && outs[i].seg_count == 1 && outs[i].m % TM != 0;
+        const int full = outs[i].m / TM;
+        for (int a = 0; a < (stackable ? full : (outs[i].m + TM - 1) / TM); ++a)
           for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b)
-            tiles.push_back(Tile{(int)si, v, (int)i, a, b, kt});
+            tiles.push_back(Tile{(int)si, v, (int)i, a, b, kt, -1});
+        if (stackable) {
+          const TcPlanSeg& g = tp.segs[outs[i].seg_begin];
+          const int rem = outs[i].m - full * TM;
+          groups[std::make_tuple(g.b, outs[i].n, g.k)].push_back(Piece{(int)i, full * TM, (rem + 7) & ~7, 0});
+        }
       }
+      for (auto& kv : groups) {
+        std::vector<Piece>& pcs = kv.second;
+        std::stable_sort(pcs.begin(), pcs.end(), [](const Piece& x, const Piece& y) { return x.nrows > y.nrows; });
+        std::vector<Stack> bins;
+        std::vector<int> used;
+        for (const Piece& pc : pcs) {
+          size_t j = 0;
+          for (; j < bins.size(); ++j)
+            if (used[j] + pc.nrows <= TM && (int)bins[j].pc.size() < TC_MAX_PIECES) break;
+          if (j == bins.size()) {
+            bins.push_back(Stack{(int)si, v, std::get<1>(kv.first), std::get<2>(kv.first), std::get<0>(kv.first), {}});
+            used.push_back(0);
+          }
+          Piece q = pc;
+          q.srow = used[j];
+          used[j] += pc.nrows;
+          bins[j].pc.push_back(q);
+        }
+        for (Stack& b : bins) {
+          const int id = (int)stacks.size();
+          stacks.push_back(std::move(b));
+          for (int nb = 0; nb < (stacks[id].n + TN - 1) / TN; ++nb)
+            tiles.push_back(Tile{(int)si, v, stacks[id].pc[0].o, 0, nb, (int64_t)stacks[id].k, id});
+        }
+      }
+    }
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& x, const Tile& y) { return x.k > y.k; });
   const int nt = (int)tiles.size();
@@ -1784,6 +1824,7 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
   };
   std::vector<TcItem> it;
   std::vector<int> beg;
+  std::vector<std::pair<size_t, size_t>> fix;   // stacked header -> index of its first piece
   for (int b = 0; b < nctas; ++b) {
     beg.push_back((int)it.size());
     for (int w = b; w < nt; w += nctas) {
@@ -1791,6 +1832,59 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
       const TcSource& sc = src[t.s];
       const TcPlan& tp = *sc.tp;
       const TcPlanOut& o = (*sc.outs)[t.o];
+      if (t.stack >= 0) {
+        const Stack& S = stacks[t.stack];
+        TcItem h{};
+        h.type = TC_ITEM_TILE;
+        h.t.c_rel = 3;
+        h.t.m0 = 0;
+        h.t.n0 = t.b * TN;
+        h.t.nt = std::min(TN, S.n - h.t.n0);
+        h.t.t_k = S.n;
+        h.t.inst = (int)S.pc.size();
+        int rows = 0;
+        for (const Piece& pc : S.pc) rows += pc.nrows;
+        h.t.mt = rows;
+        fix.push_back({it.size(), it.size() + 1});
+        it.push_back(h);
+        const TcPlanSeg* g0 = nullptr;
+        for (const Piece& pc : S.pc) {
+          const TcPlanOut& po = (*sc.outs)[pc.o];
+          const TcPlanSeg& g = tp.segs[po.seg_begin];
+          g0 = &g;
+          const TcMat& A = tp.mats[g.a];
+          const TcMat& T = tp.mats[po.tmat];
+          if (A.Rp < pc.row0 + pc.nrows || T.Rp < pc.row0 + pc.nrows || T.K != S.n)
+            throw Error(LRT_EINVAL, "tensor-core plan: stacked piece outside its matrices");
+          TcItem r{};
+          r.type = TC_ITEM_PIECE;
+          r.p.a_hi = base(sc, A, t.v, true);
+          r.p.a_lo = base(sc, A, t.v, false);
+          r.p.t_hi = base(sc, T, t.v, true);
+          r.p.t_lo = base(sc, T, t.v, false);
+          r.p.a_rp = A.Rp;
+          r.p.a_row0 = pc.row0;
+          r.p.nrows = pc.nrows;
+          r.p.smem_row = pc.srow;
+          r.p.t_rp = T.Rp;
+          r.p.t_row0 = pc.row0;
+          it.push_back(r);
+        }
+        const TcMat& A0 = tp.mats[g0->a];
+        const TcMat& B = tp.mats[g0->b];
+        TcItem r{};
+        r.type = TC_ITEM_SEG;
+        r.s.a_hi = base(sc, A0, t.v, true);
+        r.s.a_lo = base(sc, A0, t.v, false);
+        r.s.b_hi = base(sc, B, t.v, true);
+        r.s.b_lo = base(sc, B, t.v, false);
+        r.s.a_rp = A0.Rp;
+        r.s.b_rp = B.Rp;
+        r.s.k = S.k;
+        r.s.scale = g0->scale;
+        it.push_back(r);
+        continue;
+      }
       TcItem h{};
       h.type = TC_ITEM_TILE;
       h.t.m0 = t.a * TM;
@@ -1839,6 +1933,12 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
   }
   beg.push_back((int)it.size());
   items.upload(it, st);
+  if (!fix.empty()) {
+    // stacked headers point at their pieces, in the uploaded stream
+    for (const auto& f : fix) it[f.first].t.C = reinterpret_cast<double*>(items.p + f.second);
+    CK(cudaMemcpyAsync(items.p, it.data(), it.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   begins.upload(beg, st);
 }
 

@@ -104,13 +104,30 @@ struct TcSegRec {
   int k;              // valid K
   float scale;
 };
-constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2;
+// Stacked tiles (c_rel == 3): the tile's 128 rows hold several short products that share
+// their B operand and K; header.C points at the tile's piece items, header.inst counts
+// them, and every piece names the rows of its A matrix, where they go in the tile (a
+// multiple of 8, so the swizzle phase of the packed rows is kept) and the intermediate
+// they produce.  The pieces are followed by one segment item (B, k, scale).
+struct TcPieceRec {
+  const float* a_hi;
+  const float* a_lo;
+  float* t_hi;
+  float* t_lo;
+  int a_rp, a_row0;   // A matrix: padded rows, first row of the piece
+  int nrows;          // rows of the piece (multiple of 8)
+  int smem_row;       // first row of the piece in the tile (multiple of 8)
+  int t_rp, t_row0;   // intermediate: padded rows, first row written
+};
+constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2, TC_ITEM_PIECE = 3;
+constexpr int TC_MAX_PIECES = 16;
 struct TcItem {
   int type;
   int pad;
   union {
     TcTileHdr t;
     TcSegRec s;
+    TcPieceRec p;
   };
 };
 struct TcOut {

@@ -279,6 +279,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
       const int p0 = cta_begin[blockIdx.x], p1 = cta_begin[blockIdx.x + 1];
       bool have_tile = false, first_seg = true;
       TcTileHdr hdr{};
+      TcPieceRec pieces[TC_MAX_PIECES];
+      int npieces = 0;
       TcItem cur, nx1, nx2;
       if (p0 < p1) cur = load_item(items + p0);
       if (p0 + 1 < p1) nx1 = load_item(items + p0 + 1);
@@ -289,12 +291,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           hdr = cur.t;
           have_tile = true;
           first_seg = true;
+          npieces = 0;
+        } else if (cur.type == TC_ITEM_PIECE) {
+          if (npieces < TC_MAX_PIECES) pieces[npieces++] = cur.p;
         } else if (cur.s.k > 0) {
           const TcSegRec& g = cur.s;
           ok = post(EpiInfo{INFO_MMA | (first_seg ? INFO_FIRST : 0), g.scale, hdr});
           first_seg = false;
           // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
-          const uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0), rb = (uint32_t)min(TN, g.b_rp - hdr.n0);
+          uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0);
+          if (hdr.c_rel == 3) {
+            ra = 0;
+            for (int j = 0; j < npieces; ++j) ra += (uint32_t)pieces[j].nrows;
+          }
+          const uint32_t rb = (uint32_t)min(TN, g.b_rp - hdr.n0);
           const uint32_t bytes = 2u * 128u * (ra + rb);
           for (int k0 = 0, q = 0; k0 < g.k && ok; k0 += TC_K, ++q, ++it) {
             const uint32_t stage = it % STAGES, round = it / STAGES;
@@ -307,8 +317,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
             const uint32_t st = sbase + stage * Tile<TN>::STAGE_BYTES;
             const int64_t ao = ((int64_t)q * g.a_rp + hdr.m0) * TC_K, bo = ((int64_t)q * g.b_rp + hdr.n0) * TC_K;
             mbar_arrive_tx(&full_bar[stage], bytes);
-            bulk_g2s(st, g.a_hi + ao, 128u * ra, &full_bar[stage]);
-            bulk_g2s(st + A_BYTES, g.a_lo + ao, 128u * ra, &full_bar[stage]);
+            if (hdr.c_rel == 3) {
+              for (int j = 0; j < npieces; ++j) {
+                const TcPieceRec& pc = pieces[j];
+                const int64_t po = ((int64_t)q * pc.a_rp + pc.a_row0) * TC_K;
+                const uint32_t so = (uint32_t)pc.smem_row * 128u;
+                bulk_g2s(st + so, pc.a_hi + po, 128u * (uint32_t)pc.nrows, &full_bar[stage]);
+                bulk_g2s(st + A_BYTES + so, pc.a_lo + po, 128u * (uint32_t)pc.nrows, &full_bar[stage]);
+              }
+            } else {
+              bulk_g2s(st, g.a_hi + ao, 128u * ra, &full_bar[stage]);
+              bulk_g2s(st + A_BYTES, g.a_lo + ao, 128u * ra, &full_bar[stage]);
+            }
             bulk_g2s(st + 2 * A_BYTES, g.b_hi + bo, 128u * rb, &full_bar[stage]);
             bulk_g2s(st + 2 * A_BYTES + Tile<TN>::B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
           }
@@ -442,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         // the staging buffer may still be read by this warp's previous bulk stores
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         __syncwarp();
-        if (t.c_rel == 2) {
+        if (t.c_rel >= 2) {
           // Intermediate: this warp's rows as a TC-matrix image (two chunks of 32
           // columns, hi and lo planes; row r's 16-byte groups permuted by r mod 8),
           // then one bulk store per chunk and plane: rows [m0 + 32 w, + nrows) of a
@@ -464,18 +484,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
             }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
-          if (lane == 0 && nrows > 0) {
+          // one bulk store per chunk and plane of a run of rows that is contiguous both
+          // here and in its intermediate
+          auto store_rows = [&](float* th, float* tl, int trp, int64_t trow, int r0, int nr) {
             for (int q = 0; q < TN / 32; ++q) {
               const int cq = t.n0 + 32 * q;
               if (cq >= t.t_k) break;
-              const int64_t go = ((int64_t)(cq >> 5) * t.t_rp + t.m0 + rbase) * 32;
-              const uint32_t so = smem_u32(stg) + (uint32_t)(q * 32 * 128);
-              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(t.t_hi + go), "r"(so),
-                           "r"((uint32_t)nrows * 128u)
+              const int64_t go = ((int64_t)(cq >> 5) * trp + trow) * 32;
+              const uint32_t so = smem_u32(stg) + (uint32_t)(q * 32 * 128) + (uint32_t)r0 * 128u;
+              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(th + go), "r"(so),
+                           "r"((uint32_t)nr * 128u)
                            : "memory");
-              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(t.t_lo + go),
-                           "r"(so + (uint32_t)(TN / 32) * 32u * 128u), "r"((uint32_t)nrows * 128u)
+              asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(tl + go),
+                           "r"(so + (uint32_t)(TN / 32) * 32u * 128u), "r"((uint32_t)nr * 128u)
                            : "memory");
+            }
+          };
+          if (lane == 0) {
+            if (t.c_rel == 2) {
+              if (nrows > 0) store_rows(t.t_hi, t.t_lo, t.t_rp, t.m0 + rbase, 0, nrows);
+            } else {
+              // stacked tile: the pieces that overlap this warp's 32 rows
+              const TcItem* pit = reinterpret_cast<const TcItem*>(t.C);
+              for (int j = 0; j < t.inst; ++j) {
+                const TcItem pe = load_item(pit + j);
+                const int s0 = pe.p.smem_row, s1 = s0 + pe.p.nrows;
+                const int lo = max(s0, rbase), hi = min(s1, rbase + 32);
+                if (lo < hi) store_rows(pe.p.t_hi, pe.p.t_lo, pe.p.t_rp, pe.p.t_row0 + (lo - s0), lo - rbase, hi - lo);
+              }
             }
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
