@@ -37,6 +37,7 @@
 
 #include "../../include/lrt.h"
 #include "lrt_kernels.h"
+#include "lrt_fp64_tile.h"
 
 namespace lrt {
 
@@ -711,25 +712,44 @@ static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vec
 
 static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std::vector<GemmSeg>& segs,
                        cudaStream_t st) {
-  std::vector<int3> tiles;
+  // A tile costs its warps of outputs times its K chunks of DFMA issue, plus a fixed
+  // cost per chunk.  Tiles far longer than an even share of the launch (an output with
+  // many long K segments) would run on after all others finished, so they are cut into
+  // row slices of at most that share; then the longest go first.
+  std::vector<int64_t> ktot(outs.size(), 0);
   double fl = 0.0;
-  for (size_t i = 0; i < outs.size(); ++i) {
-    const int tm = (outs[i].m + GEMM_TM - 1) / GEMM_TM;
-    const int tn = (outs[i].n + GEMM_TN - 1) / GEMM_TN;
-    for (int a = 0; a < tm; ++a)
-      for (int b = 0; b < tn; ++b) tiles.push_back(make_int3((int)i, a, b));
-    for (int s = 0; s < outs[i].seg_count; ++s)
+  for (size_t i = 0; i < outs.size(); ++i)
+    for (int s = 0; s < outs[i].seg_count; ++s) {
+      ktot[i] += segs[outs[i].seg_begin + s].k;
       fl += 2.0 * outs[i].m * (double)outs[i].n * segs[outs[i].seg_begin + s].k;
-  }
-  // larger products first so the tail of the grid is short
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const int3& a, const int3& b) {
-    const GemmOut& oa = outs[a.x];
-    const GemmOut& ob = outs[b.x];
-    int64_t ka = 0, kb = 0;
-    for (int s = 0; s < oa.seg_count; ++s) ka += segs[oa.seg_begin + s].k;
-    for (int s = 0; s < ob.seg_count; ++s) kb += segs[ob.seg_begin + s].k;
-    return ka > kb;
+    }
+  auto cost = [](int64_t mt, int64_t nt, int64_t k) {
+    return ((k + GEMM_KC - 1) / GEMM_KC) * (32 * ((mt * nt + 31) / 32) + 64) + 64;
+  };
+  int64_t total = 0;
+  for (size_t i = 0; i < outs.size(); ++i)
+    for (int m0 = 0; m0 < outs[i].m; m0 += GEMM_TM)
+      for (int n0 = 0; n0 < outs[i].n; n0 += GEMM_TN)
+        total += cost(std::min(GEMM_TM, outs[i].m - m0), std::min(GEMM_TN, outs[i].n - n0), ktot[i]);
+  const int64_t cap = std::max<int64_t>(1, total / gemm_fp64_slots());
+  std::vector<std::pair<int64_t, int3>> tl;
+  for (size_t i = 0; i < outs.size(); ++i)
+    for (int m0 = 0; m0 < outs[i].m; m0 += GEMM_TM)
+      for (int n0 = 0; n0 < outs[i].n; n0 += GEMM_TN) {
+        const int mt = std::min(GEMM_TM, outs[i].m - m0), nt = std::min(GEMM_TN, outs[i].n - n0);
+        const int64_t c = cost(mt, nt, ktot[i]);
+        const int parts = (int)std::min<int64_t>(mt, (c + cap - 1) / cap);
+        for (int p = 0, r = m0; p < parts; ++p) {
+          const int rows = mt / parts + (p < mt % parts ? 1 : 0);
+          tl.push_back({cost(rows, nt, ktot[i]), gemm_tile((int)i, r, rows, n0, nt)});
+          r += rows;
+        }
+      }
+  std::stable_sort(tl.begin(), tl.end(), [](const std::pair<int64_t, int3>& a, const std::pair<int64_t, int3>& b) {
+    return a.first > b.first;
   });
+  std::vector<int3> tiles(tl.size());
+  for (size_t t = 0; t < tl.size(); ++t) tiles[t] = tl[t].second;
   P.outs.upload(outs, st);
   P.segs.upload(segs, st);
   P.tiles.upload(tiles, st);

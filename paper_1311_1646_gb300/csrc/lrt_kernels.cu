@@ -8,6 +8,7 @@
 //             one output block are summed in registers without atomics.
 //  diag:      outer products of operator diagonals (preconditioner of Eq. error).
 #include "lrt_kernels.h"
+#include "lrt_fp64_tile.h"
 
 #include <algorithm>
 
@@ -70,24 +71,56 @@ void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* t
 // grouped FP64 GEMM with K-concatenated segments
 //
 // GB300 issues about 2 FP64 FMA per clock per SM, so the kernel is bound by the
-// number of DFMA warp instructions, not by operand bandwidth.  Register tiling
-// is therefore pointless and padding is the enemy: each lane owns individual
-// output elements of a <= GEMM_TM x GEMM_TN tile (flattened, so only the last
-// warp of a tile is partly idle) and the K loop runs the exact trip count.
+// number of DFMA warp instructions once its operands arrive in time.  Padding is
+// the enemy: each lane owns individual output elements of a <= GEMM_TM x GEMM_TN
+// tile (flattened, so only the last warp of a tile is partly idle).  The segments
+// of a tile (often a dozen or more, each contracting only ~8 indices) are packed
+// along one K axis and staged GEMM_KC positions at a time with cp.async into a
+// double buffer, so a chunk's copies are all in flight at once and overlap the
+// previous chunk's FMAs (the staging plan is in lrt_fp64_tile.h).
 // ---------------------------------------------------------------------------
-constexpr int KC = 16;
-constexpr int GEMM_THREADS = 128;
 constexpr int GEMM_MAXE = GEMM_TM * GEMM_TN / GEMM_THREADS;   // outputs per thread
+static_assert(GEMM_TM == GEMM_TILE_M && GEMM_TN == GEMM_TILE_N, "tile shape of the staging plan");
 
-__global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
+struct GemmSmem {
+  double As[2][GEMM_TM][GEMM_KC + 1];
+  double Bs[2][GEMM_KC][GEMM_TN + 1];
+  double sc[2][GEMM_KC];          // scale of the segment holding each K position of a chunk
+  SegS sd[GEMM_SEGB];
+  int kst[GEMM_SEGB + 1];
+  int unit[2];                    // every scale of the chunk is 1
+};
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// acc[j] += sum_kk As[row_j][kk] Bs[kk][col_j] over a staged chunk, for the first N outputs
+template <int N>
+__device__ __forceinline__ void fma_chunk(double (&acc)[GEMM_MAXE], const uint32_t (&rc)[GEMM_MAXE],
+                                          const double* __restrict__ As, const double* __restrict__ Bs, int kc) {
+  for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      acc[j] = fma(As[(rc[j] >> 16) * (GEMM_KC + 1) + kk], Bs[kk * (GEMM_TN + 1) + (rc[j] & 0xFFFFu)], acc[j]);
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
                                                                     const GemmSeg* __restrict__ segs,
                                                                     const int3* __restrict__ tiles, int ntiles,
                                                                     const double* __restrict__ xbase,
                                                                     double* __restrict__ ybase,
                                                                     double* __restrict__ tbase,
                                                                     const GemmBases* __restrict__ multi) {
-  __shared__ double As[GEMM_TM][KC + 1];
-  __shared__ double Bs[KC][GEMM_TN + 1];
+  extern __shared__ __align__(16) unsigned char gemm_smem_raw[];
+  GemmSmem& S = *reinterpret_cast<GemmSmem*>(gemm_smem_raw);
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
@@ -98,10 +131,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOu
     ybase = b.y;
     tbase = b.t;
   }
-  const int m0 = wi.y * GEMM_TM, n0 = wi.z * GEMM_TN;
-  const int mt = min(GEMM_TM, o.m - m0), nt = min(GEMM_TN, o.n - n0);
+  const int m0 = wi.y >> 8, mt = wi.y & 255, n0 = wi.z >> 8, nt = wi.z & 255;
   const int ne = mt * nt;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t rc[GEMM_MAXE];        // (row << 16) | col of each owned output element
   double acc[GEMM_MAXE];
 #pragma unroll
@@ -111,32 +143,79 @@ __global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOu
     acc[j] = 0.0;
   }
   const int cnt = ne > tid ? (ne - tid + GEMM_THREADS - 1) / GEMM_THREADS : 0;
+  // outputs of lane 0, the most of any lane of the warp; the other lanes' extra slots
+  // accumulate (0, 0)-element products that are never stored
+  const int cntw = ne > 32 * warp ? (ne - 32 * warp + GEMM_THREADS - 1) / GEMM_THREADS : 0;
 
-  for (int s = 0; s < o.seg_count; ++s) {
-    GemmSeg g = segs[o.seg_begin + s];
-    if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : tbase) + g.a_off;
-    if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : tbase) + g.b_off;
-    for (int k0 = 0; k0 < g.k; k0 += KC) {
-      const int kc = min(KC, g.k - k0);
-      for (int e = tid; e < mt * kc; e += GEMM_THREADS) {
-        int i, kk;
-        if (!g.transA) { i = e / kc; kk = e % kc; } else { kk = e / mt; i = e % mt; }
-        const int gi = m0 + i, gk = k0 + kk;
-        As[i][kk] = g.scale * (g.transA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk]);
+  for (int b0 = 0; b0 < o.seg_count; b0 += GEMM_SEGB) {
+    const int nb = min(GEMM_SEGB, o.seg_count - b0);
+    __syncthreads();   // the previous batch's descriptors and buffers are no longer read
+    if (warp == 0) {
+      int k = 0;
+      if (lane < nb) {
+        GemmSeg g = segs[o.seg_begin + b0 + lane];
+        if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : tbase) + g.a_off;
+        if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : tbase) + g.b_off;
+        S.sd[lane] = SegS{g.A, g.B, g.lda, g.ldb, g.transA, g.transB, g.scale};
+        k = g.k;
       }
-      for (int e = tid; e < kc * nt; e += GEMM_THREADS) {
-        int j, kk;
-        if (!g.transB) { kk = e / nt; j = e % nt; } else { j = e / kc; kk = e % kc; }
-        const int gj = n0 + j, gk = k0 + kk;
-        Bs[kk][j] = g.transB ? g.B[(int64_t)gj * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gj];
-      }
-      __syncthreads();
-      for (int kk = 0; kk < kc; ++kk) {
+      int incl = k;   // inclusive prefix of k over the lanes
 #pragma unroll
-        for (int j = 0; j < GEMM_MAXE; ++j)
-          if (j < cnt) acc[j] = fma(As[rc[j] >> 16][kk], Bs[kk][rc[j] & 0xFFFFu], acc[j]);
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
       }
-      __syncthreads();
+      S.kst[lane + 1] = incl;
+      if (lane == 0) S.kst[0] = 0;
+    }
+    __syncthreads();
+    const int Kb = S.kst[nb];
+    const int nch = (Kb + GEMM_KC - 1) / GEMM_KC;
+
+    auto issue = [&](int c, int buf) {
+      const int p0 = c * GEMM_KC;
+      stage_chunk(tid, S.sd, S.kst, Kb, p0, m0, mt, n0, nt, [&](int which, int r, int col, const double* src) {
+        if (which == 0) cp_async8(&S.As[buf][r][col], src);
+        else cp_async8(&S.Bs[buf][r][col], src);
+      });
+      if (warp == 0) {
+        const int p = p0 + lane;
+        const double s = p < Kb ? S.sd[seg_at(S.kst, p, 0)].scale : 1.0;
+        S.sc[buf][lane] = s;
+        const bool u = __all_sync(0xffffffffu, s == 1.0);
+        if (lane == 0) S.unit[buf] = u ? 1 : 0;
+      }
+      cp_async_commit();
+    };
+
+    if (nch > 0) issue(0, 0);
+    for (int c = 0; c < nch; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < nch) {
+        issue(c + 1, buf ^ 1);   // buffer buf ^ 1 was last read before the previous iteration's barrier
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();           // chunk c has landed for every thread
+      const int kc = min(GEMM_KC, Kb - c * GEMM_KC);
+      if (!S.unit[buf]) {        // scale row kk of B by its segment's scale
+        if (lane < nt)
+          for (int kk = warp; kk < kc; kk += 4) S.Bs[buf][kk][lane] *= S.sc[buf][kk];
+        __syncthreads();
+      }
+      const double* As = &S.As[buf][0][0];
+      const double* Bs = &S.Bs[buf][0][0];
+      switch (cntw) {            // warp-uniform trip count: no predicated-off DFMA occupies the pipe
+#define LRT_FMA_CASE(N) \
+  case N: fma_chunk<N>(acc, rc, As, Bs, kc); break;
+        LRT_FMA_CASE(1) LRT_FMA_CASE(2) LRT_FMA_CASE(3) LRT_FMA_CASE(4) LRT_FMA_CASE(5) LRT_FMA_CASE(6)
+        LRT_FMA_CASE(7) LRT_FMA_CASE(8) LRT_FMA_CASE(9) LRT_FMA_CASE(10) LRT_FMA_CASE(11) LRT_FMA_CASE(12)
+        LRT_FMA_CASE(13) LRT_FMA_CASE(14) LRT_FMA_CASE(15) LRT_FMA_CASE(16)
+#undef LRT_FMA_CASE
+        default: break;
+      }
+      __syncthreads();           // buffer buf is free for chunk c + 2
     }
   }
 #pragma unroll
@@ -148,16 +227,41 @@ __global__ void __launch_bounds__(GEMM_THREADS, 8) gemm_fp64_kernel(const GemmOu
   }
 }
 
+int gemm_fp64_slots() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    n = std::max(1, nsm) * 4;   // __launch_bounds__ minimum, met by the registers and shared memory
+  }
+  return n;
+}
+
+static void gemm_fp64_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
+    // all of the unified L1 as shared memory, so four CTAs fit on an SM
+    cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done = true;
+  }
+}
+
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st) {
   if (ntiles <= 0) return;
-  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase, nullptr);
+  gemm_fp64_smem_attr();
+  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase,
+                                                                  nullptr);
 }
 
 void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                             const GemmBases* bases, cudaStream_t st) {
   if (ntiles <= 0) return;
-  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, 0, st>>>(outs, segs, tiles, ntiles, nullptr, nullptr, nullptr, bases);
+  gemm_fp64_smem_attr();
+  gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, nullptr, nullptr,
+                                                                  nullptr, bases);
 }
 
 // ---------------------------------------------------------------------------

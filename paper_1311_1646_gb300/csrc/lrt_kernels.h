@@ -57,9 +57,14 @@ struct DiagTerm {
   double scale;
 };
 
-// work items: (task index, tile row, tile col) packed as int3
+// gather work items: (task index, tile row, tile col) packed as int3
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
                    cudaStream_t st);
+// FP64 GEMM work items: output o, rows [m0, m0 + mt) and columns [n0, n0 + nt) of it,
+// mt <= GEMM_TM, nt <= GEMM_TN, packed as (o, (m0 << 8) | mt, (n0 << 8) | nt)
+inline int3 gemm_tile(int o, int m0, int mt, int n0, int nt) { return make_int3(o, (m0 << 8) | mt, (n0 << 8) | nt); }
+// CTAs of the FP64 GEMM resident on the GPU at once (SMs x CTAs per SM)
+int gemm_fp64_slots();
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st);
 // batched form: the bases of output o are bases[o.inst] (device array)
