@@ -56,15 +56,23 @@ struct Error : std::runtime_error {
 struct DevPool {
   std::unordered_map<void*, size_t> live;      // pointer -> size class
   std::map<size_t, std::vector<void*>> cached; // size class -> free blocks
+  size_t large_cached = 0;                     // bytes of cached blocks above POOL_MAX_BYTES
   void release() {
     for (auto& kv : cached)
       for (void* p : kv.second) cudaFree(p);
     cached.clear();
+    large_cached = 0;
   }
   ~DevPool() { release(); }
 };
 static thread_local DevPool* t_pool = nullptr;
+// Blocks up to POOL_MAX_BYTES are cached in power-of-two classes.  Larger blocks (operator
+// sets, workspaces) are cached by size rounded up to POOL_LARGE_GRAIN: the sweeps free and
+// allocate the same layouts over and over, and a cudaFree would synchronize the device.
+// At most POOL_LARGE_CACHE bytes of them are kept; a failed allocation releases the cache.
 constexpr size_t POOL_MAX_BYTES = (size_t)8 << 20;
+constexpr size_t POOL_LARGE_GRAIN = (size_t)2 << 20;
+constexpr size_t POOL_LARGE_CACHE = (size_t)32 << 30;
 
 struct PoolScope {
   DevPool* prev;
@@ -74,41 +82,49 @@ struct PoolScope {
 
 static cudaError_t dev_alloc(void** p, size_t bytes) {
   DevPool* pool = t_pool;
-  if (pool && bytes <= POOL_MAX_BYTES) {
-    size_t c = 256;
+  if (!pool) return cudaMalloc(p, bytes);
+  size_t c;
+  if (bytes <= POOL_MAX_BYTES) {
+    c = 256;
     while (c < bytes) c <<= 1;
-    auto& fl = pool->cached[c];
-    if (!fl.empty()) {
-      *p = fl.back();
-      fl.pop_back();
-      pool->live[*p] = c;
-      return cudaSuccess;
-    }
-    cudaError_t e = cudaMalloc(p, c);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      pool->release();
-      e = cudaMalloc(p, c);
-    }
-    if (e == cudaSuccess) pool->live[*p] = c;
-    return e;
+  } else {
+    c = (bytes + POOL_LARGE_GRAIN - 1) / POOL_LARGE_GRAIN * POOL_LARGE_GRAIN;
   }
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess && pool) {
+  auto it = pool->cached.find(c);
+  if (it != pool->cached.end() && !it->second.empty()) {
+    *p = it->second.back();
+    it->second.pop_back();
+    if (c > POOL_MAX_BYTES) pool->large_cached -= c;
+    pool->live[*p] = c;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc(p, c);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     pool->release();
-    e = cudaMalloc(p, bytes);
+    e = cudaMalloc(p, c);
   }
+  if (e == cudaSuccess) pool->live[*p] = c;
   return e;
 }
 
+// Freed blocks are reused by later allocations of the same context, whose work is
+// ordered after the frees on the context's stream.
 static void dev_free(void* p) {
   if (!p) return;
   if (DevPool* pool = t_pool) {
     auto it = pool->live.find(p);
     if (it != pool->live.end()) {
-      pool->cached[it->second].push_back(p);
+      const size_t c = it->second;
       pool->live.erase(it);
+      if (c > POOL_MAX_BYTES) {
+        if (pool->large_cached + c > POOL_LARGE_CACHE) {
+          cudaFree(p);
+          return;
+        }
+        pool->large_cached += c;
+      }
+      pool->cached[c].push_back(p);
       return;
     }
   }
@@ -1165,7 +1181,6 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
   build_gather(gp, tasks, srcs, c->st);
   gp.run(c->st);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
   return E;
 }
 
@@ -1181,7 +1196,6 @@ static std::unique_ptr<OpSet> enlarge_from(lrt_ctx* c, const EnlTemplate& t, con
   build_gather(gp, tasks, srcs, c->st);
   gp.run(c->st);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
   return E;
 }
 
@@ -1275,7 +1289,6 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
   p1.run(c->st, nullptr, nullptr);
   p2.run(c->st, nullptr, nullptr);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
   if (tmp) dev_free(tmp);
   N->finish_nz();
   return N;
@@ -1348,7 +1361,6 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
   p1.run(c->st, nullptr, nullptr);
   p2.run(c->st, nullptr, nullptr);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
   if (tmp) dev_free(tmp);
   N->finish_nz();
   return N;
@@ -2028,8 +2040,9 @@ static int tune_tc_stream(lrt_ctx* c, const std::vector<TcSource>& src, int nvec
   return 64;
 }
 
-// TC-matrix pools, packed operators and work streams of a plan (once per plan)
-static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
+// TC-matrix pools, packed operators and work streams of a plan (once per plan); tile
+// widths timed on the plan's data, or by the heuristic for a plan used only once
+static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec, bool tune = true) {
   if (p.tc_ready) return;
   TcPlan& tp = p.tc;
   for (int q = 0; q < 3; ++q) {
@@ -2059,9 +2072,9 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
     ys.ensure((size_t)std::max<int64_t>(p.nelem * nvec, 1));
     const TcOut scratch{ys.p, nullptr};
     p.tn1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci1,
-                           p.tcb1, p.tcn1);
+                           p.tcb1, p.tcn1, tune);
     p.tn2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci2,
-                           p.tcb2, p.tcn2);
+                           p.tcb2, p.tcn2, tune);
     CK(cudaStreamSynchronize(c->st));
   }
   CK(cudaStreamSynchronize(c->st));
@@ -2070,12 +2083,12 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
 
 // y = H_eff x through the split-TF32 tensor-core kernels (both phases), then a check
 // of the kernels' error flag (a bounded pipeline wait that expired)
-static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec) {
+static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec, bool tune = true) {
   if (!ctx->derr) {
     if (dev_alloc((void**)&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
     CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
   }
-  prepare_tc(ctx, p, nvec);
+  prepare_tc(ctx, p, nvec, tune);
   launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1], p.tc.pool_size[1],
                  nvec, ctx->st);
   const TcOut to{y_dev};
@@ -3056,10 +3069,11 @@ struct TdaRunner {
 
   TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p), mixed(p.precision == LRT_MIXED) {}
 
-  // y = (plan) x for one vector, in the current precision
-  void apply(SigmaPlan& p, const double* x, double* y) {
+  // y = (plan) x for one vector, in the current precision (once: a plan used for one call,
+  // whose tensor-core tile widths are not worth timing)
+  void apply(SigmaPlan& p, const double* x, double* y, bool once = false) {
     if (mixed) {
-      run_tc(c, p, x, y, 1);
+      run_tc(c, p, x, y, 1, !once);
     } else {
       p.p1.run(c->st, x, y, p.tbuf);
       p.p2.run(c->st, x, y, p.tbuf);
@@ -3129,7 +3143,7 @@ struct TdaRunner {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (!XE.f) return;
     auto plan = plan_sigma_sets(c, *XE.f, XE.r.get(), *c->R[i + 1], nullptr, i, 1, 1, mixed);
-    apply(*plan, C0(i).d, y.d);
+    apply(*plan, C0(i).d, y.d, true);
   }
 
   // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2)
@@ -3137,7 +3151,7 @@ struct TdaRunner {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (HR.empty()) return;
     auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1, mixed);
-    apply(*plan, C0(i).d, y.d);
+    apply(*plan, C0(i).d, y.d, true);
   }
 
   // Q^C C = C - C0 (C0 . C)
