@@ -706,8 +706,8 @@ struct GemmPlan {
   DevArray<int3> tiles;      // FP64 kernel tiles
   int ntiles = 0;
   double flops = 0.0;
-  void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr) const {
-    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st);
+  void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr, const GemmExtra* ex = nullptr) const {
+    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st, ex);
   }
 };
 
@@ -903,6 +903,9 @@ struct SigmaPlan {
   uint64_t serial = 0;      // unique per plan (batched launches detect rebuilt plans by it)
   bool has_tc = false;      // the tensor-core twin was planned
   GemmPlan p1, p2;
+  // operator sets of a plan built with relative addresses (X, Xrev, Y, Yrev at extra
+  // bases 0..3); a kept plan serves new sets of the same layout by changing these
+  GemmExtra ex{};
   DevArray<DiagOut> douts;
   DevArray<DiagTerm> dterms;
   int ndiag = 0;
@@ -1013,11 +1016,8 @@ static void reset_env(lrt_ctx* c) {
 // the TDA enlarges the first-order sets of every trial vector at a site, all alike.
 struct EnlTemplate {
   std::unique_ptr<OpSet> proto;        // layout of the enlarged set, no data
-  std::vector<GatherTask> tasks;       // dst_off[i] replaces tasks[i].dst
-  std::vector<int64_t> dst_off;
-  std::vector<GatherSrc> srcs;         // src_off[i] from X (or Xrev when src_rev[i])
-  std::vector<int64_t> src_off;
-  std::vector<char> src_rev;
+  std::unique_ptr<GatherPlan> gp;      // device task list: destinations relative to the new
+                                       // set, sources relative to X (rel 1) or Xrev (rel 2)
   uint64_t sig = 0;
 };
 
@@ -1163,19 +1163,28 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
   }
   E->finish_nz();
   if (tpl) {
+    // the same task list with addresses relative to the launch's bases, kept on the device
     tpl->proto = layout_copy(*E);
-    tpl->tasks = tasks;
-    tpl->srcs = srcs;
-    tpl->dst_off.clear();
-    for (const GatherTask& t : tasks) tpl->dst_off.push_back(t.dst - E->d);
-    tpl->src_off.clear();
-    tpl->src_rev.clear();
     tsrc_off.resize(tsrc.size());
-    for (size_t i = 0; i < tasks.size(); ++i)
-      for (const auto& so : tsrc_off[i]) {
-        tpl->src_off.push_back(so.first);
-        tpl->src_rev.push_back(so.second);
+    std::vector<GatherSrc> rsrcs;
+    rsrcs.reserve(srcs.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      tasks[i].dst_off = tasks[i].dst - E->d;
+      tasks[i].dst = nullptr;
+      for (size_t j = 0; j < tsrc[i].size(); ++j) {
+        GatherSrc g = tsrc[i][j];
+        g.src = nullptr;
+        g.src_off = tsrc_off[i][j].first;
+        g.rel = tsrc_off[i][j].second ? 2 : 1;
+        rsrcs.push_back(g);
       }
+    }
+    tpl->gp = std::make_unique<GatherPlan>();
+    build_gather(*tpl->gp, tasks, rsrcs, c->st);
+    launch_gather(tpl->gp->tasks.p, tpl->gp->srcs.p, tpl->gp->tiles.p, tpl->gp->ntiles, c->st, E->d, X.d,
+                  Xrev ? Xrev->d : nullptr);
+    CK(cudaGetLastError());
+    return E;
   }
   GatherPlan gp;
   build_gather(gp, tasks, srcs, c->st);
@@ -1184,17 +1193,12 @@ static std::unique_ptr<OpSet> enlarge_set(lrt_ctx* c, const OpSet& X, const OpSe
   return E;
 }
 
-// an enlargement replayed from its template for new input data of the same layout
+// an enlargement replayed from its template for new input data of the same layout: one
+// launch of the template's device task list with the new sets as bases
 static std::unique_ptr<OpSet> enlarge_from(lrt_ctx* c, const EnlTemplate& t, const OpSet& X, const OpSet* Xrev) {
   auto E = layout_copy(*t.proto);
   alloc_zero(*E, c->st);
-  std::vector<GatherTask> tasks = t.tasks;
-  std::vector<GatherSrc> srcs = t.srcs;
-  for (size_t i = 0; i < tasks.size(); ++i) tasks[i].dst = E->d + t.dst_off[i];
-  for (size_t i = 0; i < srcs.size(); ++i) srcs[i].src = (t.src_rev[i] ? Xrev->d : X.d) + t.src_off[i];
-  GatherPlan gp;
-  build_gather(gp, tasks, srcs, c->st);
-  gp.run(c->st);
+  launch_gather(t.gp->tasks.p, t.gp->srcs.p, t.gp->tiles.p, t.gp->ntiles, c->st, E->d, X.d, Xrev ? Xrev->d : nullptr);
   CK(cudaGetLastError());
   return E;
 }
@@ -1229,10 +1233,123 @@ static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, 
 static void run_two_phase_tc(lrt_ctx* c, const std::vector<GemmOut>& o1, const std::vector<GemmSeg>& s1,
                              const std::vector<GemmOut>& o2, const std::vector<GemmSeg>& s2);
 
+// A renormalization kept for replay: its two grouped GEMMs with every address relative to
+// launch bases, so new operator data and isometries of the same layout (the first-order
+// sets of every TDA sweep) cost one pair of launches and no host planning.  Bases: term
+// t's enlarged set, ket and bra at extra bases 3t, 3t + 1, 3t + 2, the new block at
+// REN_BASE_OUT, the intermediates at the launch's workspace.
+struct RenTemplate {
+  std::unique_ptr<OpSet> proto;
+  std::unique_ptr<GemmPlan> p1, p2;
+  int64_t toff = 0;
+  uint64_t sig = 0;
+};
+constexpr int REN_MAX_TERMS = 2, REN_BASE_OUT = 6;
+static_assert(REN_BASE_OUT < GEMM_NEXTRA && 3 * REN_MAX_TERMS <= REN_BASE_OUT, "renormalization bases");
+
+static uint64_t site_signature(const SiteTensor& T) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  mix((uint64_t)T.total);
+  for (int64_t o : T.blk_off) mix((uint64_t)o);
+  for (int r : T.blk_rows) mix((uint64_t)r);
+  return h;
+}
+static uint64_t ren_signature(int b, bool right, const std::vector<RenTerm>& terms) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  mix((uint64_t)b);
+  mix(right ? 1u : 0u);
+  for (const RenTerm& t : terms) {
+    mix(set_signature(*t.E, nullptr));
+    mix(site_signature(*t.ket));
+    mix(site_signature(*t.bra));
+  }
+  return h;
+}
+
+// the plan lists with addresses made absolute (extra bases resolved) and the workspace
+// left as offsets, the form the tensor-core two-phase path takes
+static void ren_absolute(std::vector<GemmOut>& o1, std::vector<GemmSeg>& s1, std::vector<GemmOut>& o2,
+                         std::vector<GemmSeg>& s2, const GemmExtra& ex) {
+  auto segs = [&](std::vector<GemmSeg>& v) {
+    for (GemmSeg& g : v) {
+      if (g.a_rel >= 3) g.A = ex.p[g.a_rel - 3] + g.a_off, g.a_off = 0, g.a_rel = 0;
+      if (g.b_rel >= 3) g.B = ex.p[g.b_rel - 3] + g.b_off, g.b_off = 0, g.b_rel = 0;
+      if (g.b_rel == 2) g.b_rel = 0;
+    }
+  };
+  auto outs = [&](std::vector<GemmOut>& v) {
+    for (GemmOut& o : v) {
+      if (o.c_rel >= 3) o.C = ex.p[o.c_rel - 3] + o.c_off, o.c_off = 0, o.c_rel = 0;
+      if (o.c_rel == 2) o.c_rel = 0;
+    }
+  };
+  segs(s1);
+  segs(s2);
+  outs(o1);
+  outs(o2);
+}
+
+// runs (and, given a template slot, keeps) a renormalization's two grouped GEMMs
+static void ren_run(lrt_ctx* c, std::vector<GemmOut>& o1, std::vector<GemmSeg>& s1, std::vector<GemmOut>& o2,
+                    std::vector<GemmSeg>& s2, int64_t toff, const GemmExtra& ex, int prec, RenTemplate* tpl,
+                    const OpSet& N, uint64_t sig) {
+  if (prec == LRT_MIXED) {
+    ren_absolute(o1, s1, o2, s2, ex);
+    run_two_phase_tc(c, o1, s1, o2, s2);
+    return;
+  }
+  auto p1 = std::make_unique<GemmPlan>(), p2 = std::make_unique<GemmPlan>();
+  build_gemm(*p1, o1, s1, c->st);
+  build_gemm(*p2, o2, s2, c->st);
+  double* tmp = nullptr;
+  if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "renormalize workspace");
+  launch_gemm_fp64(p1->outs.p, p1->segs.p, p1->tiles.p, p1->ntiles, nullptr, nullptr, tmp, c->st, &ex);
+  launch_gemm_fp64(p2->outs.p, p2->segs.p, p2->tiles.p, p2->ntiles, nullptr, nullptr, tmp, c->st, &ex);
+  CK(cudaGetLastError());
+  if (tmp) dev_free(tmp);
+  if (tpl) {
+    tpl->proto = layout_copy(N);
+    tpl->p1 = std::move(p1);
+    tpl->p2 = std::move(p2);
+    tpl->toff = toff;
+    tpl->sig = sig;
+  }
+}
+
+// replay of a kept renormalization; false when the template does not match
+static std::unique_ptr<OpSet> ren_replay(lrt_ctx* c, RenTemplate* tpl, uint64_t sig, GemmExtra ex, int prec) {
+  if (!tpl || prec != LRT_FP64 || !tpl->p1 || tpl->sig != sig) return nullptr;
+  auto N = layout_copy(*tpl->proto);
+  alloc_zero(*N, c->st);
+  ex.p[REN_BASE_OUT] = N->d;
+  double* tmp = nullptr;
+  if (tpl->toff > 0 && dev_alloc((void**)&tmp, (size_t)tpl->toff * sizeof(double)) != cudaSuccess)
+    throw Error(LRT_ENOMEM, "renormalize workspace");
+  const GemmPlan& p1 = *tpl->p1;
+  const GemmPlan& p2 = *tpl->p2;
+  launch_gemm_fp64(p1.outs.p, p1.segs.p, p1.tiles.p, p1.ntiles, nullptr, nullptr, tmp, c->st, &ex);
+  launch_gemm_fp64(p2.outs.p, p2.segs.p, p2.tiles.p, p2.ntiles, nullptr, nullptr, tmp, c->st, &ex);
+  CK(cudaGetLastError());
+  if (tmp) dev_free(tmp);
+  return N;
+}
+
 // left block of bond b+1 = sum_t bra_t^T E_t ket_t over the enlarged left block of bond b
 // (prec LRT_MIXED: the two grouped GEMMs as split-TF32 tensor-core products)
 static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms,
-                                                int prec = LRT_FP64) {
+                                                int prec = LRT_FP64, RenTemplate* tpl = nullptr) {
+  if (terms.empty() || (int)terms.size() > REN_MAX_TERMS) throw Error(LRT_EINVAL, "renormalize: 1 or 2 terms");
+  GemmExtra ex{};
+  for (size_t t = 0; t < terms.size(); ++t) {
+    ex.p[3 * t] = terms[t].E->d;
+    ex.p[3 * t + 1] = terms[t].ket->d;
+    ex.p[3 * t + 2] = terms[t].bra->d;
+  }
+  const uint64_t sig = tpl ? ren_signature(b, false, terms) : 0;
+  if (auto R = ren_replay(c, tpl, sig, ex, prec)) return R;
   const OpSet& E0 = *terms[0].E;
   const Fused& F = *E0.fused;
   auto N = std::make_unique<OpSet>();
@@ -1241,6 +1358,7 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
   make_keys(*N, E0.orbs, E0.mode, c->I.nso);
   layout_blocks(*N);
   alloc_zero(*N, c->st);
+  ex.p[REN_BASE_OUT] = N->d;
   std::vector<GemmOut> o1, o2;
   std::vector<GemmSeg> s1, s2;
   int64_t toff = 0;
@@ -1253,8 +1371,9 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
       if (fk < 0 || fb < 0) continue;
       const int Dq = N->basis.d[q], Dqb = N->basis.d[qb];
       const int rk = F.s.d[fk], rb = F.s.d[fb];
-      GemmOut out{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 0, 0, 0};
-      for (const RenTerm& t : terms) {
+      GemmOut out{nullptr, N->off_of((int)o, q), Dq, Dqb, Dq, (int)s2.size(), 0, 0, 3 + REN_BASE_OUT};
+      for (size_t ti = 0; ti < terms.size(); ++ti) {
+        const RenTerm& t = terms[ti];
         const OpSet& E = *t.E;
         if (E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
         const SiteTensor& K = *t.ket;
@@ -1262,9 +1381,10 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
         if (K.blk_off[q] < 0 || Bt.blk_off[qb] < 0) continue;
         if (K.blk_rows[q] != rk || Bt.blk_rows[qb] != rb)
           throw Error(LRT_EINVAL, "site tensor rows do not match the enlarged basis");
-        o1.push_back(GemmOut{nullptr, toff, Dq, rb, Dq, (int)s1.size(), 1, 0, 0});
-        s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), K.d + K.blk_off[q], 0, 0, rk, Dq, rk, 0, 0, 0, 0, 1.0});
-        s2.push_back(GemmSeg{Bt.d + Bt.blk_off[qb], nullptr, 0, toff, Dqb, Dq, rb, 1, 0, 0, 0, 1.0});
+        const int r0 = 3 + 3 * (int)ti;
+        o1.push_back(GemmOut{nullptr, toff, Dq, rb, Dq, (int)s1.size(), 1, 0, 2});
+        s1.push_back(GemmSeg{nullptr, nullptr, E.off_of((int)o, fk), K.blk_off[q], rk, Dq, rk, 0, 0, r0, r0 + 1, 1.0});
+        s2.push_back(GemmSeg{nullptr, nullptr, Bt.blk_off[qb], toff, Dqb, Dq, rb, 1, 0, r0 + 2, 2, 1.0});
         ++out.seg_count;
         toff += (int64_t)rb * Dq;
       }
@@ -1273,30 +1393,15 @@ static std::unique_ptr<OpSet> renorm_left_terms(lrt_ctx* c, int b, const std::ve
         N->bnz[o * N->ns() + q] = 1;
       }
     }
-  if (prec == LRT_MIXED) {
-    run_two_phase_tc(c, o1, s1, o2, s2);
-    N->finish_nz();
-    return N;
-  }
-  double* tmp = nullptr;
-  if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
-    throw Error(LRT_ENOMEM, "renormalize workspace");
-  for (auto& x : o1) x.C = tmp + x.c_off;
-  for (auto& x : s2) x.B = tmp + x.b_off;
-  GemmPlan p1, p2;
-  build_gemm(p1, o1, s1, c->st);
-  build_gemm(p2, o2, s2, c->st);
-  p1.run(c->st, nullptr, nullptr);
-  p2.run(c->st, nullptr, nullptr);
-  CK(cudaGetLastError());
-  if (tmp) dev_free(tmp);
   N->finish_nz();
+  ren_run(c, o1, s1, o2, s2, toff, ex, prec, tpl, *N, sig);
   return N;
 }
 
 // right block of bond b = sum_t R_bra,t [E_t] R_ket,t^T over the enlarged right block site b (+) R
 static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::vector<RenTerm>& terms,
-                                                 int prec = LRT_FP64) {
+                                                 int prec = LRT_FP64, RenTemplate* tpl = nullptr) {
+  if (terms.empty() || (int)terms.size() > REN_MAX_TERMS) throw Error(LRT_EINVAL, "renormalize: 1 or 2 terms");
   const OpSet& E0 = *terms[0].E;
   const Fused& F = *E0.fused;
   const Sectors& Lb = c->bonds[b];
@@ -1309,12 +1414,21 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
         auto off = rfused_copy(c, b, *T, *buf, F);
         rf[T] = {std::move(buf), std::move(off)};
       }
+  GemmExtra ex{};
+  for (size_t t = 0; t < terms.size(); ++t) {
+    ex.p[3 * t] = terms[t].E->d;
+    ex.p[3 * t + 1] = rf.at(terms[t].ket).first->p;
+    ex.p[3 * t + 2] = rf.at(terms[t].bra).first->p;
+  }
+  const uint64_t sig = tpl ? ren_signature(b, true, terms) : 0;
+  if (auto R = ren_replay(c, tpl, sig, ex, prec)) return R;
   auto N = std::make_unique<OpSet>();
   N->right = true;
   N->basis = Lb;
   make_keys(*N, E0.orbs, E0.mode, c->I.nso);
   layout_blocks(*N);
   alloc_zero(*N, c->st);
+  ex.p[REN_BASE_OUT] = N->d;
   std::vector<GemmOut> o1, o2;
   std::vector<GemmSeg> s1, s2;
   int64_t toff = 0;
@@ -1327,16 +1441,18 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
       if (fk < 0 || fb < 0) continue;
       const int Dq = Lb.d[q], Dqb = Lb.d[qb];
       const int ck = F.s.d[fk], cb = F.s.d[fb];
-      GemmOut out{N->d + N->off_of((int)o, q), 0, Dq, Dqb, Dq, (int)s2.size(), 0, 0, 0};
-      for (const RenTerm& t : terms) {
+      GemmOut out{nullptr, N->off_of((int)o, q), Dq, Dqb, Dq, (int)s2.size(), 0, 0, 3 + REN_BASE_OUT};
+      for (size_t ti = 0; ti < terms.size(); ++ti) {
+        const RenTerm& t = terms[ti];
         const OpSet& E = *t.E;
         if (E.bra_of((int)o, fk) != fb || !E.block_nz((int)o, fk)) continue;
         const auto& K = rf.at(t.ket);
         const auto& Bt = rf.at(t.bra);
         if (K.second[q] < 0 || Bt.second[qb] < 0) continue;
-        o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 0});
-        s1.push_back(GemmSeg{E.d + E.off_of((int)o, fk), K.first->p + K.second[q], 0, 0, ck, ck, ck, 0, 1, 0, 0, 1.0});
-        s2.push_back(GemmSeg{Bt.first->p + Bt.second[qb], nullptr, 0, toff, cb, Dq, cb, 0, 0, 0, 0, 1.0});
+        const int r0 = 3 + 3 * (int)ti;
+        o1.push_back(GemmOut{nullptr, toff, Dq, cb, Dq, (int)s1.size(), 1, 0, 2});
+        s1.push_back(GemmSeg{nullptr, nullptr, E.off_of((int)o, fk), K.second[q], ck, ck, ck, 0, 1, r0, r0 + 1, 1.0});
+        s2.push_back(GemmSeg{nullptr, nullptr, Bt.second[qb], toff, cb, Dq, cb, 0, 0, r0 + 2, 2, 1.0});
         ++out.seg_count;
         toff += (int64_t)cb * Dq;
       }
@@ -1345,24 +1461,8 @@ static std::unique_ptr<OpSet> renorm_right_terms(lrt_ctx* c, int b, const std::v
         N->bnz[o * N->ns() + q] = 1;
       }
     }
-  if (prec == LRT_MIXED) {
-    run_two_phase_tc(c, o1, s1, o2, s2);
-    N->finish_nz();
-    return N;
-  }
-  double* tmp = nullptr;
-  if (toff > 0 && dev_alloc((void**)&tmp, (size_t)toff * sizeof(double)) != cudaSuccess)
-    throw Error(LRT_ENOMEM, "renormalize workspace");
-  for (auto& x : o1) x.C = tmp + x.c_off;
-  for (auto& x : s2) x.B = tmp + x.b_off;
-  GemmPlan p1, p2;
-  build_gemm(p1, o1, s1, c->st);
-  build_gemm(p2, o2, s2, c->st);
-  p1.run(c->st, nullptr, nullptr);
-  p2.run(c->st, nullptr, nullptr);
-  CK(cudaGetLastError());
-  if (tmp) dev_free(tmp);
   N->finish_nz();
+  ren_run(c, o1, s1, o2, s2, toff, ex, prec, tpl, *N, sig);
   return N;
 }
 
@@ -1435,7 +1535,9 @@ static uint16_t transpose_mask(uint16_t m) {
 // (nsite 1) or the enlarged right block site+1 (+) R (nsite 2).  Xrev / Yrev: reverse
 // sets of first-order (transition) operator sets, read by transposed references.
 static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, const OpSet* Xrev, const OpSet& Y,
-                                                  const OpSet* Yrev, int site, int nsite, int nvec, bool tc = true) {
+                                                  const OpSet* Yrev, int site, int nsite, int nvec, bool tc = true,
+                                                  bool rel_ops = false) {
+  if (rel_ops && tc) throw Error(LRT_EINVAL, "internal: relative operator addresses are FP64 only");
   const Ints& I = c->I;
   const int k = c->k;
   const Fused& XF = *X.fused;
@@ -1690,6 +1792,26 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   std::vector<GemmOut> O1, O2;
   std::vector<GemmSeg> S1, S2;
   plan->tsize = toff * nvec;
+  // operator pointers as offsets from the set they live in (extra bases 0..3)
+  auto set_rel = [&](const OpSet* S) { return S == &X ? 3 : S == Xrev ? 4 : S == &Y ? 5 : 6; };
+  if (rel_ops) {
+    plan->ex.p[0] = X.d;
+    plan->ex.p[1] = Xrev ? Xrev->d : nullptr;
+    plan->ex.p[2] = Y.d;
+    plan->ex.p[3] = Yrev ? Yrev->d : nullptr;
+    for (size_t q = 0; q < s1.size(); ++q) {
+      s1[q].a_off = s1[q].A - s1set[q]->d;
+      s1[q].A = nullptr;
+      s1[q].a_rel = set_rel(s1set[q]);
+    }
+    for (size_t u = 0; u < seg2.size(); ++u)
+      for (size_t q = 0; q < seg2[u].size(); ++q) {
+        GemmSeg& g = seg2[u][q];
+        g.b_off = g.B - seg2set[u][q]->d;
+        g.B = nullptr;
+        g.b_rel = set_rel(seg2set[u][q]);
+      }
+  }
   for (int v = 0; v < nvec; ++v) {
     for (const GemmOut& x : o1) {
       GemmOut y = x;
@@ -2040,9 +2162,8 @@ static int tune_tc_stream(lrt_ctx* c, const std::vector<TcSource>& src, int nvec
   return 64;
 }
 
-// TC-matrix pools, packed operators and work streams of a plan (once per plan); tile
-// widths timed on the plan's data, or by the heuristic for a plan used only once
-static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec, bool tune = true) {
+// TC-matrix pools, packed operators and work streams of a plan (once per plan)
+static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
   if (p.tc_ready) return;
   TcPlan& tp = p.tc;
   for (int q = 0; q < 3; ++q) {
@@ -2072,9 +2193,9 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec, bool tune = true) {
     ys.ensure((size_t)std::max<int64_t>(p.nelem * nvec, 1));
     const TcOut scratch{ys.p, nullptr};
     p.tn1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci1,
-                           p.tcb1, p.tcn1, tune);
+                           p.tcb1, p.tcn1);
     p.tn2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci2,
-                           p.tcb2, p.tcn2, tune);
+                           p.tcb2, p.tcn2);
     CK(cudaStreamSynchronize(c->st));
   }
   CK(cudaStreamSynchronize(c->st));
@@ -2083,12 +2204,12 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec, bool tune = true) {
 
 // y = H_eff x through the split-TF32 tensor-core kernels (both phases), then a check
 // of the kernels' error flag (a bounded pipeline wait that expired)
-static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec, bool tune = true) {
+static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_dev, int nvec) {
   if (!ctx->derr) {
     if (dev_alloc((void**)&ctx->derr, sizeof(int)) != cudaSuccess) throw Error(LRT_ENOMEM, "error flag");
     CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->st));
   }
-  prepare_tc(ctx, p, nvec, tune);
+  prepare_tc(ctx, p, nvec);
   launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1], p.tc.pool_size[1],
                  nvec, ctx->st);
   const TcOut to{y_dev};
@@ -2265,8 +2386,8 @@ static double davidson_site(lrt_ctx* c, int i, int nsite, double* psi, const lrt
     if (nt < 1e-14) break;
     launch_lincomb(nullptr, n, 0, coef.p, n, t.p, 1.0 / nt, st);
     CK(cudaMemcpyAsync(V.p + (size_t)m * n, t.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    plan.p1.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf);
-    plan.p2.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf);
+    plan.p1.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf, &plan.ex);
+    plan.p2.run(st, V.p + (size_t)m * n, AV.p + (size_t)m * n, plan.tbuf, &plan.ex);
     launch_dots(V.p, n, m + 1, AV.p + (size_t)m * n, n, small.p, st);
     CK(cudaMemcpyAsync(hcol.data(), small.p, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -2346,7 +2467,7 @@ static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, 
   GatherPlan gp;
   build_gather(gp, tasks, srcs, c->st);
   gp.run(c->st);
-  CK(cudaStreamSynchronize(c->st));
+  CK(cudaGetLastError());
   return off;
 }
 
@@ -3069,14 +3190,13 @@ struct TdaRunner {
 
   TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p), mixed(p.precision == LRT_MIXED) {}
 
-  // y = (plan) x for one vector, in the current precision (once: a plan used for one call,
-  // whose tensor-core tile widths are not worth timing)
-  void apply(SigmaPlan& p, const double* x, double* y, bool once = false) {
+  // y = (plan) x for one vector, in the current precision
+  void apply(SigmaPlan& p, const double* x, double* y) {
     if (mixed) {
-      run_tc(c, p, x, y, 1, !once);
+      run_tc(c, p, x, y, 1);
     } else {
-      p.p1.run(c->st, x, y, p.tbuf);
-      p.p2.run(c->st, x, y, p.tbuf);
+      p.p1.run(c->st, x, y, p.tbuf, &p.ex);
+      p.p2.run(c->st, x, y, p.tbuf, &p.ex);
       CK(cudaGetLastError());
       CK(cudaStreamSynchronize(c->st));
     }
@@ -3139,19 +3259,47 @@ struct TdaRunner {
     e.r = enl(i, false, 1, *HL.r, HL.f.get());
     return e;
   }
+  // The first-order site products use sets that are new for every vector and sweep but
+  // keep their layout, so their plans are built once per (site, side) with operator
+  // addresses relative to the sets and replayed with the new sets as bases: two FP64
+  // launches and no host planning.  (In the tensor-core form each call would first pack
+  // the whole new set; these products run in FP64 in both precisions.)
+  struct DhTpl {
+    std::unique_ptr<SigmaPlan> plan;
+    uint64_t sig = 0;
+  };
+  std::map<std::pair<int, int>, DhTpl> dh_tpl;
+  SigmaPlan& dh_plan(int i, int side, const OpSet& X, const OpSet* Xr, const OpSet& Y, const OpSet* Yr) {
+    DhTpl& t = dh_tpl[{i, side}];
+    const uint64_t sig = set_signature(X, Xr) ^ (set_signature(Y, Yr) * 1099511628211ull);
+    if (!t.plan || t.sig != sig) {
+      t.plan = plan_sigma_sets(c, X, Xr, Y, Yr, i, 1, 1, false, true);
+      t.sig = sig;
+    }
+    SigmaPlan& p = *t.plan;
+    p.ex.p[0] = X.d;
+    p.ex.p[1] = Xr ? Xr->d : nullptr;
+    p.ex.p[2] = Y.d;
+    p.ex.p[3] = Yr ? Yr->d : nullptr;
+    return p;
+  }
   void dh_left(int i, const Enl& XE, SiteTensor& y) {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (!XE.f) return;
-    auto plan = plan_sigma_sets(c, *XE.f, XE.r.get(), *c->R[i + 1], nullptr, i, 1, 1, mixed);
-    apply(*plan, C0(i).d, y.d, true);
+    SigmaPlan& p = dh_plan(i, 0, *XE.f, XE.r.get(), *c->R[i + 1], nullptr);
+    p.p1.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
+    p.p2.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
+    CK(cudaGetLastError());
   }
 
   // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2)
   void dh_right(int i, const FirstOrder& HR, SiteTensor& y) {
     CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
     if (HR.empty()) return;
-    auto plan = plan_sigma_sets(c, *c->XL[i], nullptr, *HR.f, HR.r.get(), i, 1, 1, mixed);
-    apply(*plan, C0(i).d, y.d, true);
+    SigmaPlan& p = dh_plan(i, 1, *c->XL[i], nullptr, *HR.f, HR.r.get());
+    p.p1.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
+    p.p2.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
+    CK(cudaGetLastError());
   }
 
   // Q^C C = C - C0 (C0 . C)
@@ -3180,15 +3328,23 @@ struct TdaRunner {
   }
 
   // first-order left set at bond i+1 (Eq. lopr1st), both directions
+  // renormalizations kept for replay, per (site, right, direction, number of terms)
+  std::map<std::tuple<int, int, int, int>, RenTemplate> ren_tpl;
+  RenTemplate* rtpl(int i, bool right, int rev, int nterms) {
+    return &ren_tpl[std::make_tuple(i, right ? 1 : 0, rev, nterms)];
+  }
+
   FirstOrder grow_HL(int i, const Enl& XE, const SiteTensor& L1) {
     FirstOrder out;
     const OpSet& XL = *c->XL[i];
     if (!XE.f) {
-      out.f = renorm_left_terms(c, i, {RenTerm{&XL, &L0(i), &L1}});
-      out.r = renorm_left_terms(c, i, {RenTerm{&XL, &L1, &L0(i)}});
+      out.f = renorm_left_terms(c, i, {RenTerm{&XL, &L0(i), &L1}}, LRT_FP64, rtpl(i, false, 0, 1));
+      out.r = renorm_left_terms(c, i, {RenTerm{&XL, &L1, &L0(i)}}, LRT_FP64, rtpl(i, false, 1, 1));
     } else {
-      out.f = renorm_left_terms(c, i, {RenTerm{XE.f.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}});
-      out.r = renorm_left_terms(c, i, {RenTerm{XE.r.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}});
+      out.f = renorm_left_terms(c, i, {RenTerm{XE.f.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}}, LRT_FP64,
+                                rtpl(i, false, 0, 2));
+      out.r = renorm_left_terms(c, i, {RenTerm{XE.r.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}}, LRT_FP64,
+                                rtpl(i, false, 1, 2));
     }
     return out;
   }
@@ -3198,13 +3354,15 @@ struct TdaRunner {
     FirstOrder out;
     const OpSet& YR = *c->YR[i];
     if (HR.empty()) {
-      out.f = renorm_right_terms(c, i, {RenTerm{&YR, &R0(i), &R1}});
-      out.r = renorm_right_terms(c, i, {RenTerm{&YR, &R1, &R0(i)}});
+      out.f = renorm_right_terms(c, i, {RenTerm{&YR, &R0(i), &R1}}, LRT_FP64, rtpl(i, true, 0, 1));
+      out.r = renorm_right_terms(c, i, {RenTerm{&YR, &R1, &R0(i)}}, LRT_FP64, rtpl(i, true, 1, 1));
     } else {
       auto Yf = enl(i, true, 0, *HR.f, HR.r.get());
       auto Yr = enl(i, true, 1, *HR.r, HR.f.get());
-      out.f = renorm_right_terms(c, i, {RenTerm{Yf.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R0(i), &R1}});
-      out.r = renorm_right_terms(c, i, {RenTerm{Yr.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R1, &R0(i)}});
+      out.f = renorm_right_terms(c, i, {RenTerm{Yf.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R0(i), &R1}}, LRT_FP64,
+                                 rtpl(i, true, 0, 2));
+      out.r = renorm_right_terms(c, i, {RenTerm{Yr.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R1, &R0(i)}}, LRT_FP64,
+                                 rtpl(i, true, 1, 2));
     }
     return out;
   }
@@ -3927,8 +4085,8 @@ int sigma_launch_existing_plan(lrt_ctx* ctx, int site, int nsite, int nvec, cons
                                   " doubles of scratch, the static maximum is " + std::to_string(workspace_doubles));
     if ((const double*)y_dev < x_dev + p->nelem * nvec && x_dev < (const double*)y_dev + p->nelem * nvec)
       throw Error(LRT_EINVAL, "sigma_noalloc: x and y overlap");
-    p->p1.run(ctx->st, x_dev, y_dev, workspace);
-    p->p2.run(ctx->st, x_dev, y_dev, workspace);
+    p->p1.run(ctx->st, x_dev, y_dev, workspace, &p->ex);
+    p->p2.run(ctx->st, x_dev, y_dev, workspace, &p->ex);
     CK(cudaGetLastError());
     ctx->err.clear();
     return LRT_OK;
@@ -4106,8 +4264,8 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     if (precision == LRT_MIXED) {
       run_tc(ctx, p, x_dev, y_dev, nvec);
     } else {
-      p.p1.run(ctx->st, x_dev, y_dev, p.tbuf);
-      p.p2.run(ctx->st, x_dev, y_dev, p.tbuf);
+      p.p1.run(ctx->st, x_dev, y_dev, p.tbuf, &p.ex);
+      p.p2.run(ctx->st, x_dev, y_dev, p.tbuf, &p.ex);
     }
     CK(cudaGetLastError());
     ctx->last.flops = p.flops_alg;

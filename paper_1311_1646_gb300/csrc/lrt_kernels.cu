@@ -19,17 +19,22 @@ namespace lrt {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restrict__ tasks,
                                                      const GatherSrc* __restrict__ srcs,
-                                                     const int3* __restrict__ tiles, int ntiles) {
+                                                     const int3* __restrict__ tiles, int ntiles,
+                                                     double* __restrict__ dbase,
+                                                     const double* __restrict__ sbase1,
+                                                     const double* __restrict__ sbase2) {
   __shared__ double tile[GATHER_TILE][GATHER_TILE + 1];
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
-  const GatherTask t = tasks[wi.x];
+  GatherTask t = tasks[wi.x];
+  if (dbase) t.dst = dbase + t.dst_off;
   const int r0 = wi.y * GATHER_TILE, c0 = wi.z * GATHER_TILE;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int s = 0; s < t.src_count; ++s) {
-    const GatherSrc g = srcs[t.src_begin + s];
+    GatherSrc g = srcs[t.src_begin + s];
+    if (g.rel) g.src = (g.rel == 1 ? sbase1 : sbase2) + g.src_off;
     if (!g.trans) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -62,9 +67,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restric
 }
 
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
-                   cudaStream_t st) {
+                   cudaStream_t st, double* dbase, const double* sbase1, const double* sbase2) {
   if (ntiles <= 0) return;
-  gather_kernel<<<ntiles, dim3(32, 8), 0, st>>>(tasks, srcs, tiles, ntiles);
+  gather_kernel<<<ntiles, dim3(32, 8), 0, st>>>(tasks, srcs, tiles, ntiles, dbase, sbase1, sbase2);
 }
 
 // ---------------------------------------------------------------------------
@@ -101,6 +106,20 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// extra base i of a launch (a switch, so the parameter block is not copied to local memory)
+__device__ __forceinline__ double* extra_base(const GemmExtra& ex, int i) {
+  switch (i) {
+    case 0: return ex.p[0];
+    case 1: return ex.p[1];
+    case 2: return ex.p[2];
+    case 3: return ex.p[3];
+    case 4: return ex.p[4];
+    case 5: return ex.p[5];
+    case 6: return ex.p[6];
+    default: return ex.p[7];
+  }
+}
+
 // acc[j] += sum_kk As[row_j][kk] Bs[kk][col_j] over a staged chunk, for the first N outputs
 template <int N>
 __device__ __forceinline__ void fma_chunk(double (&acc)[GEMM_MAXE], const uint32_t (&rc)[GEMM_MAXE],
@@ -118,7 +137,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOu
                                                                     const double* __restrict__ xbase,
                                                                     double* __restrict__ ybase,
                                                                     double* __restrict__ tbase,
-                                                                    const GemmBases* __restrict__ multi) {
+                                                                    const GemmBases* __restrict__ multi,
+                                                                    const GemmExtra ex) {
   extern __shared__ __align__(16) unsigned char gemm_smem_raw[];
   GemmSmem& S = *reinterpret_cast<GemmSmem*>(gemm_smem_raw);
   const int w = blockIdx.x;
@@ -154,8 +174,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOu
       int k = 0;
       if (lane < nb) {
         GemmSeg g = segs[o.seg_begin + b0 + lane];
-        if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : tbase) + g.a_off;
-        if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : tbase) + g.b_off;
+        if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : g.a_rel == 2 ? tbase : extra_base(ex, g.a_rel - 3)) + g.a_off;
+        if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : g.b_rel == 2 ? tbase : extra_base(ex, g.b_rel - 3)) + g.b_off;
         S.sd[lane] = SegS{g.A, g.B, g.lda, g.ldb, g.transA, g.transB, g.scale};
         k = g.k;
       }
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOu
 #pragma unroll
   for (int j = 0; j < GEMM_MAXE; ++j) {
     if (j >= cnt) break;
-    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : tbase) + o.c_off : o.C) +
+    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : o.c_rel == 2 ? tbase : extra_base(ex, o.c_rel - 3)) + o.c_off : o.C) +
                 (int64_t)(m0 + (int)(rc[j] >> 16)) * o.ldc + (n0 + (int)(rc[j] & 0xFFFFu));
     *c = o.accumulate ? (*c + acc[j]) : acc[j];
   }
@@ -249,11 +269,12 @@ static void gemm_fp64_smem_attr() {
 }
 
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                      const double* xbase, double* ybase, double* tbase, cudaStream_t st) {
+                      const double* xbase, double* ybase, double* tbase, cudaStream_t st, const GemmExtra* extra) {
   if (ntiles <= 0) return;
   gemm_fp64_smem_attr();
+  const GemmExtra ex = extra ? *extra : GemmExtra{};
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase,
-                                                                  nullptr);
+                                                                  nullptr, ex);
 }
 
 void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
@@ -261,7 +282,7 @@ void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3
   if (ntiles <= 0) return;
   gemm_fp64_smem_attr();
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, nullptr, nullptr,
-                                                                  nullptr, bases);
+                                                                  nullptr, bases, GemmExtra{});
 }
 
 // ---------------------------------------------------------------------------

@@ -5,24 +5,31 @@
 
 namespace lrt {
 
-// dst (rows x cols, leading dimension ld_dst) = sum_s scale_s * op(src_s), op = transpose or not.
+// dst (rows x cols, leading dimension ld_dst) += sum_s scale_s * op(src_s), op = transpose or not.
+// A launch given base pointers reads dst as dbase + dst_off and a source with rel = 1 or 2
+// as sbase1 / sbase2 + src_off (a template replayed for new data of the same layout).
 struct GatherTask {
   double* dst;
   int ld_dst;
   int rows, cols;
   int src_begin, src_count;
+  int64_t dst_off;
 };
 struct GatherSrc {
   const double* src;
   int ld;
   int trans;
   double scale;
+  int64_t src_off;
+  int rel;
 };
 
 // C (m x n, ldc) = [C +] sum_s scale_s * op(A_s) (m x k_s) * op(B_s) (k_s x n).
 // Pointers flagged *_rel are offsets (in doubles) from a base pointer passed at
 // launch: 1 = the caller's x (A, B) or y (C) buffer, 2 = the workspace of
-// intermediates.  A plan therefore serves any caller buffers and workspace.
+// intermediates, 3.. = extra base rel - 3 (GemmExtra).  A plan therefore serves any
+// caller buffers and workspace, and a plan kept as a template serves new operator data
+// of the same layout.
 struct GemmOut {
   double* C;
   int64_t c_off;
@@ -59,14 +66,20 @@ struct DiagTerm {
 
 // gather work items: (task index, tile row, tile col) packed as int3
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
-                   cudaStream_t st);
+                   cudaStream_t st, double* dbase = nullptr, const double* sbase1 = nullptr,
+                   const double* sbase2 = nullptr);
 // FP64 GEMM work items: output o, rows [m0, m0 + mt) and columns [n0, n0 + nt) of it,
 // mt <= GEMM_TM, nt <= GEMM_TN, packed as (o, (m0 << 8) | mt, (n0 << 8) | nt)
 inline int3 gemm_tile(int o, int m0, int mt, int n0, int nt) { return make_int3(o, (m0 << 8) | mt, (n0 << 8) | nt); }
 // CTAs of the FP64 GEMM resident on the GPU at once (SMs x CTAs per SM)
 int gemm_fp64_slots();
+constexpr int GEMM_NEXTRA = 8;
+struct GemmExtra {
+  double* p[GEMM_NEXTRA];
+};
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                      const double* xbase, double* ybase, double* tbase, cudaStream_t st);
+                      const double* xbase, double* ybase, double* tbase, cudaStream_t st,
+                      const GemmExtra* extra = nullptr);
 // batched form: the bases of output o are bases[o.inst] (device array)
 struct GemmBases {
   const double* x;
