@@ -435,6 +435,33 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
                 "two-site + 4 one-site sweep_gs sweeps and tda_prepare on the GPU; resid = sum of "
                 "the site residuals^2 per root (roots with resid near 1e-4 stall there); the TDA "
                 "loop is host-bound at this size"}
+    # (5) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
+    # each precision from the same reference (a right-canonical random MPS at the full bond
+    # dimension brought to the mixed-canonical gauge by tda_prepare)
+    cfg = synth.config(3)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 11, "right")
+    res = {}
+    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
+        t = pkg.Context(device)
+        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        t.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+        t.tda_prepare()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, rs, e0 = t.sweep_tda(nr, max_iter=1, eps=1e-12, seed=0, allow_noconv=True, precision=prec)
+        torch.cuda.synchronize()
+        res[prec] = (time.perf_counter() - t0, om)
+        t.close()
+    (s64, w64), (smx, wmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
+    out["tda_water_k24_M500_6roots_2sweeps"] = {
+        "fp64_s_per_root_per_sweep": s64 / nr / 2, "mixed_s_per_root_per_sweep": smx / nr / 2,
+        "speedup": s64 / smx, "max_abs_domega_Eh": float(np.max(np.abs(np.asarray(w64) - np.asarray(wmx)))),
+        "note": "wall time of two sweep_tda sweeps (the first with m = 0) / roots / 2; mixed: both "
+                "sweeps with tensor-core H_0 site products (the first-order products are FP64 in "
+                "both); the reference is not a ground state, so the roots are not converged and "
+                "serve only as a cross-check of the two precisions after the same two sweeps"}
     return out
 
 

@@ -962,6 +962,9 @@ struct lrt_ctx {
   int last_sweeps = 0;
   int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
   std::unique_ptr<lrt::TdaState> tda;
+  // right-fused copy task lists per (bond, layout of site tensor and fused basis), relative
+  // to the copy's buffer and the site tensor
+  std::map<std::pair<int, uint64_t>, std::unique_ptr<lrt::GatherPlan>> rf_plans;
   ~lrt_ctx() {
     if (derr) lrt::dev_free(derr);
   }
@@ -1918,17 +1921,81 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
   // Stacking: single-product outputs into intermediates (phase 1) that share their B
   // operand, K and width have their last (partial) 128-row block packed with others into
   // one tile, rows rounded up to 8 (first fit, decreasing).
+  // Vector slots: when such a product is narrow (its B matrix, one vector's block of x,
+  // has at most half a tile of rows), the tile's columns hold the same product for
+  // several vectors, each slot all of one vector's B rows.  Such outputs are stacked once
+  // for all vectors, full 128-row blocks as single pieces.
   struct Piece { int o, row0, nrows, srow; };
-  struct Stack { int s, v, n, k, b; std::vector<Piece> pc; };
+  struct Stack { int s, v, n, k, b; std::vector<Piece> pc; int nv = 0, wv = 0; };   // nv > 0: vector slots
   std::vector<Stack> stacks;
   struct Tile { int s, v, o, a, b; int64_t k; int stack; };
   std::vector<Tile> tiles;
+  auto pack = [&](std::map<std::tuple<int, int, int>, std::vector<Piece>>& groups, int si, int v,
+                  std::vector<Stack>& out) {
+    for (auto& kv : groups) {
+      std::vector<Piece>& pcs = kv.second;
+      std::stable_sort(pcs.begin(), pcs.end(), [](const Piece& x, const Piece& y) { return x.nrows > y.nrows; });
+      std::vector<Stack> bins;
+      std::vector<int> used;
+      for (const Piece& pc : pcs) {
+        size_t j = 0;
+        for (; j < bins.size(); ++j)
+          if (used[j] + pc.nrows <= TM && (int)bins[j].pc.size() < TC_MAX_PIECES) break;
+        if (j == bins.size()) {
+          bins.push_back(Stack{si, v, std::get<1>(kv.first), std::get<2>(kv.first), std::get<0>(kv.first), {}});
+          used.push_back(0);
+        }
+        Piece q = pc;
+        q.srow = used[j];
+        used[j] += pc.nrows;
+        bins[j].pc.push_back(q);
+      }
+      for (Stack& b : bins) out.push_back(std::move(b));
+    }
+  };
   for (size_t si = 0; si < src.size(); ++si) {
     const TcPlan& tp = *src[si].tp;
     const std::vector<TcPlanOut>& outs = *src[si].outs;
+    // slot width of an output (its B matrix's padded rows), 0 when it does not take slots
+    auto slot_width = [&](const TcPlanOut& o) -> int {
+      if (nvec < 2 || o.tmat < 0 || o.seg_count != 1) return 0;
+      const TcPlanSeg& g = tp.segs[o.seg_begin];
+      const TcMat& A = tp.mats[g.a];
+      const TcMat& B = tp.mats[g.b];
+      const TcMat& T = tp.mats[o.tmat];
+      if (A.pool != 0 || B.pool != 1 || T.pool != 2 || 2 * B.Rp > TN || T.K > 32 || o.n > B.Rp) return 0;
+      return B.Rp;
+    };
+    {
+      std::map<std::tuple<int, int, int>, std::vector<Piece>> groups;
+      std::vector<Stack> bins;
+      for (size_t i = 0; i < outs.size(); ++i) {
+        if (!slot_width(outs[i])) continue;
+        const TcPlanSeg& g = tp.segs[outs[i].seg_begin];
+        const int full = outs[i].m / TM, rem = outs[i].m - full * TM;
+        for (int a = 0; a < full; ++a)
+          bins.push_back(Stack{(int)si, 0, outs[i].n, g.k, g.b, {Piece{(int)i, a * TM, TM, 0}}});
+        if (rem) groups[std::make_tuple(g.b, outs[i].n, g.k)].push_back(Piece{(int)i, full * TM, (rem + 7) & ~7, 0});
+      }
+      pack(groups, (int)si, 0, bins);
+      for (const Stack& b : bins) {
+        const int w = slot_width(outs[b.pc[0].o]);
+        const int spt = TN / w;
+        for (int v0 = 0; v0 < nvec; v0 += spt) {
+          Stack S = b;
+          S.v = v0;
+          S.nv = std::min(spt, nvec - v0);
+          S.wv = w;
+          const int id = (int)stacks.size();
+          stacks.push_back(std::move(S));
+          tiles.push_back(Tile{(int)si, v0, stacks[id].pc[0].o, 0, 0, (int64_t)stacks[id].k, id});
+        }
+      }
+    }
     for (int v = 0; v < nvec; ++v) {
       std::map<std::tuple<int, int, int>, std::vector<Piece>> groups;   // (B matrix, n, k) -> pieces
       for (size_t i = 0; i < outs.size(); ++i) {
+        if (slot_width(outs[i])) continue;
         int64_t kt = 0;
         for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
         const bool stackable = outs[i].tmat >= 0 && outs[i].seg_count == 1 && outs[i].m % TM != 0;
@@ -1942,30 +2009,13 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
           groups[std::make_tuple(g.b, outs[i].n, g.k)].push_back(Piece{(int)i, full * TM, (rem + 7) & ~7, 0});
         }
       }
-      for (auto& kv : groups) {
-        std::vector<Piece>& pcs = kv.second;
-        std::stable_sort(pcs.begin(), pcs.end(), [](const Piece& x, const Piece& y) { return x.nrows > y.nrows; });
-        std::vector<Stack> bins;
-        std::vector<int> used;
-        for (const Piece& pc : pcs) {
-          size_t j = 0;
-          for (; j < bins.size(); ++j)
-            if (used[j] + pc.nrows <= TM && (int)bins[j].pc.size() < TC_MAX_PIECES) break;
-          if (j == bins.size()) {
-            bins.push_back(Stack{(int)si, v, std::get<1>(kv.first), std::get<2>(kv.first), std::get<0>(kv.first), {}});
-            used.push_back(0);
-          }
-          Piece q = pc;
-          q.srow = used[j];
-          used[j] += pc.nrows;
-          bins[j].pc.push_back(q);
-        }
-        for (Stack& b : bins) {
-          const int id = (int)stacks.size();
-          stacks.push_back(std::move(b));
-          for (int nb = 0; nb < (stacks[id].n + TN - 1) / TN; ++nb)
-            tiles.push_back(Tile{(int)si, v, stacks[id].pc[0].o, 0, nb, (int64_t)stacks[id].k, id});
-        }
+      std::vector<Stack> bins;
+      pack(groups, (int)si, v, bins);
+      for (Stack& b : bins) {
+        const int id = (int)stacks.size();
+        stacks.push_back(std::move(b));
+        for (int nb = 0; nb < (stacks[id].n + TN - 1) / TN; ++nb)
+          tiles.push_back(Tile{(int)si, v, stacks[id].pc[0].o, 0, nb, (int64_t)stacks[id].k, id});
       }
     }
   }
@@ -1990,12 +2040,22 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
         const Stack& S = stacks[t.stack];
         TcItem h{};
         h.type = TC_ITEM_TILE;
-        h.t.c_rel = 3;
+        h.t.c_rel = S.nv ? 4 : 3;
         h.t.m0 = 0;
         h.t.n0 = t.b * TN;
         h.t.nt = std::min(TN, S.n - h.t.n0);
         h.t.t_k = S.n;
         h.t.inst = (int)S.pc.size();
+        if (S.nv) {
+          // slots: the vectors v0 .. v0 + nv - 1 of pools 1 (B) and 2 (intermediates)
+          h.t.n0 = 0;
+          h.t.nt = S.nv * S.wv;
+          h.t.ldc = S.wv;
+          h.t.accumulate = S.nv;
+          h.t.c_off = tp.pool_size[2];
+          if (S.nv * S.wv > TN || S.wv % 8 != 0 || S.wv > 32)
+            throw Error(LRT_EINVAL, "tensor-core plan: vector slots outside the tile");
+        }
         int rows = 0;
         for (const Piece& pc : S.pc) rows += pc.nrows;
         h.t.mt = rows;
@@ -2036,6 +2096,10 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
         r.s.b_rp = B.Rp;
         r.s.k = S.k;
         r.s.scale = g0->scale;
+        if (S.nv) {
+          if (B.Rp != S.wv || B.pool != 1) throw Error(LRT_EINVAL, "tensor-core plan: slot width of B");
+          r.s.b_vstride = tp.pool_size[1];
+        }
         it.push_back(r);
         continue;
       }
@@ -2444,29 +2508,46 @@ static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, 
   const Sectors& Lb = c->bonds[b];
   std::vector<int64_t> off(Lb.n(), -1);
   int64_t tot = 0;
+  uint64_t h = site_signature(T);
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
   for (int q = 0; q < Lb.n(); ++q) {
     const int f = F.s.find(Lb.a[q], Lb.b[q]);
+    mix((uint64_t)(f + 1));
     if (f < 0) continue;
     off[q] = tot;
     tot += (int64_t)Lb.d[q] * F.s.d[f];
+    for (int n = 0; n < 4; ++n) mix((uint64_t)F.off[f][n]);
+    mix((uint64_t)F.s.d[f]);
   }
   double* p = buf.ensure(tot);
   CK(cudaMemsetAsync(p, 0, (size_t)std::max<int64_t>(tot, 1) * sizeof(double), c->st));
-  std::vector<GatherTask> tasks;
-  std::vector<GatherSrc> srcs;
-  for (int q = 0; q < Lb.n(); ++q) {
-    if (off[q] < 0) continue;
-    const int f = F.s.find(Lb.a[q], Lb.b[q]);
-    for (int n = 0; n < 4; ++n) {
-      if (T.sub_off[q][n] < 0) continue;
-      const int Dr = c->bonds[b + 1].d[T.sub_qr[q][n]];
-      tasks.push_back(GatherTask{p + off[q] + F.off[f][n], F.s.d[f], Lb.d[q], Dr, (int)srcs.size(), 1});
-      srcs.push_back(GatherSrc{T.d + T.sub_off[q][n], Dr, 0, 1.0});
+  const std::pair<int, uint64_t> key{b, h};
+  auto it = c->rf_plans.find(key);
+  if (it == c->rf_plans.end()) {
+    if (c->rf_plans.size() > 4096) c->rf_plans.clear();   // layouts of earlier bond dimensions
+    std::vector<GatherTask> tasks;
+    std::vector<GatherSrc> srcs;
+    for (int q = 0; q < Lb.n(); ++q) {
+      if (off[q] < 0) continue;
+      const int f = F.s.find(Lb.a[q], Lb.b[q]);
+      for (int n = 0; n < 4; ++n) {
+        if (T.sub_off[q][n] < 0) continue;
+        const int Dr = c->bonds[b + 1].d[T.sub_qr[q][n]];
+        GatherTask t{nullptr, F.s.d[f], Lb.d[q], Dr, (int)srcs.size(), 1};
+        t.dst_off = off[q] + F.off[f][n];
+        tasks.push_back(t);
+        GatherSrc g{nullptr, Dr, 0, 1.0};
+        g.src_off = T.sub_off[q][n];
+        g.rel = 1;
+        srcs.push_back(g);
+      }
     }
+    auto np = std::make_unique<GatherPlan>();
+    build_gather(*np, tasks, srcs, c->st);
+    it = c->rf_plans.emplace(key, std::move(np)).first;
   }
-  GatherPlan gp;
-  build_gather(gp, tasks, srcs, c->st);
-  gp.run(c->st);
+  const GatherPlan& g = *it->second;
+  launch_gather(g.tasks.p, g.srcs.p, g.tiles.p, g.ntiles, c->st, p, T.d);
   CK(cudaGetLastError());
   return off;
 }

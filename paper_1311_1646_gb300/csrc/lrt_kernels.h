@@ -121,6 +121,7 @@ struct TcSegRec {
   int a_rp, b_rp;     // padded rows of the two matrices
   int k;              // valid K
   float scale;
+  int64_t b_vstride;  // c_rel 4: floats between the B matrices of consecutive vectors
 };
 // Stacked tiles (c_rel == 3): the tile's 128 rows hold several short products that share
 // their B operand and K; header.C points at the tile's piece items, header.inst counts
@@ -137,6 +138,12 @@ struct TcPieceRec {
   int smem_row;       // first row of the piece in the tile (multiple of 8)
   int t_rp, t_row0;   // intermediate: padded rows, first row written
 };
+// Vector-slot tiles (c_rel == 4): stacked pieces as for c_rel 3, and the tile's columns
+// split into header.accumulate slots of header.ldc columns (a multiple of 8), slot j
+// holding the product for vector v0 + j.  The producer copies slot j's B rows from
+// b + j * b_vstride; the epilogue writes slot j into the piece's intermediate plus
+// j * header.c_off floats.  Narrow products (a few columns per vector) thereby fill
+// the tile's columns with the vectors of a block-Davidson step.
 constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2, TC_ITEM_PIECE = 3;
 constexpr int TC_MAX_PIECES = 16;
 struct TcItem {

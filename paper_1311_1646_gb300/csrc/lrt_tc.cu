@@ -300,11 +300,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           first_seg = false;
           // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
           uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0);
-          if (hdr.c_rel == 3) {
+          if (hdr.c_rel >= 3) {
             ra = 0;
             for (int j = 0; j < npieces; ++j) ra += (uint32_t)pieces[j].nrows;
           }
-          const uint32_t rb = (uint32_t)min(TN, g.b_rp - hdr.n0);
+          // vector slots: hdr.accumulate slots of hdr.ldc rows, each all of one vector's B
+          const bool slots = hdr.c_rel == 4;
+          const uint32_t rb = slots ? (uint32_t)(hdr.accumulate * hdr.ldc) : (uint32_t)min(TN, g.b_rp - hdr.n0);
           const uint32_t bytes = 2u * 128u * (ra + rb);
           for (int k0 = 0, q = 0; k0 < g.k && ok; k0 += TC_K, ++q, ++it) {
             const uint32_t stage = it % STAGES, round = it / STAGES;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
             const uint32_t st = sbase + stage * Tile<TN>::STAGE_BYTES;
             const int64_t ao = ((int64_t)q * g.a_rp + hdr.m0) * TC_K, bo = ((int64_t)q * g.b_rp + hdr.n0) * TC_K;
             mbar_arrive_tx(&full_bar[stage], bytes);
-            if (hdr.c_rel == 3) {
+            if (hdr.c_rel >= 3) {
               for (int j = 0; j < npieces; ++j) {
                 const TcPieceRec& pc = pieces[j];
                 const int64_t po = ((int64_t)q * pc.a_rp + pc.a_row0) * TC_K;
@@ -329,8 +331,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
               bulk_g2s(st, g.a_hi + ao, 128u * ra, &full_bar[stage]);
               bulk_g2s(st + A_BYTES, g.a_lo + ao, 128u * ra, &full_bar[stage]);
             }
-            bulk_g2s(st + 2 * A_BYTES, g.b_hi + bo, 128u * rb, &full_bar[stage]);
-            bulk_g2s(st + 2 * A_BYTES + Tile<TN>::B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
+            if (slots) {
+              for (int j = 0; j < hdr.accumulate; ++j) {
+                const int64_t vo = (int64_t)j * g.b_vstride + (int64_t)q * g.b_rp * TC_K;
+                const uint32_t so = (uint32_t)(j * hdr.ldc) * 128u;
+                bulk_g2s(st + 2 * A_BYTES + so, g.b_hi + vo, 128u * (uint32_t)hdr.ldc, &full_bar[stage]);
+                bulk_g2s(st + 2 * A_BYTES + Tile<TN>::B_BYTES + so, g.b_lo + vo, 128u * (uint32_t)hdr.ldc,
+                         &full_bar[stage]);
+              }
+            } else {
+              bulk_g2s(st + 2 * A_BYTES, g.b_hi + bo, 128u * rb, &full_bar[stage]);
+              bulk_g2s(st + 2 * A_BYTES + Tile<TN>::B_BYTES, g.b_lo + bo, 128u * rb, &full_bar[stage]);
+            }
           }
         }
         cur = nx1;
@@ -462,7 +474,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         // the staging buffer may still be read by this warp's previous bulk stores
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         __syncwarp();
-        if (t.c_rel >= 2) {
+        if (t.c_rel == 4) {
+          // Vector slots: each thread writes its row of every slot straight into the
+          // piece's intermediate of that vector (TC-matrix image, 16-byte groups permuted
+          // by row mod 8).  A slot is at most one chunk wide; positions past it keep the
+          // zeros the intermediate was cleared to.
+          const int r = rbase + lane;
+          if (r < t.mt) {
+            const TcItem* pit = reinterpret_cast<const TcItem*>(t.C);
+            for (int j = 0; j < t.inst; ++j) {
+              const TcItem pe = load_item(pit + j);
+              if (r < pe.p.smem_row || r >= pe.p.smem_row + pe.p.nrows) continue;
+              const int64_t trow = pe.p.t_row0 + (r - pe.p.smem_row);
+#pragma unroll
+              for (int g = 0; g < TN / 4; ++g) {
+                const int c = 4 * g;
+                const int slot = c / t.ldc;
+                if (slot < t.accumulate) {
+                  const int pg = (c - slot * t.ldc) >> 2;
+                  uint32_t h[4], l[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) split_tf32(sum[c + e] - cmp[c + e], h[e], l[e]);
+                  const int64_t o = (int64_t)slot * t.c_off + trow * 32 + (((pg ^ (int)trow) & 7) << 2);
+                  *(uint4*)(pe.p.t_hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+                  *(uint4*)(pe.p.t_lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+              }
+              break;
+            }
+          }
+        } else if (t.c_rel >= 2) {
           // Intermediate: this warp's rows as a TC-matrix image (two chunks of 32
           // columns, hi and lo planes; row r's 16-byte groups permuted by r mod 8),
           // then one bulk store per chunk and plane: rows [m0 + 32 w, + nrows) of a
