@@ -27,6 +27,7 @@ namespace lrt {
 constexpr int GEMM_KC = 32;        // K positions per staged chunk
 constexpr int GEMM_SEGB = 32;      // segment descriptors staged per batch (one per lane of warp 0)
 constexpr int GEMM_THREADS = 128;
+constexpr int GEMM_WARPS = GEMM_THREADS / 32;
 constexpr int GEMM_TILE_M = 64;    // equal to GEMM_TM / GEMM_TN of lrt_kernels.h
 constexpr int GEMM_TILE_N = 32;
 
@@ -50,8 +51,8 @@ LRT_HD int seg_at(const int* kst, int p, int q) {
 template <class F>
 LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0, int m0, int mt, int n0, int nt,
                         F&& f) {
-  static_assert(GEMM_THREADS == 128 && GEMM_KC == 32 && GEMM_TILE_M == 64 && GEMM_TILE_N == 32,
-                "the lane mappings below assume 4 warps, 32-wide chunks and 64 x 32 tiles");
+  static_assert(GEMM_THREADS % 64 == 0 && GEMM_KC == 32 && GEMM_TILE_M == 64 && GEMM_TILE_N == 32,
+                "the lane mappings below assume whole pairs of warps, 32-wide chunks and 64 x 32 tiles");
   const int lane = tid & 31, warp = tid >> 5;
   // lanes along K: A and B stored K-contiguous (A row-major, B transposed)
   {
@@ -61,9 +62,9 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
       const SegS& s = sd[q];
       const int kl = p - kst[q];
       if (!s.transA)
-        for (int i = warp; i < mt; i += 4) f(0, i, lane, s.A + (int64_t)(m0 + i) * s.lda + kl);
+        for (int i = warp; i < mt; i += GEMM_WARPS) f(0, i, lane, s.A + (int64_t)(m0 + i) * s.lda + kl);
       if (s.transB)
-        for (int j = warp; j < nt; j += 4) f(1, lane, j, s.B + (int64_t)(n0 + j) * s.ldb + kl);
+        for (int j = warp; j < nt; j += GEMM_WARPS) f(1, lane, j, s.B + (int64_t)(n0 + j) * s.ldb + kl);
     }
   }
   // lanes along the rows of A stored transposed (K-major)
@@ -71,7 +72,7 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
     const int i = tid & 63;
     int q = 0;
     if (i < mt)
-      for (int kk = tid >> 6; kk < GEMM_KC; kk += 2) {
+      for (int kk = tid >> 6; kk < GEMM_KC; kk += GEMM_THREADS / 64) {
         const int p = p0 + kk;
         if (p >= Kb) break;
         q = seg_at(kst, p, q);
@@ -84,7 +85,7 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
     const int j = lane;
     int q = 0;
     if (j < nt)
-      for (int kk = warp; kk < GEMM_KC; kk += 4) {
+      for (int kk = warp; kk < GEMM_KC; kk += GEMM_WARPS) {
         const int p = p0 + kk;
         if (p >= Kb) break;
         q = seg_at(kst, p, q);

@@ -85,6 +85,7 @@ void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* t
 // previous chunk's FMAs (the staging plan is in lrt_fp64_tile.h).
 // ---------------------------------------------------------------------------
 constexpr int GEMM_MAXE = GEMM_TM * GEMM_TN / GEMM_THREADS;   // outputs per thread
+constexpr int GEMM_CTAS = 4;                                   // resident CTAs per SM (registers, shared memory)
 static_assert(GEMM_TM == GEMM_TILE_M && GEMM_TN == GEMM_TILE_N, "tile shape of the staging plan");
 
 struct GemmSmem {
@@ -131,7 +132,17 @@ __device__ __forceinline__ void fma_chunk(double (&acc)[GEMM_MAXE], const uint32
   }
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
+// fma_chunk for the warp's output count n <= N (a chain of uniform branches)
+template <int N>
+__device__ __forceinline__ void fma_dispatch(int n, double (&acc)[GEMM_MAXE], const uint32_t (&rc)[GEMM_MAXE],
+                                             const double* __restrict__ As, const double* __restrict__ Bs, int kc) {
+  if constexpr (N > 0) {
+    if (n == N) fma_chunk<N>(acc, rc, As, Bs, kc);
+    else fma_dispatch<N - 1>(n, acc, rc, As, Bs, kc);
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
                                                                     const GemmSeg* __restrict__ segs,
                                                                     const int3* __restrict__ tiles, int ntiles,
                                                                     const double* __restrict__ xbase,
@@ -221,20 +232,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 4) gemm_fp64_kernel(const GemmOu
       const int kc = min(GEMM_KC, Kb - c * GEMM_KC);
       if (!S.unit[buf]) {        // scale row kk of B by its segment's scale
         if (lane < nt)
-          for (int kk = warp; kk < kc; kk += 4) S.Bs[buf][kk][lane] *= S.sc[buf][kk];
+          for (int kk = warp; kk < kc; kk += GEMM_WARPS) S.Bs[buf][kk][lane] *= S.sc[buf][kk];
         __syncthreads();
       }
       const double* As = &S.As[buf][0][0];
       const double* Bs = &S.Bs[buf][0][0];
-      switch (cntw) {            // warp-uniform trip count: no predicated-off DFMA occupies the pipe
-#define LRT_FMA_CASE(N) \
-  case N: fma_chunk<N>(acc, rc, As, Bs, kc); break;
-        LRT_FMA_CASE(1) LRT_FMA_CASE(2) LRT_FMA_CASE(3) LRT_FMA_CASE(4) LRT_FMA_CASE(5) LRT_FMA_CASE(6)
-        LRT_FMA_CASE(7) LRT_FMA_CASE(8) LRT_FMA_CASE(9) LRT_FMA_CASE(10) LRT_FMA_CASE(11) LRT_FMA_CASE(12)
-        LRT_FMA_CASE(13) LRT_FMA_CASE(14) LRT_FMA_CASE(15) LRT_FMA_CASE(16)
-#undef LRT_FMA_CASE
-        default: break;
-      }
+      // warp-uniform trip count: no predicated-off DFMA occupies the pipe
+      fma_dispatch<GEMM_MAXE>(cntw, acc, rc, As, Bs, kc);
       __syncthreads();           // buffer buf is free for chunk c + 2
     }
   }
@@ -253,7 +257,7 @@ int gemm_fp64_slots() {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    n = std::max(1, nsm) * 4;   // __launch_bounds__ minimum, met by the registers and shared memory
+    n = std::max(1, nsm) * GEMM_CTAS;
   }
   return n;
 }
@@ -262,7 +266,7 @@ static void gemm_fp64_smem_attr() {
   static bool done = false;
   if (!done) {
     cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
-    // all of the unified L1 as shared memory, so four CTAs fit on an SM
+    // all of the unified L1 as shared memory, so GEMM_CTAS CTAs fit on an SM
     cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     done = true;
   }
@@ -296,9 +300,8 @@ constexpr int DIAG_MAXD = 128;     // rows and columns of a block staged per chu
 __global__ void __launch_bounds__(256) diag_kernel(const DiagOut* __restrict__ outs,
                                                    const DiagTerm* __restrict__ terms,
                                                    double* __restrict__ dbase) {
-  __shared__ double xs[DIAG_CHUNK][DIAG_MAXD];
+  __shared__ double xs[DIAG_CHUNK][DIAG_MAXD];   // scale_t * x_t, so one DFMA per term and element
   __shared__ double ys[DIAG_CHUNK][DIAG_MAXD];
-  __shared__ double sc[DIAG_CHUNK];
   const DiagOut o = outs[blockIdx.x];
   for (int r0 = 0; r0 < o.rows; r0 += DIAG_MAXD)
     for (int c0 = 0; c0 < o.cols; c0 += DIAG_MAXD) {
@@ -313,9 +316,8 @@ __global__ void __launch_bounds__(256) diag_kernel(const DiagOut* __restrict__ o
           for (int e = threadIdx.x; e < tc * (rt + ct); e += blockDim.x) {
             const int t = e / (rt + ct), u = e % (rt + ct);
             const DiagTerm d = terms[o.term_begin + t0 + t];
-            if (u < rt) xs[t][u] = d.x ? d.x[(int64_t)(r0 + u) * d.xs] : 1.0;
+            if (u < rt) xs[t][u] = d.x ? d.scale * d.x[(int64_t)(r0 + u) * d.xs] : d.scale;
             else ys[t][u - rt] = d.y ? d.y[(int64_t)(c0 + u - rt) * d.ys] : 1.0;
-            if (u == 0) sc[t] = d.scale;
           }
           __syncthreads();
 #pragma unroll
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(256) diag_kernel(const DiagOut* __restrict__ o
             if (e < n) {
               const int i = e / ct, jj = e % ct;
               double a = acc[j];
-              for (int t = 0; t < tc; ++t) a = fma(sc[t] * xs[t][i], ys[t][jj], a);
+              for (int t = 0; t < tc; ++t) a = fma(xs[t][i], ys[t][jj], a);
               acc[j] = a;
             }
           }
