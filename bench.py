@@ -37,7 +37,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 # for the kernel source it was taken on (sha256 prefix); otherwise the bench reports null.
 TRAFFIC = {
     "fp64": {"source": "lrt_kernels.cu", "sha256": "3309c025fc03e33c", "bytes": (9.116e6 + 52.469e6) / 2},
-    "mixed": {"source": "lrt_tc.cu", "sha256": "e9d855b8b94e80d8", "bytes": (115.224e6 + 151.780e6) / 2},
+    "mixed": {"source": "lrt_tc.cu", "sha256": "d4c9ba3ef56446b3", "bytes": (90.125e6 + 150.770e6) / 2},
 }
 
 
