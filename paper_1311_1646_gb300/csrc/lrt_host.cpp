@@ -3738,7 +3738,10 @@ struct TdaRunner {
         }
       }
       first = false;
-      m = (l < N) ? l : n;
+      // keep the whole subspace while the next one (at most l + n vectors: the GEP may drop
+      // directions of S below the cut, so l need not be a multiple of n) still fits in N;
+      // otherwise restart from the n lowest Ritz vectors
+      m = (l + n <= N) ? l : n;
     }
   }
 
