@@ -435,7 +435,44 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
                 "two-site + 4 one-site sweep_gs sweeps and tda_prepare on the GPU; resid = sum of "
                 "the site residuals^2 per root (roots with resid near 1e-4 stall there); the TDA "
                 "loop is host-bound at this size"}
-    # (5) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
+    # (5) TDA on this workload (PPP k=12, M=256, 6 roots): ground state on the GPU (two-site
+    # sweeps up to M, four one-site sweeps), then 30 TDA sweeps in each precision
+    cfg = synth.config(2)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    g = pkg.Context(device)
+    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_gs = g.sweep_gs([64, 128, cfg["M"]], max_sweeps=12, onesite_sweeps=4)
+    torch.cuda.synchronize()
+    t_gs = time.perf_counter() - t0
+    bonds, sites = g.mps_get()
+    g.close()
+    res = {}
+    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
+        t = pkg.Context(device)
+        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
+        t.tda_prepare()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, rs, e0 = t.sweep_tda(nr, max_iter=30, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
+                                 refine_tol=1e-5)
+        torch.cuda.synchronize()
+        res[prec] = (time.perf_counter() - t0, om, rs)
+        t.close()
+    (s64, w64, r64), (smx, wmx, rmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
+    out["tda_ppp_k12_M256_6roots"] = {
+        "gs_s": t_gs, "e0": e_gs, "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr,
+        "omega_fp64": list(w64), "omega_mixed": list(wmx), "abs_domega_Eh": list(np.abs(w64 - wmx)),
+        "resid_fp64": list(r64), "resid_mixed": list(rmx), "eps": 1e-8,
+        "note": "ground state: two-site sweeps with M = 64, 128, 256 and four one-site sweeps on the "
+                "GPU; TDA: 30 sweeps at most, diagonal start; mixed: tensor-core H_0 site products "
+                "until sum |r|^2 < 1e-5, then FP64; resid = sum of the site residuals^2 per root"}
+    # (6) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
     # each precision from the same reference (a right-canonical random MPS at the full bond
     # dimension brought to the mixed-canonical gauge by tda_prepare)
     cfg = synth.config(3)
