@@ -168,11 +168,13 @@ typedef struct {
   uint64_t seed;      /* initial trial vectors projected by Q^C: SplitMix64 Gaussians of this
                          seed, or (seed 0) at every site the unit vector on the root's rank
                          among the lowest diagonal elements of H_0 where |C0| < 1/2 */
-  int precision;      /* LRT_FP64, or LRT_MIXED: the site products H_0 C and dH C0 run as
-                         split-TF32 tensor-core products until every root's sum |r|^2 is
-                         below refine_tol (or two thirds of max_iter have passed), then the
-                         sweeps continue in FP64 to eps (the FP64 residual correction); the
-                         results always come from FP64 sweeps */
+  int precision;      /* LRT_FP64, or LRT_MIXED: the site products H_0 C run as split-TF32
+                         tensor-core products until every root's sum |r|^2 is below
+                         refine_tol (or two thirds of max_iter have passed), then the sweeps
+                         continue in FP64 to eps (the FP64 residual correction); with
+                         max_iter >= 2 the results come from FP64 sweeps.  The first-order
+                         products dH C0 are FP64 in both (their operator sets are new every
+                         sweep) */
   double refine_tol;  /* LRT_MIXED: switch to FP64 below this sum |r|^2 (<= 0: 1e-6) */
 } lrt_tda_params;
 int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);

@@ -234,7 +234,7 @@ class Context:
                   pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
                   precision: int = LRT_FP64, refine_tol: float = 0.0):
         """DMRG-TDA roots: returns (omega, resid, e0); omega are excitation energies.  With
-        precision=LRT_MIXED the site products run on the tensor cores until the residuals
+        precision=LRT_MIXED the H_0 site products run on the tensor cores until the residuals
         fall below refine_tol, then the sweeps finish in FP64."""
         om = np.zeros(nroots)
         rs = np.zeros(nroots)
