@@ -36,7 +36,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 # sigma launches of the middle position (profiles/gemm_*_ppp_k12_M256_twosite.md), valid only
 # for the kernel source it was taken on (sha256 prefix); otherwise the bench reports null.
 TRAFFIC = {
-    "fp64": {"source": "lrt_kernels.cu", "sha256": "3bb5da7729367bbf", "bytes": (8.899e6 + 52.431e6) / 2},
+    "fp64": {"source": "lrt_kernels.cu", "sha256": "bb2c0751cad8230e", "bytes": (9.020e6 + 52.461e6) / 2},
     "mixed": {"source": "lrt_tc.cu", "sha256": "d4c9ba3ef56446b3", "bytes": (90.125e6 + 150.770e6) / 2},
 }
 

@@ -2,7 +2,7 @@
 //
 //  gather:    scaled, optionally transposed block copies summed into destination
 //             sub-blocks (building enlarged-block operators, the "x h_i" of
-//             Eq. lopr1st); HBM-bound, 32x32 tiles staged through shared memory.
+//             Eq. lopr1st); 32x32 tiles, source descriptors staged in shared memory.
 //  gemm_fp64: grouped GEMM whose output tiles each loop over a list of
 //             (A, B, scale) products (K-concatenation), so all contributions to
 //             one output block are summed in registers without atomics.
@@ -17,13 +17,20 @@ namespace lrt {
 // ---------------------------------------------------------------------------
 // gather
 // ---------------------------------------------------------------------------
+// The sources of a task (a dozen on average for an enlarged operator set, most of them
+// blocks of a few tens of rows) are staged as descriptors in shared memory, and their
+// loads are unrolled so that several are in flight: a tile costs a few memory round trips
+// instead of two per source.  Transposed sources are read straight from global memory;
+// the CTA's reads of one source block stay in L1.
+constexpr int GATHER_SRC_STAGE = 64;
+
 __global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restrict__ tasks,
                                                      const GatherSrc* __restrict__ srcs,
                                                      const int3* __restrict__ tiles, int ntiles,
                                                      double* __restrict__ dbase,
                                                      const double* __restrict__ sbase1,
                                                      const double* __restrict__ sbase2) {
-  __shared__ double tile[GATHER_TILE][GATHER_TILE + 1];
+  __shared__ GatherSrc sd[GATHER_SRC_STAGE];
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
@@ -31,31 +38,27 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restric
   if (dbase) t.dst = dbase + t.dst_off;
   const int r0 = wi.y * GATHER_TILE, c0 = wi.z * GATHER_TILE;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const int tid = ty * 32 + tx;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int s = 0; s < t.src_count; ++s) {
-    GatherSrc g = srcs[t.src_begin + s];
-    if (g.rel) g.src = (g.rel == 1 ? sbase1 : sbase2) + g.src_off;
-    if (!g.trans) {
+  for (int s0 = 0; s0 < t.src_count; s0 += GATHER_SRC_STAGE) {
+    const int ns = min(GATHER_SRC_STAGE, t.src_count - s0);
+    __syncthreads();   // the previous descriptors are no longer read
+    if (tid < ns) {
+      GatherSrc g = srcs[t.src_begin + s0 + tid];
+      if (g.rel) g.src = (g.rel == 1 ? sbase1 : sbase2) + g.src_off;
+      sd[tid] = g;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int s = 0; s < ns; ++s) {
+      const double* src = sd[s].src;
+      const int64_t ld = sd[s].ld;
+      const double sc = sd[s].scale;
+      const bool tr = sd[s].trans != 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = r0 + ty + 8 * i, c = c0 + tx;
-        if (r < t.rows && c < t.cols) acc[i] += g.scale * g.src[(int64_t)r * g.ld + c];
-      }
-    } else {
-      // dst(r, c) = src(c, r): stage src rows c0.. (cols r0..) coalesced, read transposed
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int cc = ty + 8 * i;          // src row offset (= dst col)
-        const int rr = tx;                  // src col offset (= dst row)
-        const int c = c0 + cc, r = r0 + rr;
-        tile[cc][rr] = (c < t.cols && r < t.rows) ? g.src[(int64_t)c * g.ld + r] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int rr = ty + 8 * i, cc = tx;
-        acc[i] += g.scale * tile[cc][rr];
+        if (r < t.rows && c < t.cols) acc[i] += sc * (tr ? src[(int64_t)c * ld + r] : src[(int64_t)r * ld + c]);
       }
     }
   }
