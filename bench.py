@@ -247,7 +247,10 @@ def run_ours(args):
         cpu = cpu_baseline(ctx, H, left, right, nvec, sizes)
     side = None
     if rank == 0 and world == 1 and not args.no_extras:
-        side = extras(pkg, ctx, device, xs, ys, positions, nvec, stream)
+        try:
+            side = extras(pkg, ctx, device, xs, ys, positions, nvec, stream)
+        except Exception as e:   # the side measurements never cost the metric line
+            side = {"error": repr(e)}
     if rank == 0:
         if args.precision == "mixed":
             peak, peak_note = tf32_peak()
@@ -472,7 +475,44 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
         "note": "ground state: two-site sweeps with M = 64, 128, 256 and four one-site sweeps on the "
                 "GPU; TDA: 30 sweeps at most, diagonal start; mixed: tensor-core H_0 site products "
                 "until sum |r|^2 < 1e-5, then FP64; resid = sum of the site residuals^2 per root"}
-    # (6) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
+    # (6) batched TDA on 8 instances of the config-4 shapes (4 roots each, two sweeps from a
+    # prepared random reference): one instance after another against sweep_tda_batched
+    # (host threads, one stream per context)
+    def tda_instances(streams):
+        cs = []
+        for b in range(8):
+            cfg = synth.config(4, batch_index=b)
+            H = cfg["ham"]
+            m = synth.random_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 700 + b, "right")
+            c = pkg.Context(device, stream=streams[b].cuda_stream if streams else None)
+            c.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+            c.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+            c.tda_prepare()
+            cs.append(c)
+        torch.cuda.synchronize()
+        return cs
+    cs = tda_instances(None)
+    t0 = time.perf_counter()
+    seq = [c.sweep_tda(4, max_iter=1, eps=1e-12, seed=0, allow_noconv=True) for c in cs]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for c in cs:
+        c.close()
+    streams = [torch.cuda.Stream(device=device) for _ in range(8)]
+    cs = tda_instances(streams)
+    t0 = time.perf_counter()
+    wb, rb, eb = pkg.sweep_tda_batched(cs, 4, max_iter=1, eps=1e-12, seed=0, allow_noconv=True)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    for c in cs:
+        c.close()
+    out["tda_batched_config4_8inst_4roots_2sweeps"] = {
+        "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
+        "max_abs_domega_Eh": float(max(np.abs(np.asarray(seq[j][0]) - wb[j]).max() for j in range(8))),
+        "host_threads": os.cpu_count(),
+        "note": "8 instances with the config-4 shapes, each a right-canonical random MPS at its M "
+                "prepared by tda_prepare; two sweeps (the first with m = 0) of 4 roots, FP64"}
+    # (7) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
     # each precision from the same reference (a right-canonical random MPS at the full bond
     # dimension brought to the mixed-canonical gauge by tda_prepare)
     cfg = synth.config(3)

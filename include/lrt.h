@@ -188,6 +188,18 @@ int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);
  * zero Schmidt values (dropped by pinv_cut in sweep_tda). */
 int tda_prepare(lrt_t ctx, double* norm);
 int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0);
+/* sweep_tda_batched: the DMRG-TDA sweeps of Fig. alg:dmrgtda for n_inst independent
+ * instances, each its own context (its own Hamiltonian and reference, prepared by
+ * tda_load or tda_prepare), run concurrently: host threads (at most the host's hardware
+ * threads) take the instances in turn, each driving its instance's context and stream,
+ * so the host-side work of the instances overlaps, and their kernels overlap on the GPU
+ * when the contexts were created on different streams.  Every instance uses nroots and
+ * params.  omega and resid: n_inst * nroots values, instance-major; e0: n_inst values
+ * (may be NULL).  Returns LRT_OK; LRT_ENOCONV when some instance reached max_iter first
+ * (all results written); else the first other error code, whose message is in that
+ * instance's lrt_last_error.  The contexts must be distinct. */
+int sweep_tda_batched(const lrt_t* ctxs, int n_inst, int nroots, const lrt_tda_params* params, double* omega,
+                      double* resid, double* e0);
 
 /* Read back the loaded MPS: bond tables (bond_nsect[k+1], bond_sectors[3 * total])
  * and the left-fused data of one site (host_out may be NULL to query *nelem). */

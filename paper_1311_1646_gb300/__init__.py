@@ -20,7 +20,8 @@ LRT_MIXED = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda", "sigma_batched"]
+           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda", "sigma_batched",
+           "sweep_tda_batched"]
 
 _lib = None
 
@@ -91,6 +92,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
+    lib.sweep_tda_batched.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(TdaParams), dp, dp, dp]
     for name in EXPORTS:
         if name != "lrt_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -287,3 +289,24 @@ def sigma_batched(ctxs: list, sites: list, nsite: int, xs: list, ys: list, nvec:
     py = (ctypes.c_void_p * n)(*[_tensor_ptr(y, ctxs[j].wfn_layout(sites[j], nsite)[0] * nvec)
                                  for j, y in enumerate(ys)])
     ctxs[0]._check(ctxs[0].lib.sigma_batched(hs, n, st, nsite, nvec, px, py, precision), "sigma_batched")
+
+
+def sweep_tda_batched(ctxs: list, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
+                      pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
+                      precision: int = LRT_FP64, refine_tol: float = 0.0):
+    """DMRG-TDA of several independent instances (one prepared Context each), run
+    concurrently; returns (omega, resid, e0) with omega and resid of shape (n, nroots)."""
+    n = len(ctxs)
+    if n == 0:
+        raise LrtError("sweep_tda_batched: no instances")
+    om = np.zeros(n * nroots)
+    rs = np.zeros(n * nroots)
+    e0 = np.zeros(n)
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
+    p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol)
+    lib = ctxs[0].lib
+    rc = lib.sweep_tda_batched(hs, n, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), _dptr(e0))
+    if rc != 0 and not (allow_noconv and rc == -4):
+        msgs = "; ".join(c.lib.lrt_last_error(c.h).decode() for c in ctxs)
+        raise LrtError(f"sweep_tda_batched failed ({rc}): {msgs}")
+    return om.reshape(n, nroots), rs.reshape(n, nroots), e0

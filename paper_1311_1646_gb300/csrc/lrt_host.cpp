@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -31,6 +32,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -1558,7 +1560,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
   if (I.e_core != 0.0) terms.push_back({I.e_core, {KI, -1, -1, 0}, {KI, -1, -1, 0}});
 
   auto plan = std::make_unique<SigmaPlan>();
-  static uint64_t next_serial = 0;
+  static std::atomic<uint64_t> next_serial{0};   // plans are built from several threads in sweep_tda_batched
   plan->serial = ++next_serial;
   plan->nelem = nelem;
   plan->n_terms = (int)terms.size();
@@ -4224,7 +4226,7 @@ int lrt_create(lrt_t* out, int device, void* cuda_stream) {
   }
   auto* c = new (std::nothrow) lrt_ctx();
   if (!c) return LRT_ENOMEM;
-  static uint64_t next_id = 0;
+  static std::atomic<uint64_t> next_id{0};
   c->id = ++next_id;
   c->dev = device;
   c->st = (cudaStream_t)cuda_stream;
@@ -4456,6 +4458,40 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, dou
   if (e0) *e0 = E0;
   if (rc != LRT_OK) ctx->err = "sweep_tda: not converged within max_iter (results written)";
   return rc;
+}
+
+int sweep_tda_batched(const lrt_t* ctxs, int n_inst, int nroots, const lrt_tda_params* p, double* omega,
+                      double* resid, double* e0) {
+  if (!ctxs || n_inst <= 0 || nroots <= 0 || !p || !omega || !resid) return LRT_EINVAL;
+  for (int j = 0; j < n_inst; ++j) {
+    if (!ctxs[j]) return LRT_EINVAL;
+    for (int q = 0; q < j; ++q)
+      if (ctxs[q] == ctxs[j]) {
+        ctxs[j]->err = "sweep_tda_batched: an instance appears twice";
+        return LRT_EINVAL;
+      }
+  }
+  // lazily initialized device queries, before the threads start
+  lrt::gemm_fp64_slots();
+  lrt::tc_num_ctas(1);
+  std::vector<int> rc(n_inst, LRT_OK);
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int j = next++; j < n_inst; j = next++)
+      rc[j] = sweep_tda(ctxs[j], nroots, p, omega + (size_t)j * nroots, resid + (size_t)j * nroots,
+                        e0 ? e0 + j : nullptr);
+  };
+  const int nt = std::max(1, std::min(n_inst, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> threads;
+  for (int t = 1; t < nt; ++t) threads.emplace_back(work);
+  work();
+  for (auto& t : threads) t.join();
+  int out = LRT_OK;
+  for (int j = 0; j < n_inst; ++j) {
+    if (rc[j] != LRT_OK && rc[j] != LRT_ENOCONV) return rc[j];
+    if (rc[j] == LRT_ENOCONV) out = LRT_ENOCONV;
+  }
+  return out;
 }
 
 int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors) {

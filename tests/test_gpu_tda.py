@@ -164,3 +164,33 @@ def test_gpu_ground_state_then_tda_is_variational(pkg):
     assert abs(e0 - E) < 1e-7
     assert e0 >= ef[0] - 1e-9
     assert np.all(omega + e0 >= ef[1:n + 1] - 1e-8)
+
+
+def test_tda_batched_matches_each_instance_alone(pkg):
+    """sweep_tda_batched runs several independent instances concurrently (host threads,
+    one stream per context); each instance's roots equal those of its own sweep_tda."""
+    cases = [(5, 3, 2, 10, 11), (6, 3, 3, 12, 12), (5, 2, 2, 8, 13)]
+    refs, ctxs, streams = [], [], []
+    for k, na, nb, M, seed in cases:
+        H = synth.ab_initio(k, na, nb, seed)
+        t, v = fock.spin_integrals(H.h, H.eri)
+        E, sites, _ = dmrg.ground_state(H, t, v, [M], synth.random_mps(k, na, nb, M, 3))
+        E, sites, _ = dmrg.onesite_sweeps(H, t, v, sites)
+        alone = _prepared(pkg, H, sites)
+        refs.append(alone.sweep_tda(2, max_iter=8, eps=1e-13, seed=0, allow_noconv=True))
+        alone.close()
+        tables, Rp = _right_form(H.k, sites)
+        streams.append(torch.cuda.Stream())
+        ctx = pkg.Context(0, stream=streams[-1].cuda_stream)
+        ctx.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        ctx.mps_load(H.k, H.n_alpha, H.n_beta, tables, Rp, 0)
+        ctx.tda_prepare()
+        ctxs.append(ctx)
+    torch.cuda.synchronize()
+    omega, resid, e0 = pkg.sweep_tda_batched(ctxs, 2, max_iter=8, eps=1e-13, seed=0, allow_noconv=True)
+    for c in ctxs:
+        c.close()
+    for j, (w, r, e) in enumerate(refs):
+        assert abs(e0[j] - e) < 1e-12
+        assert np.abs(omega[j] - w).max() < 1e-10
+        assert np.abs(resid[j] - r).max() <= 1e-10 * max(1.0, np.abs(r).max())
