@@ -3568,6 +3568,11 @@ struct TdaRunner {
         for (int a = 0; a < lprev; ++a)
           for (int j = 0; j < m; ++j) alpha[(size_t)a * m + j] = U[(size_t)a * mcols + j];
         theta.assign(w.begin(), w.begin() + m);
+        // every root needs a Ritz vector: a subspace whose overlap matrix keeps fewer than
+        // n directions above the cut cannot continue the sweep Davidson
+        if (m < n)
+          throw Error(LRT_EINVAL, "sweep_tda: the trial subspace spans fewer directions than roots (" +
+                                      std::to_string(m) + " < " + std::to_string(n) + ")");
       }
       const int l = m + n;
       Hr.assign((size_t)l * l, 0.0);
