@@ -48,6 +48,18 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert lib.sigma(None, 0, 1, 1, None, None, 0) == -1
     lib.lrt_destroy.argtypes = [ctypes.c_void_p]
     assert lib.lrt_destroy(None) == -1
+    vp = ctypes.c_void_p
+    lib.sigma_batched.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int]
+    assert lib.sigma_batched(None, 1, None, 1, 1, None, None, 0) == -1
+    one_null = (vp * 1)(None)
+    assert lib.sigma_batched(one_null, 1, None, 1, 1, None, None, 0) == -1
+    lib.sweep_tda_batched.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+    assert lib.sweep_tda_batched(None, 1, 1, None, None, None, None) == -1
+    om = (ctypes.c_double * 1)()
+    params = (ctypes.c_char * 64)()
+    assert lib.sweep_tda_batched(one_null, 1, 1, params, om, om, None) == -1
+    lib.tda_prepare.argtypes = [vp, vp]
+    assert lib.tda_prepare(None, None) == -1
 
 
 def test_product_path_fails_loudly_without_the_library(tmp_path):
