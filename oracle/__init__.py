@@ -20,6 +20,8 @@ Modules:
   tda     DMRG-TDA: the sweep algorithm of Fig. alg:dmrgtda and the
           tangent-space Rayleigh-Ritz definition it approximates (Eqs.
           dmrgrpa with W = 0, hsub ... param).
+  transition  one-particle transition densities of the TDA states and their
+          square norm (Table site_excitation).
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
 closed form, a brute-force determinant-space computation, an invariant or a

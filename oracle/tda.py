@@ -119,14 +119,14 @@ def onesite_shapes(left_dims, right_dims):
 # ----------------------------------------------------------------------------
 # the definition: Rayleigh-Ritz on the tangent space
 # ----------------------------------------------------------------------------
-def tangent_rr(ham, L0, R0, C0, Lam, nroots, cut=1e-10):
-    """TDA total energies by Rayleigh-Ritz of H on (sum_i V_i) minus Psi_0 (determinant space)."""
+def tangent_space(ham, L0, R0, C0, Lam, cut=1e-10):
+    """Orthonormal basis (determinant space, columns) of (sum_i V_i) minus Psi_0, with the
+    normalized reference, the sector Hamiltonian and its determinants."""
     k = ham.k
     Hd, dets = fock.fci_hamiltonian(ham.h, ham.eri_full(), ham.e_core, k, ham.n_alpha, ham.n_beta)
     cols = []
     psi0 = None
     for i in range(k):
-        left = {q: m.shape[0] for (q, n, qr), m in L0[i].items()} if i > 0 else {(0, 0): 1}
         left = {q: len(Lam[i][q]) for q in Lam[i]}
         right = {q: len(Lam[i + 1][q]) for q in Lam[i + 1]}
         shapes = onesite_shapes(left, right)
@@ -141,7 +141,12 @@ def tangent_rr(ham, L0, R0, C0, Lam, nroots, cut=1e-10):
     psi0 = psi0 / np.linalg.norm(psi0)
     U = U - np.outer(psi0, psi0 @ U)
     U2, s2, _ = np.linalg.svd(U, full_matrices=False)
-    U2 = U2[:, s2 > cut]
+    return U2[:, s2 > cut], psi0, Hd, dets
+
+
+def tangent_rr(ham, L0, R0, C0, Lam, nroots, cut=1e-10):
+    """TDA total energies by Rayleigh-Ritz of H on (sum_i V_i) minus Psi_0 (determinant space)."""
+    U2, psi0, Hd, _ = tangent_space(ham, L0, R0, C0, Lam, cut)
     w = np.linalg.eigvalsh(U2.T @ Hd @ U2)
     E0 = psi0 @ Hd @ psi0
     return w[:nroots], E0, U2.shape[1]
