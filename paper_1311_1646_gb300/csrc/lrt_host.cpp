@@ -48,13 +48,11 @@ struct Error : std::runtime_error {
   Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
-// Caching device allocator for the library's small buffers (plans, site tensors, bond
-// matrices, work vectors): blocks of up to 8 MiB are rounded up to a power of two and
-// kept for reuse by the context that freed them, so the TDA sweep's thousands of small
-// temporaries cost neither a cudaMalloc nor the device synchronization of a cudaFree.
-// Every ABI call makes its context's pool current for the calling thread; a context
-// launches on one stream, so a reused block is ordered after the work that last used
-// it.  Larger blocks go straight to the driver.
+// Caching device allocator of a context: freed blocks are kept for reuse by the context
+// that freed them, so the sweeps' thousands of temporaries cost neither a cudaMalloc nor
+// the device synchronization of a cudaFree (size classes below).  Every ABI call makes
+// its context's pool current for the calling thread; a context launches on one stream,
+// so a reused block is ordered after the work that last used it.
 struct DevPool {
   std::unordered_map<void*, size_t> live;      // pointer -> size class
   std::map<size_t, std::vector<void*>> cached; // size class -> free blocks
