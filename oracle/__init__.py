@@ -22,6 +22,10 @@ Modules:
           dmrgrpa with W = 0, hsub ... param).
   transition  one-particle transition densities of the TDA states and their
           square norm (Table site_excitation).
+  rpa     DMRG-RPA: the second-order matrix W of Eq. dmrgrpa, both as the energy
+          functional's Hessian in a chart and by the paper's pairwise construction
+          (Eq. bmatrix), the RPA frequencies, and the reduced-problem Davidson of
+          Eq. reducedrpa.
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
 closed form, a brute-force determinant-space computation, an invariant or a

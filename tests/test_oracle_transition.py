@@ -48,9 +48,9 @@ def _reference(k, na, nb, M, seed=7):
     return H, om.mixed_canonical(sites)
 
 
-def test_tda_transition_densities_conserve_particles_and_satisfy_the_adjoint_identity():
-    k, na, nb = 5, 3, 2
-    H, (L0, R0, C0, Lam, _) = _reference(k, na, nb, 8)
+def test_tda_transition_densities_conserve_particles_and_satisfy_the_adjoint_identity(stationary_k5):
+    H, (L0, R0, C0, Lam, _) = stationary_k5
+    k = H.k
     theta, X, E0, psi0, dets = transition.tda_states(H, L0, R0, C0, Lam, 3)
     w, E0r, _ = tda.tangent_rr(H, L0, R0, C0, Lam, 3)
     assert np.abs(theta - w).max() < 1e-12 and abs(E0 - E0r) < 1e-12
