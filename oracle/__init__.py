@@ -26,6 +26,9 @@ Modules:
           functional's Hessian in a chart and by the paper's pairwise construction
           (Eq. bmatrix), the RPA frequencies, and the reduced-problem Davidson of
           Eq. reducedrpa.
+  response  frequency-dependent linear response to a one-body perturbation at the
+          TDA and RPA levels, and the exact response function (Eqs. pt_ext,
+          realresp, imagresp).
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
 closed form, a brute-force determinant-space computation, an invariant or a
