@@ -22,10 +22,10 @@ Modules:
           dmrgrpa with W = 0, hsub ... param).
   transition  one-particle transition densities of the TDA states and their
           square norm (Table site_excitation).
-  rpa     DMRG-RPA: the second-order matrix W of Eq. dmrgrpa, both as the energy
-          functional's Hessian in a chart and by the paper's pairwise construction
-          (Eq. bmatrix), the RPA frequencies, and the reduced-problem Davidson of
-          Eq. reducedrpa.
+  rpa     DMRG-RPA: the second-order matrix W of Eq. dmrgrpa as the energy
+          functional's Hessian in a chart, by the paper's pairwise construction and
+          through the sweep (Eq. bmatrix), the RPA frequencies, and the
+          reduced-problem Davidson of Eq. reducedrpa.
   response  frequency-dependent linear response to a one-body perturbation at the
           TDA and RPA levels, and the exact response function (Eqs. pt_ext,
           realresp, imagresp).

@@ -35,6 +35,9 @@ Two constructions of W:
   sites, L1_i on the left and R1_j on the right, joined by Lam (neighbours) or by the
   zeroth-order sites between them (C0 on the first of them).
 
+* `w_sweep` is Eq. bmatrix as the sweep evaluates it, site by site, from the reverse
+  first-order left sets; it equals `w_paper` term by term.
+
 Reading: the paper's complex conjugates are trivial here (real MPS); omega are the
 positive RPA frequencies, ascending.  Brute force in the determinant basis; small k only.
 """
@@ -42,6 +45,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import blocks as ob
 from . import mps as om
 from . import tda as ot
 
@@ -343,3 +347,35 @@ def _orth_pairs(dX, dY, X, Y, cut=1e-10):
     if not outX:
         return np.zeros((dX.shape[0], 0)), np.zeros((dX.shape[0], 0))
     return np.stack(outX, axis=1), np.stack(outY, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# W through the sweep (Eq. bmatrix)
+# ----------------------------------------------------------------------------
+def w_sweep(ham, t, v, L0, R0, C0, Lam, Xs, tg=None):
+    """W_mu,nu = sum_i W^[i]_mu,nu for the tangent vectors Xs (determinant-space columns), by
+    Eq. bmatrix: W^[i]_mu,nu = (Lam_i R1_i^mu)^T (Delta H_nu^[i])^dag C0_i + (mu <-> nu).
+
+    Lam_i R1_i^mu = C1_i^mu Q^R (Eq. right1st), and (Delta H_nu^[i])^dag C0_i is the site-i
+    vector <l1_nu n r0|H|Psi_0>: the effective Hamiltonian of Eq. hleft_sb built on the
+    reverse first-order left set <l1|O|l0> of nu (Eq. lopr1st, grown from
+    L1_j^nu = Q^L C1_j^nu Lam^-1 for j < i) and applied to C0_i.  Contracted with
+    C1_i^mu Q^R it is the overlap of (H - E0) Psi_0 with the second-order chains
+    L1_j^nu ... (Lam R1^mu)_i of every j < i."""
+    tg = tg or Tangent(ham, L0, R0, C0, Lam)
+    sw = ot.TDASweeper(ham, t, v, L0, R0, C0, Lam)
+    k = ham.k
+    n = Xs.shape[1]
+    HL = [ot._zero_block(ob.left_mode(0, k), v) for _ in range(n)]
+    W = np.zeros((n, n))
+    for i in range(k):
+        cr = [ot.proj_R(tg.c1(Xs[:, a], i), R0[i]) for a in range(n)]
+        if i > 0:
+            dh = [sw.dh_left(i, HL[b].rev) for b in range(n)]
+            for a in range(n):
+                for b in range(n):
+                    W[a, b] += ot.t_dot(cr[a], dh[b])
+        if i + 1 < k:
+            for b in range(n):
+                HL[b] = sw.grow_HL(i, HL[b], tg.l1(Xs[:, b], i))
+    return W + W.T

@@ -10,6 +10,8 @@
 * The RPA frequencies come in +-omega pairs and the lowest lies at or below the lowest
   TDA one (Thouless' minimum principle); the TDA limit is the tangent-space Rayleigh-Ritz.
 * At the exact bond dimension Psi_0 is an eigenstate: W = 0 and RPA = TDA = FCI.
+* Eq. bmatrix through the sweep (the reverse first-order left sets applied to C0, contracted
+  with C1 Q^R site by site) equals the pairwise W on any set of tangent vectors.
 """
 import numpy as np
 import pytest
@@ -109,6 +111,16 @@ def test_rpa_pairs_and_thouless_bound(truncated):
     assert np.abs(w_tda - (theta - E0)).max() < 1e-12
     assert w[0] <= w_tda[0] + 1e-12
     assert w_tda[0] - w[0] > 1e-3                 # strictly lower here: the bound is not vacuous
+
+
+def test_w_by_the_sweep_equals_the_pairwise_form(truncated):
+    H, tg, (L0, R0, C0, Lam) = truncated
+    t, v = fock.spin_integrals(H.h, H.eri)
+    A = np.random.default_rng(2).standard_normal((tg.U.shape[1], 5))
+    Ws = rpa.w_sweep(H, t, v, L0, R0, C0, Lam, tg.U @ A, tg)
+    want = A.T @ rpa.w_paper(tg) @ A
+    assert np.abs(want).max() > 1.0
+    assert np.abs(Ws - want).max() < 1e-12 * np.abs(want).max()
 
 
 def test_exact_bond_dimension_gives_fci():
