@@ -379,3 +379,39 @@ def w_sweep(ham, t, v, L0, R0, C0, Lam, Xs, tg=None):
             for b in range(n):
                 HL[b] = sw.grow_HL(i, HL[b], tg.l1(Xs[:, b], i))
     return W + W.T
+
+
+def w_action(ham, t, v, L0, R0, C0, Lam, y, tg=None):
+    """The tangent vector W y (determinant space), through the sweep.
+
+    Every pair of W couples the left-gauge tensor of one vector with the right-gauge tensor
+    of the other, so W(x, y) = sum_i <C1_i^x, c_i^y> with
+
+        c_i^y = a_i^y Q^R + Q^L b_i^y,
+        a_i^y = (Delta H_y^[i])^dag C0_i   from the reverse first-order left set of y
+                                            (sites j < i, Eq. lopr1st),
+        b_i^y = (Delta H'_y^[i])^dag C0_i  from the reverse first-order right set of y
+                                            (sites j > i, Eq. ropr1st),
+
+    and W y = sum_i L0_<i c_i^y R0_>i with Psi_0 projected out."""
+    tg = tg or Tangent(ham, L0, R0, C0, Lam)
+    sw = ot.TDASweeper(ham, t, v, L0, R0, C0, Lam)
+    k = ham.k
+    a, b = [{}] * k, [{}] * k
+    HL = ot._zero_block(ob.left_mode(0, k), v)
+    for i in range(k):
+        if i > 0:
+            a[i] = sw.dh_left(i, HL.rev)
+        if i + 1 < k:
+            HL = sw.grow_HL(i, HL, tg.l1(y, i))
+    HR = None
+    for i in range(k - 1, -1, -1):
+        if HR is not None:
+            b[i] = sw.dh_right(i, HR.rev)
+        if i > 0:
+            HR = sw.grow_HR(i, HR, tg.r1(y, i))
+    w = np.zeros(len(tg.dets))
+    for i in range(k):
+        c = ot.t_add(ot.proj_R(sw._full(i, a[i]), R0[i]), ot.proj_L(sw._full(i, b[i]), L0[i]))
+        w += tg.P[i] @ om.blocks_to_vec(c, tg.idx[i])
+    return w - tg.psi0 * (tg.psi0 @ w)

@@ -11,7 +11,8 @@
   TDA one (Thouless' minimum principle); the TDA limit is the tangent-space Rayleigh-Ritz.
 * At the exact bond dimension Psi_0 is an eigenstate: W = 0 and RPA = TDA = FCI.
 * Eq. bmatrix through the sweep (the reverse first-order left sets applied to C0, contracted
-  with C1 Q^R site by site) equals the pairwise W on any set of tangent vectors.
+  with C1 Q^R site by site) equals the pairwise W on any set of tangent vectors, and the
+  action W y built from the reverse left and right sets of y is the dense W applied to y.
 """
 import numpy as np
 import pytest
@@ -121,6 +122,18 @@ def test_w_by_the_sweep_equals_the_pairwise_form(truncated):
     want = A.T @ rpa.w_paper(tg) @ A
     assert np.abs(want).max() > 1.0
     assert np.abs(Ws - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_w_action_by_the_sweep_is_the_dense_product(truncated):
+    H, tg, (L0, R0, C0, Lam) = truncated
+    t, v = fock.spin_integrals(H.h, H.eri)
+    Wp = rpa.w_paper(tg)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        c = rng.standard_normal(tg.U.shape[1])
+        w = rpa.w_action(H, t, v, L0, R0, C0, Lam, tg.U @ c, tg)
+        assert np.linalg.norm(w - tg.U @ (tg.U.T @ w)) < 1e-12     # W y lies in the tangent space
+        assert np.abs(tg.U.T @ w - Wp @ c).max() < 1e-12 * np.abs(Wp @ c).max()
 
 
 def test_exact_bond_dimension_gives_fci():
