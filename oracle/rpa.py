@@ -36,7 +36,8 @@ Two constructions of W:
   zeroth-order sites between them (C0 on the first of them).
 
 * `w_sweep` is Eq. bmatrix as the sweep evaluates it, site by site, from the reverse
-  first-order left sets; it equals `w_paper` term by term.
+  first-order left sets; it equals `w_paper` term by term.  `w_action` applies W to one
+  vector through the sweep, for the residuals of the RPA Davidson.
 
 Reading: the paper's complex conjugates are trivial here (real MPS); omega are the
 positive RPA frequencies, ascending.  Brute force in the determinant basis; small k only.
