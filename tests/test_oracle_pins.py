@@ -360,3 +360,36 @@ def test_tda_first_order_gauge_conditions_and_overlap_structure():
         fused_rows[qr] = fused_rows.get(qr, 0) + a
     expect = sum((fused_rows[qr] - len(Lam[i + 1][qr])) * len(Lam[i + 1][qr]) for qr in fused_rows)
     assert rank == expect
+
+
+def test_tangent_space_equals_the_mps_tangent_projector(stationary_k5):
+    # The MPS tangent-space projector P_T = sum_i P_L<i x 1_i x P_R>i - sum_i P_L<=i x P_R>i
+    # (one-site product spaces V_i minus the bond spaces they share) must be the orthogonal
+    # projector onto the span the TDA definition builds (its basis plus Psi_0).
+    H, (L0, R0, C0, Lam, _) = stationary_k5
+    k = H.k
+    U, psi0, _, dets = tda.tangent_space(H, L0, R0, C0, Lam)
+    P = np.zeros((len(dets), len(dets)))
+    for i in range(k):
+        left = {q: len(Lam[i][q]) for q in Lam[i]}
+        right = {q: len(Lam[i + 1][q]) for q in Lam[i + 1]}
+        shapes = tda.onesite_shapes(left, right)
+        sites = [L0[j] for j in range(i)] + [tda.t_zero(shapes)] + [R0[j] for j in range(i + 1, k)]
+        Pi, idx = om.product_basis_onesite(sites, i, k, dets)
+        P += Pi @ Pi.T
+        if i == k - 1:
+            continue
+        # bond space between sites i and i+1: site-i coefficients L0_i G, G a bond matrix
+        cols = []
+        for qr, dr in right.items():
+            for a in range(dr):
+                for b in range(dr):
+                    C = {kk: np.outer(m[:, a], np.eye(dr)[b]) for kk, m in L0[i].items() if kk[2] == qr}
+                    cols.append(Pi @ om.blocks_to_vec(C, idx))
+        Bm = np.array(cols).T
+        assert np.abs(Bm.T @ Bm - np.eye(Bm.shape[1])).max() < 1e-12
+        P -= Bm @ Bm.T
+    want = U @ U.T + np.outer(psi0, psi0)
+    assert np.abs(P - P.T).max() < 1e-12
+    assert np.abs(P @ P - P).max() < 1e-11
+    assert np.abs(P - want).max() < 1e-11
