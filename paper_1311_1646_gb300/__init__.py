@@ -104,6 +104,14 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _site_size(left, right) -> int:
+    """Elements of a site tensor in the boundary's left-fused layout: for every right sector
+    q_r and site state n whose left sector q_r - n exists, a D(q_l) x D(q_r) block."""
+    ldim = {(int(a), int(b)): int(d) for a, b, d in left}
+    return sum(ldim.get((int(ra) - sa, int(rb) - sb), 0) * int(dr)
+               for ra, rb, dr in right for sa, sb in ((0, 0), (1, 0), (0, 1), (1, 1)))
+
+
 def _tensor_ptr(t, nelem: int) -> int:
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
@@ -131,6 +139,7 @@ class Context:
         self.h = h
         self.device = device
         self._keep = []
+        self._k = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -153,6 +162,12 @@ class Context:
         h = np.ascontiguousarray(h, dtype=np.float64)
         e = np.ascontiguousarray(eri, dtype=np.float64) if eri is not None else None
         b = np.ascontiguousarray(B, dtype=np.float64) if B is not None else None
+        if h.shape != (k, k):
+            raise LrtError(f"op_build: h has shape {h.shape}, need ({k}, {k})")
+        if e is not None and e.size != k ** 4:
+            raise LrtError(f"op_build: eri has {e.size} elements, need k^4 = {k ** 4}")
+        if b is not None and (b.ndim != 3 or b.shape[1:] != (k, k)):
+            raise LrtError(f"op_build: B has shape {b.shape}, need (n_factor, {k}, {k})")
         nL = 0 if b is None else b.shape[0]
         self._check(self.lib.op_build(self.h, k, _dptr(h), _dptr(e) if e is not None else None, nL,
                                       _dptr(b) if b is not None else None, float(e_core)), "op_build")
@@ -161,13 +176,26 @@ class Context:
                  sites_right: list | None = None):
         """Load an MPS: `sites` (left-orthonormal form, left-fused layout) and optionally the
         right-orthonormal form `sites_right` of every site (same layout)."""
+        if len(bonds) != k + 1 or len(sites) != k or (sites_right is not None and len(sites_right) != k):
+            raise LrtError(f"mps_load: need {k + 1} bond tables and {k} sites")
         nsect = np.array([len(t) for t in bonds], dtype=np.int32)
         secs = np.array([x for t in bonds for s in t for x in s], dtype=np.int32)
-        arrs = [np.ascontiguousarray(s, dtype=np.float64) for s in sites]
+        if len(secs) != 3 * int(nsect.sum()):
+            raise LrtError("mps_load: every bond sector is a triple (n_alpha, n_beta, dim)")
+
+        def fused(arrays, what):
+            out = [np.ascontiguousarray(s, dtype=np.float64).ravel() for s in arrays]
+            for i, a in enumerate(out):
+                want = _site_size(bonds[i], bonds[i + 1])
+                if a.size != want:
+                    raise LrtError(f"mps_load: {what} {i} has {a.size} elements, its layout has {want}")
+            return out
+
+        arrs = fused(sites, "site")
         ptrs = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in arrs])
         rptrs = None
         if sites_right is not None:
-            rarrs = [np.ascontiguousarray(s, dtype=np.float64) for s in sites_right]
+            rarrs = fused(sites_right, "right-orthonormal site")
             rptrs = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in rarrs])
         desc = MpsDesc(k, n_alpha, n_beta, nsect.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                        secs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ptrs, center, rptrs)
@@ -220,8 +248,20 @@ class Context:
 
     def tda_load(self, C0: list, lam: list):
         """Zeroth-order centre tensors C0_i (left-fused layout) and Schmidt values per bond."""
-        c0 = [np.ascontiguousarray(x, dtype=np.float64) for x in C0]
-        lm = [np.ascontiguousarray(x, dtype=np.float64) for x in lam]
+        bonds = self._bond_tables()
+        k = len(bonds) - 1
+        if len(C0) != k or len(lam) != k + 1:
+            raise LrtError(f"tda_load: need {k} centre tensors and {k + 1} Schmidt-value arrays")
+        c0 = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in C0]
+        lm = [np.ascontiguousarray(x, dtype=np.float64).ravel() for x in lam]
+        for i, a in enumerate(c0):
+            want = _site_size(bonds[i], bonds[i + 1])
+            if a.size != want:
+                raise LrtError(f"tda_load: C0 {i} has {a.size} elements, its layout has {want}")
+        for b, a in enumerate(lm):
+            want = sum(int(d) for _, _, d in bonds[b])
+            if a.size != want:
+                raise LrtError(f"tda_load: Lambda of bond {b} has {a.size} values, the bond has {want} states")
         pc = (ctypes.POINTER(ctypes.c_double) * len(c0))(*[_dptr(a) for a in c0])
         pl = (ctypes.POINTER(ctypes.c_double) * len(lm))(*[_dptr(a) for a in lm])
         self._check(self.lib.tda_load(self.h, pc, pl), "tda_load")
@@ -247,8 +287,8 @@ class Context:
             self._check(rc, "sweep_tda")
         return om, rs, e0.value
 
-    def mps_get(self):
-        """The loaded MPS as (bonds, sites): bond tables [(na, nb, dim)] and left-fused site arrays."""
+    def _bond_tables(self):
+        """Bond tables [(na, nb, dim)] of the MPS the context holds now."""
         tot = ctypes.c_int()
         self._check(self.lib.mps_get_bonds(self.h, None, None, ctypes.byref(tot)), "mps_get_bonds")
         k = self._k
@@ -259,6 +299,12 @@ class Context:
         for b in range(k + 1):
             bonds.append([(sec[3 * (pos + s)], sec[3 * (pos + s) + 1], sec[3 * (pos + s) + 2]) for s in range(ns[b])])
             pos += ns[b]
+        return bonds
+
+    def mps_get(self):
+        """The loaded MPS as (bonds, sites): bond tables [(na, nb, dim)] and left-fused site arrays."""
+        bonds = self._bond_tables()
+        k = self._k
         sites = []
         for i in range(k):
             n = ctypes.c_int64()

@@ -71,3 +71,30 @@ def test_product_path_fails_loudly_without_the_library(tmp_path):
             pkg.load(str(tmp_path / "missing.so"))
     finally:
         pkg._lib = saved
+
+
+def test_binding_checks_host_array_sizes_before_the_call():
+    # the loaders read exactly the documented layout from host memory: the binding rejects
+    # arrays of the wrong size or count before anything reaches the library
+    import numpy as np
+    import synth
+    import paper_1311_1646_gb300 as pkg
+    for k, na, nb, M in [(4, 2, 2, 8), (6, 3, 2, 20), (5, 1, 3, 12)]:
+        m = synth.random_mps(k, na, nb, M, 1)
+        for i in range(k):
+            assert pkg._site_size(m.bonds[i], m.bonds[i + 1]) == len(m.sites[i])
+    ctx = object.__new__(pkg.Context)            # no device: the checks run first
+    H = synth.ab_initio(4, 2, 2, 3)
+    m = synth.random_mps(4, 2, 2, 8, 1)
+    bad = [
+        lambda: ctx.op_build(4, H.h[:3, :3], H.eri),
+        lambda: ctx.op_build(4, H.h, H.eri.ravel()[:-1]),
+        lambda: ctx.op_build(4, H.h, None, B=np.zeros((2, 4, 3))),
+        lambda: ctx.mps_load(4, 2, 2, m.bonds[:-1], m.sites, 0),
+        lambda: ctx.mps_load(4, 2, 2, m.bonds, m.sites[:-1], 0),
+        lambda: ctx.mps_load(4, 2, 2, m.bonds, [m.sites[0][:-1]] + list(m.sites[1:]), 0),
+        lambda: ctx.mps_load(4, 2, 2, m.bonds, m.sites, 0, sites_right=list(m.sites[:-1]) + [np.zeros(1)]),
+    ]
+    for f in bad:
+        with pytest.raises(pkg.LrtError):
+            f()
