@@ -19,7 +19,7 @@ first-order gauge relations of the paper:
 with Lam the Schmidt values of the bond to the right (left) of site i.  In code, bond b
 sits between sites b-1 and b, so L1_i uses Lam[i+1] and R1_i uses Lam[i].
 
-Two constructions of W:
+Three constructions of W:
 
 * `w_chart` is the definition through the manifold: in the chart centred at site c,
 
