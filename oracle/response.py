@@ -96,3 +96,44 @@ def alpha_exact(ham, d, omega):
     V = one_body(dets, ham.k, d)
     f = (U[:, 1:].T @ (V @ U[:, 0])) ** 2
     return alpha_sum_over_states(e[1:] - e[0], f, omega)
+
+
+def site_sweep(tg, d, omega, sign=+1, sweeps=30, tol=1e-12):
+    """The first-order wavefunction by the paper's site equations (Eqs. realresp, imagresp),
+    solved site by site in forward and backward sweeps.
+
+    At site i the component C1_i of X on V_i solves
+
+        (H_0^[i] - (E0 - sign*omega)) C1_i = -Q^C (Delta H_i C0 + V_i C0),
+
+    where H_0^[i] = P_i^T H P_i is the site effective Hamiltonian, V_i C0 = P_i^T V Psi_0 and
+    Delta H_i C0 = P_i^T H X_i' is the first-order change from the rest of X (X_i', the
+    part of X orthogonal to V_i), kept fixed while site i is solved.  The sweep then moves
+    to the next site with the updated X.  sign = +1 is the component of Eq. realresp, -1
+    that of Eq. imagresp.  Determinant-space brute force; `tg` is an rpa.Tangent.
+    Returns (X, sweeps used, |change| of the last sweep)."""
+    n = len(tg.dets)
+    Hd, psi0, E0 = tg.Hd, tg.psi0, tg.E0
+    vpsi = one_body(tg.dets, tg.k, d) @ psi0
+    shift = E0 - sign * omega
+    X = np.zeros(n)
+    order = list(range(tg.k)) + list(range(tg.k - 2, 0, -1))
+    change = np.inf
+    for sw in range(1, sweeps + 1):
+        X_old = X.copy()
+        for i in order:
+            P = tg.P[i]
+            c0 = P.T @ psi0                                  # C0_i in the product basis
+            Xp = X - P @ (P.T @ X)                           # the rest of X
+            rhs = -(P.T @ (Hd @ Xp) + P.T @ vpsi)
+            rhs -= c0 * (c0 @ rhs)                           # Q^C
+            Hi = P.T @ Hd @ P - shift * np.eye(P.shape[1])
+            Q = np.eye(P.shape[1]) - np.outer(c0, c0)
+            # solve on the range of Q^C: (Q Hi Q) c = rhs with c orthogonal to C0_i
+            c = np.linalg.lstsq(Q @ Hi @ Q, rhs, rcond=None)[0]
+            c -= c0 * (c0 @ c)
+            X = Xp + P @ c
+        change = np.linalg.norm(X - X_old)
+        if change < tol:
+            return X, sw, change
+    return X, sweeps, change

@@ -7,6 +7,8 @@ realresp, imagresp, psi1st).
   eigenpairs (the amplitudes normalized to X.X - Y.Y = 1 and solving Eq. dmrgrpa).
 * The static RPA response is the curvature of the variational energy: one-site DMRG at
   fixed bond dimension with h + lambda d, second differences extrapolated in the step.
+* The paper's site equations (Eqs. realresp, imagresp), solved site by site in sweeps,
+  reach the dense tangent-space solution.
 """
 import dataclasses
 
@@ -93,3 +95,21 @@ def test_static_rpa_response_is_the_variational_energy_curvature():
     curv = (4 * d2[2.5e-3] - d2[5e-3]) / 3
     assert abs(curv - a_rpa) < 1e-6 * abs(a_rpa)
     assert abs(curv - a_tda) > 0.1                          # the TDA level misses it here
+
+
+def test_site_sweep_solves_the_tangent_space_response(stationary_k5):
+    # Eqs. realresp / imagresp solved site by site in sweeps reach the dense tangent-space
+    # solution of (H -+ omega) X = -v below the first pole
+    H, (L0, R0, C0, Lam, _) = stationary_k5
+    tg = rpa.Tangent(H, L0, R0, C0, Lam)
+    d = _perturbation(H.k)
+    v = response.drive(tg, d)
+    Ht = rpa.h_tangent(tg)
+    w1 = np.linalg.eigvalsh(Ht)[0]
+    n = len(v)
+    for w in (0.0, 0.5 * w1):
+        for sign in (+1, -1):
+            X, sweeps, change = response.site_sweep(tg, d, w, sign, sweeps=60, tol=1e-13)
+            assert sweeps < 60 and change < 1e-13
+            want = -tg.U @ np.linalg.solve(Ht + sign * w * np.eye(n), v)
+            assert np.abs(X - want).max() < 1e-10 * np.abs(want).max()
