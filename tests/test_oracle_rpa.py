@@ -148,6 +148,11 @@ def test_exact_bond_dimension_gives_fci():
     assert abs(tg.E0 - e[0]) < 1e-10
     assert np.abs(w[:5] - (e[1:6] - e[0])).max() < 1e-8
     assert np.abs(w - np.linalg.eigvalsh(Ht)).max() < 1e-9
+    # the one-call wrapper, by both routes
+    for route in ("paper", "chart"):
+        w_r, w_t, e0 = rpa.rpa_roots(H, L0, R0, C0, Lam, 3, route=route)
+        assert abs(e0 - e[0]) < 1e-10
+        assert np.abs(w_r - (e[1:4] - e[0])).max() < 1e-8 and np.abs(w_t - w_r).max() < 1e-9
 
 
 def test_reduced_rpa_davidson_reaches_the_dense_roots(truncated):
