@@ -181,6 +181,20 @@ def test_renormalized_operators_match_definition():
             bk, Pk = EL[qk]
             assert np.abs(Pb.T @ F[np.ix_(bb, bk)] @ Pk - m).max() < 1e-13
     assert {"H", "C", "S", "A", "B", "I"} <= seen
+    # conservation: the renormalized N_alpha = sum_x B_{x a, x a} (and N_beta) is diagonal
+    # with the sector label: every block state is an eigenstate, so <l'|N|l> = N(q) <l'|l>,
+    # the label times the renormalized identity (the Gram matrix of this non-orthonormal
+    # block) on the (q, q) blocks, and nothing between different sectors
+    ident = next(op for key, op in L.ops.items() if key[0] == "I")
+    for spin in (0, 1):
+        N = {}
+        for x in range(spin, nso, 2):
+            for blk, m in L.ops[("B", x, x)].items():
+                N[blk] = N.get(blk, 0.0) + m
+        for (qb, qk), m in N.items():
+            want = qb[spin] * ident[(qb, qk)] if qb == qk else np.zeros_like(m)
+            assert np.abs(m - want).max() < 1e-13
+        assert any(qb[spin] > 0 for qb, _ in N)
 
 
 def _brute_env(k, na, nb, M, seed):
