@@ -407,3 +407,20 @@ def test_tangent_space_equals_the_mps_tangent_projector(stationary_k5):
     assert np.abs(P - P.T).max() < 1e-12
     assert np.abs(P @ P - P).max() < 1e-11
     assert np.abs(P - want).max() < 1e-11
+
+
+def test_tda_roots_interlace_above_the_exact_excited_states(stationary_k5):
+    # at a stationary reference (<T|H|Psi_0> = 0) H is block diagonal on span{Psi_0} + T, so
+    # Cauchy interlacing on that space gives E0 >= lambda_1 and theta_j >= lambda_{j+1}
+    # for every TDA root, within the same (N_alpha, N_beta) sector
+    H, (L0, R0, C0, Lam, _) = stationary_k5
+    U, psi0, Hd, _ = tda.tangent_space(H, L0, R0, C0, Lam)
+    assert np.linalg.norm(U.T @ (Hd @ psi0)) < 1e-6
+    theta = np.linalg.eigvalsh(U.T @ Hd @ U)
+    lam = np.linalg.eigvalsh(Hd)
+    E0 = psi0 @ Hd @ psi0
+    assert E0 >= lam[0] - 1e-12 and E0 <= theta[0]
+    assert np.all(theta >= lam[1:len(theta) + 1] - 1e-10)
+    # and the upper interlacing side: theta_j <= lambda_{j + 1 + (n - dim)}
+    n, m = len(lam), len(theta) + 1
+    assert np.all(theta <= lam[n - m + 1:] + 1e-10)
