@@ -50,3 +50,24 @@ def test_replica_throughput_single_process():
     import bench
     ms, tflops = bench.replica_throughput(40.0, 4, 1e9, 1)
     assert ms == 10.0 and tflops == pytest.approx(0.1)
+
+
+def test_reference_arm_prints_its_contract_line():
+    # bench.py --impl reference times the oracle on the host cores: one JSON line with the
+    # metric of the GPU arm, the cpu_baseline it describes and an e2e block with no copies
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                         capture_output=True, text=True, cwd=root, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
+    assert d["metric"].startswith("H_eff sigma") and d["unit"] == "TFLOP/s"
+    assert d["config"]["workload"] and d["dtype"] == "f64" and d["data"] == "synthetic"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
