@@ -363,7 +363,10 @@ def sweep_tda(ham, t, v, L0, R0, C0, Lam, nroots, N=None, eps=1e-14, max_iter=60
                 sig = t_add(sw.h0(i, C1[mu]), sw.dh_left(i, HLcur[mu]))
                 sig = t_add(sig, sw.dh_right(i, HRrot[mu]))
                 sig = sw._full(i, sig)
-                r = t_add(sig, C1[mu], -theta[mu])
+                # Eq. rnorm, projected by Q^C: at a stationary reference the C0 component
+                # <Psi0|H|Psi_mu> of r is zero; elsewhere the projected sum is the residual of the
+                # Rayleigh-Ritz problem on the tangent space minus Psi_0
+                r = proj_C(t_add(sig, C1[mu], -theta[mu]), C0[i])
                 r2[mu] += t_dot(r, r)
                 z = {}
                 for kk, rm in r.items():
