@@ -1,11 +1,12 @@
 """Benchmark of the DMRG effective-Hamiltonian sigma vector on one GB300.
 
-Workload (the PPP polyene case): 12-site Pariser-Parr-Pople trans-polyene,
-6 alpha + 6 beta electrons, bond dimension M = 256, two-site sigma with a
-block of 6 trial vectors (the 6 TDA roots), FP64.  One step = diag(H_eff)
-plus H_eff X for every two-site position i = 0..10 of a sweep, on environments
-(renormalized left/right blocks) built once before timing from a random
-mixed-canonical MPS with the workload's sector structure.
+Workload (the water-shaped ab initio case, the largest of the workloads that fits this
+design on one GPU): k = 24 spatial orbitals, 5 alpha + 5 beta electrons, integrals from a
+seeded factor with |v_ijkl| decaying as exp(-|i-j|/6), bond dimension M = 500, one-site
+sigma with a block of 6 trial vectors (the 6 TDA roots), FP64.  One step = diag(H_eff)
+plus H_eff X at every one-site position i = 0..23 of a sweep, on environments
+(renormalized left/right blocks) built once before timing from random left- and
+right-orthonormal MPS with the workload's sector structure.
 
 Prints one JSON line.  --impl reference times the CPU oracle instead.
 """
@@ -29,7 +30,6 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (152 SMs x 2 FMA/clk x 2 flop x ~2.06 GHz)
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the two
@@ -60,7 +60,7 @@ def tf32_peak():
             return json.load(f)["bf16_tflops"] * TF32_PER_BF16, "of measured (bf16 burst x 1.1/2.25)"
     except (OSError, KeyError, ValueError):
         return 1900.0 * TF32_PER_BF16, "of fallback (1.9 PF bf16 x 1.1/2.25)"
-WORKLOAD = "ppp_polyene_k12_M256_twosite_6roots_fp64"
+WORKLOAD = "water_k24_e10_M500_onesite_6vec_fp64"
 
 
 def parse():
@@ -73,7 +73,10 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="sigma arithmetic: FP64, or split-TF32 tensor-core products (LRT_MIXED)")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the side measurements (mixed sigma, water-shaped sigma, TDA s/root)")
+                   help="skip the side measurements (mixed sigma, PPP sigma, batching, TDA s/root)")
+    p.add_argument("--quick-tda", action="store_true", help="TDA side measurement on the 8-orbital workload only")
+    p.add_argument("--tda-water", action="store_true",
+                   help="also the TDA to convergence on the k = 24, M = 500 workload (long)")
     return p.parse_args()
 
 
@@ -140,8 +143,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(pkg, device):
-    cfg = synth.config(2)
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def build_workload(pkg, device, cfg_idx=3, nsite=1):
+    """Environments for every position of a sweep: all left blocks from a random
+    left-orthonormal MPS, all right blocks from a random right-orthonormal one."""
+    cfg = synth.config(cfg_idx)
     H = cfg["ham"]
     k, na, nb, M, nvec = H.k, H.n_alpha, H.n_beta, cfg["M"], cfg["nroots"]
     left = synth.random_mps(k, na, nb, M, 2024, "left")
@@ -151,11 +168,71 @@ def build_workload(pkg, device):
     ctx.mps_load(k, na, nb, left.bonds, left.sites, 0, sites_right=right.sites)
     for b in range(k - 1):
         ctx.renormalize(b, +1)
-    for b in range(k - 1, 1, -1):
+    for b in range(k - 1, nsite - 1, -1):
         ctx.renormalize(b, -1)
-    positions = list(range(k - 1))
-    sizes = {i: ctx.wfn_layout(i, 2)[0] for i in positions}
-    return ctx, H, left, right, positions, sizes, nvec
+    positions = list(range(k - nsite + 1))
+    sizes = {i: ctx.wfn_layout(i, nsite)[0] for i in positions}
+    return ctx, H, positions, sizes, nvec
+
+
+def fp64_peak(clocks):
+    """FP64 FMA-pipe peak of GB300 at the sampled maximum SM clock: 152 SMs x 2 DFMA/clk x 2."""
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
+class SigmaStep:
+    """One step: diag + sigma (nvec vectors) at every position, on the library's stream."""
+
+    def __init__(self, ctx, positions, sizes, nvec, nsite, device, prec):
+        import torch
+        self.ctx, self.positions, self.nvec, self.nsite, self.prec = ctx, positions, nvec, nsite, prec
+        self.xs = {i: torch.tensor(synth.random_vector(nvec * sizes[i], 100 + i), dtype=torch.float64,
+                                   device=f"cuda:{device}") for i in positions}
+        self.ys = {i: torch.empty_like(self.xs[i]) for i in positions}
+        self.ds = {i: torch.empty(sizes[i], dtype=torch.float64, device=f"cuda:{device}") for i in positions}
+        # algorithmic flops and launches of one step (plans are built on the first call)
+        self.flops, self.launches = 0.0, 0
+        for i in positions:
+            ctx.heff_diag(i, nsite, self.ds[i])
+            ctx.sigma(i, nsite, self.xs[i], self.ys[i], nvec=nvec, precision=prec)
+            st = ctx.stats()
+            self.flops += st["flops"]
+            self.launches += st["launches"] + 1
+        torch.cuda.synchronize()
+
+    def run(self, stream, ev=None):
+        for n, i in enumerate(self.positions):
+            self.ctx.heff_diag(i, self.nsite, self.ds[i])
+            if ev is not None:
+                ev[n][0].record(stream)
+            self.ctx.sigma(i, self.nsite, self.xs[i], self.ys[i], nvec=self.nvec, precision=self.prec)
+            if ev is not None:
+                ev[n][1].record(stream)
+
+    def timed(self, stream, steps, warmup, flush, sampler=None):
+        """(step ms, sigma ms, clocks) over `steps` timed steps, L2 flushed before each."""
+        import torch
+        for _ in range(warmup):
+            self.run(stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        step_ms, sigma_ms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in self.positions]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            self.run(stream, ev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            sigma_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        clocks = sampler.stop() if sampler else None
+        return step_ms, sigma_ms, clocks
 
 
 def run_ours(args):
@@ -168,60 +245,21 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     device = local
     torch.cuda.set_device(device)
-    ctx, H, left, right, positions, sizes, nvec = build_workload(pkg, device)
+    nsite = 1
+    ctx, H, positions, sizes, nvec = build_workload(pkg, device, 3, nsite)
     prec = pkg.LRT_MIXED if args.precision == "mixed" else pkg.LRT_FP64
     stream = torch.cuda.current_stream(device)
-    xs = {i: torch.tensor(synth.random_vector(nvec * sizes[i], 100 + i), dtype=torch.float64,
-                          device=f"cuda:{device}") for i in positions}
-    ys = {i: torch.empty_like(xs[i]) for i in positions}
-    ds = {i: torch.empty(sizes[i], dtype=torch.float64, device=f"cuda:{device}") for i in positions}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{device}")  # 512 MB > L2
-
-    # algorithmic flops and launches of one step (plans are built on the first call)
-    flops_step, launches_step = 0.0, 0
-    for i in positions:
-        ctx.heff_diag(i, 2, ds[i])
-        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
-        st = ctx.stats()
-        flops_step += st["flops"]
-        launches_step += st["launches"] + 1
-    torch.cuda.synchronize()
-
-    def step(ev=None):
-        for n, i in enumerate(positions):
-            ctx.heff_diag(i, 2, ds[i])
-            if ev is not None:
-                ev[n][0].record(stream)
-            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
-            if ev is not None:
-                ev[n][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    S = SigmaStep(ctx, positions, sizes, nvec, nsite, device, prec)
     if world > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(device)
-    sampler.start()
-    step_ms, sigma_ms = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in positions]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        step(ev)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        sigma_ms.append(sum(a.elapsed_time(b) for a, b in ev))
-    clocks = sampler.stop()
-    ms_per_step, value = replica_throughput(sum(step_ms), args.steps, flops_step, world,
+    step_ms, sigma_ms, clocks = S.timed(stream, args.steps, args.warmup, flush, ClockSampler(device))
+    ms_per_step, value = replica_throughput(sum(step_ms), args.steps, S.flops, world,
                                             f"cuda:{device}" if world > 1 else "cpu")
-    achieved = flops_step / (sum(sigma_ms) / args.steps * 1e-3) / 1e12
+    achieved = S.flops / (sum(sigma_ms) / args.steps * 1e-3) / 1e12
 
     # end to end through the public API: pinned host inputs -> device -> sigma -> host
-    hx = {i: xs[i].cpu().pin_memory() for i in positions}
+    hx = {i: S.xs[i].cpu().pin_memory() for i in positions}
     hy = {i: torch.empty(nvec * sizes[i], dtype=torch.float64).pin_memory() for i in positions}
     h2d = sum(hx[i].numel() * 8 for i in positions)
     d2h = h2d
@@ -232,25 +270,34 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in positions:
-            xs[i].copy_(hx[i], non_blocking=True)
-            ctx.heff_diag(i, 2, ds[i])
-            ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=prec)
-            hy[i].copy_(ys[i], non_blocking=True)
+            S.xs[i].copy_(hx[i], non_blocking=True)
+            ctx.heff_diag(i, nsite, S.ds[i])
+            ctx.sigma(i, nsite, S.xs[i], S.ys[i], nvec=nvec, precision=prec)
+            hy[i].copy_(S.ys[i], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         if rep >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = world * flops_step / (statistics.mean(e2e_ms) * 1e-3) / 1e12
+    e2e_value = world * S.flops / (statistics.mean(e2e_ms) * 1e-3) / 1e12
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ctx, H, left, right, nvec, sizes)
+    mid = H.k // 2 - 1
+    # algorithmic flops of one vector at the middle position (the CPU baseline's unit)
+    xd = S.xs[mid][: sizes[mid]].clone()
+    yd = torch.empty_like(xd)
+    ctx.sigma(mid, nsite, xd, yd, nvec=1)
+    flops_vec = ctx.stats()["flops"]
+    flops_step, launches_step = S.flops, S.launches
     side = None
     if rank == 0 and world == 1 and not args.no_extras:
         try:
-            side = extras(pkg, ctx, device, xs, ys, positions, nvec, stream)
+            side = extras(pkg, ctx, device, S, stream, flush, args)
         except Exception as e:   # the side measurements never cost the metric line
             side = {"error": repr(e)}
+    del S
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mid, flops_vec)
     if rank == 0:
         if args.precision == "mixed":
             peak, peak_note = tf32_peak()
@@ -261,10 +308,13 @@ def run_ours(args):
                                  "(the tensor pipe issues it 3x)"}
             metric, dtype = "H_eff sigma TFLOP/s (algorithmic, split-TF32 mixed)", "tf32x3"
         else:
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic("fp64"),
+            peak = fp64_peak(clocks)
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic("fp64"),
                     "kernel": "gemm_fp64_kernel (sigma phases 1+2)",
-                    "peak_note": "nominal FP64 of GB300; FMA probe measured 1.20 TFLOP/s"}
+                    "peak_note": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop at the sampled maximum SM "
+                                 "clock (sm_103a has no FP64 tensor kind); an FMA probe measured "
+                                 "1.20 TFLOP/s"}
             metric, dtype = "H_eff sigma TFLOP/s (algorithmic, FP64)", "f64"
         out = {
             "metric": metric,
@@ -280,8 +330,9 @@ def run_ours(args):
             "dtype": dtype,
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.precision == "fp64" else WORKLOAD.replace("fp64", "mixed"),
-                       "k": 12, "electrons": 12, "M": 256, "nsite": 2,
-                       "nvec": nvec, "positions": len(positions), "l2": "flushed between timed steps (512 MB write)",
+                       "k": H.k, "electrons": H.n_alpha + H.n_beta, "M": 500, "nsite": nsite,
+                       "nvec": nvec, "positions": len(positions),
+                       "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -293,77 +344,99 @@ def run_ours(args):
             "extras": side,
         }
         print(json.dumps(out))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def _timed(fn, reps, stream):
+# settings of the TDA side measurements: a thick restart (3 n Ritz vectors kept, subspace
+# 48), the sweep correction, start vectors damped by their diagonal energy
+TDA_KW = dict(max_space=48, correction=1, start_shift=0.1)
+
+
+def _tda_run(pkg, device, H, bonds, sites, nr, prec, eps, max_iter):
     import torch
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = pkg.Context(device)
+    t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
+    t.tda_prepare()
+    g2, _ = t.tda_stationarity()
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        fn()
-    e1.record(stream)
+    t0 = time.perf_counter()
+    om, rs, e0 = t.sweep_tda(nr, max_iter=max_iter, eps=eps, allow_noconv=True, precision=prec,
+                             keep=3 * nr, **TDA_KW)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps
+    dt = time.perf_counter() - t0
+    sweeps = t.sweeps()
+    t.close()
+    return dt, om, rs, e0, g2, sweeps
 
 
-def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
-    """Side measurements, outside the timed steps: the mixed path on this workload, the
-    water-shaped workload where it matters most, and TDA seconds per root."""
+def _tda_converged(pkg, device, cfg_idx, schedule, eps, max_iter):
+    """Ground state on the GPU (two-site sweeps along `schedule`, then one-site sweeps to a
+    stationary point), then sweep_tda to convergence in FP64 and in the mixed form."""
+    import torch
+    cfg = synth.config(cfg_idx)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    g = pkg.Context(device)
+    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_gs = g.sweep_gs(schedule, max_sweeps=14, e_tol=1e-12, dav_tol=1e-10, onesite_sweeps=20)
+    torch.cuda.synchronize()
+    t_gs = time.perf_counter() - t0
+    bonds, sites = g.mps_get()
+    g.close()
+    r64 = _tda_run(pkg, device, H, bonds, sites, nr, pkg.LRT_FP64, eps, max_iter)
+    rmx = _tda_run(pkg, device, H, bonds, sites, nr, pkg.LRT_MIXED, eps, max_iter)
+    (s64, w64, q64, e64, g2, n64), (smx, wmx, qmx, emx, _, nmx) = r64, rmx
+    return {
+        "gs_s": t_gs, "e0": e64, "reference_gradient2": g2, "nroots": nr,
+        "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "mixed_speedup": s64 / smx,
+        "fp64_sweeps": n64, "mixed_sweeps": nmx,
+        "omega_fp64": list(w64), "omega_mixed": list(wmx), "abs_domega_Eh": list(np.abs(w64 - wmx)),
+        "resid_fp64": list(q64), "resid_mixed": list(qmx), "eps": eps,
+        "converged": bool(np.all(q64 < eps) and np.all(qmx < eps)),
+        "note": "ground state on the GPU: two-site sweeps with M = %s, then one-site sweeps "
+                "(reference_gradient2 = sum_i |Q^C (H_0^[i] - E0) C0_i|^2); TDA: sweep_tda to sum "
+                "|Q^C r|^2 < eps for every root, thick restart (3 n kept, subspace 48), sweep "
+                "correction, diagonal-damped random start; mixed: tensor-core H_0 site products "
+                "until sum |r|^2 < 1e-6, then FP64 sweeps to eps" % schedule}
+
+
+def extras(pkg, ctx, device, S, stream, flush, args):
+    """Side measurements, outside the timed steps."""
     import torch
     out = {}
-    # (1) mixed sigma on the polyene workload, error against the FP64 result
-    flops, t64, tmx, err = 0.0, 0.0, 0.0, 0.0
-    for i in positions:
-        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec)
-        y64 = ys[i].clone()
-        flops += ctx.stats()["flops"]
-        ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=pkg.LRT_MIXED)
-        err = max(err, float((ys[i] - y64).abs().max() / y64.abs().max()))
-        t64 += _timed(lambda: ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec), 3, stream)
-        tmx += _timed(lambda: ctx.sigma(i, 2, xs[i], ys[i], nvec=nvec, precision=pkg.LRT_MIXED), 3, stream)
-    out["mixed_same_workload"] = {"fp64_tflops": flops / t64 / 1e9, "mixed_tflops": flops / tmx / 1e9,
-                                  "speedup": t64 / tmx, "max_rel_err_vs_fp64": err}
-    # (2) water-shaped k=24, M=500, one-site sigma at the middle, 6 vectors
-    cfg = synth.config(3)
-    H = cfg["ham"]
-    i, nv = H.k // 2 - 1, 6
-    m = synth.mixed_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 5, center=i)
-    ren = {}
-    for name, prec in (("mixed", pkg.LRT_MIXED), ("fp64", pkg.LRT_FP64)):
-        w = pkg.Context(device)
-        w.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-        w.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, i)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for b in range(i):
-            w.renormalize(b, +1, prec)
-        for b in range(H.k - 1, i, -1):
-            w.renormalize(b, -1, prec)
-        torch.cuda.synchronize()
-        ren[name] = time.perf_counter() - t0
-        if name == "mixed":
-            w.close()
-    n, _ = w.wfn_layout(i, 1)
-    x = torch.tensor(synth.random_vector(n * nv, 77), dtype=torch.float64, device=f"cuda:{device}")
-    y = torch.empty_like(x)
-    w.sigma(i, 1, x, y, nvec=nv)
-    y64 = y.clone()
-    fl = w.stats()["flops"]
-    w.sigma(i, 1, x, y, nvec=nv, precision=pkg.LRT_MIXED)
-    err = float((y - y64).abs().max() / y64.abs().max())
-    t64 = _timed(lambda: w.sigma(i, 1, x, y, nvec=nv), 3, stream)
-    tmx = _timed(lambda: w.sigma(i, 1, x, y, nvec=nv, precision=pkg.LRT_MIXED), 5, stream)
-    out["water_k24_M500_onesite"] = {"site": i, "nvec": nv, "gflop": fl / 1e9, "fp64_ms": t64, "mixed_ms": tmx,
-                                     "environment_build_s": {"fp64": ren["fp64"], "mixed": ren["mixed"],
-                                                             "note": "all 23 renormalizations to the middle "
-                                                                     "site, wall time incl. planning"},
-                                     "fp64_tflops": fl / t64 / 1e9, "mixed_tflops": fl / tmx / 1e9,
-                                     "speedup": t64 / tmx, "max_rel_err_vs_fp64": err}
-    w.close()
+    # (1) the mixed form on the same workload: every position, 6 vectors
+    y64 = {i: S.ys[i].clone() for i in S.positions}
+    M = SigmaStep(ctx, S.positions, {i: S.ds[i].numel() for i in S.positions}, S.nvec, S.nsite, device,
+                  pkg.LRT_MIXED)
+    for i in S.positions:
+        M.xs[i].copy_(S.xs[i])
+    step_ms, sigma_ms, _ = M.timed(stream, 3, 1, flush)
+    err = max(float((M.ys[i] - y64[i]).abs().max() / y64[i].abs().max()) for i in S.positions)
+    peak, note = tf32_peak()
+    mx = M.flops / (statistics.mean(sigma_ms) * 1e-3) / 1e12
+    out["mixed_same_workload"] = {
+        "tflops": mx, "fp64_tflops_same_run": S.flops / 1e9 / statistics.mean(
+            S.timed(stream, 2, 1, flush)[1]),
+        "roofline": {"bound": "tensor", "achieved": mx, "peak": peak, "frac": mx / peak, "peak_note": note},
+        "max_rel_err_vs_fp64": err, "ms_per_step": statistics.mean(step_ms)}
+    del M
+    # (2) the PPP polyene workload (12 sites, M = 256, two-site, 6 vectors), both precisions
+    pctx, PH, ppos, psz, pnv = build_workload(pkg, device, 2, 2)
+    res = {}
+    for name, prec in (("fp64", pkg.LRT_FP64), ("mixed", pkg.LRT_MIXED)):
+        P = SigmaStep(pctx, ppos, psz, pnv, 2, device, prec)
+        st, sg, _ = P.timed(stream, 3, 1, flush)
+        res[name] = {"tflops": P.flops / (statistics.mean(sg) * 1e-3) / 1e12, "ms_per_step": statistics.mean(st)}
+        del P
+    pctx.close()
+    res["note"] = "diag + two-site sigma with 6 vectors at all 11 positions"
+    out["ppp_k12_M256_twosite"] = res
     # (3) 32 independent instances (config 4 shapes), one-site sigma with 4 vectors at the
     # middle site of each: one grouped launch per phase (sigma_batched, CUDA graph replay)
     # against the same instances called one after another
@@ -402,147 +475,17 @@ def extras(pkg, ctx, device, xs, ys, positions, nvec, stream):
     for c in bctx:
         c.close()
     out["batch32_config4_onesite"] = batch
-    # (4) TDA s/root on the 8-orbital ab initio workload, the whole path on the GPU: two-site
-    # and one-site ground-state sweeps once, then tda_prepare + sweep_tda in each precision
-    cfg = synth.config(1)
-    H = cfg["ham"]
-    nr = cfg["nroots"]
-    g = pkg.Context(device)
-    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
-    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
-    e_gs = g.sweep_gs([32, cfg["M"]], max_sweeps=8, onesite_sweeps=4)
-    bonds, sites = g.mps_get()
-    g.close()
-    res = {}
-    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
-        t = pkg.Context(device)
-        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-        t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
-        t.tda_prepare()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        om, rs, e0 = t.sweep_tda(nr, max_iter=60, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
-                                 refine_tol=1e-4)
-        torch.cuda.synchronize()
-        res[prec] = (time.perf_counter() - t0, om, rs, e0)
-        t.close()
-    (s64, w64, r64, e64), (smx, wmx, rmx, emx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
-    out["tda_abinitio_k8_M64_4roots"] = {
-        "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr, "e0": e64,
-        "omega_fp64": list(w64), "omega_mixed": list(wmx),
-        "abs_domega_Eh": list(np.abs(w64 - wmx)),
-        "resid_fp64": list(r64), "resid_mixed": list(rmx), "eps": 1e-8,
-        "note": "wall time of sweep_tda (60 sweeps at most, diagonal start, subspace 32; mixed: "
-                "tensor-core site products until sum |r|^2 < 1e-4, then FP64) / roots; reference: "
-                "two-site + 4 one-site sweep_gs sweeps and tda_prepare on the GPU; resid = sum of "
-                "the site residuals^2 per root (roots with resid near 1e-4 stall there); the TDA "
-                "loop is host-bound at this size"}
-    # (5) TDA on this workload (PPP k=12, M=256, 6 roots): ground state on the GPU (two-site
-    # sweeps up to M, four one-site sweeps), then 30 TDA sweeps in each precision
-    cfg = synth.config(2)
-    H = cfg["ham"]
-    nr = cfg["nroots"]
-    g = pkg.Context(device)
-    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
-    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e_gs = g.sweep_gs([64, 128, cfg["M"]], max_sweeps=12, onesite_sweeps=4)
-    torch.cuda.synchronize()
-    t_gs = time.perf_counter() - t0
-    bonds, sites = g.mps_get()
-    g.close()
-    res = {}
-    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
-        t = pkg.Context(device)
-        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-        t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
-        t.tda_prepare()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        om, rs, e0 = t.sweep_tda(nr, max_iter=30, eps=1e-8, seed=0, allow_noconv=True, precision=prec,
-                                 refine_tol=1e-5)
-        torch.cuda.synchronize()
-        res[prec] = (time.perf_counter() - t0, om, rs)
-        t.close()
-    (s64, w64, r64), (smx, wmx, rmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
-    out["tda_ppp_k12_M256_6roots"] = {
-        "gs_s": t_gs, "e0": e_gs, "fp64_s_per_root": s64 / nr, "mixed_s_per_root": smx / nr,
-        "omega_fp64": list(w64), "omega_mixed": list(wmx), "abs_domega_Eh": list(np.abs(w64 - wmx)),
-        "resid_fp64": list(r64), "resid_mixed": list(rmx), "eps": 1e-8,
-        "note": "ground state: two-site sweeps with M = 64, 128, 256 and four one-site sweeps on the "
-                "GPU; TDA: 30 sweeps at most, diagonal start; mixed: tensor-core H_0 site products "
-                "until sum |r|^2 < 1e-5, then FP64; resid = sum of the site residuals^2 per root"}
-    # (6) batched TDA on 8 instances of the config-4 shapes (4 roots each, two sweeps from a
-    # prepared random reference): one instance after another against sweep_tda_batched
-    # (host threads, one stream per context)
-    def tda_instances(streams):
-        cs = []
-        for b in range(8):
-            cfg = synth.config(4, batch_index=b)
-            H = cfg["ham"]
-            m = synth.random_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 700 + b, "right")
-            c = pkg.Context(device, stream=streams[b].cuda_stream if streams else None)
-            c.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-            c.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
-            c.tda_prepare()
-            cs.append(c)
-        torch.cuda.synchronize()
-        return cs
-    cs = tda_instances(None)
-    t0 = time.perf_counter()
-    seq = [c.sweep_tda(4, max_iter=1, eps=1e-12, seed=0, allow_noconv=True) for c in cs]
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    for c in cs:
-        c.close()
-    streams = [torch.cuda.Stream(device=device) for _ in range(8)]
-    cs = tda_instances(streams)
-    t0 = time.perf_counter()
-    wb, rb, eb = pkg.sweep_tda_batched(cs, 4, max_iter=1, eps=1e-12, seed=0, allow_noconv=True)
-    torch.cuda.synchronize()
-    t_bat = time.perf_counter() - t0
-    for c in cs:
-        c.close()
-    out["tda_batched_config4_8inst_4roots_2sweeps"] = {
-        "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
-        "max_abs_domega_Eh": float(max(np.abs(np.asarray(seq[j][0]) - wb[j]).max() for j in range(8))),
-        "host_threads": os.cpu_count(),
-        "note": "8 instances with the config-4 shapes, each a right-canonical random MPS at its M "
-                "prepared by tda_prepare; two sweeps (the first with m = 0) of 4 roots, FP64"}
-    # (7) TDA sweep cost on the water-shaped k=24, M=500 workload, 6 roots: two sweeps in
-    # each precision from the same reference (a right-canonical random MPS at the full bond
-    # dimension brought to the mixed-canonical gauge by tda_prepare)
-    cfg = synth.config(3)
-    H = cfg["ham"]
-    nr = cfg["nroots"]
-    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 11, "right")
-    res = {}
-    for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
-        t = pkg.Context(device)
-        t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
-        t.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
-        t.tda_prepare()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        om, rs, e0 = t.sweep_tda(nr, max_iter=1, eps=1e-12, seed=0, allow_noconv=True, precision=prec)
-        torch.cuda.synchronize()
-        res[prec] = (time.perf_counter() - t0, om)
-        t.close()
-    (s64, w64), (smx, wmx) = res[pkg.LRT_FP64], res[pkg.LRT_MIXED]
-    out["tda_water_k24_M500_6roots_2sweeps"] = {
-        "fp64_s_per_root_per_sweep": s64 / nr / 2, "mixed_s_per_root_per_sweep": smx / nr / 2,
-        "speedup": s64 / smx, "max_abs_domega_Eh": float(np.max(np.abs(np.asarray(w64) - np.asarray(wmx)))),
-        "note": "wall time of two sweep_tda sweeps (the first with m = 0) / roots / 2; mixed: both "
-                "sweeps with tensor-core H_0 site products (the first-order products are FP64 in "
-                "both); the reference is not a ground state, so the roots are not converged and "
-                "serve only as a cross-check of the two precisions after the same two sweeps"}
+    # (4) TDA s/root at convergence, FP64 against the mixed form: the 8-orbital ab initio
+    # workload (M = 64, 4 roots) and the PPP polyene (M = 256, 6 roots)
+    out["tda_abinitio_k8_M64_4roots"] = _tda_converged(pkg, device, 1, [32, 64], 1e-9, 200)
+    if not args.quick_tda:
+        out["tda_ppp_k12_M256_6roots"] = _tda_converged(pkg, device, 2, [64, 128, 256], 1e-9, 200)
+    if args.tda_water:
+        out["tda_water_k24_M500_6roots"] = _tda_converged(pkg, device, 3, [128, 256, 500], 1e-8, 200)
     return out
 
 
-def _oracle_setup(H, left, right, i):
+def _oracle_setup(H, left, right, i, nsite):
     from oracle import blocks as ob
     from oracle import fock
     from oracle import mps as om
@@ -553,36 +496,91 @@ def _oracle_setup(H, left, right, i):
     R = [om.unpack_site(right.sites[j], right.bonds[j], right.bonds[j + 1]) for j in range(k)]
     for b in range(i):
         env.grow_left(b, L[b])
-    for b in range(k - 1, i + 1, -1):
+    for b in range(k - 1, i + nsite - 1, -1):
         env.grow_right(b, R[b])
-    Xe, Ye = env.left_enlarged(i), env.right_enlarged(i + 1)
-    return env, Xe, Ye
+    return env
 
 
-def cpu_baseline(ctx, H, left, right, nvec, sizes):
-    """Oracle two-site sigma at the middle position, one vector at a time, on the host cores."""
-    import torch
+_CHILD = {}
+
+
+def _child_sigma(seed):
     from oracle import blocks as ob
     from oracle import mps as om
-    i = 5
-    env, Xe, Ye = _oracle_setup(H, left, right, i)
-    x = synth.random_vector(sizes[i], 7)
-    xd = torch.tensor(x, dtype=torch.float64, device=f"cuda:{ctx.device}")
-    yd = torch.empty_like(xd)
-    ctx.sigma(i, 2, xd, yd, nvec=1)
-    flops = ctx.stats()["flops"]
-    w = om.unpack_twosite(x, left.bonds[i], left.bonds[i + 2])
+    c = _CHILD
+    w = om.unpack_site(synth.random_vector(c["n"], seed), c["lb"], c["rb"])
+    ob.sigma_onesite(c["env"], c["i"], w)
+    return seed
+
+
+def cpu_baseline_child(spec):
+    """Runs in a fresh process that never touches the GPU: the oracle's one-site sigma at the
+    middle position of the workload, one vector per call, single-threaded and then with one
+    forked worker per host core (the workers share the environment copy-on-write)."""
+    import multiprocessing as mp
+    from oracle import blocks as ob
+    from oracle import mps as om
+    cfg = synth.config(3)
+    H = cfg["ham"]
+    k, na, nb, M = H.k, H.n_alpha, H.n_beta, cfg["M"]
+    left = synth.random_mps(k, na, nb, M, 2024, "left")
+    right = synth.random_mps(k, na, nb, M, 2025, "right")
+    i = spec["site"]
+    t0 = time.perf_counter()
+    env = _oracle_setup(H, left, right, i, 1)
+    t_env = time.perf_counter() - t0
+    n = synth.layout_size(synth.site_layout(left.bonds[i], left.bonds[i + 1]))
+    _CHILD.update(env=env, i=i, n=n, lb=left.bonds[i], rb=left.bonds[i + 1])
+    w = om.unpack_site(synth.random_vector(n, 7), left.bonds[i], left.bonds[i + 1])
     reps, t0 = 0, time.perf_counter()
     while True:
-        ob.sigma_twosite(env, i, w, Xe, Ye)
+        ob.sigma_onesite(env, i, w)
         reps += 1
-        if time.perf_counter() - t0 > 10.0 or reps >= 20:
+        if time.perf_counter() - t0 > spec["budget_s"] or reps >= 3:
             break
-    dt = (time.perf_counter() - t0) / reps
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle two-site sigma at the middle position (i=5), 1 of {nvec} vectors, "
-                      f"{reps} repetitions, environment built outside the timing; FLOPs = the same "
-                      f"algorithmic count as the GPU line"}
+    dt1 = (time.perf_counter() - t0) / reps
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("fork")
+    with ctx.Pool(cores) as pool:
+        pool.map(_child_sigma, range(cores))           # warm the workers
+        t0 = time.perf_counter()
+        pool.map(_child_sigma, range(100, 100 + 2 * cores))
+        dtp = time.perf_counter() - t0
+    print(json.dumps({"env_s": t_env, "single_s": dt1, "single_reps": reps, "cores": cores,
+                      "parallel_calls": 2 * cores, "parallel_s": dtp}))
+
+
+def _host_cpu():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_baseline(site, flops_vec, budget_s=10.0):
+    """The oracle timed on the host cores, in a child process (this one has used the GPU)."""
+    spec = json.dumps({"site": site, "budget_s": budget_s})
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", spec],
+                           capture_output=True, text=True, timeout=900, cwd=ROOT)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"value": None, "unit": "TFLOP/s", "cores": None, "kind": "oracle", "error": repr(e)}
+    single = flops_vec / d["single_s"] / 1e12
+    allc = d["parallel_calls"] * flops_vec / d["parallel_s"] / 1e12
+    return {"value": allc, "unit": "TFLOP/s", "cores": d["cores"], "kind": "oracle",
+            "single_thread": {"value": single, "cores": 1, "reps": d["single_reps"]},
+            "host_cores": os.cpu_count(), "host_cpu": _host_cpu(),
+            "environment_build_s": d["env_s"],
+            "sample": f"oracle one-site sigma at the middle position (i={site}) of the workload, one vector "
+                      f"per call (the GPU step does 6 vectors at 24 positions): single-threaded "
+                      f"{d['single_reps']} calls; all cores: {d['parallel_calls']} calls on {d['cores']} "
+                      f"forked workers sharing the environment; environment built outside the timing; "
+                      f"FLOPs = the GPU line's algorithmic count for the same call"}
 
 
 def run_reference(args):
@@ -591,22 +589,22 @@ def run_reference(args):
         return
     from oracle import blocks as ob
     from oracle import mps as om
-    cfg = synth.config(2)
+    cfg = synth.config(3)
     H = cfg["ham"]
     k, na, nb, M, nvec = H.k, H.n_alpha, H.n_beta, cfg["M"], cfg["nroots"]
     left = synth.random_mps(k, na, nb, M, 2024, "left")
     right = synth.random_mps(k, na, nb, M, 2025, "right")
-    i = 5
-    env, Xe, Ye = _oracle_setup(H, left, right, i)
-    lay = synth.twosite_layout(left.bonds[i], left.bonds[i + 2])
-    x = synth.random_vector(synth.twosite_size(lay), 7)
-    w = om.unpack_twosite(x, left.bonds[i], left.bonds[i + 2])
+    i = k // 2 - 1
+    env = _oracle_setup(H, left, right, i, 1)
+    lay = synth.site_layout(left.bonds[i], left.bonds[i + 1])
+    x = synth.random_vector(synth.layout_size(lay), 7)
+    w = om.unpack_site(x, left.bonds[i], left.bonds[i + 1])
     for _ in range(args.warmup):
-        ob.sigma_twosite(env, i, w, Xe, Ye)
+        ob.sigma_onesite(env, i, w)
     ob.FLOP_COUNTER[0] = 0.0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ob.sigma_twosite(env, i, w, Xe, Ye)
+        ob.sigma_onesite(env, i, w)
     dt = time.perf_counter() - t0
     flops = ob.FLOP_COUNTER[0]
     value = flops / dt / 1e12
@@ -614,15 +612,19 @@ def run_reference(args):
            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "k": 12, "electrons": 12, "M": 256, "nsite": 2, "nvec": nvec},
+           "config": {"workload": WORKLOAD, "k": k, "electrons": na + nb, "M": M, "nsite": 1, "nvec": nvec},
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                            "sample": "one step = oracle two-site sigma at the middle position for 1 vector; "
-                                      "FLOPs counted from the oracle's own block products"},
+                            "sample": f"one step = oracle one-site sigma at the middle position (i={i}) for "
+                                      "1 vector, single thread; FLOPs counted from the oracle's own block "
+                                      "products; environment built before the timed steps"},
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
 if __name__ == "__main__":
+    if len(sys.argv) > 2 and sys.argv[1] == "--oracle-child":
+        cpu_baseline_child(json.loads(sys.argv[2]))
+        sys.exit(0)
     a = parse()
     if a.impl == "reference":
         run_reference(a)

@@ -158,7 +158,12 @@ int sweep_gs(lrt_t ctx, const lrt_gs_params* params, double* e0);
  * residual (Eq. rnorm), diagonal preconditioner (Eq. error), projection (Eq. param),
  * reduced matrices (Eqs. hleft2, sleft2) and first-order renormalization (Eqs. lopr1st,
  * ropr1st).  Outputs omega[nroots] = theta - E0 (excitation energies, ascending),
- * resid[nroots] = sum_i |r_i|^2 of the last sweep and *e0 = <Psi0|H|Psi0>.
+ * resid[nroots] = sum_i |Q^C r_i|^2 of the last sweep and *e0 = <Psi0|H|Psi0>.  The
+ * site residual is projected by Q^C = 1 - C0 C0^T before its norm and the
+ * preconditioner: at a stationary reference its C0 component <Psi0|H|Psi_mu> vanishes
+ * (Eq. rnorm assumes that); elsewhere the projected sum is the residual of the
+ * Rayleigh-Ritz problem on the tangent space minus Psi0, which tends to zero at
+ * convergence while the unprojected one keeps that component.
  * Returns LRT_ENOCONV (results written) when max_iter is reached first. */
 typedef struct {
   int max_space;      /* N, maximum number of trial vectors (0: min(48, max(8 nroots, 24))); <= 48 */
@@ -176,7 +181,23 @@ typedef struct {
                          products dH C0 are FP64 in both (their operator sets are new every
                          sweep) */
   double refine_tol;  /* LRT_MIXED: switch to FP64 below this sum |r|^2 (<= 0: 1e-6) */
+  int keep;           /* Ritz vectors kept when the subspace restarts (0: nroots, the deflation
+                         of Fig. alg:dmrgtda); at most max_space - nroots */
+  int correction;     /* LRT_CORR_SITE (0): the correction of site i is the preconditioned
+                         residual of Eq. error alone.  LRT_CORR_SWEEP (1): for a root whose last
+                         sum |r|^2 is below corr_tol it also takes the coupling to the
+                         corrections already formed at sites < i of the same forward sweep,
+                         [H_z^{L_{i-1}} x h_i x H_0^{R_i}] C0_i with the first-order left blocks
+                         of the new vector z (a forward Gauss-Seidel pass over the site blocks
+                         of the tangent space, whose off-diagonal overlaps vanish, Eq. sleft2);
+                         far from convergence that recursion can grow along the sweep, hence
+                         the gate.  The roots it converges to are the same */
+  double corr_tol;    /* LRT_CORR_SWEEP gate (<= 0: 1.0) */
+  double start_shift; /* > 0: the random start vectors are damped elementwise by
+                         1 / (|diag(H_0^[i]) - E0| + start_shift), which weights the
+                         low-lying single-site configurations (0: plain Gaussians) */
 } lrt_tda_params;
+enum { LRT_CORR_SITE = 0, LRT_CORR_SWEEP = 1 };
 int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);
 /* tda_prepare: the mixed-canonical gauge on the GPU instead of tda_load.  Takes the
  * loaded MPS with sites 1..k-1 right-orthonormal and the centre on site 0 (the state
@@ -187,7 +208,16 @@ int tda_load(lrt_t ctx, const double* const* C0, const double* const* lam);
  * Bond dimensions do not change; a sector with fewer fused rows than states gets
  * zero Schmidt values (dropped by pinv_cut in sweep_tda). */
 int tda_prepare(lrt_t ctx, double* norm);
+/* tda_stationarity: how far the loaded reference is from a stationary point of the
+ * one-site MPS manifold (Eq. dmrg at every site): *grad2 = sum_i |Q^C (H_0^[i] - E0) C0_i|^2
+ * with E0 = <Psi0|H|Psi0>, the squared norm of the site components of <T|H|Psi0> (zero at
+ * a one-site DMRG fixed point, the reference the TDA assumes).  Needs tda_load or
+ * tda_prepare first; builds the zeroth-order environments as sweep_tda does. */
+int tda_stationarity(lrt_t ctx, double* grad2, double* e0);
 int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0);
+/* lrt_sweeps: *sweeps = the number of sweeps the last sweep_gs (two-site sweeps) or
+ * sweep_tda (Davidson iterations after the start sweep) on this context ran. */
+int lrt_sweeps(lrt_t ctx, int* sweeps);
 /* sweep_tda_batched: the DMRG-TDA sweeps of Fig. alg:dmrgtda for n_inst independent
  * instances, each its own context (its own Hamiltonian and reference, prepared by
  * tda_load or tda_prepare), run concurrently: host threads (at most the host's hardware
@@ -241,7 +271,11 @@ int sigma_stats(lrt_t ctx, lrt_sigma_stats* out);
  * the library.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  The
  *    intermediates live in one static device array of LRT_NOALLOC_SCRATCH_DOUBLES
- *    doubles (32 MiB) that every GPU loading the library holds until process exit.
+ *    doubles (32 MiB) per device, held until process exit.  The driver reserves it
+ *    on a device when the library's module is first loaded there (CUDA loads modules
+ *    lazily by default), which can be the first sigma_noalloc call on that device:
+ *    make that first call during set-up, where the reservation is acceptable; later
+ *    calls take no device memory.
  *  - Reuses the plan that a regular sigma() call with the same (site, nsite, nvec)
  *    prepared after the last renormalize(); without one it returns LRT_ESTATE.
  *    A plan whose intermediates exceed the static array is rejected with LRT_EINVAL

@@ -17,10 +17,12 @@ LIB_PATH = os.path.join(HERE, "liblrt.so")
 
 LRT_FP64 = 0
 LRT_MIXED = 1
+LRT_CORR_SITE = 0
+LRT_CORR_SWEEP = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "sweep_tda", "sigma_batched",
+           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "lrt_sweeps", "sigma_batched",
            "sweep_tda_batched"]
 
 _lib = None
@@ -51,7 +53,8 @@ class GsParams(ctypes.Structure):
 class TdaParams(ctypes.Structure):
     _fields_ = [("max_space", ctypes.c_int), ("max_iter", ctypes.c_int), ("eps", ctypes.c_double),
                 ("pinv_cut", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("keep", ctypes.c_int), ("correction", ctypes.c_int),
+                ("corr_tol", ctypes.c_double), ("start_shift", ctypes.c_double)]
 
 
 class LrtError(RuntimeError):
@@ -89,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     ppd = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
     lib.tda_load.argtypes = [vp, ppd, ppd]
     lib.tda_prepare.argtypes = [vp, dp]
+    lib.tda_stationarity.argtypes = [vp, dp, dp]
+    lib.lrt_sweeps.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
@@ -272,16 +277,31 @@ class Context:
         self._check(self.lib.tda_prepare(self.h, ctypes.byref(nrm)), "tda_prepare")
         return nrm.value
 
+    def sweeps(self) -> int:
+        """Sweeps run by the last sweep_gs or sweep_tda on this context."""
+        n = ctypes.c_int()
+        self._check(self.lib.lrt_sweeps(self.h, ctypes.byref(n)), "lrt_sweeps")
+        return n.value
+
+    def tda_stationarity(self):
+        """(sum_i |Q^C (H_0^[i] - E0) C0_i|^2, E0) of the loaded reference."""
+        g = ctypes.c_double()
+        e = ctypes.c_double()
+        self._check(self.lib.tda_stationarity(self.h, ctypes.byref(g), ctypes.byref(e)), "tda_stationarity")
+        return g.value, e.value
+
     def sweep_tda(self, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
                   pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
-                  precision: int = LRT_FP64, refine_tol: float = 0.0):
+                  precision: int = LRT_FP64, refine_tol: float = 0.0, keep: int = 0, correction: int = 0,
+                  corr_tol: float = 0.0, start_shift: float = 0.0):
         """DMRG-TDA roots: returns (omega, resid, e0); omega are excitation energies.  With
         precision=LRT_MIXED the H_0 site products run on the tensor cores until the residuals
         fall below refine_tol, then the sweeps finish in FP64."""
         om = np.zeros(nroots)
         rs = np.zeros(nroots)
         e0 = ctypes.c_double()
-        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol)
+        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol, keep, correction,
+                      corr_tol, start_shift)
         rc = self.lib.sweep_tda(self.h, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), ctypes.byref(e0))
         if rc != 0 and not (allow_noconv and rc == -4):
             self._check(rc, "sweep_tda")
@@ -339,7 +359,8 @@ def sigma_batched(ctxs: list, sites: list, nsite: int, xs: list, ys: list, nvec:
 
 def sweep_tda_batched(ctxs: list, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
                       pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
-                      precision: int = LRT_FP64, refine_tol: float = 0.0):
+                      precision: int = LRT_FP64, refine_tol: float = 0.0, keep: int = 0, correction: int = 0,
+                      corr_tol: float = 0.0, start_shift: float = 0.0):
     """DMRG-TDA of several independent instances (one prepared Context each), run
     concurrently; returns (omega, resid, e0) with omega and resid of shape (n, nroots)."""
     n = len(ctxs)
@@ -349,7 +370,8 @@ def sweep_tda_batched(ctxs: list, nroots: int, max_space: int = 0, max_iter: int
     rs = np.zeros(n * nroots)
     e0 = np.zeros(n)
     hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
-    p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol)
+    p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol, keep, correction,
+                  corr_tol, start_shift)
     lib = ctxs[0].lib
     rc = lib.sweep_tda_batched(hs, n, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), _dptr(e0))
     if rc != 0 and not (allow_noconv and rc == -4):

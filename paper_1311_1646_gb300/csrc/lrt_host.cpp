@@ -677,6 +677,16 @@ struct DevBuf {
     o.p = nullptr;
     o.n = 0;
   }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      if (p) dev_free(p);
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
   ~DevBuf() {
     if (p) dev_free(p);
   }
@@ -3258,34 +3268,108 @@ static double sweep_onesite_impl(lrt_ctx* c, const lrt_gs_params& P, int nsweeps
   return E;
 }
 
+// ---------------------------------------------------------------------------
+// batched site algebra of the TDA sweeps
+// ---------------------------------------------------------------------------
+// nv site tensors of one site's layout, contiguous (stride = the layout's size); capacity
+// rounded up to whole blocks of `block` vectors, so multi-vector sigma calls can run on
+// whole blocks (the padding vectors are zero)
+struct SiteBatch {
+  int nv = 0;
+  int64_t stride = 0;
+  DevBuf buf;
+  double* v(int j) const { return buf.p + (int64_t)j * stride; }
+};
+
+static void batch_alloc(lrt_ctx* c, SiteBatch& B, int64_t stride, int nv, int block) {
+  B.nv = nv;
+  B.stride = std::max<int64_t>(stride, 1);
+  const int cap = std::max(1, (nv + block - 1) / block * block);
+  B.buf.ensure((size_t)cap * B.stride);
+  CK(cudaMemsetAsync(B.buf.p, 0, (size_t)cap * B.stride * sizeof(double), c->st));
+}
+
+// nv dense bond matrices of one bond's layout (one D x D block per sector), contiguous
+struct BondBatch {
+  std::vector<int64_t> off;
+  int64_t stride = 0;
+  int nv = 0;
+  DevBuf buf;
+};
+
+static void bond_batch(lrt_ctx* c, int b, BondBatch& B, int nv) {
+  const Sectors& S = c->bonds[b];
+  B.off.assign(S.n(), 0);
+  int64_t t = 0;
+  for (int q = 0; q < S.n(); ++q) {
+    B.off[q] = t;
+    t += (int64_t)S.d[q] * S.d[q];
+  }
+  B.stride = std::max<int64_t>(t, 1);
+  B.nv = nv;
+  B.buf.ensure((size_t)std::max(nv, 1) * B.stride);
+  CK(cudaMemsetAsync(B.buf.p, 0, (size_t)std::max(nv, 1) * B.stride * sizeof(double), c->st));
+}
+
+// nv first-order operator sets of one bond (both directions), one layout each
+struct SetBatch {
+  std::unique_ptr<OpSet> fp, rp;   // layouts (no data)
+  uint64_t sig = 0;                // set_signature(fp, rp)
+  int64_t fs = 0, rs = 0;          // strides
+  int nv = 0;
+  DevBuf f, r;
+  bool empty() const { return !fp; }
+  double* fv(int j) const { return f.p + (int64_t)j * fs; }
+  double* rv(int j) const { return r.p + (int64_t)j * rs; }
+};
+
+static void set_batch(lrt_ctx* c, SetBatch& B, const OpSet& f, const OpSet& r, int nv) {
+  B.fp = layout_copy(f);
+  B.rp = layout_copy(r);
+  B.sig = set_signature(*B.fp, B.rp.get());
+  B.fs = std::max<int64_t>(f.total, 1);
+  B.rs = std::max<int64_t>(r.total, 1);
+  B.nv = nv;
+  B.f.ensure((size_t)std::max(nv, 1) * B.fs);
+  B.r.ensure((size_t)std::max(nv, 1) * B.rs);
+  CK(cudaMemsetAsync(B.f.p, 0, (size_t)std::max(nv, 1) * B.fs * sizeof(double), c->st));
+  CK(cudaMemsetAsync(B.r.p, 0, (size_t)std::max(nv, 1) * B.rs * sizeof(double), c->st));
+}
+
+// a site tensor that borrows its data (a slot of a batch) and never frees it
+struct SiteView {
+  SiteTensor t;
+  SiteView(const SiteTensor& lay, double* p) {
+    t.blk_off = lay.blk_off;
+    t.blk_rows = lay.blk_rows;
+    t.sub_off = lay.sub_off;
+    t.sub_qr = lay.sub_qr;
+    t.total = lay.total;
+    t.d = p;
+  }
+  ~SiteView() { t.d = nullptr; }
+};
+
 struct TdaRunner {
   lrt_ctx* c;
   int k;
   const lrt_tda_params& P;
   std::vector<BondMat> lam, ilam;
   std::vector<DevBuf> diag;
-  std::vector<std::unique_ptr<SigmaPlan>> h0plan;
+  std::vector<SiteTensor> lay;       // layout of every site (no data)
+  std::vector<std::unique_ptr<SigmaPlan>> h0one;   // H_0^[i] plans for one vector
+  std::map<std::pair<int, int>, std::unique_ptr<SigmaPlan>> h0blk;   // (site, block) plans
   DevBuf tmp;
   double E0 = 0.0;
   bool mixed = false;   // site products on the tensor cores (until the FP64 refinement)
+  int blk = 1;          // vectors per multi-vector H_0 call (the number of roots)
 
   TdaRunner(lrt_ctx* cc, const lrt_tda_params& p) : c(cc), k(cc->k), P(p), mixed(p.precision == LRT_MIXED) {}
-
-  // y = (plan) x for one vector, in the current precision
-  void apply(SigmaPlan& p, const double* x, double* y) {
-    if (mixed) {
-      run_tc(c, p, x, y, 1);
-    } else {
-      p.p1.run(c->st, x, y, p.tbuf, &p.ex);
-      p.p2.run(c->st, x, y, p.tbuf, &p.ex);
-      CK(cudaGetLastError());
-      CK(cudaStreamSynchronize(c->st));
-    }
-  }
 
   const SiteTensor& L0(int i) { return c->sites[i]; }
   const SiteTensor& R0(int i) { return c->sites_r[i]; }
   const SiteTensor& C0(int i) { return c->tda->C0[i]; }
+  int64_t T(int i) const { return lay[i].total; }
 
   void setup() {
     lam.resize(k + 1);
@@ -3298,29 +3382,183 @@ struct TdaRunner {
       enlarged(c, i, false);
       if (i > 0) enlarged(c, i, true);
     }
-    h0plan.resize(k);
+    lay.resize(k);
+    h0one.resize(k);
     diag.resize(k);
     for (int i = 0; i < k; ++i) {
-      h0plan[i] = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, 1, mixed);
-      diag[i].ensure(std::max<int64_t>(h0plan[i]->nelem, 1));
-      launch_diag(h0plan[i]->douts.p, h0plan[i]->dterms.p, h0plan[i]->ndiag, diag[i].p, c->st);
+      site_layout(lay[i], c->bonds[i], c->bonds[i + 1]);
+      h0one[i] = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, 1, false);
+      diag[i].ensure(std::max<int64_t>(h0one[i]->nelem, 1));
+      launch_diag(h0one[i]->douts.p, h0one[i]->dterms.p, h0one[i]->ndiag, diag[i].p, c->st);
     }
     SiteTensor y = new_site(c, 0);
-    const bool m = mixed;
-    mixed = false;            // the reference energy is FP64
-    h0(0, C0(0), y);
-    mixed = m;
+    run_plan(*h0one[0], C0(0).d, y.d, 1, false);    // the reference energy is FP64
     E0 = t_dot(c, C0(0), y, tmp);
   }
 
-  // y = H_0^[i] C  (Eq. hzero_sb)
-  void h0(int i, const SiteTensor& C, SiteTensor& y) {
-    apply(*h0plan[i], C.d, y.d);
+  void run_plan(SigmaPlan& p, const double* x, double* y, int nvec, bool tc) {
+    if (tc) {
+      run_tc(c, p, x, y, nvec);
+    } else {
+      p.p1.run(c->st, x, y, p.tbuf, &p.ex);
+      p.p2.run(c->st, x, y, p.tbuf, &p.ex);
+      CK(cudaGetLastError());
+    }
   }
 
-  // y = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i  (Eq. hleft_sb on C0)
-  // the first-order left sets of one vector enlarged by site i (both directions), shared
-  // by the site product below and the first-order renormalization of grow_HL
+  // Y = H_0^[i] X for the first nv vectors of a batch (Eq. hzero_sb), as multi-vector sigma
+  // calls on whole blocks of `blk` vectors (the block-Davidson right-hand sides)
+  void h0(int i, const SiteBatch& X, int nv, SiteBatch& Y) {
+    auto& p = h0blk[{i, blk}];
+    if (!p) p = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, blk, mixed);
+    if (mixed && !p->has_tc) p = plan_sigma_sets(c, *c->XL[i], nullptr, *c->R[i + 1], nullptr, i, 1, blk, true);
+    for (int v0 = 0; v0 < nv; v0 += blk) run_plan(*p, X.v(v0), Y.v(v0), blk, mixed);
+  }
+
+  // ---- batched bond/site products: grouped GEMMs planned once per (kind, site, nv) with
+  // every per-vector address relative to extra bases 0 (batched A), 1 (batched B) and 2
+  // (output), replayed for new batches ----
+  enum { K_LC, K_RMUL, K_RMULB, K_RC, K_LMUL, K_LMULB };
+  std::map<std::tuple<int, int, int, int, int, const void*>, std::unique_ptr<GemmPlan>> bops;
+  GemmPlan& bop(int kind, int i, int nv, bool acc, double scale, const void* fixed, int64_t sa, int64_t sb,
+                int64_t so, const std::vector<int64_t>* boff) {
+    const int sgn = scale < 0 ? -1 : 1;
+    auto& p = bops[std::make_tuple(kind, i, nv, acc ? 1 : 0, sgn, fixed)];
+    if (p) return *p;
+    std::vector<GemmOut> o;
+    std::vector<GemmSeg> g;
+    const SiteTensor& L = lay[i];
+    const int A0 = 3, B1 = 4, O2 = 5;
+    for (int v = 0; v < nv; ++v) {
+      if (kind == K_LC || kind == K_RMUL || kind == K_RMULB) {
+        // per right sector q of bond i+1
+        const Sectors& R = c->bonds[i + 1];
+        for (int q = 0; q < R.n(); ++q) {
+          if (L.blk_off[q] < 0) continue;
+          const int D = R.d[q], rows = L.blk_rows[q];
+          const int64_t bo = L.blk_off[q];
+          if (kind == K_LC) {            // out_v = A^T B_v   (A fixed, B batched)
+            const SiteTensor& A = *(const SiteTensor*)fixed;
+            o.push_back(GemmOut{nullptr, (*boff)[q] + v * so, D, D, D, (int)g.size(), 1, acc ? 1 : 0, O2, 0});
+            g.push_back(GemmSeg{A.d + bo, nullptr, 0, bo + v * sb, D, D, rows, 1, 0, 0, B1, scale});
+          } else if (kind == K_RMUL) {   // out_v = A_v X     (X fixed bond matrices)
+            const BondMat& X = *(const BondMat*)fixed;
+            o.push_back(GemmOut{nullptr, bo + v * so, D, rows, D, (int)g.size(), 1, acc ? 1 : 0, O2, 0});
+            g.push_back(GemmSeg{nullptr, X.buf.p + X.off[q], bo + v * sa, 0, D, D, D, 0, 0, A0, 0, scale});
+          } else {                       // out_v = A X_v     (A fixed, X batched)
+            const SiteTensor& A = *(const SiteTensor*)fixed;
+            o.push_back(GemmOut{nullptr, bo + v * so, D, rows, D, (int)g.size(), 1, acc ? 1 : 0, O2, 0});
+            g.push_back(GemmSeg{A.d + bo, nullptr, 0, (*boff)[q] + v * sb, D, D, D, 0, 0, 0, B1, scale});
+          }
+        }
+      } else if (kind == K_RC) {         // out_v,ql = sum_n A_v(ql,n) B(ql,n)^T  (B fixed)
+        const SiteTensor& Bf = *(const SiteTensor*)fixed;
+        const Sectors& Lb = c->bonds[i];
+        for (int q = 0; q < Lb.n(); ++q) {
+          const int D = Lb.d[q];
+          GemmOut x{nullptr, (*boff)[q] + v * so, D, D, D, (int)g.size(), 0, acc ? 1 : 0, O2, 0};
+          for (int n = 0; n < 4; ++n) {
+            if (L.sub_off[q][n] < 0) continue;
+            const int Dr = c->bonds[i + 1].d[L.sub_qr[q][n]];
+            g.push_back(GemmSeg{nullptr, Bf.d + L.sub_off[q][n], L.sub_off[q][n] + v * sa, 0, Dr, Dr, Dr, 0, 1, A0,
+                                0, scale});
+            ++x.seg_count;
+          }
+          if (x.seg_count) o.push_back(x);
+        }
+      } else {                           // per (ql, n) sub-block
+        const Sectors& Lb = c->bonds[i];
+        for (int q = 0; q < Lb.n(); ++q)
+          for (int n = 0; n < 4; ++n) {
+            if (L.sub_off[q][n] < 0) continue;
+            const int D = Lb.d[q];
+            const int Dr = c->bonds[i + 1].d[L.sub_qr[q][n]];
+            const int64_t so_ = L.sub_off[q][n];
+            o.push_back(GemmOut{nullptr, so_ + v * so, Dr, D, Dr, (int)g.size(), 1, acc ? 1 : 0, O2, 0});
+            if (kind == K_LMUL) {        // out_v = X A_v   (X fixed bond matrices)
+              const BondMat& X = *(const BondMat*)fixed;
+              g.push_back(GemmSeg{X.buf.p + X.off[q], nullptr, 0, so_ + v * sb, D, Dr, D, 0, 0, 0, B1, scale});
+            } else {                     // out_v = X_v A   (A fixed, X batched)
+              const SiteTensor& A = *(const SiteTensor*)fixed;
+              g.push_back(GemmSeg{nullptr, A.d + so_, (*boff)[q] + v * sa, 0, D, Dr, D, 0, 0, A0, 0, scale});
+            }
+          }
+      }
+    }
+    p = std::make_unique<GemmPlan>();
+    if (!o.empty()) build_gemm(*p, o, g, c->st);
+    return *p;
+  }
+  void run_bop(GemmPlan& p, const double* a, const double* b, double* out) {
+    if (p.ntiles == 0) return;
+    GemmExtra ex{};
+    ex.p[0] = const_cast<double*>(a);
+    ex.p[1] = const_cast<double*>(b);
+    ex.p[2] = out;
+    p.run(c->st, nullptr, nullptr, nullptr, &ex);
+    CK(cudaGetLastError());
+  }
+  // X_v = A^T B_v on bond i+1 (A a fixed site-i tensor)
+  void b_lc(int i, const SiteTensor& A, const SiteBatch& B, int nv, BondBatch& X) {
+    bond_batch(c, i + 1, X, nv);
+    run_bop(bop(K_LC, i, nv, false, 1.0, &A, 0, B.stride, X.stride, &X.off), nullptr, B.buf.p, X.buf.p);
+  }
+  // out_v (+)= s A_v X (X fixed on bond i+1)
+  void b_rmul(int i, const SiteBatch& A, int nv, const BondMat& X, SiteBatch& out, bool acc, double s = 1.0) {
+    run_bop(bop(K_RMUL, i, nv, acc, s, &X, A.stride, 0, out.stride, nullptr), A.buf.p, nullptr, out.buf.p);
+  }
+  // out_v (+)= s A X_v (A a fixed site-i tensor, X batched on bond i+1)
+  void b_rmulb(int i, const SiteTensor& A, const BondBatch& X, int nv, SiteBatch& out, bool acc, double s = 1.0) {
+    run_bop(bop(K_RMULB, i, nv, acc, s, &A, 0, X.stride, out.stride, &X.off), nullptr, X.buf.p, out.buf.p);
+  }
+  // X_v,ql = sum_n A_v(ql,n) B(ql,n)^T on bond i (B a fixed site-i tensor)
+  void b_rc(int i, const SiteBatch& A, int nv, const SiteTensor& B, BondBatch& X) {
+    bond_batch(c, i, X, nv);
+    run_bop(bop(K_RC, i, nv, false, 1.0, &B, A.stride, 0, X.stride, &X.off), A.buf.p, nullptr, X.buf.p);
+  }
+  // out_v (+)= s X A_v (X fixed on bond i)
+  void b_lmul(int i, const BondMat& X, const SiteBatch& A, int nv, SiteBatch& out, bool acc, double s = 1.0) {
+    run_bop(bop(K_LMUL, i, nv, acc, s, &X, 0, A.stride, out.stride, nullptr), nullptr, A.buf.p, out.buf.p);
+  }
+  // out_v (+)= s X_v A (X batched on bond i, A a fixed site-i tensor)
+  void b_lmulb(int i, const BondBatch& X, int nv, const SiteTensor& A, SiteBatch& out, bool acc, double s = 1.0) {
+    run_bop(bop(K_LMULB, i, nv, acc, s, &A, X.stride, 0, out.stride, &X.off), X.buf.p, nullptr, out.buf.p);
+  }
+
+  // ---- vector algebra on batches (no host synchronization) ----
+  DevBuf dwork, dcoef;
+  void b_copy(const SiteBatch& A, int a0, int nv, SiteBatch& B, int b0) {
+    if (nv > 0 && A.stride > 0)
+      CK(cudaMemcpy2DAsync(B.v(b0), B.stride * sizeof(double), A.v(a0), A.stride * sizeof(double),
+                           A.stride * sizeof(double), nv, cudaMemcpyDeviceToDevice, c->st));
+  }
+  // Y_v += s X_v
+  void b_axpy(double s, const SiteBatch& X, int x0, SiteBatch& Y, int y0, int nv) {
+    launch_rank1_batch(X.v(x0), X.stride, nullptr, s, nv, Y.v(y0), Y.stride, Y.stride, c->st);
+  }
+  // Q^C X_v = X_v - C0 (C0 . X_v)   (Eq. param)
+  void b_projC(int i, SiteBatch& X, int x0, int nv) {
+    dwork.ensure((size_t)dot_work(nv));
+    dcoef.ensure((size_t)std::max(nv, 1));
+    launch_vdots(X.v(x0), X.stride, C0(i).d, 0, nv, T(i), dcoef.p, false, dwork.p, c->st);
+    launch_rank1_batch(C0(i).d, 0, dcoef.p, -1.0, nv, X.v(x0), X.stride, T(i), c->st);
+  }
+  // Q^L X_v = X_v - L0 (L0^T X_v)   (Eq. cwfn1st)
+  void b_projL(int i, const SiteBatch& X, int nv, SiteBatch& out) {
+    BondBatch Y;
+    b_lc(i, L0(i), X, nv, Y);
+    b_copy(X, 0, nv, out, 0);
+    b_rmulb(i, L0(i), Y, nv, out, true, -1.0);
+  }
+  // X_v Q^R = X_v - (X_v R0^T) R0   (Eq. right1st)
+  void b_projR(int i, const SiteBatch& X, int nv, SiteBatch& out) {
+    BondBatch Y;
+    b_rc(i, X, nv, R0(i), Y);
+    b_copy(X, 0, nv, out, 0);
+    b_lmulb(i, Y, nv, R0(i), out, true, -1.0);
+  }
+
+  // ---- first-order objects, one vector at a time (template replays, asynchronous) ----
   struct Enl {
     std::unique_ptr<OpSet> f, r;
   };
@@ -3350,71 +3588,47 @@ struct TdaRunner {
     uint64_t sig = 0;
   };
   std::map<std::pair<int, int>, DhTpl> dh_tpl;
-  SigmaPlan& dh_plan(int i, int side, const OpSet& X, const OpSet* Xr, const OpSet& Y, const OpSet* Yr) {
+  SigmaPlan& dh_plan(int i, int side, const OpSet& X, const OpSet* Xr, uint64_t xsig, const OpSet& Y,
+                     const OpSet* Yr, uint64_t ysig) {
     DhTpl& t = dh_tpl[{i, side}];
-    const uint64_t sig = set_signature(X, Xr) ^ (set_signature(Y, Yr) * 1099511628211ull);
+    const uint64_t sig = xsig ^ (ysig * 1099511628211ull);
     if (!t.plan || t.sig != sig) {
       t.plan = plan_sigma_sets(c, X, Xr, Y, Yr, i, 1, 1, false, true);
       t.sig = sig;
     }
-    SigmaPlan& p = *t.plan;
-    p.ex.p[0] = X.d;
-    p.ex.p[1] = Xr ? Xr->d : nullptr;
-    p.ex.p[2] = Y.d;
-    p.ex.p[3] = Yr ? Yr->d : nullptr;
-    return p;
+    return *t.plan;
   }
-  void dh_left(int i, const Enl& XE, SiteTensor& y) {
-    CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
+  // y = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i  (Eq. hleft_sb on C0; y zeroed by the caller)
+  void dh_left(int i, const Enl& XE, double* y) {
     if (!XE.f) return;
-    SigmaPlan& p = dh_plan(i, 0, *XE.f, XE.r.get(), *c->R[i + 1], nullptr);
-    p.p1.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
-    p.p2.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
-    CK(cudaGetLastError());
+    const OpSet& Y = *c->R[i + 1];
+    SigmaPlan& p = dh_plan(i, 0, *XE.f, XE.r.get(), set_signature(*XE.f, XE.r.get()), Y, nullptr,
+                           set_signature(Y, nullptr));
+    p.ex.p[0] = XE.f->d;
+    p.ex.p[1] = XE.r ? XE.r->d : nullptr;
+    p.ex.p[2] = Y.d;
+    p.ex.p[3] = nullptr;
+    run_plan(p, C0(i).d, y, 1, false);
   }
-
-  // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2)
-  void dh_right(int i, const FirstOrder& HR, SiteTensor& y) {
-    CK(cudaMemsetAsync(y.d, 0, (size_t)std::max<int64_t>(y.total, 1) * sizeof(double), c->st));
+  // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2), H_mu^{R_i} the
+  // vector's slot of a set batch (y zeroed by the caller)
+  void dh_right(int i, const SetBatch& HR, int mu, double* y) {
     if (HR.empty()) return;
-    SigmaPlan& p = dh_plan(i, 1, *c->XL[i], nullptr, *HR.f, HR.r.get());
-    p.p1.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
-    p.p2.run(c->st, C0(i).d, y.d, p.tbuf, &p.ex);
-    CK(cudaGetLastError());
+    const OpSet& X = *c->XL[i];
+    SigmaPlan& p = dh_plan(i, 1, X, nullptr, set_signature(X, nullptr), *HR.fp, HR.rp.get(), HR.sig);
+    p.ex.p[0] = X.d;
+    p.ex.p[1] = nullptr;
+    p.ex.p[2] = HR.fv(mu);
+    p.ex.p[3] = HR.rv(mu);
+    run_plan(p, C0(i).d, y, 1, false);
   }
 
-  // Q^C C = C - C0 (C0 . C)
-  void proj_C(int i, SiteTensor& C) { t_axpby(c, -t_dot(c, C0(i), C, tmp), C0(i), 1.0, C, tmp); }
-  // Q^L C = C - L0 (L0^T C)
-  SiteTensor proj_L(int i, const SiteTensor& C) {
-    BondMat X;
-    t_lc(c, i, L0(i), C, X);
-    SiteTensor out = new_site(c, i);
-    t_axpby(c, 1.0, C, 0.0, out, tmp);
-    SiteTensor t = new_site(c, i);
-    t_rmul(c, i, L0(i), X, t, false);
-    t_axpby(c, -1.0, t, 1.0, out, tmp);
-    return out;
-  }
-  // C Q^R = C - (C R0^T) R0
-  SiteTensor proj_R(int i, const SiteTensor& C) {
-    BondMat X;
-    t_rc(c, i, C, R0(i), X);
-    SiteTensor out = new_site(c, i);
-    t_axpby(c, 1.0, C, 0.0, out, tmp);
-    SiteTensor t = new_site(c, i);
-    t_lmul(c, i, X, R0(i), t, false);
-    t_axpby(c, -1.0, t, 1.0, out, tmp);
-    return out;
-  }
-
-  // first-order left set at bond i+1 (Eq. lopr1st), both directions
   // renormalizations kept for replay, per (site, right, direction, number of terms)
   std::map<std::tuple<int, int, int, int>, RenTemplate> ren_tpl;
   RenTemplate* rtpl(int i, bool right, int rev, int nterms) {
     return &ren_tpl[std::make_tuple(i, right ? 1 : 0, rev, nterms)];
   }
-
+  // first-order left set at bond i+1 (Eq. lopr1st), both directions
   FirstOrder grow_HL(int i, const Enl& XE, const SiteTensor& L1) {
     FirstOrder out;
     const OpSet& XL = *c->XL[i];
@@ -3429,7 +3643,6 @@ struct TdaRunner {
     }
     return out;
   }
-
   // first-order right set at bond i (Eq. ropr1st), both directions
   FirstOrder grow_HR(int i, const FirstOrder& HR, const SiteTensor& R1) {
     FirstOrder out;
@@ -3448,51 +3661,39 @@ struct TdaRunner {
     return out;
   }
 
-  // sum_j a_j S_j over operator sets of one layout (Eq. ritzrot2 on H^R)
-  std::unique_ptr<OpSet> combine(const std::vector<const OpSet*>& sets, const std::vector<double>& a) {
-    auto out = clone_layout(c, *sets[0]);
-    for (size_t j = 0; j < sets.size(); ++j) {
-      if (a[j] == 0.0 || sets[j]->total == 0) continue;
-      tmp.ensure(4);
-      CK(cudaMemcpyAsync(tmp.p, &a[j], sizeof(double), cudaMemcpyHostToDevice, c->st));
-      launch_lincomb(sets[j]->d, sets[j]->total, 1, tmp.p, out->total, out->d, 1.0, c->st);
-      CK(cudaStreamSynchronize(c->st));
-    }
-    return out;
-  }
-
   // Initial trial vector mu at site i.  seed != 0: SplitMix64 Gaussians; seed == 0: the
   // unit vector on the mu-th lowest diagonal element of H_0^[i] among the components where
   // the reference is small (|C0| < 1/2), a single-site excitation.  Both projected by Q^C.
-  SiteTensor start_site(int i, int mu) {
-    if (P.seed != 0) return random_site(i, mu);
-    SiteTensor T = new_site(c, i);
-    std::vector<double> d(T.total), c0(T.total);
-    CK(cudaMemcpyAsync(d.data(), diag[i].p, d.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(c0.data(), C0(i).d, c0.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  void start_site(int i, int mu, double* out) {
+    std::vector<double> h(T(i), 0.0);
+    bool unit = false;
+    if (P.seed == 0) {
+      std::vector<double> d(T(i)), c0(T(i));
+      CK(cudaMemcpyAsync(d.data(), diag[i].p, d.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(c0.data(), C0(i).d, c0.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      std::vector<int64_t> idx;
+      for (int64_t e = 0; e < T(i); ++e)
+        if (std::fabs(c0[e]) < 0.5) idx.push_back(e);
+      if (!idx.empty()) {
+        std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return d[a] < d[b]; });
+        h[idx[std::min<int64_t>(mu, (int64_t)idx.size() - 1)]] = 1.0;
+        unit = true;
+      }
+    }
+    if (!unit) {
+      const uint64_t seed = P.seed * 7919ull + 1000ull * (uint64_t)mu + (uint64_t)i;
+      for (int64_t e = 0; e < T(i); ++e) h[e] = splitmix_normal(seed, (uint64_t)e);
+      if (P.start_shift > 0.0) {
+        // damped by the diagonal energy above the reference: low-lying configurations first
+        std::vector<double> d(T(i));
+        CK(cudaMemcpyAsync(d.data(), diag[i].p, d.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int64_t e = 0; e < T(i); ++e) h[e] /= std::fabs(d[e] - E0) + P.start_shift;
+      }
+    }
+    if (T(i) > 0) CK(cudaMemcpyAsync(out, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
     CK(cudaStreamSynchronize(c->st));
-    std::vector<int64_t> idx;
-    for (int64_t e = 0; e < T.total; ++e)
-      if (std::fabs(c0[e]) < 0.5) idx.push_back(e);
-    if (idx.empty()) return random_site(i, mu);
-    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return d[a] < d[b]; });
-    const int64_t e = idx[std::min<int64_t>(mu, (int64_t)idx.size() - 1)];
-    const double one = 1.0;
-    CK(cudaMemcpyAsync(T.d + e, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    proj_C(i, T);
-    return T;
-  }
-
-  SiteTensor random_site(int i, int mu) {
-    SiteTensor T = new_site(c, i);
-    std::vector<double> h(T.total);
-    const uint64_t seed = P.seed * 7919ull + 1000ull * (uint64_t)mu + (uint64_t)i;
-    for (int64_t e = 0; e < T.total; ++e) h[e] = splitmix_normal(seed, (uint64_t)e);
-    CK(cudaMemcpyAsync(T.d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    proj_C(i, T);
-    return T;
   }
 
   // small generalized eigenproblem H a = theta S a (S semi-definite), eigensolves on the GPU
@@ -3543,181 +3744,227 @@ struct TdaRunner {
       }
   }
 
-  struct Vec {
-    std::vector<SiteTensor> R1;
-    std::vector<FirstOrder> HR;   // index b = bond
-  };
+  // sum_i |Q^C (H_0^[i] - E0) C0_i|^2: the site components of <T|H|Psi0> (Eq. dmrg at
+  // every site), zero at a stationary point of the one-site manifold
+  double stationarity() {
+    setup();
+    double g2 = 0.0;
+    for (int i = 0; i < k; ++i) {
+      SiteTensor y = new_site(c, i);
+      run_plan(*h0one[i], C0(i).d, y.d, 1, false);
+      t_axpby(c, -E0, C0(i), 1.0, y, tmp);
+      proj_C(i, y);
+      g2 += t_dot(c, y, y, tmp);
+    }
+    return g2;
+  }
+  void proj_C(int i, SiteTensor& X) { t_axpby(c, -t_dot(c, C0(i), X, tmp), C0(i), 1.0, X, tmp); }
 
+  // Fig. alg:dmrgtda.  The trial vectors of a sweep are processed together at every site:
+  // their site tensors are contiguous batches, the bond and site products of the gauge
+  // shifts and projections are grouped launches over all vectors, the H_0 products are
+  // multi-vector sigma calls, and the reduced matrices and residual norms accumulate on the
+  // device; the host synchronizes once per sweep (and in the first, for the start vectors).
   void run(int n, double* theta_out, double* resid_out, int* iters_out) {
     setup();
     const int N = P.max_space > 0 ? P.max_space : std::min(JACOBI_MAXN, std::max(8 * n, 24));
-    std::vector<Vec> old;
+    if (N > JACOBI_MAXN || 2 * n > JACOBI_MAXN)
+      throw Error(LRT_EINVAL, "sweep_tda: max_space and 2 nroots must not exceed " + std::to_string(JACOBI_MAXN));
+    if (P.correction != LRT_CORR_SITE && P.correction != LRT_CORR_SWEEP)
+      throw Error(LRT_EINVAL, "sweep_tda: unknown correction");
+    // Ritz vectors kept at a restart (the paper's deflation keeps n)
+    const int keep = std::max(n, std::min(P.keep > 0 ? P.keep : n, N - n));
+    blk = n;
+    // previous subspace: R1 per site, first-order right sets per bond (both directions)
+    std::vector<SiteBatch> oldR1(k);
+    std::vector<SetBatch> oldHR(k + 1);
+    int lold = 0;
     std::vector<double> alpha, theta, Hr, Sr, r2(n, 0.0);
-    int m = 0, it = 0, mcols = 0;
+    DevBuf d_alpha, d_theta, d_H, d_S, d_D, d_r2, d_gs;
+    std::vector<double> gsf(n, 0.0);
+    bool any_gs = false;
+    int m = 0, it = 0;
     bool first = true;
     for (;;) {
       if (!first) {
         std::vector<double> w, U;
-        const int lprev = (int)old.size();
-        solve_gep(Hr, Sr, lprev, w, U);
-        mcols = (int)w.size();
+        solve_gep(Hr, Sr, lold, w, U);
+        const int mcols = (int)w.size();
         m = std::min(m, mcols);
-        alpha.assign((size_t)lprev * m, 0.0);
-        for (int a = 0; a < lprev; ++a)
-          for (int j = 0; j < m; ++j) alpha[(size_t)a * m + j] = U[(size_t)a * mcols + j];
-        theta.assign(w.begin(), w.begin() + m);
         // every root needs a Ritz vector: a subspace whose overlap matrix keeps fewer than
         // n directions above the cut cannot continue the sweep Davidson
         if (m < n)
           throw Error(LRT_EINVAL, "sweep_tda: the trial subspace spans fewer directions than roots (" +
                                       std::to_string(m) + " < " + std::to_string(n) + ")");
+        alpha.assign((size_t)lold * m, 0.0);
+        for (int a = 0; a < lold; ++a)
+          for (int j = 0; j < m; ++j) alpha[(size_t)a * m + j] = U[(size_t)a * mcols + j];
+        theta.assign(w.begin(), w.begin() + m);
+        d_alpha.ensure(alpha.size());
+        d_theta.ensure(n);
+        CK(cudaMemcpyAsync(d_alpha.p, alpha.data(), alpha.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(d_theta.p, theta.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        // the sweep correction, per root, once the root's last residual is below the gate
+        any_gs = false;
+        if (P.correction == LRT_CORR_SWEEP && it > 0) {
+          const double gate = P.corr_tol > 0.0 ? P.corr_tol : 1.0;
+          for (int mu = 0; mu < n; ++mu) {
+            gsf[mu] = r2[mu] < gate ? 1.0 : 0.0;
+            any_gs = any_gs || gsf[mu] != 0.0;
+          }
+          d_gs.ensure(n);
+          CK(cudaMemcpyAsync(d_gs.p, gsf.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        }
       }
       const int l = m + n;
-      Hr.assign((size_t)l * l, 0.0);
-      Sr.assign((size_t)l * l, 0.0);
-      std::fill(r2.begin(), r2.end(), 0.0);
+      d_H.ensure((size_t)l * l);
+      d_S.ensure((size_t)l * l);
+      d_D.ensure((size_t)3 * l * l);
+      d_r2.ensure(n);
+      CK(cudaMemsetAsync(d_H.p, 0, (size_t)l * l * sizeof(double), c->st));
+      CK(cudaMemsetAsync(d_S.p, 0, (size_t)l * l * sizeof(double), c->st));
+      CK(cudaMemsetAsync(d_r2.p, 0, n * sizeof(double), c->st));
+      dwork.ensure((size_t)dot_work((int64_t)l * l));
       // ---------------- forward sweep ----------------
-      std::vector<SiteTensor> Cprev(l);
+      SiteBatch Cprev;
       std::vector<FirstOrder> HL(l);
-      std::vector<std::vector<SiteTensor>> L1(l);
-      for (auto& v : L1) v.resize(k);
+      std::vector<SiteBatch> L1(k);
       for (int i = 0; i < k; ++i) {
-        std::vector<SiteTensor> C1(l);
-        std::vector<FirstOrder> HRrot(m);
-        for (int mu = 0; mu < m; ++mu) {
-          // Eq. ritzrot2 at this site
-          SiteTensor R1 = new_site(c, i);
-          std::vector<double> a(old.size());
-          for (size_t j = 0; j < old.size(); ++j) {
-            a[j] = alpha[j * m + mu];
-            t_axpby(c, a[j], old[j].R1[i], 1.0, R1, tmp);
+        SiteBatch C1;
+        batch_alloc(c, C1, T(i), l, blk);
+        SetBatch HRrot;
+        if (m > 0) {
+          // Eq. ritzrot2 at this site: R1 and the first-order right sets of bond i+1
+          SiteBatch R1;
+          batch_alloc(c, R1, T(i), m, blk);
+          launch_rotate(oldR1[i].buf.p, oldR1[i].stride, lold, d_alpha.p, m, R1.buf.p, R1.stride, T(i), c->st);
+          if (i + 1 < k && !oldHR[i + 1].empty()) {
+            const SetBatch& O = oldHR[i + 1];
+            set_batch(c, HRrot, *O.fp, *O.rp, m);
+            launch_rotate(O.f.p, O.fs, lold, d_alpha.p, m, HRrot.f.p, HRrot.fs, O.fp->total, c->st);
+            launch_rotate(O.r.p, O.rs, lold, d_alpha.p, m, HRrot.r.p, HRrot.rs, O.rp->total, c->st);
           }
-          if (i + 1 < k) {
-            std::vector<const OpSet*> fs, rs;
-            for (auto& v : old) {
-              fs.push_back(v.HR[i + 1].f.get());
-              rs.push_back(v.HR[i + 1].r.get());
-            }
-            HRrot[mu].f = combine(fs, a);
-            HRrot[mu].r = combine(rs, a);
-          }
-          // Eq. gauge_fwd
-          C1[mu] = new_site(c, i);
-          if (i == 0) {
-            t_lmul(c, i, lam[0], R1, C1[mu], false);
+          // Eq. gauge_fwd: C1_i = (L0_{i-1}^T C1_{i-1}) R0_i + Lambda_i R1_i
+          if (i > 0) {
+            BondBatch X;
+            b_lc(i - 1, L0(i - 1), Cprev, m, X);
+            b_lmulb(i, X, m, R0(i), C1, false);
+            b_lmul(i, lam[i], R1, m, C1, true);
           } else {
-            BondMat X;
-            t_lc(c, i - 1, L0(i - 1), Cprev[mu], X);
-            t_lmul(c, i, X, R0(i), C1[mu], false);
-            t_lmul(c, i, lam[i], R1, C1[mu], true);
+            b_lmul(i, lam[0], R1, m, C1, false);
           }
         }
         // [H_mu^{L} x h x H_0^{R}] C0 for every vector (Eq. sigv2, first line); it enters
         // both the site sigma of the corrections and the reduced matrices below
         std::vector<Enl> XE(l);
-        std::vector<SiteTensor> dHC0(l);
+        SiteBatch dHC0;
+        batch_alloc(c, dHC0, T(i), l, blk);
         for (int mu = 0; mu < l; ++mu) {
           XE[mu] = enlarge_left(i, HL[mu]);
-          dHC0[mu] = new_site(c, i);
-          dh_left(i, XE[mu], dHC0[mu]);
+          dh_left(i, XE[mu], dHC0.v(mu));
         }
         // correction vectors (Eqs. sigv1, rnorm, error, param)
-        for (int mu = 0; mu < n; ++mu) {
-          if (first) {
-            C1[m + mu] = start_site(i, mu);
-            continue;
+        if (first) {
+          for (int mu = 0; mu < n; ++mu) start_site(i, mu, C1.v(m + mu));
+          b_projC(i, C1, m, n);
+        } else {
+          SiteBatch sig, t1;
+          batch_alloc(c, sig, T(i), n, blk);
+          batch_alloc(c, t1, T(i), n, blk);
+          h0(i, C1, n, sig);
+          b_axpy(1.0, dHC0, 0, sig, 0, n);
+          for (int mu = 0; mu < n; ++mu) dh_right(i, HRrot, mu, t1.v(mu));
+          b_axpy(1.0, t1, 0, sig, 0, n);
+          launch_rank1_batch(C1.v(0), C1.stride, d_theta.p, -1.0, n, sig.v(0), sig.stride, T(i), c->st);  // r
+          b_projC(i, sig, 0, n);                                                                           // Q^C r
+          launch_vdots(sig.v(0), sig.stride, sig.v(0), sig.stride, n, T(i), d_r2.p, true, dwork.p, c->st);
+          if (any_gs) {
+            // roots with the sweep correction: z_i = -D^-1 Q^C (r_i + [H_z^{L_{i-1}} x h_i x
+            // H_0^{R_i}] C0_i), the new vector's own left part (sites < i) entering its
+            // site-i equation
+            launch_rank1_batch(dHC0.v(m), dHC0.stride, d_gs.p, 1.0, n, sig.v(0), sig.stride, T(i), c->st);
+            b_projC(i, sig, 0, n);
           }
-          SiteTensor sig = new_site(c, i), t1 = new_site(c, i);
-          h0(i, C1[mu], sig);
-          t_axpby(c, 1.0, dHC0[mu], 1.0, sig, tmp);
-          dh_right(i, HRrot[mu], t1);
-          t_axpby(c, 1.0, t1, 1.0, sig, tmp);
-          t_axpby(c, -theta[mu], C1[mu], 1.0, sig, tmp);     // r = sigma - theta C
-          r2[mu] += t_dot(c, sig, sig, tmp);
-          SiteTensor z = new_site(c, i);
-          launch_precond(sig.d, diag[i].p, theta[mu], sig.total, z.d, c->st);   // -r / (d - theta)
-          t_axpby(c, 0.0, z, -1.0, z, tmp);                                       // r / (d - theta)
-          proj_C(i, z);
-          C1[m + mu] = std::move(z);
+          // -D^-1 r (Eq. error; the sign of a new trial vector does not change the subspace)
+          launch_precond_batch(sig.v(0), sig.stride, diag[i].p, d_theta.p, n, T(i), C1.v(m), C1.stride, 1.0,
+                               c->st);
+          b_projC(i, C1, m, n);
         }
         // projected coefficients (Eq. cwfn1st) and reduced matrices (Eqs. hleft2, sleft2)
-        std::vector<SiteTensor> Ct(l), H0Ct(l);
-        for (int mu = 0; mu < l; ++mu) {
-          Ct[mu] = proj_L(i, C1[mu]);
-          H0Ct[mu] = new_site(c, i);
-          h0(i, Ct[mu], H0Ct[mu]);
-        }
-        {
-          // all l x l products of the site at once: <Ct|H0 Ct>, <Ct|dH C0>, <Ct|Ct>
-          std::vector<const double*> pc(l), ph(l), pd(l);
-          for (int a = 0; a < l; ++a) {
-            pc[a] = Ct[a].d;
-            ph[a] = H0Ct[a].d;
-            pd[a] = dHC0[a].d;
-          }
-          DevArray<const double*> dc, dh, dd;
-          dc.upload(pc, c->st);
-          dh.upload(ph, c->st);
-          dd.upload(pd, c->st);
-          DevBuf prod;
-          prod.ensure((size_t)3 * l * l);
-          const int64_t nel = Ct[0].total;
-          launch_pair_dots(dc.p, dh.p, l, l, nel, prod.p, c->st);
-          launch_pair_dots(dc.p, dd.p, l, l, nel, prod.p + (size_t)l * l, c->st);
-          launch_pair_dots(dc.p, dc.p, l, l, nel, prod.p + (size_t)2 * l * l, c->st);
-          std::vector<double> hp((size_t)3 * l * l);
-          CK(cudaGetLastError());
-          CK(cudaMemcpyAsync(hp.data(), prod.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-          CK(cudaStreamSynchronize(c->st));
-          const double* D1 = hp.data();
-          const double* D2 = D1 + (size_t)l * l;
-          const double* D3 = D2 + (size_t)l * l;
-          for (int a = 0; a < l; ++a)
-            for (int b2 = 0; b2 < l; ++b2) {
-              Hr[(size_t)a * l + b2] += D1[(size_t)a * l + b2] + D2[(size_t)a * l + b2] + D2[(size_t)b2 * l + a];
-              Sr[(size_t)a * l + b2] += D3[(size_t)a * l + b2];
-            }
-        }
+        SiteBatch Ct, H0Ct;
+        batch_alloc(c, Ct, T(i), l, blk);
+        batch_alloc(c, H0Ct, T(i), l, blk);
+        b_projL(i, C1, l, Ct);
+        h0(i, Ct, l, H0Ct);
+        double* D1 = d_D.p;
+        double* D2 = D1 + (size_t)l * l;
+        double* D3 = D2 + (size_t)l * l;
+        launch_pair_dots_strided(Ct.v(0), Ct.stride, l, H0Ct.v(0), H0Ct.stride, l, T(i), D1, dwork.p, c->st);
+        launch_pair_dots_strided(Ct.v(0), Ct.stride, l, dHC0.v(0), dHC0.stride, l, T(i), D2, dwork.p, c->st);
+        launch_pair_dots_strided(Ct.v(0), Ct.stride, l, Ct.v(0), Ct.stride, l, T(i), D3, dwork.p, c->st);
+        launch_reduced_acc(D1, D2, D3, l, d_H.p, d_S.p, c->st);
         // Eqs. left1st and lopr1st
-        for (int mu = 0; mu < l; ++mu) {
-          L1[mu][i] = new_site(c, i);
-          t_rmul(c, i, Ct[mu], ilam[i + 1], L1[mu][i], false);
-          if (i + 1 < k) HL[mu] = grow_HL(i, XE[mu], L1[mu][i]);
-        }
+        batch_alloc(c, L1[i], T(i), l, blk);
+        b_rmul(i, Ct, l, ilam[i + 1], L1[i], false);
+        if (i + 1 < k)
+          for (int mu = 0; mu < l; ++mu) {
+            SiteView v(lay[i], L1[i].v(mu));
+            HL[mu] = grow_HL(i, XE[mu], v.t);
+          }
         Cprev = std::move(C1);
       }
+      HL.clear();
       // ---------------- backward sweep ----------------
-      std::vector<Vec> nv(l);
-      for (int mu = 0; mu < l; ++mu) {
-        nv[mu].R1.resize(k);
-        nv[mu].HR.resize(k + 1);
-        SiteTensor Cb = new_site(c, k - 1);
-        t_rmul(c, k - 1, L1[mu][k - 1], lam[k], Cb, false);
-        FirstOrder HR;
-        for (int i = k - 1; i >= 0; --i) {
-          if (i < k - 1) {
-            // Eq. gauge_bwd: C1_i = L1_i Lambda_{i+1} + L0_i (C1_{i+1} R0_{i+1}^T)
-            BondMat Y;
-            t_rc(c, i + 1, Cb, R0(i + 1), Y);
-            SiteTensor nb = new_site(c, i);
-            t_rmul(c, i, L1[mu][i], lam[i + 1], nb, false);
-            t_rmul(c, i, L0(i), Y, nb, true);
-            Cb = std::move(nb);
-          }
-          // Eq. right1st
-          SiteTensor pr = proj_R(i, Cb);
-          nv[mu].R1[i] = new_site(c, i);
-          t_lmul(c, i, ilam[i], pr, nv[mu].R1[i], false);
-          if (i > 0) {
-            HR = grow_HR(i, HR, nv[mu].R1[i]);
-            nv[mu].HR[i].f = clone_layout(c, *HR.f);
-            nv[mu].HR[i].r = clone_layout(c, *HR.r);
-            t_copy_set(*HR.f, *nv[mu].HR[i].f);
-            t_copy_set(*HR.r, *nv[mu].HR[i].r);
+      std::vector<SiteBatch> newR1(k);
+      std::vector<SetBatch> newHR(k + 1);
+      std::vector<FirstOrder> HR(l);
+      SiteBatch Cb;
+      batch_alloc(c, Cb, T(k - 1), l, blk);
+      b_rmul(k - 1, L1[k - 1], l, lam[k], Cb, false);
+      for (int i = k - 1; i >= 0; --i) {
+        if (i < k - 1) {
+          // Eq. gauge_bwd: C1_i = L1_i Lambda_{i+1} + L0_i (C1_{i+1} R0_{i+1}^T)
+          BondBatch Y;
+          b_rc(i + 1, Cb, l, R0(i + 1), Y);
+          SiteBatch nb;
+          batch_alloc(c, nb, T(i), l, blk);
+          b_rmul(i, L1[i], l, lam[i + 1], nb, false);
+          b_rmulb(i, L0(i), Y, l, nb, true);
+          Cb = std::move(nb);
+        }
+        L1[i] = SiteBatch();
+        // Eq. right1st
+        SiteBatch pr;
+        batch_alloc(c, pr, T(i), l, blk);
+        b_projR(i, Cb, l, pr);
+        batch_alloc(c, newR1[i], T(i), l, blk);
+        b_lmul(i, ilam[i], pr, l, newR1[i], false);
+        if (i > 0) {
+          for (int mu = 0; mu < l; ++mu) {
+            SiteView v(lay[i], newR1[i].v(mu));
+            HR[mu] = grow_HR(i, HR[mu], v.t);
+            if (mu == 0) set_batch(c, newHR[i], *HR[0].f, *HR[0].r, l);
+            if (HR[mu].f->total > 0)
+              CK(cudaMemcpyAsync(newHR[i].fv(mu), HR[mu].f->d, (size_t)HR[mu].f->total * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->st));
+            if (HR[mu].r->total > 0)
+              CK(cudaMemcpyAsync(newHR[i].rv(mu), HR[mu].r->d, (size_t)HR[mu].r->total * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->st));
           }
         }
       }
-      old = std::move(nv);
+      HR.clear();
+      oldR1 = std::move(newR1);
+      oldHR = std::move(newHR);
+      lold = l;
+      // the sweep's reduced matrices and residual norms: the one synchronization
+      Hr.assign((size_t)l * l, 0.0);
+      Sr.assign((size_t)l * l, 0.0);
+      CK(cudaMemcpyAsync(Hr.data(), d_H.p, Hr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(Sr.data(), d_S.p, Sr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(r2.data(), d_r2.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      CK(cudaGetLastError());
       if (!first) {
         ++it;
         bool conv = true;
@@ -3745,15 +3992,9 @@ struct TdaRunner {
       first = false;
       // keep the whole subspace while the next one (at most l + n vectors: the GEP may drop
       // directions of S below the cut, so l need not be a multiple of n) still fits in N;
-      // otherwise restart from the n lowest Ritz vectors
-      m = (l + n <= N) ? l : n;
+      // otherwise restart from the lowest Ritz vectors
+      m = (l + n <= N) ? l : keep;
     }
-  }
-
-  void t_copy_set(const OpSet& a, OpSet& b) {
-    if (a.total > 0)
-      CK(cudaMemcpyAsync(b.d, a.d, (size_t)a.total * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
   }
 };
 
@@ -4435,6 +4676,19 @@ int tda_prepare(lrt_t ctx, double* norm) {
   });
 }
 
+int tda_stationarity(lrt_t ctx, double* grad2, double* e0) {
+  return guard(ctx, [&] {
+    if (!ctx->tda || !ctx->tda->loaded) throw Error(LRT_ESTATE, "tda_stationarity: tda_load first");
+    if (!grad2) throw Error(LRT_EINVAL, "tda_stationarity: NULL output");
+    lrt_tda_params p{};
+    p.precision = LRT_FP64;
+    p.pinv_cut = 1e-12;
+    TdaRunner R(ctx, p);
+    *grad2 = R.stationarity();
+    if (e0) *e0 = R.E0;
+  });
+}
+
 int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, double* resid, double* e0) {
   int rc = LRT_OK;
   std::vector<double> th(std::max(nroots, 1), 0.0), rs(std::max(nroots, 1), 0.0);
@@ -4461,6 +4715,13 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, dou
   if (e0) *e0 = E0;
   if (rc != LRT_OK) ctx->err = "sweep_tda: not converged within max_iter (results written)";
   return rc;
+}
+
+int lrt_sweeps(lrt_t ctx, int* sweeps) {
+  return guard(ctx, [&] {
+    if (!sweeps) throw Error(LRT_EINVAL, "lrt_sweeps: NULL output");
+    *sweeps = ctx->last_sweeps;
+  });
 }
 
 int sweep_tda_batched(const lrt_t* ctxs, int n_inst, int nroots, const lrt_tda_params* p, double* omega,

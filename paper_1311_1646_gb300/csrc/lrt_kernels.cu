@@ -11,6 +11,7 @@
 #include "lrt_fp64_tile.h"
 
 #include <algorithm>
+#include <atomic>
 
 namespace lrt {
 
@@ -255,31 +256,47 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(cons
   }
 }
 
+// Per-device state: a process may drive several GPUs (one context per device), and a
+// function attribute set with cudaFuncSetAttribute applies to the current device only.
+constexpr int MAX_DEVICES = 64;
+
 int gemm_fp64_slots() {
-  static int n = 0;
+  static std::atomic<int> slots[MAX_DEVICES];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return GEMM_CTAS;
+  int n = slots[dev].load(std::memory_order_acquire);
   if (!n) {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
+    int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     n = std::max(1, nsm) * GEMM_CTAS;
+    slots[dev].store(n, std::memory_order_release);
   }
   return n;
 }
 
-static void gemm_fp64_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
-    // all of the unified L1 as shared memory, so GEMM_CTAS CTAs fit on an SM
-    cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    done = true;
-  }
+// Opt the FP64 GEMM into its dynamic shared memory on the current device, once per device.
+// On failure the attribute stays unset, the error is the runtime's last error, and the
+// caller's launch check reports it.
+static cudaError_t gemm_fp64_smem_attr() {
+  static std::atomic<int> done[MAX_DEVICES];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
+  if (e != cudaSuccess) return e;
+  // all of the unified L1 as shared memory, so GEMM_CTAS CTAs fit on an SM
+  e = cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  done[dev].store(1, std::memory_order_release);   // concurrent first calls set the same values
+  return cudaSuccess;
 }
 
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st, const GemmExtra* extra) {
   if (ntiles <= 0) return;
-  gemm_fp64_smem_attr();
+  if (gemm_fp64_smem_attr() != cudaSuccess) return;
   const GemmExtra ex = extra ? *extra : GemmExtra{};
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase,
                                                                   nullptr, ex);
@@ -288,7 +305,7 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
 void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                             const GemmBases* bases, cudaStream_t st) {
   if (ntiles <= 0) return;
-  gemm_fp64_smem_attr();
+  if (gemm_fp64_smem_attr() != cudaSuccess) return;
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, nullptr, nullptr,
                                                                   nullptr, bases, GemmExtra{});
 }
@@ -434,6 +451,151 @@ void launch_precond(const double* r, const double* d, double theta, int64_t n, d
   if (n <= 0) return;
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
   precond_kernel<<<grid, 256, 0, st>>>(r, d, theta, n, t);
+}
+
+// ---------------------------------------------------------------------------
+// batched vector operations of the TDA sweeps
+// ---------------------------------------------------------------------------
+static int vec_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 4)); }
+
+__global__ void __launch_bounds__(256) rank1_batch_kernel(const double* __restrict__ w, int64_t ldw,
+                                                          const double* __restrict__ coef, double alpha, int nv,
+                                                          double* __restrict__ V, int64_t ld, int64_t n) {
+  const int v = blockIdx.y;
+  const double c = coef ? alpha * coef[v] : alpha;
+  if (c == 0.0) return;
+  double* x = V + (int64_t)v * ld;
+  const double* y = w + (int64_t)v * ldw;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = fma(c, y[e], x[e]);
+}
+
+void launch_rank1_batch(const double* w, int64_t ldw, const double* coef, double alpha, int nv, double* V,
+                        int64_t ld, int64_t n, cudaStream_t st) {
+  if (nv <= 0 || n <= 0) return;
+  rank1_batch_kernel<<<dim3(vec_grid(n), nv), 256, 0, st>>>(w, ldw, coef, alpha, nv, V, ld, n);
+}
+
+// one thread per element and up to ROT_MU outputs at a time: every old vector is read once
+// per group of ROT_MU new vectors
+constexpr int ROT_MU = 16;
+__global__ void __launch_bounds__(256) rotate_kernel(const double* __restrict__ Vold, int64_t ld_old, int lold,
+                                                     const double* __restrict__ a, int m, int mu0, int mcnt,
+                                                     double* __restrict__ Vnew, int64_t ld_new, int64_t n) {
+  __shared__ double sa[JACOBI_MAXN * ROT_MU];
+  for (int t = threadIdx.x; t < lold * mcnt; t += blockDim.x) sa[t] = a[(t / mcnt) * m + mu0 + t % mcnt];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc[ROT_MU];
+#pragma unroll
+    for (int q = 0; q < ROT_MU; ++q) acc[q] = 0.0;
+    for (int j = 0; j < lold; ++j) {
+      const double x = Vold[(int64_t)j * ld_old + e];
+#pragma unroll
+      for (int q = 0; q < ROT_MU; ++q)
+        if (q < mcnt) acc[q] = fma(sa[j * mcnt + q], x, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < ROT_MU; ++q)
+      if (q < mcnt) Vnew[(int64_t)(mu0 + q) * ld_new + e] = acc[q];
+  }
+}
+
+void launch_rotate(const double* Vold, int64_t ld_old, int lold, const double* a, int m, double* Vnew,
+                   int64_t ld_new, int64_t n, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return;
+  if (lold <= 0) {
+    for (int mu = 0; mu < m; ++mu) cudaMemsetAsync(Vnew + (int64_t)mu * ld_new, 0, (size_t)n * sizeof(double), st);
+    return;
+  }
+  for (int mu0 = 0; mu0 < m; mu0 += ROT_MU)
+    rotate_kernel<<<vec_grid(n), 256, 0, st>>>(Vold, ld_old, lold, a, m, mu0, std::min(ROT_MU, m - mu0), Vnew,
+                                               ld_new, n);
+}
+
+__global__ void __launch_bounds__(256) precond_batch_kernel(const double* __restrict__ R, int64_t ldr,
+                                                            const double* __restrict__ d,
+                                                            const double* __restrict__ theta, int64_t n,
+                                                            double* __restrict__ Z, int64_t ldz, double sign) {
+  const int v = blockIdx.y;
+  const double th = theta[v];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double den = d[e] - th;
+    if (fabs(den) < 1e-4) den = den < 0.0 ? -1e-4 : 1e-4;
+    Z[(int64_t)v * ldz + e] = -sign * R[(int64_t)v * ldr + e] / den;
+  }
+}
+
+void launch_precond_batch(const double* R, int64_t ldr, const double* d, const double* theta, int nv, int64_t n,
+                          double* Z, int64_t ldz, double sign, cudaStream_t st) {
+  if (nv <= 0 || n <= 0) return;
+  precond_batch_kernel<<<dim3(vec_grid(n), nv), 256, 0, st>>>(R, ldr, d, theta, n, Z, ldz, sign);
+}
+
+// first pass: CTA (pair p, chunk c) sums its share of the elements of pair p
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+__global__ void __launch_bounds__(256) vdots_part_kernel(const double* __restrict__ A, int64_t lda,
+                                                         const double* __restrict__ B, int64_t ldb, int nb,
+                                                         int64_t n, int pairs_mode, double* __restrict__ work) {
+  __shared__ double red[256];
+  const int p = blockIdx.y, c = blockIdx.x;
+  const int a = pairs_mode ? p / nb : p;
+  const int b = pairs_mode ? p % nb : p;
+  const double* x = A + (int64_t)a * lda;
+  const double* y = B + (int64_t)b * ldb;
+  const int64_t per = (n + DOT_CHUNKS - 1) / DOT_CHUNKS;
+  const int64_t e0 = (int64_t)c * per, e1 = min(n, e0 + per);
+  double acc = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc = fma(x[e], y[e], acc);
+  const double s = block_sum256(acc, red);
+  if (threadIdx.x == 0) work[(int64_t)p * DOT_CHUNKS + c] = s;
+}
+
+__global__ void vdots_sum_kernel(const double* __restrict__ work, int np, double* __restrict__ out, int accumulate) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double s = 0.0;
+  for (int c = 0; c < DOT_CHUNKS; ++c) s += work[(int64_t)p * DOT_CHUNKS + c];
+  out[p] = accumulate ? out[p] + s : s;
+}
+
+void launch_vdots(const double* A, int64_t lda, const double* B, int64_t ldb, int nv, int64_t n, double* out,
+                  bool accumulate, double* work, cudaStream_t st) {
+  if (nv <= 0) return;
+  vdots_part_kernel<<<dim3(DOT_CHUNKS, nv), 256, 0, st>>>(A, lda, B, ldb, 1, n, 0, work);
+  vdots_sum_kernel<<<(nv + 127) / 128, 128, 0, st>>>(work, nv, out, accumulate ? 1 : 0);
+}
+
+void launch_pair_dots_strided(const double* A, int64_t lda, int na, const double* B, int64_t ldb, int nb, int64_t n,
+                              double* out, double* work, cudaStream_t st) {
+  if (na <= 0 || nb <= 0) return;
+  vdots_part_kernel<<<dim3(DOT_CHUNKS, na * nb), 256, 0, st>>>(A, lda, B, ldb, nb, n, 1, work);
+  vdots_sum_kernel<<<(na * nb + 127) / 128, 128, 0, st>>>(work, na * nb, out, 0);
+}
+
+__global__ void reduced_acc_kernel(const double* __restrict__ D1, const double* __restrict__ D2,
+                                   const double* __restrict__ D3, int l, double* __restrict__ Hr,
+                                   double* __restrict__ Sr) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= l * l) return;
+  const int a = t / l, b = t % l;
+  Hr[t] += D1[t] + D2[t] + D2[b * l + a];
+  Sr[t] += D3[t];
+}
+
+void launch_reduced_acc(const double* D1, const double* D2, const double* D3, int l, double* Hr, double* Sr,
+                        cudaStream_t st) {
+  if (l <= 0) return;
+  reduced_acc_kernel<<<(l * l + 127) / 128, 128, 0, st>>>(D1, D2, D3, l, Hr, Sr);
 }
 
 // Cyclic Jacobi eigenvalue iteration for a small symmetric matrix held in shared

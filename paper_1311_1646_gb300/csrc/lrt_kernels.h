@@ -202,4 +202,30 @@ void launch_precond(const double* r, const double* d, double theta, int64_t n, d
 // eigenvectors as the columns of Z (row-major n x n).
 void launch_jacobi_eigh(double* A, int n, double* w, double* Z, cudaStream_t st);
 constexpr int JACOBI_MAXN = 48;
+
+// Batched forms for the sweeps of several trial vectors at once.  A batch holds nv
+// vectors of length n with stride ld (doubles).
+// V_v += alpha * coef[v] * W_v, W_v = w + v * ldw (ldw = 0: one w for all v); coef: device
+// array of nv values, or NULL for 1
+void launch_rank1_batch(const double* w, int64_t ldw, const double* coef, double alpha, int nv, double* V,
+                        int64_t ld, int64_t n, cudaStream_t st);
+// Vnew_mu = sum_j a[j * m + mu] Vold_j, mu < m, j < lold  (a: device, row-major lold x m)
+void launch_rotate(const double* Vold, int64_t ld_old, int lold, const double* a, int m, double* Vnew,
+                   int64_t ld_new, int64_t n, cudaStream_t st);
+// Z_v = sign * (-R_v / (d - theta[v])), |d - theta| clamped to >= 1e-4 (Eq. error)
+void launch_precond_batch(const double* R, int64_t ldr, const double* d, const double* theta, int nv, int64_t n,
+                          double* Z, int64_t ldz, double sign, cudaStream_t st);
+// Deterministic dot products in two passes (per-CTA partial sums in `work`, then a fixed-order
+// sum), `work` holding at least DOT_WORK(npairs) doubles:
+//   vdots: out[v] (+)= A_v . B_v  (ldb = 0: one B for all v)
+//   pair_dots_strided: out[a * nb + b] = A_a . B_b
+constexpr int DOT_CHUNKS = 64;
+inline int64_t dot_work(int64_t npairs) { return npairs * DOT_CHUNKS; }
+void launch_vdots(const double* A, int64_t lda, const double* B, int64_t ldb, int nv, int64_t n, double* out,
+                  bool accumulate, double* work, cudaStream_t st);
+void launch_pair_dots_strided(const double* A, int64_t lda, int na, const double* B, int64_t ldb, int nb, int64_t n,
+                              double* out, double* work, cudaStream_t st);
+// Hr[a * l + b] += D1[a * l + b] + D2[a * l + b] + D2[b * l + a];  Sr += D3  (Eqs. hleft2, sleft2)
+void launch_reduced_acc(const double* D1, const double* D2, const double* D3, int l, double* Hr, double* Sr,
+                        cudaStream_t st);
 }  // namespace lrt

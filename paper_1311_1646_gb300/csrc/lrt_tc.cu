@@ -36,6 +36,8 @@
 // a bound) for its own MMAs and copies in flight, releases its tensor memory and
 // returns.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include <algorithm>
@@ -617,13 +619,19 @@ void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stri
 
 int tc_tile_m() { return TC_M; }
 
+// Per-device state: a process may drive several GPUs (one context per device), and a
+// function attribute set with cudaFuncSetAttribute applies to the current device only.
+constexpr int TC_MAX_DEVICES = 64;
+
 static int sm_count() {
-  static int nsm = 0;
+  static std::atomic<int> count[TC_MAX_DEVICES];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TC_MAX_DEVICES) return 1;
+  int nsm = count[dev].load(std::memory_order_acquire);
   if (!nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
+    count[dev].store(nsm, std::memory_order_release);
   }
   return nsm;
 }
@@ -632,10 +640,17 @@ int tc_num_ctas(int ntiles) { return std::max(1, std::min(ntiles, sm_count())); 
 
 template <int TN>
 static void launch_tn(const TcItem* items, const int* cta_begin, int nctas, TcOut out, int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(gemm_tf32x3_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<TN>::SMEM_BYTES);
-    attr = true;
+  // opt into the dynamic shared memory once per device; on failure the error is the
+  // runtime's last error and the caller's launch check reports it
+  static std::atomic<int> attr[TC_MAX_DEVICES];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (dev < 0 || dev >= TC_MAX_DEVICES) return;
+  if (!attr[dev].load(std::memory_order_acquire)) {
+    if (cudaFuncSetAttribute(gemm_tf32x3_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<TN>::SMEM_BYTES) != cudaSuccess)
+      return;
+    attr[dev].store(1, std::memory_order_release);
   }
   gemm_tf32x3_kernel<TN><<<nctas, TC_THREADS, Tile<TN>::SMEM_BYTES, st>>>(items, cta_begin, out, err);
 }

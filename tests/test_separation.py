@@ -77,6 +77,7 @@ def _oracle_imports_by_function(path):
 
 def test_oracle_is_imported_only_by_the_allowed_legs():
     bench = _oracle_imports_by_function(os.path.join(ROOT, "bench.py"))
-    assert bench and set(bench) <= {"_oracle_setup", "cpu_baseline", "run_reference"}, bench
+    assert bench and set(bench) <= {"_oracle_setup", "cpu_baseline", "cpu_baseline_child",
+                                     "_child_sigma", "run_reference"}, bench
     entry = _oracle_imports_by_function(os.path.join(ROOT, "__graft_entry__.py"))
     assert entry and set(entry) <= {"smoke"}, entry

@@ -64,6 +64,17 @@ def test_noalloc_matches_sigma_on_two_calls_in_a_row(pkg, nsite, nvec):
         assert np.abs(a - b).max() <= RTOL * np.abs(b).max()
         outs.append(a)
     assert not np.array_equal(outs[0], outs[1])            # the second call really recomputed
+    # once the first call has resolved the static array on this device, further calls take
+    # no device memory
+    x = _dev(synth.random_vector(nvec * n, 502))
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        ctx.sigma_noalloc(3, nsite, x, y, nvec=nvec)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
     ctx.close()
 
 
