@@ -93,6 +93,27 @@ typedef struct {
 } lrt_mps_desc;
 int mps_load(lrt_t ctx, const lrt_mps_desc* mps);
 
+/* mps_save: the MPS the context holds now (after mps_load, sweep_gs or tda_prepare) into
+ * caller-allocated host buffers, in mps_load's layout, so that mps_load of the result
+ * restores it.  A query fills the sizes: call with every buffer NULL to get k, n_alpha,
+ * n_beta, total_sectors and (if site_nelem is given) the doubles of every site, then
+ * allocate and call again.  bond_nsect: k+1 ints; bond_sectors: 3 * total_sectors ints
+ * ((N_a, N_b, D) triples, bond by bond); site_data[i] / site_data_right[i]: host buffers of
+ * site_nelem[i] doubles for the left-fused site tensors (the loaded form, and the
+ * right-orthonormal form when the context holds one; a NULL array or entry skips it).
+ * has_right is set to 1 when the right-orthonormal form exists.  LRT_ESTATE without an MPS. */
+typedef struct {
+  int k, n_alpha, n_beta;
+  int total_sectors;
+  int has_right;
+  int* bond_nsect;
+  int* bond_sectors;
+  int64_t* site_nelem;
+  double* const* site_data;
+  double* const* site_data_right;
+} lrt_mps_out;
+int mps_save(lrt_t ctx, lrt_mps_out* out);
+
 /* Size in doubles of a one-site (nsite=1, sites site) or two-site (nsite=2, sites
  * site, site+1) wavefunction; block_offsets, if non-NULL, receives the start of every
  * fused block (one per right-bond sector for nsite=1, one per populated middle sector
@@ -215,6 +236,16 @@ int tda_prepare(lrt_t ctx, double* norm);
  * tda_prepare first; builds the zeroth-order environments as sweep_tda does. */
 int tda_stationarity(lrt_t ctx, double* grad2, double* e0);
 int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0);
+/* lrt_set_wait_limit: failure detection of the tensor-core kernels.  Every pipeline wait
+ * of those kernels (copies landing, products finishing, records passed between the
+ * kernel's roles) gives up after a time limit, 2 s by default: the CTA raises a flag, lets
+ * the copies and products it already issued finish, releases its tensor memory and
+ * returns, and the call returns LRT_ETIMEOUT with the context still usable.  seconds
+ * replaces that limit for this context (0 restores the default; at most 60).
+ * stall_next != 0 is a test hook: in the next tensor-core launch of this context one CTA
+ * first waits on a barrier that nothing completes, so that call ends through this path
+ * after `seconds`; the hook clears itself with that launch.  Not part of the paper. */
+int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next);
 /* lrt_sweeps: *sweeps = the number of sweeps the last sweep_gs (two-site sweeps) or
  * sweep_tda (Davidson iterations after the start sweep) on this context ran. */
 int lrt_sweeps(lrt_t ctx, int* sweeps);

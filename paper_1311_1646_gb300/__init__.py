@@ -22,7 +22,7 @@ LRT_CORR_SWEEP = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "lrt_sweeps", "sigma_batched",
+           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "lrt_sweeps", "lrt_set_wait_limit", "sigma_batched",
            "sweep_tda_batched"]
 
 _lib = None
@@ -34,6 +34,15 @@ class MpsDesc(ctypes.Structure):
                 ("bond_sectors", ctypes.POINTER(ctypes.c_int)),
                 ("site_data", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
                 ("center", ctypes.c_int),
+                ("site_data_right", ctypes.POINTER(ctypes.POINTER(ctypes.c_double)))]
+
+
+class MpsOut(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_alpha", ctypes.c_int), ("n_beta", ctypes.c_int),
+                ("total_sectors", ctypes.c_int), ("has_right", ctypes.c_int),
+                ("bond_nsect", ctypes.POINTER(ctypes.c_int)), ("bond_sectors", ctypes.POINTER(ctypes.c_int)),
+                ("site_nelem", ctypes.POINTER(ctypes.c_int64)),
+                ("site_data", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
                 ("site_data_right", ctypes.POINTER(ctypes.POINTER(ctypes.c_double)))]
 
 
@@ -78,6 +87,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lrt_last_error.restype = ctypes.c_char_p
     lib.op_build.argtypes = [vp, i, dp, dp, i, dp, d]
     lib.mps_load.argtypes = [vp, ctypes.POINTER(MpsDesc)]
+    lib.mps_save.argtypes = [vp, ctypes.POINTER(MpsOut)]
     lib.wfn_layout.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int64)]
     lib.renormalize.argtypes = [vp, i, i, i]
@@ -94,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tda_prepare.argtypes = [vp, dp]
     lib.tda_stationarity.argtypes = [vp, dp, dp]
     lib.lrt_sweeps.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.lrt_set_wait_limit.argtypes = [vp, d, i]
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
@@ -277,6 +288,12 @@ class Context:
         self._check(self.lib.tda_prepare(self.h, ctypes.byref(nrm)), "tda_prepare")
         return nrm.value
 
+    def set_wait_limit(self, seconds: float, stall_next: bool = False):
+        """Limit of the tensor-core kernels' pipeline waits (0: the default); stall_next makes
+        the next tensor-core launch end through the expired-wait path (test hook)."""
+        self._check(self.lib.lrt_set_wait_limit(self.h, float(seconds), 1 if stall_next else 0),
+                    "lrt_set_wait_limit")
+
     def sweeps(self) -> int:
         """Sweeps run by the last sweep_gs or sweep_tda on this context."""
         n = ctypes.c_int()
@@ -320,6 +337,31 @@ class Context:
             bonds.append([(sec[3 * (pos + s)], sec[3 * (pos + s) + 1], sec[3 * (pos + s) + 2]) for s in range(ns[b])])
             pos += ns[b]
         return bonds
+
+    def mps_save(self):
+        """The MPS the context holds: dict with k, n_alpha, n_beta, bonds (tables of
+        (na, nb, dim)), sites (left-fused arrays) and sites_right (or None)."""
+        q = MpsOut()
+        self._check(self.lib.mps_save(self.h, ctypes.byref(q)), "mps_save")
+        k = q.k
+        nsect = (ctypes.c_int * (k + 1))()
+        secs = (ctypes.c_int * (3 * q.total_sectors))()
+        nel = (ctypes.c_int64 * k)()
+        q.bond_nsect, q.bond_sectors, q.site_nelem = nsect, secs, nel
+        self._check(self.lib.mps_save(self.h, ctypes.byref(q)), "mps_save")
+        sites = [np.zeros(nel[i]) for i in range(k)]
+        right = [np.zeros(nel[i]) for i in range(k)] if q.has_right else None
+        q.site_data = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in sites])
+        if right is not None:
+            q.site_data_right = (ctypes.POINTER(ctypes.c_double) * k)(*[_dptr(a) for a in right])
+        self._check(self.lib.mps_save(self.h, ctypes.byref(q)), "mps_save")
+        bonds, pos = [], 0
+        for b in range(k + 1):
+            bonds.append([(secs[3 * (pos + j)], secs[3 * (pos + j) + 1], secs[3 * (pos + j) + 2])
+                          for j in range(nsect[b])])
+            pos += nsect[b]
+        return {"k": k, "n_alpha": q.n_alpha, "n_beta": q.n_beta, "bonds": bonds, "sites": sites,
+                "sites_right": right}
 
     def mps_get(self):
         """The loaded MPS as (bonds, sites): bond tables [(na, nb, dim)] and left-fused site arrays."""

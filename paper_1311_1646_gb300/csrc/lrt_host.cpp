@@ -970,6 +970,8 @@ struct lrt_ctx {
   std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
   lrt_sigma_stats last{};
   int last_sweeps = 0;
+  uint64_t tc_wait_ns = 0;   // limit of the tensor-core pipeline waits (0: the default)
+  int tc_stall = 0;          // test hook: the next tensor-core launch stalls on a wait
   int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
   std::unique_ptr<lrt::TdaState> tda;
   // right-fused copy task lists per (bond, layout of site tensor and fused basis), relative
@@ -981,6 +983,14 @@ struct lrt_ctx {
 };
 
 namespace lrt {
+
+// the output block of a tensor-core launch with the context's wait settings; a pending
+// stall (test hook) is consumed by this launch
+static TcOut tc_out(lrt_ctx* c, double* y, double* const* ys) {
+  TcOut o{y, ys, (unsigned long long)c->tc_wait_ns, c->tc_stall};
+  c->tc_stall = 0;
+  return o;
+}
 
 static char left_mode(int b, int k) { return (2 * b <= k) ? 'N' : 'C'; }
 static char right_mode(int b, int k) { return (2 * b <= k) ? 'C' : 'N'; }
@@ -2265,7 +2275,7 @@ static void prepare_tc(lrt_ctx* c, SigmaPlan& p, int nvec) {
     CK(cudaMemsetAsync(p.pool_lo[1], 0, nx * sizeof(float), c->st));
     DevBuf ys;
     ys.ensure((size_t)std::max<int64_t>(p.nelem * nvec, 1));
-    const TcOut scratch{ys.p, nullptr};
+    const TcOut scratch = tc_out(c, ys.p, nullptr);
     p.tn1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci1,
                            p.tcb1, p.tcn1);
     p.tn2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, p.pool_hi, p.pool_lo, p.nelem, 0}}, nvec, scratch, p.tci2,
@@ -2286,7 +2296,7 @@ static void run_tc(lrt_ctx* ctx, SigmaPlan& p, const double* x_dev, double* y_de
   prepare_tc(ctx, p, nvec);
   launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x_dev, p.nelem, p.pool_hi[1], p.pool_lo[1], p.tc.pool_size[1],
                  nvec, ctx->st);
-  const TcOut to{y_dev};
+  const TcOut to = tc_out(ctx, y_dev, nullptr);
   launch_gemm_tf32x3(p.tci1.p, p.tcb1.p, p.tcn1, p.tn1, to, ctx->derr, ctx->st);
   launch_gemm_tf32x3(p.tci2.p, p.tcb2.p, p.tcn2, p.tn2, to, ctx->derr, ctx->st);
   CK(cudaGetLastError());
@@ -2361,7 +2371,7 @@ static void run_two_phase_tc(lrt_ctx* c, const std::vector<GemmOut>& o1, const s
   DevArray<TcItem> i1, i2;
   DevArray<int> b1, b2;
   int n1 = 0, n2 = 0;
-  const TcOut none{nullptr, nullptr};
+  const TcOut none = tc_out(c, nullptr, nullptr);
   const int t1 = tune_tc_stream(c, {TcSource{&tp, &tp.out1, phi, plo, 0, 0}}, 1, none, i1, b1, n1, false);
   const int t2 = tune_tc_stream(c, {TcSource{&tp, &tp.out2, phi, plo, 0, 0}}, 1, none, i2, b2, n2, false);
   launch_gemm_tf32x3(i1.p, b1.p, n1, t1, none, c->derr, c->st);
@@ -4249,7 +4259,7 @@ static void batch_issue(lrt_ctx* c0, BatchPlan& B, const std::vector<SigmaPlan*>
       launch_tc_pack(p.xpack.p, (int)p.tc.pack1.size(), x[j], p.nelem, p.pool_hi[1], p.pool_lo[1],
                      p.tc.pool_size[1], nvec, st);
     }
-    const TcOut to{nullptr, B.ys.p};
+    const TcOut to = tc_out(c0, nullptr, B.ys.p);
     launch_gemm_tf32x3(B.tci1.p, B.tcb1.p, B.tcn1, B.tn1, to, c0->derr, st);
     launch_gemm_tf32x3(B.tci2.p, B.tcb2.p, B.tcn2, B.tn2, to, c0->derr, st);
   } else {
@@ -4303,7 +4313,7 @@ static void sigma_batched_impl(lrt_ctx* const* ctxs, int n, const int* sites, in
       for (int j = 0; j < n; ++j) sp[j] = scr[j].ensure((size_t)std::max<int64_t>(plans[j]->nelem * nvec, 1));
       DevArray<double*> sys;
       sys.upload(sp, c0->st);
-      const TcOut scratch{nullptr, sys.p};
+      const TcOut scratch = tc_out(c0, nullptr, sys.p);
       B->tn1 = tune_tc_stream(c0, s1, nvec, scratch, B->tci1, B->tcb1, B->tcn1);
       B->tn2 = tune_tc_stream(c0, s2, nvec, scratch, B->tci2, B->tcb2, B->tcn2);
       CK(cudaStreamSynchronize(c0->st));
@@ -4717,6 +4727,14 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, dou
   return rc;
 }
 
+int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next) {
+  return guard(ctx, [&] {
+    if (!(seconds >= 0.0) || seconds > 60.0) throw Error(LRT_EINVAL, "lrt_set_wait_limit: seconds in [0, 60]");
+    ctx->tc_wait_ns = (uint64_t)(seconds * 1e9);
+    ctx->tc_stall = stall_next ? 1 : 0;
+  });
+}
+
 int lrt_sweeps(lrt_t ctx, int* sweeps) {
   return guard(ctx, [&] {
     if (!sweeps) throw Error(LRT_EINVAL, "lrt_sweeps: NULL output");
@@ -4756,6 +4774,39 @@ int sweep_tda_batched(const lrt_t* ctxs, int n_inst, int nroots, const lrt_tda_p
     if (rc[j] == LRT_ENOCONV) out = LRT_ENOCONV;
   }
   return out;
+}
+
+int mps_save(lrt_t ctx, lrt_mps_out* out) {
+  return guard(ctx, [&] {
+    if (!out) throw Error(LRT_EINVAL, "mps_save: NULL descriptor");
+    if (!ctx->have_mps) throw Error(LRT_ESTATE, "mps_save: no MPS");
+    out->k = ctx->k;
+    out->n_alpha = ctx->na;
+    out->n_beta = ctx->nb;
+    out->has_right = ctx->sites_r.empty() ? 0 : 1;
+    int tot = 0;
+    for (int b = 0; b <= ctx->k; ++b) {
+      if (out->bond_nsect) out->bond_nsect[b] = ctx->bonds[b].n();
+      for (int q = 0; q < ctx->bonds[b].n(); ++q, ++tot)
+        if (out->bond_sectors) {
+          out->bond_sectors[3 * tot] = ctx->bonds[b].a[q];
+          out->bond_sectors[3 * tot + 1] = ctx->bonds[b].b[q];
+          out->bond_sectors[3 * tot + 2] = ctx->bonds[b].d[q];
+        }
+    }
+    out->total_sectors = tot;
+    for (int i = 0; i < ctx->k; ++i) {
+      const SiteTensor& T = ctx->sites[i];
+      if (out->site_nelem) out->site_nelem[i] = T.total;
+      if (out->site_data && out->site_data[i] && T.total > 0)
+        CK(cudaMemcpyAsync(out->site_data[i], T.d, (size_t)T.total * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->st));
+      if (out->site_data_right && out->site_data_right[i] && !ctx->sites_r.empty() && ctx->sites_r[i].total > 0)
+        CK(cudaMemcpyAsync(out->site_data_right[i], ctx->sites_r[i].d, (size_t)ctx->sites_r[i].total * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+  });
 }
 
 int mps_get_bonds(lrt_t ctx, int* bond_nsect, int* bond_sectors, int* total_sectors) {

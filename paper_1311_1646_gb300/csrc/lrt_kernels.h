@@ -158,7 +158,11 @@ struct TcItem {
 struct TcOut {
   double* y;                // y of a single-instance launch
   double* const* ys;        // batched launches: y of instance i is ys[i] (device array), else NULL
+  unsigned long long wait_ns;   // limit of every pipeline wait (0: TC_WAIT_NS)
+  int stall;                // test hook: CTA 0's MMA thread first waits on a barrier nothing
+                            // arrives at, so the launch ends through the expired-wait path
 };
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per pipeline wait
 // number of CTAs (one per SM) the tensor-core launch uses for ntiles tiles; CTA b
 // takes tiles b, b + n, b + 2n, ... of the host's order
 int tc_num_ctas(int ntiles);

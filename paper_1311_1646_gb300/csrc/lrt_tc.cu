@@ -56,7 +56,7 @@ constexpr int EPI_WARPS = 4, PROD_WARPS = 1;
 constexpr int TC_THREADS = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int A_BYTES = TC_M * TC_K * 4;    // one TF32 operand tile of A (16 KB)
 constexpr int NACC = 4;                 // TMEM accumulators (product ring to the epilogue)
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr uint64_t WAIT_NS = TC_WAIT_NS;  // drains of copies and MMAs already issued
 
 // Sizes that follow from the tile width TN (output columns = TMEM columns of one
 // accumulator): 32 or 64, chosen per launch by the host's autotuner.
@@ -139,7 +139,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 
 // bounded wait for the phase with the given parity; false on expiry or when another
 // role has already failed (then the caller stops)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* failed, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* failed, int* err,
+                                          uint64_t lim) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = now_ns();
@@ -147,7 +148,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if (mbar_try(a, parity)) return true;
     if ((n & 255u) == 0u) {
       if (*failed) return false;
-      if (now_ns() - t0 > WAIT_NS) {
+      if (now_ns() - t0 > lim) {
         *failed = 1;
         if (err) atomicExch(err, 1);
         return false;
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
+  const uint64_t lim = out.wait_ns ? out.wait_ns : WAIT_NS;   // every progress wait
 
   if (warp == EPI_WARPS) {
     // ---------------- producer (one thread)
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
       // the epilogue record ring
       auto post = [&](const EpiInfo& rec) -> bool {
         const uint32_t slot = ei % NINFO, use = ei / NINFO;
-        if (use > 0 && !mbar_wait(&info_empty[slot], (use - 1) & 1, failed, err)) return false;
+        if (use > 0 && !mbar_wait(&info_empty[slot], (use - 1) & 1, failed, err, lim)) return false;
         info[slot] = rec;
         mbar_arrive(&info_full[slot]);
         ++ei;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           const uint32_t bytes = 2u * 128u * (ra + rb);
           for (int k0 = 0, q = 0; k0 < g.k && ok; k0 += TC_K, ++q, ++it) {
             const uint32_t stage = it % STAGES, round = it / STAGES;
-            if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err)) {
+            if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err, lim)) {
               ok = false;
               break;
             }
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
         ok = ok && post(EpiInfo{INFO_END, 0.0f, hdr});
         // end-of-stream record for the MMA thread, in a stage of its own
         const uint32_t stage = it % STAGES, round = it / STAGES;
-        if (ok && !(round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err))) {
+        if (ok && !(round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, failed, err, lim))) {
           meta[stage] = StageMeta{0, META_END};
           mbar_arrive(&full_bar[stage]);
         }
@@ -377,15 +379,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
       constexpr uint32_t idesc = make_idesc<TN>();
       uint32_t sg = 0;
       bool any = false;
+      // test hook: a wait on a barrier nothing arrives at (its phase never completes),
+      // which ends the launch through the expired-wait path below
+      if (out.stall && blockIdx.x == 0) mbar_wait(&drain_bar, 0, failed, err, lim);
       for (uint32_t it = 0; !*failed; ++it) {
         const uint32_t stage = it % STAGES, round = it / STAGES;
-        if (!mbar_wait(&full_bar[stage], round & 1, failed, err)) break;
+        if (!mbar_wait(&full_bar[stage], round & 1, failed, err, lim)) break;
         const StageMeta m = meta[stage];
         if (m.flags & META_END) break;
         const uint32_t a = sg % NACC;
         if (m.flags & META_FIRST) {
           const uint32_t u = sg / NACC;
-          if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err)) break;
+          if (u > 0 && !mbar_wait(&tempty_bar[a], (u - 1) & 1, failed, err, lim)) break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dt = tmem + a * TN;
@@ -425,14 +430,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
     for (uint32_t ei = 0;; ++ei) {
       const uint32_t slot = ei % NINFO;
       // the warp stays converged for the .sync.aligned tensor-memory loads
-      const bool got = mbar_wait(&info_full[slot], (ei / NINFO) & 1, failed, err);
+      const bool got = mbar_wait(&info_full[slot], (ei / NINFO) & 1, failed, err, lim);
       if (!__all_sync(0xffffffffu, got)) break;
       const EpiInfo rec = info[slot];
       mbar_arrive(&info_empty[slot]);
       if (rec.flags & INFO_END) break;
       if (rec.flags & INFO_MMA) {
         const uint32_t a = sg % NACC, u = sg / NACC;
-        const bool ok = mbar_wait(&tfull_bar[a], u & 1, failed, err);
+        const bool ok = mbar_wait(&tfull_bar[a], u & 1, failed, err, lim);
         if (!__all_sync(0xffffffffu, ok)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + a * TN;

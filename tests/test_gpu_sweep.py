@@ -89,3 +89,38 @@ def test_onesite_sweeps_lower_the_energy_and_keep_the_form(pkg):
             # rank-deficient sectors keep zero rows; the others are orthonormal
             d = np.diag(g)
             assert np.all((np.abs(d - 1.0) < 1e-10) | (np.abs(d) < 1e-10))
+
+
+def test_mps_save_round_trip(pkg):
+    """mps_save returns the loaded MPS (both forms) in mps_load's layout, and loading the
+    saved copy reproduces sigma exactly."""
+    k, na, nb, M, i = 6, 3, 3, 12, 2
+    H = synth.ab_initio(k, na, nb, 5)
+    left = synth.random_mps(k, na, nb, M, 61, "left")
+    right = synth.random_mps(k, na, nb, M, 62, "right")
+    ctx = pkg.Context(0)
+    ctx.op_build(k, H.h, H.eri, e_core=H.e_core)
+    ctx.mps_load(k, na, nb, left.bonds, left.sites, 0, sites_right=right.sites)
+    out = ctx.mps_save()
+    assert (out["k"], out["n_alpha"], out["n_beta"]) == (k, na, nb)
+    assert [list(map(tuple, b)) for b in out["bonds"]] == [list(map(tuple, b)) for b in left.bonds]
+    for j in range(k):
+        assert np.array_equal(out["sites"][j], np.asarray(left.sites[j]))
+        assert np.array_equal(out["sites_right"][j], np.asarray(right.sites[j]))
+    copy = pkg.Context(0)
+    copy.op_build(k, H.h, H.eri, e_core=H.e_core)
+    copy.mps_load(k, na, nb, out["bonds"], out["sites"], 0, sites_right=out["sites_right"])
+    ys = []
+    for c in (ctx, copy):
+        for b in range(i):
+            c.renormalize(b, +1)
+        for b in range(k - 1, i, -1):
+            c.renormalize(b, -1)
+        n, _ = c.wfn_layout(i, 1)
+        x = torch.tensor(synth.random_vector(n, 8), dtype=torch.float64, device="cuda:0")
+        y = torch.empty_like(x)
+        c.sigma(i, 1, x, y)
+        torch.cuda.synchronize()
+        ys.append(y.cpu().numpy())
+        c.close()
+    assert np.array_equal(ys[0], ys[1])
