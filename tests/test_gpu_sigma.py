@@ -144,6 +144,28 @@ def test_sigma_ppp_polyene_full_size(pkg):
     c.ctx.close()
 
 
+def test_sigma_water_k24_M500_middle_site_both_precisions(pkg):
+    """The headline workload of the benchmark at full size: water-shaped k = 24, 5 alpha 5 beta,
+    M = 500, one-site sigma at the middle position with 6 vectors.  FP64 against the oracle
+    at 1e-12; the split-TF32 path against the oracle at 1e-5 (relative to max|y|)."""
+    cfg = synth.config(3)
+    H = cfg["ham"]
+    c = Case(pkg, H, cfg["M"], H.k // 2 - 1, 1, 303)
+    nvec = cfg["nroots"]
+    x = synth.random_vector(nvec * c.n, 10)
+    y = c.gpu_sigma(x, nvec=nvec)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda:0")
+    yd = torch.full_like(xd, np.nan)
+    c.ctx.sigma(c.i, 1, xd, yd, nvec=nvec, precision=pkg.LRT_MIXED)
+    torch.cuda.synchronize()
+    ymx = yd.cpu().numpy()
+    for v in (0, nvec - 1):
+        yo = c.oracle_sigma(x[v * c.n:(v + 1) * c.n])
+        assert _rel(y[v * c.n:(v + 1) * c.n], yo) < RTOL
+        assert _rel(ymx[v * c.n:(v + 1) * c.n], yo) < 1e-5
+    c.ctx.close()
+
+
 def test_state_errors_are_reported(pkg):
     H = synth.ab_initio(4, 2, 2, 3)
     m = synth.mixed_mps(4, 2, 2, 8, 3, center=1)

@@ -3,7 +3,10 @@
 Every sweep here runs to convergence (sweep_tda raises when max_iter is reached first) and
 its roots are compared with the oracle's Rayleigh-Ritz on the tangent space
 (`oracle.tda.tangent_rr`, the definition of the TDA roots) at 1e-8 Eh for the FP64 path
-and 1e-6 Eh for the mixed path.  The zeroth-order reference is either produced by the CPU
+and 1e-6 Eh for the mixed path.  The convergence threshold on the projected residual sum
+is 1e-12 to 1e-9 by case: below it the sum settles at a floor of its own (about 1e-11 on
+the 5-orbital references, 1e-10 on the 8-orbital one) while the roots agree with the
+definition to about 1e-11 Eh.  The zeroth-order reference is either produced by the CPU
 oracle from seeded inputs and handed to both sides, or (the 8-orbital workload) computed on
 the GPU and read back for the oracle.
 """
@@ -102,7 +105,7 @@ def test_tda_odd_electrons_restart_and_correction_forms(pkg, keep, correction):
     H, t, v, ref = _reference(k, na, nb, M)
     L0, R0, C0, Lam, _ = ref
     w, E0, dim = tda.tangent_rr(H, L0, R0, C0, Lam, n)
-    eps = 1e-11
+    eps = 1e-10
     omega, resid, e0 = _gpu_tda(pkg, H, ref, n, max_iter=150, eps=eps, keep=keep, correction=correction,
                                 max_space=18)
     assert np.all(resid < eps)
@@ -143,11 +146,11 @@ def test_tda_prepare_gauge_matches_tangent_space_definition(pkg):
     w, E0, dim = tda.tangent_rr(H, L0, R0, C0, Lam, n)
     ctx = _prepared(pkg, H, sites)
     g2, e0s = ctx.tda_stationarity()
-    omega, resid, e0 = ctx.sweep_tda(n, max_iter=120, eps=1e-11, keep=4)
+    omega, resid, e0 = ctx.sweep_tda(n, max_iter=120, eps=1e-10, keep=4)
     ctx.close()
     assert abs(e0 - E0) < 1e-10 and abs(e0s - E0) < 1e-10
     assert g2 < 1e-10                       # tight one-site sweeps: a stationary reference
-    assert np.all(resid < 1e-11)
+    assert np.all(resid < 1e-10)
     assert np.abs(omega + e0 - w).max() < TOL_FP64
 
 
@@ -192,11 +195,11 @@ def test_tda_mixed_precision_matches_fp64_and_the_definition(pkg):
     out = {}
     for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
         ctx = _prepared(pkg, H, sites)
-        out[prec] = ctx.sweep_tda(n, max_iter=120, eps=1e-11, keep=4, precision=prec)
+        out[prec] = ctx.sweep_tda(n, max_iter=120, eps=1e-10, keep=4, precision=prec)
         ctx.close()
     (w64, r64, e64), (wmx, rmx, emx) = out[pkg.LRT_FP64], out[pkg.LRT_MIXED]
     assert abs(e64 - emx) < 1e-12          # the reference energy is FP64 in both
-    assert np.all(rmx < 1e-11)
+    assert np.all(rmx < 1e-10)
     assert np.abs(w64 + e64 - w).max() < TOL_FP64
     assert np.abs(w64 - wmx).max() < TOL_MIXED
     assert np.abs(wmx + emx - w).max() < TOL_MIXED
@@ -258,7 +261,7 @@ def test_tda_batched_matches_each_instance_and_the_definition(pkg):
     oracle's Rayleigh-Ritz on its tangent space."""
     cases = [(5, 3, 2, 10, 11), (6, 3, 3, 12, 12), (5, 2, 2, 8, 13)]
     refs, ctxs, streams, defs = [], [], [], []
-    kw = dict(max_iter=150, eps=1e-11, keep=4)
+    kw = dict(max_iter=150, eps=1e-10, keep=4)
     for k, na, nb, M, seed in cases:
         H = synth.ab_initio(k, na, nb, seed)
         sites = _stationary_sites(H, M)
@@ -276,5 +279,5 @@ def test_tda_batched_matches_each_instance_and_the_definition(pkg):
     for j, (w, r, e) in enumerate(refs):
         assert abs(e0[j] - e) < 1e-12
         assert np.abs(omega[j] - w).max() < 1e-10
-        assert np.all(resid[j] < 1e-11)
+        assert np.all(resid[j] < 1e-10)
         assert np.abs(omega[j] + e0[j] - defs[j]).max() < TOL_FP64
