@@ -77,6 +77,12 @@ def parse():
     p.add_argument("--quick-tda", action="store_true", help="TDA side measurement on the 8-orbital workload only")
     p.add_argument("--tda-water", action="store_true",
                    help="also the TDA to convergence on the k = 24, M = 500 workload (long)")
+    p.add_argument("--no-fe2s2", action="store_true",
+                   help="skip the side measurement on the k = 36, M = 1500 workload")
+    p.add_argument("--profile", choices=["fp64", "mixed", "gather"],
+                   help="profiler run: one sigma (fp64 / mixed) or one enlargement + renormalization "
+                        "(gather) at the middle position, between cudaProfilerStart and Stop")
+    p.add_argument("--profile-M", type=int, default=0, help="bond dimension of the profiler run (0: 500)")
     return p.parse_args()
 
 
@@ -295,6 +301,11 @@ def run_ours(args):
             side = {"error": repr(e)}
     del S
     ctx.close()
+    if isinstance(side, dict) and not args.no_fe2s2:
+        try:
+            side["fe2s2_k36_M1500_onesite_8vec"] = fe2s2_sigma(pkg, device, stream)
+        except Exception as e:
+            side["fe2s2_k36_M1500_onesite_8vec"] = {"error": repr(e)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mid, flops_vec)
@@ -485,6 +496,105 @@ def extras(pkg, ctx, device, S, stream, flush, args):
     return out
 
 
+def _device_gb(device):
+    import torch
+    free, total = torch.cuda.mem_get_info(device)
+    return (total - free) / 1e9
+
+
+def fe2s2_sigma(pkg, device, stream):
+    """The [2Fe-2S]-shaped workload (k = 36, 15a + 15b electrons, rank-200 factor, M = 1500):
+    environments of the middle one-site position from random left/right-orthonormal MPS,
+    then sigma with its 8 roots in FP64 and in the mixed form.  Two-electron integrals stay
+    in factor form (the k^4 tensor is never formed)."""
+    import torch
+    cfg = synth.config(5, keep_eri=False)
+    H = cfg["ham"]
+    k, na, nb, M, nvec = H.k, H.n_alpha, H.n_beta, cfg["M"], cfg["nroots"]
+    i = k // 2 - 1
+    left = synth.random_mps(k, na, nb, M, 2024, "left")
+    right = synth.random_mps(k, na, nb, M, 2025, "right")
+    ctx = pkg.Context(device)
+    try:
+        ctx.op_build(k, H.h, None, B=H.B, e_core=H.e_core)
+        ctx.mps_load(k, na, nb, left.bonds, left.sites, 0, sites_right=right.sites)
+        del left, right
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(i):
+            ctx.renormalize(b, +1)
+        for b in range(k - 1, i, -1):
+            ctx.renormalize(b, -1)
+        torch.cuda.synchronize()
+        t_env = time.perf_counter() - t0
+        n, _ = ctx.wfn_layout(i, 1)
+        x = torch.tensor(synth.random_vector(n * nvec, 11), dtype=torch.float64, device=f"cuda:{device}")
+        y = torch.empty_like(x)
+        ym = torch.empty_like(x)
+        ctx.sigma(i, 1, x, y, nvec=nvec)
+        fl = ctx.stats()["flops"]
+        t64 = _timed(lambda: ctx.sigma(i, 1, x, y, nvec=nvec), 3, stream)
+        # H_eff is symmetric: <a, H b> = <H a, b> for the first two vectors
+        a, b, ha, hb = x[:n], x[n:2 * n], y[:n], y[n:2 * n]
+        sym = float((a @ hb - ha @ b).abs() / (a.norm() * hb.norm()))
+        ctx.sigma(i, 1, x, ym, nvec=nvec, precision=pkg.LRT_MIXED)
+        tmx = _timed(lambda: ctx.sigma(i, 1, x, ym, nvec=nvec, precision=pkg.LRT_MIXED), 3, stream)
+        err = float((ym - y).abs().max() / y.abs().max())
+        tf64, tfmx = fl / t64 / 1e9, fl / tmx / 1e9
+        peak, note = tf32_peak()
+        return {"site": i, "wfn_elements": n, "nvec": nvec, "gflop": fl / 1e9, "environment_build_s": t_env,
+                "fp64_ms": t64, "fp64_tflops": tf64, "fp64_frac": tf64 / fp64_peak(None),
+                "mixed_ms": tmx, "mixed_tflops": tfmx, "mixed_frac": tfmx / peak, "mixed_peak_note": note,
+                "mixed_max_rel_err_vs_fp64": err, "symmetry_rel": sym, "device_gb": _device_gb(device)}
+    finally:
+        ctx.close()
+
+
+def run_profile(args):
+    """A short run for ncu: environments of the k = 24 water workload (bond dimension
+    --profile-M) up to the middle one-site position, then one region between
+    cudaProfilerStart and cudaProfilerStop: one sigma with the 6 vectors (fp64, mixed), or
+    the enlargement and renormalization of the left block into the middle bond (gather)."""
+    import torch
+    import paper_1311_1646_gb300 as pkg
+    device = 0
+    torch.cuda.set_device(device)
+    cfg = synth.config(3)
+    H = cfg["ham"]
+    k, na, nb, nvec = H.k, H.n_alpha, H.n_beta, cfg["nroots"]
+    M = args.profile_M or cfg["M"]
+    left = synth.random_mps(k, na, nb, M, 2024, "left")
+    right = synth.random_mps(k, na, nb, M, 2025, "right")
+    ctx = pkg.Context(device)
+    ctx.op_build(k, H.h, H.eri, e_core=H.e_core)
+    ctx.mps_load(k, na, nb, left.bonds, left.sites, 0, sites_right=right.sites)
+    i = k // 2 - 1
+    for b in range(i - 1):
+        ctx.renormalize(b, +1)
+    for b in range(k - 1, i, -1):
+        ctx.renormalize(b, -1)
+    prec = pkg.LRT_MIXED if args.profile == "mixed" else pkg.LRT_FP64
+    x = y = None
+    if args.profile != "gather":
+        ctx.renormalize(i - 1, +1)
+        n, _ = ctx.wfn_layout(i, 1)
+        x = torch.tensor(synth.random_vector(n * nvec, 5), dtype=torch.float64, device=f"cuda:{device}")
+        y = torch.empty_like(x)
+        ctx.sigma(i, 1, x, y, nvec=nvec, precision=prec)    # plans built outside the region
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    if args.profile == "gather":
+        ctx.renormalize(i - 1, +1)
+    else:
+        ctx.sigma(i, 1, x, y, nvec=nvec, precision=prec)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    st = ctx.stats()
+    print(json.dumps({"profile": args.profile, "M": M, "site": i, "device_gb": _device_gb(device),
+                      "flops": st["flops"], "launches": st["launches"]}))
+    ctx.close()
+
+
 def _oracle_setup(H, left, right, i, nsite):
     from oracle import blocks as ob
     from oracle import fock
@@ -626,7 +736,9 @@ if __name__ == "__main__":
         cpu_baseline_child(json.loads(sys.argv[2]))
         sys.exit(0)
     a = parse()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

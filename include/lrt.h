@@ -246,6 +246,18 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega
  * first waits on a barrier that nothing completes, so that call ends through this path
  * after `seconds`; the hook clears itself with that launch.  Not part of the paper. */
 int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next);
+/* sweep_tda_density: sweep_tda, and for every root mu the one-particle transition density
+ * gamma[mu * k * k + p * k + q] = <Psi^mu| sum_sigma a+_{p sigma} a_{q sigma} |Psi0> over spatial
+ * orbitals p, q, with Psi^mu the root's normalized tangent vector (its overall sign is
+ * arbitrary) and sum_pq gamma_pq^2 the square norm that marks single-particle excitations
+ * (Sec. "Qualitative understanding of DMRG-LRT excitations", Table site_excitation).  Taken
+ * from the Ritz vectors of the sweep whose residuals are reported: the vector is split at
+ * the centre site k/2 into one-site pieces, each contracted with the renormalized creation
+ * and pair operators of its environment (FP64, dense per bond: a bond of M states costs
+ * O(M^2) doubles per operator, which limits it to bond dimensions of a few thousand).
+ * Arguments and status as for sweep_tda; gamma holds nroots * k * k doubles (host). */
+int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0,
+                      double* gamma);
 /* lrt_sweeps: *sweeps = the number of sweeps the last sweep_gs (two-site sweeps) or
  * sweep_tda (Davidson iterations after the start sweep) on this context ran. */
 int lrt_sweeps(lrt_t ctx, int* sweeps);

@@ -22,7 +22,7 @@ LRT_CORR_SWEEP = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "lrt_sweeps", "lrt_set_wait_limit", "sigma_batched",
+           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "sweep_tda_density", "lrt_sweeps", "lrt_set_wait_limit", "sigma_batched",
            "sweep_tda_batched"]
 
 _lib = None
@@ -108,6 +108,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     lib.sweep_tda.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp]
+    lib.sweep_tda_density.argtypes = [vp, i, ctypes.POINTER(TdaParams), dp, dp, dp, dp]
     lib.sweep_tda_batched.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(TdaParams), dp, dp, dp]
     for name in EXPORTS:
         if name != "lrt_last_error":
@@ -323,6 +324,24 @@ class Context:
         if rc != 0 and not (allow_noconv and rc == -4):
             self._check(rc, "sweep_tda")
         return om, rs, e0.value
+
+    def sweep_tda_density(self, nroots: int, max_space: int = 0, max_iter: int = 60, eps: float = 1e-14,
+                          pinv_cut: float = 1e-12, seed: int = 12345, allow_noconv: bool = False,
+                          precision: int = LRT_FP64, refine_tol: float = 0.0, keep: int = 0, correction: int = 0,
+                          corr_tol: float = 0.0, start_shift: float = 0.0):
+        """sweep_tda plus the roots' one-particle transition densities: returns
+        (omega, resid, e0, gamma) with gamma of shape (nroots, k, k)."""
+        om = np.zeros(nroots)
+        rs = np.zeros(nroots)
+        e0 = ctypes.c_double()
+        g = np.zeros(nroots * self._k * self._k)
+        p = TdaParams(max_space, max_iter, eps, pinv_cut, seed, precision, refine_tol, keep, correction,
+                      corr_tol, start_shift)
+        rc = self.lib.sweep_tda_density(self.h, nroots, ctypes.byref(p), _dptr(om), _dptr(rs), ctypes.byref(e0),
+                                        _dptr(g))
+        if rc != 0 and not (allow_noconv and rc == -4):
+            self._check(rc, "sweep_tda_density")
+        return om, rs, e0.value, g.reshape(nroots, self._k, self._k)
 
     def _bond_tables(self):
         """Bond tables [(na, nb, dim)] of the MPS the context holds now."""

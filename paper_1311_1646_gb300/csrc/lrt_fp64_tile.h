@@ -31,14 +31,39 @@ constexpr int GEMM_WARPS = GEMM_THREADS / 32;
 constexpr int GEMM_TILE_M = 64;    // equal to GEMM_TM / GEMM_TN of lrt_kernels.h
 constexpr int GEMM_TILE_N = 32;
 
-// a segment with its relative pointers resolved
+// a segment with its relative pointers resolved.  Vector blocking: when avr > 0 the rows of
+// op(A) come in blocks of avr, block v starting at A + v * avs (the same block product for
+// the v-th trial vector); when bvc > 0 the columns of op(B) come in blocks of bvc, block v
+// starting at B + v * bvs.  A tile then spans the products of several vectors at once.
 struct SegS {
   const double* A;
   const double* B;
   int lda, ldb;
   int transA, transB;
   double scale;
+  int avr, bvc;
+  int64_t avs, bvs;
 };
+
+// address of op(A)(row, kl) and op(B)(kl, col) of a segment
+LRT_HD const double* seg_a(const SegS& s, int row, int kl) {
+  const double* a = s.A;
+  if (s.avr > 0) {
+    const int v = row / s.avr;
+    a += (int64_t)v * s.avs;
+    row -= v * s.avr;
+  }
+  return s.transA ? a + (int64_t)kl * s.lda + row : a + (int64_t)row * s.lda + kl;
+}
+LRT_HD const double* seg_b(const SegS& s, int kl, int col) {
+  const double* b = s.B;
+  if (s.bvc > 0) {
+    const int v = col / s.bvc;
+    b += (int64_t)v * s.bvs;
+    col -= v * s.bvc;
+  }
+  return s.transB ? b + (int64_t)col * s.ldb + kl : b + (int64_t)kl * s.ldb + col;
+}
 
 // the segment holding K position p (p < kst[nb]), searching forward from q
 LRT_HD int seg_at(const int* kst, int p, int q) {
@@ -62,9 +87,9 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
       const SegS& s = sd[q];
       const int kl = p - kst[q];
       if (!s.transA)
-        for (int i = warp; i < mt; i += GEMM_WARPS) f(0, i, lane, s.A + (int64_t)(m0 + i) * s.lda + kl);
+        for (int i = warp; i < mt; i += GEMM_WARPS) f(0, i, lane, seg_a(s, m0 + i, kl));
       if (s.transB)
-        for (int j = warp; j < nt; j += GEMM_WARPS) f(1, lane, j, s.B + (int64_t)(n0 + j) * s.ldb + kl);
+        for (int j = warp; j < nt; j += GEMM_WARPS) f(1, lane, j, seg_b(s, kl, n0 + j));
     }
   }
   // lanes along the rows of A stored transposed (K-major)
@@ -77,7 +102,7 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
         if (p >= Kb) break;
         q = seg_at(kst, p, q);
         const SegS& s = sd[q];
-        if (s.transA) f(0, i, kk, s.A + (int64_t)(p - kst[q]) * s.lda + m0 + i);
+        if (s.transA) f(0, i, kk, seg_a(s, m0 + i, p - kst[q]));
       }
   }
   // lanes along the columns of B stored row-major (K-major)
@@ -90,7 +115,7 @@ LRT_HD void stage_chunk(int tid, const SegS* sd, const int* kst, int Kb, int p0,
         if (p >= Kb) break;
         q = seg_at(kst, p, q);
         const SegS& s = sd[q];
-        if (!s.transB) f(1, kk, j, s.B + (int64_t)(p - kst[q]) * s.ldb + n0 + j);
+        if (!s.transB) f(1, kk, j, seg_b(s, p - kst[q], n0 + j));
       }
   }
 }

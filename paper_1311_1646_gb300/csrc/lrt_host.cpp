@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <stdexcept>
@@ -725,10 +726,9 @@ static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vec
                          cudaStream_t st) {
   std::vector<int3> tiles;
   for (size_t i = 0; i < tasks.size(); ++i) {
-    const int tr = (tasks[i].rows + GATHER_TILE - 1) / GATHER_TILE;
-    const int tc = (tasks[i].cols + GATHER_TILE - 1) / GATHER_TILE;
-    for (int a = 0; a < tr; ++a)
-      for (int b = 0; b < tc; ++b) tiles.push_back(make_int3((int)i, a, b));
+    const int64_t nch = ((int64_t)tasks[i].rows * tasks[i].cols + GATHER_CHUNK - 1) / GATHER_CHUNK;
+    if (nch > INT32_MAX) throw Error(LRT_EINVAL, "gather: destination block too large");
+    for (int64_t a = 0; a < nch; ++a) tiles.push_back(make_int3((int)i, (int)a, 0));
   }
   P.tasks.upload(tasks, st);
   P.srcs.upload(srcs, st);
@@ -1835,45 +1835,60 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
         g.b_rel = set_rel(seg2set[u][q]);
       }
   }
-  for (int v = 0; v < nvec; ++v) {
-    for (const GemmOut& x : o1) {
-      GemmOut y = x;
-      y.C = nullptr;
-      y.c_off = x.c_off + (int64_t)v * toff;
-      y.c_rel = 2;
-      y.seg_begin = (int)S1.size();
-      for (int q = 0; q < x.seg_count; ++q) {
-        GemmSeg g = s1[x.seg_begin + q];
-        g.b_off += (int64_t)v * nelem;
-        S1.push_back(g);
-      }
-      O1.push_back(y);
+  // The vectors of a call share every operator block: phase 1 (T = X x) places them side by
+  // side along the columns of one output (x's block of vector v at + v * nelem, T of vector v
+  // at + v * toff), phase 2 (y = sum T Y^T) stacks them along the rows (the T or x rows of
+  // vector v at + v * toff or + v * nelem, y of vector v at + v * nelem).  One output then
+  // holds the same block product for every vector, which fills the GEMM's tiles.
+  const bool vb = nvec > 1;
+  for (const GemmOut& x : o1) {
+    GemmOut y = x;
+    y.C = nullptr;
+    y.c_rel = 2;
+    y.seg_begin = (int)S1.size();
+    if (vb) {
+      y.n = x.n * nvec;
+      y.c_vc = x.n;
+      y.c_vs = toff;
     }
-    for (size_t u = 0; u < osub.size(); ++u) {
-      const OutSub& os = osub[u];
-      const WfnBlock& w = wb[os.blk];
-      const int fx = XF.s.find(w.label_a, w.label_b);
-      int64_t coff = w.off + (int64_t)XF.off[fx][os.r] * w.cols;
-      int ncols = w.cols;
-      if (nsite == 2) {
-        const int fy = YF->s.find(w.label_a, w.label_b);
-        coff += YF->off[fy][os.mcol];
-        ncols = YF->dim[fy][os.mcol];
+    for (int q = 0; q < x.seg_count; ++q) {
+      GemmSeg g = s1[x.seg_begin + q];
+      if (vb) {
+        g.b_vc = x.n;
+        g.b_vs = nelem;
       }
-      GemmOut y{nullptr, coff + (int64_t)v * nelem, w.cols, XF.dim[fx][os.r], ncols, (int)S2.size(),
-                (int)seg2[u].size(), 0, 1};
-      for (size_t q = 0; q < seg2[u].size(); ++q) {
-        GemmSeg g = seg2[u][q];
-        if (g.a_rel) {
-          g.a_off += (int64_t)v * nelem;
-        } else {
-          g.a_rel = 2;
-          g.a_off += (int64_t)v * toff;
-        }
-        S2.push_back(g);
-      }
-      O2.push_back(y);
+      S1.push_back(g);
     }
+    O1.push_back(y);
+  }
+  for (size_t u = 0; u < osub.size(); ++u) {
+    const OutSub& os = osub[u];
+    const WfnBlock& w = wb[os.blk];
+    const int fx = XF.s.find(w.label_a, w.label_b);
+    int64_t coff = w.off + (int64_t)XF.off[fx][os.r] * w.cols;
+    int ncols = w.cols;
+    if (nsite == 2) {
+      const int fy = YF->s.find(w.label_a, w.label_b);
+      coff += YF->off[fy][os.mcol];
+      ncols = YF->dim[fy][os.mcol];
+    }
+    const int m1 = XF.dim[fx][os.r];
+    GemmOut y{nullptr, coff, w.cols, m1 * nvec, ncols, (int)S2.size(), (int)seg2[u].size(), 0, 1};
+    if (vb) {
+      y.c_vr = m1;
+      y.c_vs = nelem;
+    }
+    for (size_t q = 0; q < seg2[u].size(); ++q) {
+      GemmSeg g = seg2[u][q];
+      const int64_t vs = g.a_rel ? nelem : toff;
+      if (!g.a_rel) g.a_rel = 2;
+      if (vb) {
+        g.a_vr = m1;
+        g.a_vs = vs;
+      }
+      S2.push_back(g);
+    }
+    O2.push_back(y);
   }
   build_gemm(plan->p1, O1, S1, c->st);
   build_gemm(plan->p2, O2, S2, c->st);
@@ -1945,11 +1960,33 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
   // has at most half a tile of rows), the tile's columns hold the same product for
   // several vectors, each slot all of one vector's B rows.  Such outputs are stacked once
   // for all vectors, full 128-row blocks as single pieces.
+  // Row slots: an FP64 output of at most half a tile of rows whose A operands are all
+  // per-vector matrices of its own (padded) height and whose B operands are shared
+  // operator blocks takes several vectors in the tile's rows (c_rel 5).
   struct Piece { int o, row0, nrows, srow; };
   struct Stack { int s, v, n, k, b; std::vector<Piece> pc; int nv = 0, wv = 0; };   // nv > 0: vector slots
   std::vector<Stack> stacks;
-  struct Tile { int s, v, o, a, b; int64_t k; int stack; };
+  struct Tile { int s, v, o, a, b; int64_t k; int stack; int rs; };   // rs > 0: vectors v .. v + rs - 1 in row slots
   std::vector<Tile> tiles;
+  // vectors per row-slot tile: at most a tile's rows, fewer when that would leave too few
+  // tiles to spread over the SMs (at least two per CTA)
+  auto row_slots = [&](const TcPlan& tp, const TcPlanOut& o) -> int {
+    if (nvec < 2 || o.tmat >= 0 || o.C || o.seg_count < 1) return 0;
+    const int Rp = (o.m + 7) & ~7;
+    if (2 * Rp > TM) return 0;
+    for (int q = 0; q < o.seg_count; ++q) {
+      const TcPlanSeg& g = tp.segs[o.seg_begin + q];
+      const TcMat& A = tp.mats[g.a];
+      const TcMat& B = tp.mats[g.b];
+      if (A.pool == 0 || B.pool != 0 || A.Rp != Rp) return 0;
+    }
+    return std::min(TM / Rp, nvec);
+  };
+  int64_t rs_products = 0;
+  for (const TcSource& sc : src)
+    for (const TcPlanOut& o : *sc.outs)
+      if (row_slots(*sc.tp, o)) rs_products += (int64_t)nvec * ((o.n + TN - 1) / TN);
+  const int rs_cap = (int)std::max<int64_t>(1, rs_products / (2 * (int64_t)tc_num_ctas(1 << 30)));
   auto pack = [&](std::map<std::tuple<int, int, int>, std::vector<Piece>>& groups, int si, int v,
                   std::vector<Stack>& out) {
     for (auto& kv : groups) {
@@ -2008,21 +2045,30 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
           S.wv = w;
           const int id = (int)stacks.size();
           stacks.push_back(std::move(S));
-          tiles.push_back(Tile{(int)si, v0, stacks[id].pc[0].o, 0, 0, (int64_t)stacks[id].k, id});
+          tiles.push_back(Tile{(int)si, v0, stacks[id].pc[0].o, 0, 0, (int64_t)stacks[id].k, id, 0});
         }
       }
+    }
+    for (size_t i = 0; i < outs.size(); ++i) {
+      const int rs = std::min(row_slots(tp, outs[i]), rs_cap);
+      if (rs <= 0) continue;
+      int64_t kt = 0;
+      for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
+      for (int v0 = 0; v0 < nvec; v0 += rs)
+        for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b)
+          tiles.push_back(Tile{(int)si, v0, (int)i, 0, b, kt, -1, std::min(rs, nvec - v0)});
     }
     for (int v = 0; v < nvec; ++v) {
       std::map<std::tuple<int, int, int>, std::vector<Piece>> groups;   // (B matrix, n, k) -> pieces
       for (size_t i = 0; i < outs.size(); ++i) {
-        if (slot_width(outs[i])) continue;
+        if (slot_width(outs[i]) || row_slots(tp, outs[i])) continue;
         int64_t kt = 0;
         for (int q = 0; q < outs[i].seg_count; ++q) kt += tp.segs[outs[i].seg_begin + q].k;
         const bool stackable = outs[i].tmat >= 0 && outs[i].seg_count == 1 && outs[i].m % TM != 0;
         const int full = outs[i].m / TM;
         for (int a = 0; a < (stackable ? full : (outs[i].m + TM - 1) / TM); ++a)
           for (int b = 0; b < (outs[i].n + TN - 1) / TN; ++b)
-            tiles.push_back(Tile{(int)si, v, (int)i, a, b, kt, -1});
+            tiles.push_back(Tile{(int)si, v, (int)i, a, b, kt, -1, 0});
         if (stackable) {
           const TcPlanSeg& g = tp.segs[outs[i].seg_begin];
           const int rem = outs[i].m - full * TM;
@@ -2035,7 +2081,7 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
         const int id = (int)stacks.size();
         stacks.push_back(std::move(b));
         for (int nb = 0; nb < (stacks[id].n + TN - 1) / TN; ++nb)
-          tiles.push_back(Tile{(int)si, v, stacks[id].pc[0].o, 0, nb, (int64_t)stacks[id].k, id});
+          tiles.push_back(Tile{(int)si, v, stacks[id].pc[0].o, 0, nb, (int64_t)stacks[id].k, id, 0});
       }
     }
   }
@@ -2130,7 +2176,20 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
       h.t.mt = std::min(TM, o.m - h.t.m0);
       h.t.nt = std::min(TN, o.n - h.t.n0);
       h.t.inst = sc.inst;
-      if (o.tmat >= 0) {
+      const int Rp = (o.m + 7) & ~7;
+      if (t.rs > 0) {
+        if (sc.nelem > INT32_MAX || t.rs * Rp > TM)
+          throw Error(LRT_EINVAL, "tensor-core plan: row slots outside the tile");
+        h.t.c_rel = 5;
+        h.t.m0 = 0;
+        h.t.mt = t.rs * Rp;
+        h.t.vslots = t.rs;
+        h.t.vrows = Rp;
+        h.t.vvalid = o.m;
+        h.t.vstride = (int)sc.nelem;
+        h.t.c_off = o.c_off + (int64_t)t.v * sc.nelem;
+        h.t.ldc = o.ldc;
+      } else if (o.tmat >= 0) {
         const TcMat& m = tp.mats[o.tmat];
         h.t.c_rel = 2;
         h.t.t_hi = base(sc, m, t.v, true);
@@ -2165,6 +2224,10 @@ static void build_tc_stream(const std::vector<TcSource>& src, int nvec, int TN, 
         r.s.b_rp = B.Rp;
         r.s.k = g.k;
         r.s.scale = g.scale;
+        if (t.rs > 0) {
+          if (A.pool == 0 || A.Rp != Rp) throw Error(LRT_EINVAL, "tensor-core plan: row-slot operand");
+          r.s.a_vstride = tp.pool_size[A.pool];
+        }
         it.push_back(r);
       }
     }
@@ -2524,10 +2587,26 @@ static std::vector<int64_t> site_rfused(lrt_ctx* c, int b, DevBuf& buf, const Fu
   return rfused_copy(c, b, c->sites[b], buf, F);
 }
 
+// the layout of a right-fused copy (offsets per left sector, total) and its kept gather plan
+static const GatherPlan& rfused_plan(lrt_ctx* c, int b, const SiteTensor& T, const Fused& F, std::vector<int64_t>& off,
+                                     int64_t& tot);
+
 static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, DevBuf& buf, const Fused& F) {
-  const Sectors& Lb = c->bonds[b];
-  std::vector<int64_t> off(Lb.n(), -1);
+  std::vector<int64_t> off;
   int64_t tot = 0;
+  const GatherPlan& g = rfused_plan(c, b, T, F, off, tot);
+  double* p = buf.ensure(tot);
+  CK(cudaMemsetAsync(p, 0, (size_t)std::max<int64_t>(tot, 1) * sizeof(double), c->st));
+  launch_gather(g.tasks.p, g.srcs.p, g.tiles.p, g.ntiles, c->st, p, T.d);
+  CK(cudaGetLastError());
+  return off;
+}
+
+static const GatherPlan& rfused_plan(lrt_ctx* c, int b, const SiteTensor& T, const Fused& F, std::vector<int64_t>& off,
+                                     int64_t& tot) {
+  const Sectors& Lb = c->bonds[b];
+  off.assign(Lb.n(), -1);
+  tot = 0;
   uint64_t h = site_signature(T);
   auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
   for (int q = 0; q < Lb.n(); ++q) {
@@ -2539,8 +2618,6 @@ static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, 
     for (int n = 0; n < 4; ++n) mix((uint64_t)F.off[f][n]);
     mix((uint64_t)F.s.d[f]);
   }
-  double* p = buf.ensure(tot);
-  CK(cudaMemsetAsync(p, 0, (size_t)std::max<int64_t>(tot, 1) * sizeof(double), c->st));
   const std::pair<int, uint64_t> key{b, h};
   auto it = c->rf_plans.find(key);
   if (it == c->rf_plans.end()) {
@@ -2566,10 +2643,7 @@ static std::vector<int64_t> rfused_copy(lrt_ctx* c, int b, const SiteTensor& T, 
     build_gather(*np, tasks, srcs, c->st);
     it = c->rf_plans.emplace(key, std::move(np)).first;
   }
-  const GatherPlan& g = *it->second;
-  launch_gather(g.tasks.p, g.srcs.p, g.tiles.p, g.ntiles, c->st, p, T.d);
-  CK(cudaGetLastError());
-  return off;
+  return *it->second;
 }
 
 // theta(i) = site i (left-fused) x site i+1 (right-fused), in the two-site layout
@@ -3581,13 +3655,6 @@ struct TdaRunner {
     t.sig = sig;
     return enlarge_set(c, X, Xr, i, right, &t);
   }
-  Enl enlarge_left(int i, const FirstOrder& HL) {
-    Enl e;
-    if (HL.empty()) return e;
-    e.f = enl(i, false, 0, *HL.f, HL.r.get());
-    e.r = enl(i, false, 1, *HL.r, HL.f.get());
-    return e;
-  }
   // The first-order site products use sets that are new for every vector and sweep but
   // keep their layout, so their plans are built once per (site, side) with operator
   // addresses relative to the sets and replayed with the new sets as bases: two FP64
@@ -3620,17 +3687,293 @@ struct TdaRunner {
     p.ex.p[3] = nullptr;
     run_plan(p, C0(i).d, y, 1, false);
   }
-  // y = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i  (second line of Eq. sigv2), H_mu^{R_i} the
-  // vector's slot of a set batch (y zeroed by the caller)
-  void dh_right(int i, const SetBatch& HR, int mu, double* y) {
-    if (HR.empty()) return;
+  // ---- the per-vector first-order work of all vectors at once ----
+  // The enlargements, ΔH C0 products and first-order renormalizations of the l vectors of a
+  // site share their layouts, so each is one kept plan replayed over the vectors as the
+  // instances of one launch per phase (instance mu's bases: its own sets).  A template is
+  // (re)built by the first vector whose layout it does not match (its own launch), and a
+  // vector whose layout differs from the template's runs on its own.
+  static void inst_check(int64_t ntiles, int n) {
+    if (n < 1 || n > GEMM_MAX_INST || ntiles * n > INT32_MAX) throw Error(LRT_EINVAL, "batched replay: launch size");
+  }
+  // the enlarged sets of X[mu] (with reverse Xr[mu]) for every mu
+  std::vector<std::unique_ptr<OpSet>> enl_batch(int i, bool right, int rev, const std::vector<const OpSet*>& X,
+                                                const std::vector<const OpSet*>& Xr) {
+    const int nv = (int)X.size();
+    std::vector<std::unique_ptr<OpSet>> out(nv);
+    EnlTemplate& t = enl_tpl[std::make_tuple(i, right ? 1 : 0, rev)];
+    std::vector<int> batch;
+    for (int mu = 0; mu < nv; ++mu) {
+      const uint64_t sig = set_signature(*X[mu], Xr[mu]);
+      if (t.proto && t.sig == sig) {
+        batch.push_back(mu);
+      } else if (batch.empty()) {
+        out[mu] = enl(i, right, rev, *X[mu], Xr[mu]);   // builds the template
+      } else {
+        // another layout than the template's: build a separate set, keep the template
+        EnlTemplate tmp;
+        tmp.sig = sig;
+        out[mu] = enlarge_set(c, *X[mu], Xr[mu], i, right, &tmp);
+      }
+    }
+    const GatherPlan* gp = t.gp.get();
+    for (size_t j0 = 0; j0 < batch.size(); j0 += GEMM_MAX_INST) {
+      const int n = (int)std::min<size_t>(GEMM_MAX_INST, batch.size() - j0);
+      inst_check(gp->ntiles, n);
+      GatherInstSet B{};
+      for (int j = 0; j < n; ++j) {
+        const int mu = batch[j0 + j];
+        out[mu] = layout_copy(*t.proto);
+        alloc_zero(*out[mu], c->st);
+        B.b[j] = GatherBases{out[mu]->d, X[mu]->d, Xr[mu] ? Xr[mu]->d : nullptr};
+      }
+      launch_gather_inst(gp->tasks.p, gp->srcs.p, gp->tiles.p, gp->ntiles, B, n, c->st);
+      CK(cudaGetLastError());
+    }
+    return out;
+  }
+  std::vector<Enl> enlarge_left_batch(int i, const std::vector<FirstOrder>& HL) {
+    std::vector<Enl> e(HL.size());
+    std::vector<const OpSet*> f, r;
+    std::vector<int> idx;
+    for (size_t mu = 0; mu < HL.size(); ++mu)
+      if (!HL[mu].empty()) {
+        idx.push_back((int)mu);
+        f.push_back(HL[mu].f.get());
+        r.push_back(HL[mu].r.get());
+      }
+    if (idx.empty()) return e;
+    auto ef = enl_batch(i, false, 0, f, r);
+    auto er = enl_batch(i, false, 1, r, f);
+    for (size_t j = 0; j < idx.size(); ++j) {
+      e[idx[j]].f = std::move(ef[j]);
+      e[idx[j]].r = std::move(er[j]);
+    }
+    return e;
+  }
+  DevBuf iws;   // per-instance workspaces of the batched replays
+  // one kept two-phase plan over instances: per instance x, y, workspace offset and extras
+  void run_inst(const GemmPlan& p1, const GemmPlan& p2, int n, const GemmInstSet& B) {
+    inst_check(std::max(p1.ntiles, p2.ntiles), n);
+    launch_gemm_fp64_inst(p1.outs.p, p1.segs.p, p1.tiles.p, p1.ntiles, B, n, c->st);
+    launch_gemm_fp64_inst(p2.outs.p, p2.segs.p, p2.tiles.p, p2.ntiles, B, n, c->st);
+    CK(cudaGetLastError());
+  }
+  // out.v(mu) = [H_mu^{L_{i-1}} x h_i x H_0^{R_i}] C0_i for every mu with a first-order set
+  // (Eq. hleft_sb on C0; out zeroed by the caller)
+  void dh_left_batch(int i, const std::vector<Enl>& XE, SiteBatch& out) {
+    const OpSet& Y = *c->R[i + 1];
+    const uint64_t ysig = set_signature(Y, nullptr);
+    std::vector<int> batch;
+    uint64_t sig0 = 0;
+    for (size_t mu = 0; mu < XE.size(); ++mu) {
+      if (!XE[mu].f) continue;
+      const uint64_t sig = set_signature(*XE[mu].f, XE[mu].r.get());
+      if (batch.empty()) {
+        sig0 = sig;
+        batch.push_back((int)mu);
+      } else if (sig == sig0) {
+        batch.push_back((int)mu);
+      } else {
+        dh_left(i, XE[mu], out.v((int)mu));   // another layout: on its own (after the batch's plan is used)
+      }
+    }
+    if (batch.empty()) return;
+    SigmaPlan& p = dh_plan(i, 0, *XE[batch[0]].f, XE[batch[0]].r.get(), sig0, Y, nullptr, ysig);
+    const int64_t ts = std::max<int64_t>(p.tsize, 1);
+    for (size_t j0 = 0; j0 < batch.size(); j0 += GEMM_MAX_INST) {
+      const int n = (int)std::min<size_t>(GEMM_MAX_INST, batch.size() - j0);
+      iws.ensure((size_t)ts * n);
+      GemmInstSet B{};
+      for (int j = 0; j < n; ++j) {
+        const Enl& e = XE[batch[j0 + j]];
+        GemmInst& b = B.b[j];
+        b.x = C0(i).d;
+        b.y = out.v(batch[j0 + j]);
+        b.t = iws.p + (int64_t)j * ts;
+        b.e[0] = e.f->d;
+        b.e[1] = e.r ? e.r->d : nullptr;
+        b.e[2] = Y.d;
+      }
+      run_inst(p.p1, p.p2, n, B);
+    }
+  }
+  // y_mu = [H_0^{L_{i-1}} x h_i x H_mu^{R_i}] C0_i for mu < nv, H_mu^{R_i} slot mu of a set
+  // batch (second line of Eq. sigv2; out zeroed by the caller)
+  void dh_right_batch(int i, const SetBatch& HR, int nv, SiteBatch& out) {
+    if (HR.empty() || nv <= 0) return;
     const OpSet& X = *c->XL[i];
     SigmaPlan& p = dh_plan(i, 1, X, nullptr, set_signature(X, nullptr), *HR.fp, HR.rp.get(), HR.sig);
-    p.ex.p[0] = X.d;
-    p.ex.p[1] = nullptr;
-    p.ex.p[2] = HR.fv(mu);
-    p.ex.p[3] = HR.rv(mu);
-    run_plan(p, C0(i).d, y, 1, false);
+    const int64_t ts = std::max<int64_t>(p.tsize, 1);
+    for (int v0 = 0; v0 < nv; v0 += GEMM_MAX_INST) {
+      const int n = std::min(GEMM_MAX_INST, nv - v0);
+      iws.ensure((size_t)ts * n);
+      GemmInstSet B{};
+      for (int j = 0; j < n; ++j) {
+        GemmInst& b = B.b[j];
+        b.x = C0(i).d;
+        b.y = out.v(v0 + j);
+        b.t = iws.p + (int64_t)j * ts;
+        b.e[0] = X.d;
+        b.e[2] = HR.fv(v0 + j);
+        b.e[3] = HR.rv(v0 + j);
+      }
+      run_inst(p.p1, p.p2, n, B);
+    }
+  }
+  // kept renormalization over instances: terms[mu] for every mu in `batch`, the template
+  // matching them all; returns the new blocks
+  void ren_batch(RenTemplate* tp, const std::vector<std::vector<RenTerm>>& terms, const std::vector<int>& batch,
+                 const std::vector<std::vector<double*>>& kets, const std::vector<std::vector<double*>>& bras,
+                 std::vector<std::unique_ptr<OpSet>>& out) {
+    const int64_t ts = std::max<int64_t>(tp->toff, 1);
+    for (size_t j0 = 0; j0 < batch.size(); j0 += GEMM_MAX_INST) {
+      const int n = (int)std::min<size_t>(GEMM_MAX_INST, batch.size() - j0);
+      iws.ensure((size_t)ts * n);
+      GemmInstSet B{};
+      for (int j = 0; j < n; ++j) {
+        const int mu = batch[j0 + j];
+        out[mu] = layout_copy(*tp->proto);
+        alloc_zero(*out[mu], c->st);
+        GemmInst& b = B.b[j];
+        b.t = iws.p + (int64_t)j * ts;
+        for (size_t t = 0; t < terms[mu].size(); ++t) {
+          b.e[3 * t] = terms[mu][t].E->d;
+          b.e[3 * t + 1] = kets[mu][t];
+          b.e[3 * t + 2] = bras[mu][t];
+        }
+        b.e[REN_BASE_OUT] = out[mu]->d;
+      }
+      run_inst(*tp->p1, *tp->p2, n, B);
+    }
+  }
+  // first-order left sets at bond i+1 (Eq. lopr1st), both directions, for every vector
+  std::vector<FirstOrder> grow_HL_batch(int i, const std::vector<Enl>& XE, const SiteBatch& L1, int nv) {
+    std::vector<FirstOrder> res(nv);
+    const OpSet& XL = *c->XL[i];
+    std::deque<SiteView> views;   // site tensors borrowing the batch's slots (not movable)
+    for (int mu = 0; mu < nv; ++mu) views.emplace_back(lay[i], L1.v(mu));
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<std::vector<RenTerm>> terms(nv);
+      std::vector<std::vector<double*>> kets(nv), bras(nv);
+      for (int mu = 0; mu < nv; ++mu) {
+        const SiteTensor& l1 = views[mu].t;
+        const OpSet* E = XE[mu].f ? (dir == 0 ? XE[mu].f.get() : XE[mu].r.get()) : nullptr;
+        if (E) terms[mu].push_back(RenTerm{E, &L0(i), &L0(i)});
+        terms[mu].push_back(dir == 0 ? RenTerm{&XL, &L0(i), &l1} : RenTerm{&XL, &l1, &L0(i)});
+        for (const RenTerm& t : terms[mu]) {
+          kets[mu].push_back(t.ket->d);
+          bras[mu].push_back(t.bra->d);
+        }
+      }
+      std::vector<std::unique_ptr<OpSet>> out(nv);
+      // vectors grouped by the number of terms (with or without a first-order set)
+      for (int nt = 1; nt <= 2; ++nt) {
+        RenTemplate* tp = rtpl(i, false, dir, nt);
+        std::vector<int> batch;
+        uint64_t sig0 = 0;
+        for (int mu = 0; mu < nv; ++mu) {
+          if ((int)terms[mu].size() != nt) continue;
+          const uint64_t sig = ren_signature(i, false, terms[mu]);
+          if (tp->p1 && tp->sig == sig && (batch.empty() || sig == sig0)) {
+            sig0 = sig;
+            batch.push_back(mu);
+          } else if (batch.empty() && !(tp->p1 && tp->sig == sig)) {
+            out[mu] = renorm_left_terms(c, i, terms[mu], LRT_FP64, tp);   // builds the template
+          } else {
+            out[mu] = renorm_left_terms(c, i, terms[mu], LRT_FP64, nullptr);
+          }
+        }
+        ren_batch(tp, terms, batch, kets, bras, out);
+      }
+      for (int mu = 0; mu < nv; ++mu) (dir == 0 ? res[mu].f : res[mu].r) = std::move(out[mu]);
+    }
+    return res;
+  }
+  // first-order right sets at bond i (Eq. ropr1st), both directions, for every vector
+  std::vector<FirstOrder> grow_HR_batch(int i, const std::vector<FirstOrder>& HR, const SiteBatch& R1, int nv) {
+    std::vector<FirstOrder> res(nv);
+    const OpSet& YR = *c->YR[i];
+    // enlarged first-order sets site (+) H_mu^{R_{i+1}}
+    std::vector<std::unique_ptr<OpSet>> Yf(nv), Yr(nv);
+    {
+      std::vector<const OpSet*> f, r;
+      std::vector<int> idx;
+      for (int mu = 0; mu < nv; ++mu)
+        if (!HR[mu].empty()) {
+          idx.push_back(mu);
+          f.push_back(HR[mu].f.get());
+          r.push_back(HR[mu].r.get());
+        }
+      if (!idx.empty()) {
+        auto ef = enl_batch(i, true, 0, f, r);
+        auto er = enl_batch(i, true, 1, r, f);
+        for (size_t j = 0; j < idx.size(); ++j) {
+          Yf[idx[j]] = std::move(ef[j]);
+          Yr[idx[j]] = std::move(er[j]);
+        }
+      }
+    }
+    // right-fused copies of R0_i (once) and of every R1_mu (one batched gather)
+    const Fused& F = *YR.fused;
+    DevBuf rf0;
+    const std::vector<int64_t> off0 = rfused_copy(c, i, R0(i), rf0, F);
+    std::deque<SiteView> views;   // site tensors borrowing the batch's slots (not movable)
+    for (int mu = 0; mu < nv; ++mu) views.emplace_back(lay[i], R1.v(mu));
+    std::vector<int64_t> off1;
+    int64_t tot1 = 0;
+    const GatherPlan& gp = rfused_plan(c, i, views[0].t, F, off1, tot1);
+    if (off1 != off0) throw Error(LRT_EINVAL, "first-order right set: R1 and R0 layouts differ");
+    DevBuf rf1;
+    const int64_t st1 = std::max<int64_t>(tot1, 1);
+    rf1.ensure((size_t)st1 * nv);
+    CK(cudaMemsetAsync(rf1.p, 0, (size_t)st1 * nv * sizeof(double), c->st));
+    for (int v0 = 0; v0 < nv; v0 += GEMM_MAX_INST) {
+      const int n = std::min(GEMM_MAX_INST, nv - v0);
+      inst_check(gp.ntiles, n);
+      GatherInstSet B{};
+      for (int j = 0; j < n; ++j) B.b[j] = GatherBases{rf1.p + (int64_t)(v0 + j) * st1, R1.v(v0 + j), nullptr};
+      launch_gather_inst(gp.tasks.p, gp.srcs.p, gp.tiles.p, gp.ntiles, B, n, c->st);
+      CK(cudaGetLastError());
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<std::vector<RenTerm>> terms(nv);
+      std::vector<std::vector<double*>> kets(nv), bras(nv);
+      for (int mu = 0; mu < nv; ++mu) {
+        const SiteTensor& r1 = views[mu].t;
+        double* rf1mu = rf1.p + (int64_t)mu * st1;
+        const OpSet* E = dir == 0 ? Yf[mu].get() : Yr[mu].get();
+        if (E) {
+          terms[mu].push_back(RenTerm{E, &R0(i), &R0(i)});
+          kets[mu].push_back(rf0.p);
+          bras[mu].push_back(rf0.p);
+        }
+        terms[mu].push_back(dir == 0 ? RenTerm{&YR, &R0(i), &r1} : RenTerm{&YR, &r1, &R0(i)});
+        kets[mu].push_back(dir == 0 ? rf1mu : rf0.p);
+        bras[mu].push_back(dir == 0 ? rf0.p : rf1mu);
+      }
+      std::vector<std::unique_ptr<OpSet>> out(nv);
+      for (int nt = 1; nt <= 2; ++nt) {
+        RenTemplate* tp = rtpl(i, true, dir, nt);
+        std::vector<int> batch;
+        uint64_t sig0 = 0;
+        for (int mu = 0; mu < nv; ++mu) {
+          if ((int)terms[mu].size() != nt) continue;
+          const uint64_t sig = ren_signature(i, true, terms[mu]);
+          if (tp->p1 && tp->sig == sig && (batch.empty() || sig == sig0)) {
+            sig0 = sig;
+            batch.push_back(mu);
+          } else if (batch.empty() && !(tp->p1 && tp->sig == sig)) {
+            out[mu] = renorm_right_terms(c, i, terms[mu], LRT_FP64, tp);   // builds the template
+          } else {
+            out[mu] = renorm_right_terms(c, i, terms[mu], LRT_FP64, nullptr);
+          }
+        }
+        ren_batch(tp, terms, batch, kets, bras, out);
+      }
+      for (int mu = 0; mu < nv; ++mu) (dir == 0 ? res[mu].f : res[mu].r) = std::move(out[mu]);
+    }
+    return res;
   }
 
   // renormalizations kept for replay, per (site, right, direction, number of terms)
@@ -3638,39 +3981,6 @@ struct TdaRunner {
   RenTemplate* rtpl(int i, bool right, int rev, int nterms) {
     return &ren_tpl[std::make_tuple(i, right ? 1 : 0, rev, nterms)];
   }
-  // first-order left set at bond i+1 (Eq. lopr1st), both directions
-  FirstOrder grow_HL(int i, const Enl& XE, const SiteTensor& L1) {
-    FirstOrder out;
-    const OpSet& XL = *c->XL[i];
-    if (!XE.f) {
-      out.f = renorm_left_terms(c, i, {RenTerm{&XL, &L0(i), &L1}}, LRT_FP64, rtpl(i, false, 0, 1));
-      out.r = renorm_left_terms(c, i, {RenTerm{&XL, &L1, &L0(i)}}, LRT_FP64, rtpl(i, false, 1, 1));
-    } else {
-      out.f = renorm_left_terms(c, i, {RenTerm{XE.f.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L0(i), &L1}}, LRT_FP64,
-                                rtpl(i, false, 0, 2));
-      out.r = renorm_left_terms(c, i, {RenTerm{XE.r.get(), &L0(i), &L0(i)}, RenTerm{&XL, &L1, &L0(i)}}, LRT_FP64,
-                                rtpl(i, false, 1, 2));
-    }
-    return out;
-  }
-  // first-order right set at bond i (Eq. ropr1st), both directions
-  FirstOrder grow_HR(int i, const FirstOrder& HR, const SiteTensor& R1) {
-    FirstOrder out;
-    const OpSet& YR = *c->YR[i];
-    if (HR.empty()) {
-      out.f = renorm_right_terms(c, i, {RenTerm{&YR, &R0(i), &R1}}, LRT_FP64, rtpl(i, true, 0, 1));
-      out.r = renorm_right_terms(c, i, {RenTerm{&YR, &R1, &R0(i)}}, LRT_FP64, rtpl(i, true, 1, 1));
-    } else {
-      auto Yf = enl(i, true, 0, *HR.f, HR.r.get());
-      auto Yr = enl(i, true, 1, *HR.r, HR.f.get());
-      out.f = renorm_right_terms(c, i, {RenTerm{Yf.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R0(i), &R1}}, LRT_FP64,
-                                 rtpl(i, true, 0, 2));
-      out.r = renorm_right_terms(c, i, {RenTerm{Yr.get(), &R0(i), &R0(i)}, RenTerm{&YR, &R1, &R0(i)}}, LRT_FP64,
-                                 rtpl(i, true, 1, 2));
-    }
-    return out;
-  }
-
   // Initial trial vector mu at site i.  seed != 0: SplitMix64 Gaussians; seed == 0: the
   // unit vector on the mu-th lowest diagonal element of H_0^[i] among the components where
   // the reference is small (|C0| < 1/2), a single-site excitation.  Both projected by Q^C.
@@ -3770,13 +4080,309 @@ struct TdaRunner {
   }
   void proj_C(int i, SiteTensor& X) { t_axpby(c, -t_dot(c, C0(i), X, tmp), C0(i), 1.0, X, tmp); }
 
+  // ---- one-particle transition densities of the roots (Sec. "Results", Table
+  // site_excitation): gamma^mu_pq = <Psi^mu| sum_sigma a+_{p sigma} a_{q sigma} |Psi0> ----
+  //
+  // The tangent vector of root mu is split at the centre c = k/2 into pieces that touch one
+  // site each: Q^L C1_i for i < c, C1_c, and C1_i Q^R for i > c (C1_i its mixed-canonical site
+  // tensor, Q^L and Q^R the projectors of Eqs. cwfn1st and right1st).  The pieces sum to the
+  // vector exactly and gamma_pq = sum_i <piece_i| E_pq |Psi0>, each term a contraction of the
+  // piece with the block operators of site i's environment acting on C0_i.  A piece left of
+  // c is orthogonal to every operator acting only on the right block (its fused rows avoid
+  // the span of L0_i), a piece right of c to every operator acting only on the left block, so
+  // the pair operators B_pq = a+_p a_q are needed only where the library keeps them: in the
+  // left blocks up to c and the right blocks from c + 1 on (the normal sides).  Creation
+  // operators exist in every block.  The contractions run densely per bond (sector blocks
+  // scattered into M x M matrices, fermion signs as diagonal factors) on the FP64 GEMM.
+  bool want_gamma = false;
+  std::vector<SiteBatch> keepC;   // the roots' C1_i of the sweep whose residuals are reported
+
+  struct DenseBond {
+    int M = 0;
+    std::vector<int64_t> off;
+  };
+  DenseBond dense_bond(int b) {
+    DenseBond d;
+    const Sectors& S = c->bonds[b];
+    d.off.resize(S.n());
+    for (int q = 0; q < S.n(); ++q) {
+      d.off[q] = d.M;
+      d.M += S.d[q];
+    }
+    return d;
+  }
+  // nv site tensors of site i (stride `stride`) into dense [v][n][Ml][Mr]; sub-blocks scaled by
+  // (-1)^{N(q_l)} when signL
+  void site_to_dense(int i, const double* src, int64_t stride, int nv, double* dst, const DenseBond& dl,
+                     const DenseBond& dr, bool signL) {
+    std::vector<GatherTask> t;
+    std::vector<GatherSrc> s;
+    const SiteTensor& L = lay[i];
+    const Sectors& Lb = c->bonds[i];
+    const int64_t ms = (int64_t)dl.M * dr.M;
+    for (int v = 0; v < nv; ++v)
+      for (int q = 0; q < Lb.n(); ++q)
+        for (int n = 0; n < 4; ++n) {
+          if (L.sub_off[q][n] < 0) continue;
+          const int qr = L.sub_qr[q][n];
+          const int Dl = Lb.d[q], Dr = c->bonds[i + 1].d[qr];
+          const double sg = (signL && ((Lb.a[q] + Lb.b[q]) & 1)) ? -1.0 : 1.0;
+          t.push_back(GatherTask{dst + (int64_t)v * 4 * ms + n * ms + dl.off[q] * dr.M + dr.off[qr], dr.M, Dl, Dr,
+                                 (int)s.size(), 1, 0});
+          s.push_back(GatherSrc{src + (int64_t)v * stride + L.sub_off[q][n], Dr, 0, sg, 0, 0});
+        }
+    run_gathers(c, t, s);
+  }
+  // operator o of set S (basis = the bond's sectors) into a dense M x M matrix
+  void op_to_dense(const OpSet& S, int o, double* dst, const DenseBond& d, std::vector<GatherTask>& t,
+                   std::vector<GatherSrc>& s) {
+    for (int q = 0; q < S.ns(); ++q) {
+      const int qb = S.bra_of(o, q);
+      if (qb < 0 || !S.block_nz(o, q)) continue;
+      t.push_back(GatherTask{dst + d.off[qb] * d.M + d.off[q], d.M, S.basis.d[qb], S.basis.d[q], (int)s.size(), 1, 0});
+      s.push_back(GatherSrc{S.d + S.off_of(o, q), S.basis.d[q], 0, 1.0, 0, 0});
+    }
+  }
+
+  void compute_gamma(int n, double* gamma_out) {
+    const int cc = k / 2;
+    const int64_t kk = (int64_t)k * k;
+    DevBuf dg;
+    dg.ensure((size_t)std::max<int64_t>(n * kk, 1));
+    CK(cudaMemsetAsync(dg.p, 0, (size_t)n * kk * sizeof(double), c->st));
+    static const int NEL[4] = {0, 1, 1, 2};
+    static const double SGN[4] = {1.0, -1.0, -1.0, 1.0};
+    // site annihilators a_sigma[n][n'] (basis |0>, |a>, |b>, |ab>), nonzero entries
+    struct E { int n, m; double v; };
+    const std::vector<E> ann[2] = {{{0, 1, 1.0}, {2, 3, 1.0}}, {{0, 2, 1.0}, {1, 3, -1.0}}};
+    const std::vector<E> cre[2] = {{{1, 0, 1.0}, {3, 2, 1.0}}, {{2, 0, 1.0}, {3, 1, -1.0}}};
+    for (int i = 0; i < k; ++i) {
+      if (keepC[i].nv < n) throw Error(LRT_ESTATE, "transition density: no Ritz vectors kept");
+      const DenseBond dl = dense_bond(i), dr = dense_bond(i + 1);
+      const int Ml = dl.M, Mr = dr.M;
+      const int64_t ms = (int64_t)Ml * Mr, ml2 = (int64_t)Ml * Ml, mr2 = (int64_t)Mr * Mr;
+      // pieces of the centred decomposition
+      SiteBatch P;
+      batch_alloc(c, P, T(i), n, blk);
+      if (i < cc) b_projL(i, keepC[i], n, P);
+      else if (i == cc) b_copy(keepC[i], 0, n, P, 0);
+      else b_projR(i, keepC[i], n, P);
+      DevBuf Dd, C0d, C0P;
+      Dd.ensure((size_t)std::max<int64_t>(n * 4 * ms, 1));
+      C0d.ensure((size_t)std::max<int64_t>(4 * ms, 1));
+      C0P.ensure((size_t)std::max<int64_t>(4 * ms, 1));
+      CK(cudaMemsetAsync(Dd.p, 0, (size_t)n * 4 * ms * sizeof(double), c->st));
+      CK(cudaMemsetAsync(C0d.p, 0, (size_t)4 * ms * sizeof(double), c->st));
+      CK(cudaMemsetAsync(C0P.p, 0, (size_t)4 * ms * sizeof(double), c->st));
+      site_to_dense(i, P.buf.p, P.stride, n, Dd.p, dl, dr, false);
+      site_to_dense(i, C0(i).d, T(i), 1, C0d.p, dl, dr, false);
+      site_to_dense(i, C0(i).d, T(i), 1, C0P.p, dl, dr, true);     // P_L C0
+      auto Dn = [&](int mu, int nn) { return Dd.p + (int64_t)mu * 4 * ms + nn * ms; };
+      auto C0n = [&](int nn) { return C0d.p + nn * ms; };
+      auto CPn = [&](int nn) { return C0P.p + nn * ms; };
+      // dense block operators: left C_x (x < 2i) and, up to the centre, B_xy of same spin;
+      // right C_y (y >= 2(i+1)) and, from the centre on, B_xy of same spin
+      const OpSet* Ls = c->L[i].get();
+      const OpSet* Rs = c->R[i + 1].get();
+      struct Op { int x, y; };              // y < 0: creation operator of x
+      std::vector<Op> lops, rops;
+      for (int x = 0; x < 2 * i; ++x) lops.push_back({x, -1});
+      if (i <= cc)
+        for (int p = 0; p < i; ++p)
+          for (int q = p; q < i; ++q)
+            for (int s = 0; s < 2; ++s) lops.push_back({2 * p + s, 2 * q + s});
+      for (int y = 2 * (i + 1); y < 2 * k; ++y) rops.push_back({y, -1});
+      if (i >= cc)
+        for (int p = i + 1; p < k; ++p)
+          for (int q = p; q < k; ++q)
+            for (int s = 0; s < 2; ++s) rops.push_back({2 * p + s, 2 * q + s});
+      auto key_of = [&](const Op& o) { return o.y < 0 ? Key{KC, o.x, -1} : Key{KB, o.x, o.y}; };
+      DevBuf LO, RO;
+      LO.ensure((size_t)std::max<int64_t>((int64_t)lops.size() * ml2, 1));
+      RO.ensure((size_t)std::max<int64_t>((int64_t)rops.size() * mr2, 1));
+      CK(cudaMemsetAsync(LO.p, 0, LO.n * sizeof(double), c->st));
+      CK(cudaMemsetAsync(RO.p, 0, RO.n * sizeof(double), c->st));
+      {
+        std::vector<GatherTask> t;
+        std::vector<GatherSrc> s;
+        for (size_t a = 0; a < lops.size(); ++a) {
+          const int o = Ls ? Ls->find(key_of(lops[a])) : -1;
+          if (o < 0) throw Error(LRT_EINVAL, "transition density: left block operator missing");
+          op_to_dense(*Ls, o, LO.p + (int64_t)a * ml2, dl, t, s);
+        }
+        for (size_t a = 0; a < rops.size(); ++a) {
+          const int o = Rs ? Rs->find(key_of(rops[a])) : -1;
+          if (o < 0) throw Error(LRT_EINVAL, "transition density: right block operator missing");
+          op_to_dense(*Rs, o, RO.p + (int64_t)a * mr2, dr, t, s);
+        }
+        run_gathers(c, t, s);
+      }
+      const int nLC = 2 * i, nRC = 2 * (k - i - 1);
+      // root-independent: Z_y = (P_L C0_n) C_y  and  Z'_x = (P_L C0_n) C_x^T  (Ml x Mr)
+      DevBuf Z, Zt;
+      Z.ensure((size_t)std::max<int64_t>((int64_t)nRC * 4 * ms, 1));
+      Zt.ensure((size_t)std::max<int64_t>((int64_t)nRC * 4 * ms, 1));
+      if (nRC > 0 && Ml > 0 && Mr > 0) {
+        std::vector<GemmOut> o;
+        std::vector<GemmSeg> g;
+        for (int a = 0; a < nRC; ++a)
+          for (int nn = 0; nn < 4; ++nn) {
+            const double* Cy = RO.p + (int64_t)a * mr2;
+            o.push_back(GemmOut{Z.p + ((int64_t)a * 4 + nn) * ms, 0, Mr, Ml, Mr, (int)g.size(), 1, 0, 0});
+            g.push_back(GemmSeg{CPn(nn), Cy, 0, 0, Mr, Mr, Mr, 0, 0, 0, 0, 1.0});
+            o.push_back(GemmOut{Zt.p + ((int64_t)a * 4 + nn) * ms, 0, Mr, Ml, Mr, (int)g.size(), 1, 0, 0});
+            g.push_back(GemmSeg{CPn(nn), Cy, 0, 0, Mr, Mr, Mr, 0, 1, 0, 0, 1.0});
+          }
+        run_gemms(c, o, g);
+      }
+      // per root: the left (Ml x Ml) and right (Mr x Mr) reduced transition matrices
+      //   left:  ML, MLT, N_a, N_b, N'T_a, N'T_b, K_y (y right), QT_x (x right)
+      //   right: MR, MRT, UT_a, UT_b, V_a, V_b
+      const int nLM = 6 + 2 * nRC, nRM = 6;
+      DevBuf LM, RM;
+      LM.ensure((size_t)std::max<int64_t>((int64_t)n * nLM * ml2, 1));
+      RM.ensure((size_t)std::max<int64_t>((int64_t)n * nRM * mr2, 1));
+      CK(cudaMemsetAsync(LM.p, 0, LM.n * sizeof(double), c->st));
+      CK(cudaMemsetAsync(RM.p, 0, RM.n * sizeof(double), c->st));
+      if (Ml > 0 && Mr > 0) {
+        std::vector<GemmOut> o;
+        std::vector<GemmSeg> g;
+        auto out = [&](double* C, int ld, int m, int nn) { o.push_back(GemmOut{C, 0, ld, m, nn, (int)g.size(), 0, 0, 0}); };
+        // seg: op(A) op(B), A and B dense Ml x Mr (row-major, ld Mr); tA / tB transpose
+        auto seg = [&](const double* A, int tA, const double* B, int tB, int kdim, double s) {
+          g.push_back(GemmSeg{A, B, 0, 0, Mr, Mr, kdim, tA, tB, 0, 0, s});
+          o.back().seg_count++;
+        };
+        for (int mu = 0; mu < n; ++mu) {
+          double* L0m = LM.p + (int64_t)mu * nLM * ml2;
+          double* R0m = RM.p + (int64_t)mu * nRM * mr2;
+          out(L0m + 0 * ml2, Ml, Ml, Ml);                              // ML = sum D_n C0_n^T
+          for (int nn = 0; nn < 4; ++nn) seg(Dn(mu, nn), 0, C0n(nn), 1, Mr, 1.0);
+          out(L0m + 1 * ml2, Ml, Ml, Ml);                              // MLT = sum C0_n D_n^T
+          for (int nn = 0; nn < 4; ++nn) seg(C0n(nn), 0, Dn(mu, nn), 1, Mr, 1.0);
+          for (int s = 0; s < 2; ++s) {
+            out(L0m + (2 + s) * ml2, Ml, Ml, Ml);                      // N_s = sum a_s[n,n'] D_n (P C0_n')^T
+            for (const E& e : ann[s]) seg(Dn(mu, e.n), 0, CPn(e.m), 1, Mr, e.v);
+            out(L0m + (4 + s) * ml2, Ml, Ml, Ml);                      // N'T_s = sum c_s[n,n'] (P C0_n') D_n^T
+            for (const E& e : cre[s]) seg(CPn(e.m), 0, Dn(mu, e.n), 1, Mr, e.v);
+          }
+          for (int a = 0; a < nRC; ++a) {
+            out(L0m + (6 + a) * ml2, Ml, Ml, Ml);                      // K_y = sum s_n D_n Z_{y,n}^T
+            for (int nn = 0; nn < 4; ++nn) seg(Dn(mu, nn), 0, Z.p + ((int64_t)a * 4 + nn) * ms, 1, Mr, SGN[nn]);
+            out(L0m + (6 + nRC + a) * ml2, Ml, Ml, Ml);                // QT_x = sum s_n Z'_{x,n} D_n^T
+            for (int nn = 0; nn < 4; ++nn) seg(Zt.p + ((int64_t)a * 4 + nn) * ms, 0, Dn(mu, nn), 1, Mr, SGN[nn]);
+          }
+          // right matrices: contractions over the left index (k = Ml), A and B transposed roles
+          auto rseg = [&](const double* A, const double* B, double s) {   // A^T B, A and B Ml x Mr
+            g.push_back(GemmSeg{A, B, 0, 0, Mr, Mr, Ml, 1, 0, 0, 0, s});
+            o.back().seg_count++;
+          };
+          out(R0m + 0 * mr2, Mr, Mr, Mr);                              // MR = sum D_n^T C0_n
+          for (int nn = 0; nn < 4; ++nn) rseg(Dn(mu, nn), C0n(nn), 1.0);
+          out(R0m + 1 * mr2, Mr, Mr, Mr);                              // MRT = sum C0_n^T D_n
+          for (int nn = 0; nn < 4; ++nn) rseg(C0n(nn), Dn(mu, nn), 1.0);
+          for (int s = 0; s < 2; ++s) {
+            out(R0m + (2 + s) * mr2, Mr, Mr, Mr);                      // UT_s = sum c_s[n,n'] s_n' C0_n'^T D_n
+            for (const E& e : cre[s]) rseg(C0n(e.m), Dn(mu, e.n), e.v * SGN[e.m]);
+            out(R0m + (4 + s) * mr2, Mr, Mr, Mr);                      // V_s = sum a_s[n,n'] s_n' D_n^T C0_n'
+            for (const E& e : ann[s]) rseg(Dn(mu, e.n), C0n(e.m), e.v * SGN[e.m]);
+          }
+        }
+        run_gemms(c, o, g);
+      }
+      // dot products: every left operator with every left matrix, every right operator with
+      // every right matrix (per root), and the site-diagonal terms <D_n, C0_n>
+      const int nl = (int)lops.size(), nr = (int)rops.size();
+      const int64_t nres = (int64_t)n * (nl * nLM + nr * nRM + 4);
+      DevBuf res;
+      res.ensure((size_t)std::max<int64_t>(nres, 1));
+      CK(cudaMemsetAsync(res.p, 0, (size_t)nres * sizeof(double), c->st));
+      dwork.ensure((size_t)dot_work(std::max<int64_t>(std::max<int64_t>((int64_t)nl * nLM, (int64_t)nr * nRM), 4)));
+      auto rL = [&](int mu, int a, int m) { return (int64_t)mu * (nl * nLM + nr * nRM + 4) + (int64_t)a * nLM + m; };
+      auto rR = [&](int mu, int a, int m) {
+        return (int64_t)mu * (nl * nLM + nr * nRM + 4) + (int64_t)nl * nLM + (int64_t)a * nRM + m;
+      };
+      auto rS = [&](int mu, int nn) { return (int64_t)mu * (nl * nLM + nr * nRM + 4) + (int64_t)nl * nLM + nr * nRM + nn; };
+      for (int mu = 0; mu < n; ++mu) {
+        if (nl > 0 && Ml > 0)
+          launch_pair_dots_strided(LO.p, ml2, nl, LM.p + (int64_t)mu * nLM * ml2, ml2, nLM, ml2, res.p + rL(mu, 0, 0),
+                                   dwork.p, c->st);
+        if (nr > 0 && Mr > 0)
+          launch_pair_dots_strided(RO.p, mr2, nr, RM.p + (int64_t)mu * nRM * mr2, mr2, nRM, mr2, res.p + rR(mu, 0, 0),
+                                   dwork.p, c->st);
+        if (ms > 0) launch_vdots(Dn(mu, 0), ms, C0d.p, ms, 4, ms, res.p + rS(mu, 0), false, dwork.p, c->st);
+      }
+      // gamma[mu][p][q] += sum of coefficient x result, lists per output entry
+      std::vector<std::vector<std::pair<int64_t, double>>> terms((size_t)n * kk);
+      auto add = [&](int mu, int p, int q, int64_t r, double v) { terms[(size_t)mu * kk + (size_t)p * k + q].push_back({r, v}); };
+      for (int mu = 0; mu < n; ++mu) {
+        for (int nn = 0; nn < 4; ++nn)
+          if (NEL[nn]) add(mu, i, i, rS(mu, nn), NEL[nn]);
+        for (int a = 0; a < nl; ++a) {
+          const Op& op = lops[a];
+          if (op.y >= 0) {                         // B_xy, both in the left block
+            const int p = op.x / 2, q = op.y / 2;
+            add(mu, p, q, rL(mu, a, 0), 1.0);
+            if (p != q) add(mu, q, p, rL(mu, a, 1), 1.0);
+            continue;
+          }
+          const int x = op.x, p = x / 2, s = x & 1;
+          add(mu, p, i, rL(mu, a, 2 + s), 1.0);    // a+_x (left) a_(i s)
+          add(mu, i, p, rL(mu, a, 4 + s), -1.0);   // a+_(i s) a_x (left)
+          for (int b = 0; b < nRC; ++b) {
+            const int y = 2 * (i + 1) + b;
+            if ((y & 1) != s) continue;
+            add(mu, p, y / 2, rL(mu, a, 6 + b), 1.0);          // a+_x (left) a_y (right)
+            add(mu, y / 2, p, rL(mu, a, 6 + nRC + b), -1.0);   // a+_y (right) a_x (left)
+          }
+        }
+        for (int a = 0; a < nr; ++a) {
+          const Op& op = rops[a];
+          if (op.y >= 0) {                         // B_xy, both in the right block
+            const int p = op.x / 2, q = op.y / 2;
+            add(mu, p, q, rR(mu, a, 0), 1.0);
+            if (p != q) add(mu, q, p, rR(mu, a, 1), 1.0);
+            continue;
+          }
+          const int y = op.x, q = y / 2, s = y & 1;
+          add(mu, i, q, rR(mu, a, 2 + s), 1.0);    // a+_(i s) a_y (right)
+          add(mu, q, i, rR(mu, a, 4 + s), -1.0);   // a+_y (right) a_(i s)
+        }
+      }
+      std::vector<int> beg(1, 0), idx;
+      std::vector<double> coef;
+      for (auto& tl : terms) {
+        for (auto& pr : tl) {
+          idx.push_back((int)pr.first);
+          coef.push_back(pr.second);
+        }
+        beg.push_back((int)idx.size());
+      }
+      DevArray<int> dbeg, didx;
+      DevArray<double> dcf;
+      dbeg.upload(beg, c->st);
+      didx.upload(idx, c->st);
+      dcf.upload(coef, c->st);
+      launch_gather_sum(res.p, dbeg.p, didx.p, dcf.p, (int)(n * kk), dg.p, c->st);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(c->st));
+    }
+    CK(cudaMemcpyAsync(gamma_out, dg.p, (size_t)n * kk * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+
   // Fig. alg:dmrgtda.  The trial vectors of a sweep are processed together at every site:
   // their site tensors are contiguous batches, the bond and site products of the gauge
   // shifts and projections are grouped launches over all vectors, the H_0 products are
   // multi-vector sigma calls, and the reduced matrices and residual norms accumulate on the
   // device; the host synchronizes once per sweep (and in the first, for the start vectors).
-  void run(int n, double* theta_out, double* resid_out, int* iters_out) {
+  void run(int n, double* theta_out, double* resid_out, int* iters_out, double* gamma_out = nullptr) {
     setup();
+    want_gamma = gamma_out != nullptr;
+    if (want_gamma) {
+      keepC.clear();
+      keepC.resize(k);
+    }
     const int N = P.max_space > 0 ? P.max_space : std::min(JACOBI_MAXN, std::max(8 * n, 24));
     if (N > JACOBI_MAXN || 2 * n > JACOBI_MAXN)
       throw Error(LRT_EINVAL, "sweep_tda: max_space and 2 nroots must not exceed " + std::to_string(JACOBI_MAXN));
@@ -3864,15 +4470,16 @@ struct TdaRunner {
             b_lmul(i, lam[0], R1, m, C1, false);
           }
         }
+        if (want_gamma && m > 0) {       // the roots' site tensors of this sweep (transition densities)
+          batch_alloc(c, keepC[i], T(i), n, blk);
+          b_copy(C1, 0, n, keepC[i], 0);
+        }
         // [H_mu^{L} x h x H_0^{R}] C0 for every vector (Eq. sigv2, first line); it enters
         // both the site sigma of the corrections and the reduced matrices below
-        std::vector<Enl> XE(l);
         SiteBatch dHC0;
         batch_alloc(c, dHC0, T(i), l, blk);
-        for (int mu = 0; mu < l; ++mu) {
-          XE[mu] = enlarge_left(i, HL[mu]);
-          dh_left(i, XE[mu], dHC0.v(mu));
-        }
+        std::vector<Enl> XE = enlarge_left_batch(i, HL);
+        dh_left_batch(i, XE, dHC0);
         // correction vectors (Eqs. sigv1, rnorm, error, param)
         if (first) {
           for (int mu = 0; mu < n; ++mu) start_site(i, mu, C1.v(m + mu));
@@ -3883,7 +4490,7 @@ struct TdaRunner {
           batch_alloc(c, t1, T(i), n, blk);
           h0(i, C1, n, sig);
           b_axpy(1.0, dHC0, 0, sig, 0, n);
-          for (int mu = 0; mu < n; ++mu) dh_right(i, HRrot, mu, t1.v(mu));
+          dh_right_batch(i, HRrot, n, t1);
           b_axpy(1.0, t1, 0, sig, 0, n);
           launch_rank1_batch(C1.v(0), C1.stride, d_theta.p, -1.0, n, sig.v(0), sig.stride, T(i), c->st);  // r
           b_projC(i, sig, 0, n);                                                                           // Q^C r
@@ -3916,11 +4523,7 @@ struct TdaRunner {
         // Eqs. left1st and lopr1st
         batch_alloc(c, L1[i], T(i), l, blk);
         b_rmul(i, Ct, l, ilam[i + 1], L1[i], false);
-        if (i + 1 < k)
-          for (int mu = 0; mu < l; ++mu) {
-            SiteView v(lay[i], L1[i].v(mu));
-            HL[mu] = grow_HL(i, XE[mu], v.t);
-          }
+        if (i + 1 < k) HL = grow_HL_batch(i, XE, L1[i], l);
         Cprev = std::move(C1);
       }
       HL.clear();
@@ -3950,10 +4553,11 @@ struct TdaRunner {
         batch_alloc(c, newR1[i], T(i), l, blk);
         b_lmul(i, ilam[i], pr, l, newR1[i], false);
         if (i > 0) {
+          HR = grow_HR_batch(i, HR, newR1[i], l);
+          set_batch(c, newHR[i], *HR[0].f, *HR[0].r, l);
           for (int mu = 0; mu < l; ++mu) {
-            SiteView v(lay[i], newR1[i].v(mu));
-            HR[mu] = grow_HR(i, HR[mu], v.t);
-            if (mu == 0) set_batch(c, newHR[i], *HR[0].f, *HR[0].r, l);
+            if (HR[mu].f->total != HR[0].f->total || HR[mu].r->total != HR[0].r->total)
+              throw Error(LRT_EINVAL, "sweep_tda: first-order right sets of different layouts");
             if (HR[mu].f->total > 0)
               CK(cudaMemcpyAsync(newHR[i].fv(mu), HR[mu].f->d, (size_t)HR[mu].f->total * sizeof(double),
                                  cudaMemcpyDeviceToDevice, c->st));
@@ -3995,6 +4599,7 @@ struct TdaRunner {
             resid_out[mu] = r2[mu];
           }
           if (iters_out) *iters_out = it;
+          if (want_gamma) compute_gamma(n, gamma_out);
           if (!conv) throw Error(LRT_ENOCONV, "sweep_tda: not converged within max_iter");
           return;
         }
@@ -4724,6 +5329,35 @@ int sweep_tda(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, dou
   }
   if (e0) *e0 = E0;
   if (rc != LRT_OK) ctx->err = "sweep_tda: not converged within max_iter (results written)";
+  return rc;
+}
+
+int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* p, double* omega, double* resid, double* e0,
+                      double* gamma) {
+  int rc = LRT_OK;
+  std::vector<double> th(std::max(nroots, 1), 0.0), rs(std::max(nroots, 1), 0.0);
+  double E0 = 0.0;
+  const int r = guard(ctx, [&] {
+    if (!ctx->tda || !ctx->tda->loaded) throw Error(LRT_ESTATE, "sweep_tda_density: tda_load first");
+    if (!p || nroots <= 0 || !omega || !resid || !gamma) throw Error(LRT_EINVAL, "sweep_tda_density: bad arguments");
+    TdaRunner R(ctx, *p);
+    int its = 0;
+    try {
+      R.run(nroots, th.data(), rs.data(), &its, gamma);
+    } catch (const Error& e) {
+      if (e.code != LRT_ENOCONV) throw;
+      rc = LRT_ENOCONV;
+    }
+    E0 = R.E0;
+    ctx->last_sweeps = its;
+  });
+  if (r != LRT_OK) return r;
+  for (int mu = 0; mu < nroots; ++mu) {
+    omega[mu] = th[mu] - E0;
+    resid[mu] = rs[mu];
+  }
+  if (e0) *e0 = E0;
+  if (rc != LRT_OK) ctx->err = "sweep_tda_density: not converged within max_iter (results written)";
   return rc;
 }
 

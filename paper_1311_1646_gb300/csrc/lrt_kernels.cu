@@ -23,24 +23,30 @@ namespace lrt {
 // loads are unrolled so that several are in flight: a tile costs a few memory round trips
 // instead of two per source.  Transposed sources are read straight from global memory;
 // the CTA's reads of one source block stay in L1.
+// A work item is a chunk of GATHER_CHUNK consecutive elements of the task's row-major
+// destination (thread t owns elements t, t + 256, ...): blocks only a few columns wide
+// still fill every lane, where square 32 x 32 tiles left most of them idle.  Each
+// element sums its sources in the order they are listed.
 constexpr int GATHER_SRC_STAGE = 64;
+constexpr int GATHER_PER_THREAD = GATHER_CHUNK / 256;
 
-__global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restrict__ tasks,
-                                                     const GatherSrc* __restrict__ srcs,
-                                                     const int3* __restrict__ tiles, int ntiles,
-                                                     double* __restrict__ dbase,
-                                                     const double* __restrict__ sbase1,
-                                                     const double* __restrict__ sbase2) {
-  __shared__ GatherSrc sd[GATHER_SRC_STAGE];
-  const int w = blockIdx.x;
-  if (w >= ntiles) return;
-  const int3 wi = tiles[w];
+__device__ __forceinline__ void gather_item(const GatherTask* __restrict__ tasks, const GatherSrc* __restrict__ srcs,
+                                            const int3 wi, double* dbase, const double* sbase1,
+                                            const double* sbase2, GatherSrc* sd) {
   GatherTask t = tasks[wi.x];
   if (dbase) t.dst = dbase + t.dst_off;
-  const int r0 = wi.y * GATHER_TILE, c0 = wi.z * GATHER_TILE;
-  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  const int tid = ty * 32 + tx;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int tid = threadIdx.x;
+  const int64_t n = (int64_t)t.rows * t.cols;
+  const int64_t e0 = (int64_t)wi.y * GATHER_CHUNK + tid;
+  int rr[GATHER_PER_THREAD], cc[GATHER_PER_THREAD];
+  double acc[GATHER_PER_THREAD];
+#pragma unroll
+  for (int i = 0; i < GATHER_PER_THREAD; ++i) {
+    const int64_t e = e0 + 256 * i;
+    rr[i] = e < n ? (int)(e / t.cols) : -1;
+    cc[i] = e < n ? (int)(e - (int64_t)rr[i] * t.cols) : 0;
+    acc[i] = 0.0;
+  }
   for (int s0 = 0; s0 < t.src_count; s0 += GATHER_SRC_STAGE) {
     const int ns = min(GATHER_SRC_STAGE, t.src_count - s0);
     __syncthreads();   // the previous descriptors are no longer read
@@ -57,23 +63,48 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restric
       const double sc = sd[s].scale;
       const bool tr = sd[s].trans != 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = r0 + ty + 8 * i, c = c0 + tx;
-        if (r < t.rows && c < t.cols) acc[i] += sc * (tr ? src[(int64_t)c * ld + r] : src[(int64_t)r * ld + c]);
-      }
+      for (int i = 0; i < GATHER_PER_THREAD; ++i)
+        if (rr[i] >= 0) acc[i] += sc * (tr ? src[(int64_t)cc[i] * ld + rr[i]] : src[(int64_t)rr[i] * ld + cc[i]]);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 8 * i, c = c0 + tx;
-    if (r < t.rows && c < t.cols) t.dst[(int64_t)r * t.ld_dst + c] += acc[i];
-  }
+  for (int i = 0; i < GATHER_PER_THREAD; ++i)
+    if (rr[i] >= 0) t.dst[(int64_t)rr[i] * t.ld_dst + cc[i]] += acc[i];
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(const GatherTask* __restrict__ tasks,
+                                                     const GatherSrc* __restrict__ srcs,
+                                                     const int3* __restrict__ tiles, int ntiles,
+                                                     double* __restrict__ dbase,
+                                                     const double* __restrict__ sbase1,
+                                                     const double* __restrict__ sbase2) {
+  __shared__ GatherSrc sd[GATHER_SRC_STAGE];
+  if ((int)blockIdx.x >= ntiles) return;
+  gather_item(tasks, srcs, tiles[blockIdx.x], dbase, sbase1, sbase2, sd);
+}
+
+__global__ void __launch_bounds__(256) gather_inst_kernel(const GatherTask* __restrict__ tasks,
+                                                          const GatherSrc* __restrict__ srcs,
+                                                          const int3* __restrict__ tiles, int ntiles,
+                                                          const __grid_constant__ GatherInstSet P, int ninst) {
+  __shared__ GatherSrc sd[GATHER_SRC_STAGE];
+  const int w = blockIdx.x / ninst;
+  if (w >= ntiles) return;
+  const GatherBases* b = &P.b[blockIdx.x % ninst];
+  gather_item(tasks, srcs, tiles[w], b->d, b->s1, b->s2, sd);
 }
 
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
                    cudaStream_t st, double* dbase, const double* sbase1, const double* sbase2) {
   if (ntiles <= 0) return;
-  gather_kernel<<<ntiles, dim3(32, 8), 0, st>>>(tasks, srcs, tiles, ntiles, dbase, sbase1, sbase2);
+  gather_kernel<<<ntiles, 256, 0, st>>>(tasks, srcs, tiles, ntiles, dbase, sbase1, sbase2);
+}
+
+void launch_gather_inst(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
+                        const GatherInstSet& bases, int ninst, cudaStream_t st) {
+  // the caller checks 1 <= ninst <= 64 and ntiles * ninst < 2^31
+  if (ntiles <= 0 || ninst <= 0) return;
+  gather_inst_kernel<<<(unsigned)((long long)ntiles * ninst), 256, 0, st>>>(tasks, srcs, tiles, ntiles, bases, ninst);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,26 +171,13 @@ __device__ __forceinline__ void fma_chunk(double (&acc)[GEMM_MAXE], const uint32
 // a chain of compares measured ~10% slower on the small tiles of phase 1
 static_assert(GEMM_MAXE == 16, "the switch below lists the output counts 1..16");
 
-__global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
-                                                                    const GemmSeg* __restrict__ segs,
-                                                                    const int3* __restrict__ tiles, int ntiles,
-                                                                    const double* __restrict__ xbase,
-                                                                    double* __restrict__ ybase,
-                                                                    double* __restrict__ tbase,
-                                                                    const GemmBases* __restrict__ multi,
-                                                                    const GemmExtra ex) {
+// one tile of the grouped GEMM; extra(i) resolves extra base i of the tile's instance
+template <class Extra>
+__device__ __forceinline__ void gemm_fp64_tile(const GemmOut* __restrict__ outs, const GemmSeg* __restrict__ segs,
+                                               const int3 wi, const double* xbase, double* ybase, double* tbase,
+                                               const GemmOut& o, const Extra& extra) {
   extern __shared__ __align__(16) unsigned char gemm_smem_raw[];
   GemmSmem& S = *reinterpret_cast<GemmSmem*>(gemm_smem_raw);
-  const int w = blockIdx.x;
-  if (w >= ntiles) return;
-  const int3 wi = tiles[w];
-  const GemmOut o = outs[wi.x];
-  if (multi) {
-    const GemmBases b = multi[o.inst];
-    xbase = b.x;
-    ybase = b.y;
-    tbase = b.t;
-  }
   const int m0 = wi.y >> 8, mt = wi.y & 255, n0 = wi.z >> 8, nt = wi.z & 255;
   const int ne = mt * nt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -183,9 +201,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(cons
       int k = 0;
       if (lane < nb) {
         GemmSeg g = segs[o.seg_begin + b0 + lane];
-        if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : g.a_rel == 2 ? tbase : extra_base(ex, g.a_rel - 3)) + g.a_off;
-        if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : g.b_rel == 2 ? tbase : extra_base(ex, g.b_rel - 3)) + g.b_off;
-        S.sd[lane] = SegS{g.A, g.B, g.lda, g.ldb, g.transA, g.transB, g.scale};
+        if (g.a_rel) g.A = (g.a_rel == 1 ? xbase : g.a_rel == 2 ? tbase : extra(g.a_rel - 3)) + g.a_off;
+        if (g.b_rel) g.B = (g.b_rel == 1 ? xbase : g.b_rel == 2 ? tbase : extra(g.b_rel - 3)) + g.b_off;
+        S.sd[lane] = SegS{g.A, g.B, g.lda, g.ldb, g.transA, g.transB, g.scale, g.a_vr, g.b_vc, g.a_vs, g.b_vs};
         k = g.k;
       }
       int incl = k;   // inclusive prefix of k over the lanes
@@ -247,11 +265,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(cons
       __syncthreads();           // buffer buf is free for chunk c + 2
     }
   }
+  double* cbase = o.c_rel ? (o.c_rel == 1 ? ybase : o.c_rel == 2 ? tbase : extra(o.c_rel - 3)) + o.c_off : o.C;
 #pragma unroll
   for (int j = 0; j < GEMM_MAXE; ++j) {
     if (j >= cnt) break;
-    double* c = (o.c_rel ? (o.c_rel == 1 ? ybase : o.c_rel == 2 ? tbase : extra_base(ex, o.c_rel - 3)) + o.c_off : o.C) +
-                (int64_t)(m0 + (int)(rc[j] >> 16)) * o.ldc + (n0 + (int)(rc[j] & 0xFFFFu));
+    int r = m0 + (int)(rc[j] >> 16), col = n0 + (int)(rc[j] & 0xFFFFu);
+    double* c = cbase;
+    if (o.c_vr > 0) {            // row blocks of the vectors
+      const int v = r / o.c_vr;
+      c += (int64_t)v * o.c_vs;
+      r -= v * o.c_vr;
+    } else if (o.c_vc > 0) {     // column blocks of the vectors
+      const int v = col / o.c_vc;
+      c += (int64_t)v * o.c_vs;
+      col -= v * o.c_vc;
+    }
+    c += (int64_t)r * o.ldc + col;
     *c = o.accumulate ? (*c + acc[j]) : acc[j];
   }
 }
@@ -277,6 +306,41 @@ int gemm_fp64_slots() {
 // Opt the FP64 GEMM into its dynamic shared memory on the current device, once per device.
 // On failure the attribute stays unset, the error is the runtime's last error, and the
 // caller's launch check reports it.
+__global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(const GemmOut* __restrict__ outs,
+                                                                    const GemmSeg* __restrict__ segs,
+                                                                    const int3* __restrict__ tiles, int ntiles,
+                                                                    const double* __restrict__ xbase,
+                                                                    double* __restrict__ ybase,
+                                                                    double* __restrict__ tbase,
+                                                                    const GemmBases* __restrict__ multi,
+                                                                    const GemmExtra ex) {
+  const int w = blockIdx.x;
+  if (w >= ntiles) return;
+  const int3 wi = tiles[w];
+  const GemmOut o = outs[wi.x];
+  if (multi) {
+    const GemmBases b = multi[o.inst];
+    xbase = b.x;
+    ybase = b.y;
+    tbase = b.t;
+  }
+  gemm_fp64_tile(outs, segs, wi, xbase, ybase, tbase, o, [&](int i) { return extra_base(ex, i); });
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_inst_kernel(const GemmOut* __restrict__ outs,
+                                                                         const GemmSeg* __restrict__ segs,
+                                                                         const int3* __restrict__ tiles,
+                                                                         int ntiles,
+                                                                         const __grid_constant__ GemmInstSet P,
+                                                                         int ninst) {
+  const int w = blockIdx.x / ninst;
+  if (w >= ntiles) return;
+  const GemmInst* b = &P.b[blockIdx.x % ninst];
+  const int3 wi = tiles[w];
+  const GemmOut o = outs[wi.x];
+  gemm_fp64_tile(outs, segs, wi, b->x, b->y, b->t, o, [&](int i) { return b->e[i]; });
+}
+
 static cudaError_t gemm_fp64_smem_attr() {
   static std::atomic<int> done[MAX_DEVICES];
   int dev = 0;
@@ -284,11 +348,13 @@ static cudaError_t gemm_fp64_smem_attr() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
   if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
-  e = cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
-  if (e != cudaSuccess) return e;
-  // all of the unified L1 as shared memory, so GEMM_CTAS CTAs fit on an SM
-  e = cudaFuncSetAttribute(gemm_fp64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return e;
+  for (const void* f : {(const void*)gemm_fp64_kernel, (const void*)gemm_fp64_inst_kernel}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GemmSmem));
+    if (e != cudaSuccess) return e;
+    // all of the unified L1 as shared memory, so GEMM_CTAS CTAs fit on an SM
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+  }
   done[dev].store(1, std::memory_order_release);   // concurrent first calls set the same values
   return cudaSuccess;
 }
@@ -300,6 +366,15 @@ void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tile
   const GemmExtra ex = extra ? *extra : GemmExtra{};
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase,
                                                                   nullptr, ex);
+}
+
+void launch_gemm_fp64_inst(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                           const GemmInstSet& bases, int ninst, cudaStream_t st) {
+  // the caller checks 1 <= ninst <= GEMM_MAX_INST and ntiles * ninst < 2^31
+  if (ntiles <= 0 || ninst <= 0) return;
+  if (gemm_fp64_smem_attr() != cudaSuccess) return;
+  gemm_fp64_inst_kernel<<<(unsigned)((long long)ntiles * ninst), GEMM_THREADS, sizeof(GemmSmem), st>>>(
+      outs, segs, tiles, ntiles, bases, ninst);
 }
 
 void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
@@ -580,6 +655,22 @@ void launch_pair_dots_strided(const double* A, int64_t lda, int na, const double
   if (na <= 0 || nb <= 0) return;
   vdots_part_kernel<<<dim3(DOT_CHUNKS, na * nb), 256, 0, st>>>(A, lda, B, ldb, nb, n, 1, work);
   vdots_sum_kernel<<<(na * nb + 127) / 128, 128, 0, st>>>(work, na * nb, out, 0);
+}
+
+__global__ void gather_sum_kernel(const double* __restrict__ src, const int* __restrict__ beg,
+                                  const int* __restrict__ idx, const double* __restrict__ coef, int nout,
+                                  double* __restrict__ out) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nout) return;
+  double s = 0.0;
+  for (int j = beg[d]; j < beg[d + 1]; ++j) s = fma(coef[j], src[idx[j]], s);
+  out[d] += s;
+}
+
+void launch_gather_sum(const double* src, const int* beg, const int* idx, const double* coef, int nout, double* out,
+                       cudaStream_t st) {
+  if (nout <= 0) return;
+  gather_sum_kernel<<<(nout + 127) / 128, 128, 0, st>>>(src, beg, idx, coef, nout, out);
 }
 
 __global__ void reduced_acc_kernel(const double* __restrict__ D1, const double* __restrict__ D2,

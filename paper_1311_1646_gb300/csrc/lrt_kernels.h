@@ -30,6 +30,10 @@ struct GatherSrc {
 // intermediates, 3.. = extra base rel - 3 (GemmExtra).  A plan therefore serves any
 // caller buffers and workspace, and a plan kept as a template serves new operator data
 // of the same layout.
+// Vector blocking (several trial vectors in one output): with c_vr > 0 the output's rows
+// come in blocks of c_vr, block v at C + v * c_vs; with c_vc > 0 its columns come in blocks
+// of c_vc, block v at C + v * c_vs.  A segment's A rows (a_vr, a_vs) and B columns (b_vc,
+// b_vs) are blocked the same way.  Zero: an ordinary dense operand.
 struct GemmOut {
   double* C;
   int64_t c_off;
@@ -39,6 +43,8 @@ struct GemmOut {
   int accumulate;
   int c_rel;
   int inst;      // batched launches: index of the instance whose bases the rel pointers use
+  int c_vr, c_vc;
+  int64_t c_vs;
 };
 struct GemmSeg {
   const double* A;
@@ -49,6 +55,8 @@ struct GemmSeg {
   int transA, transB;
   int a_rel, b_rel;
   double scale;
+  int a_vr, b_vc;
+  int64_t a_vs, b_vs;
 };
 
 // diag (rows x cols block, row-major) += sum_t scale_t * x_t[i] * y_t[j]   (x_t, y_t strided diagonals)
@@ -64,10 +72,22 @@ struct DiagTerm {
   double scale;
 };
 
-// gather work items: (task index, tile row, tile col) packed as int3
+// gather work items: (task index, chunk of GATHER_CHUNK destination elements, 0) packed as int3
 void launch_gather(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
                    cudaStream_t st, double* dbase = nullptr, const double* sbase1 = nullptr,
                    const double* sbase2 = nullptr);
+// one gather plan over up to GEMM_MAX_INST instances: CTA b runs work item b / ninst with
+// the bases of instance b % ninst (in the launch's parameter block)
+struct GatherBases {
+  double* d;
+  const double* s1;
+  const double* s2;
+};
+struct GatherInstSet {
+  GatherBases b[64];
+};
+void launch_gather_inst(const GatherTask* tasks, const GatherSrc* srcs, const int3* tiles, int ntiles,
+                        const GatherInstSet& bases, int ninst, cudaStream_t st);
 // FP64 GEMM work items: output o, rows [m0, m0 + mt) and columns [n0, n0 + nt) of it,
 // mt <= GEMM_TM, nt <= GEMM_TN, packed as (o, (m0 << 8) | mt, (n0 << 8) | nt)
 inline int3 gemm_tile(int o, int m0, int mt, int n0, int nt) { return make_int3(o, (m0 << 8) | mt, (n0 << 8) | nt); }
@@ -88,6 +108,23 @@ struct GemmBases {
 };
 void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                             const GemmBases* bases, cudaStream_t st);
+// One plan replayed over up to GEMM_MAX_INST instances in one launch: CTA b runs tile
+// b / ninst of instance b % ninst, every base (x, y, t and the extra bases) taken from
+// that instance's entry.  The entries travel in the launch's parameter block (no upload,
+// no host synchronization); the instances' tiles interleave, so the plan's longest-first
+// order holds across them.
+constexpr int GEMM_MAX_INST = 64;
+struct GemmInst {
+  const double* x;
+  double* y;
+  double* t;
+  double* e[GEMM_NEXTRA];
+};
+struct GemmInstSet {
+  GemmInst b[GEMM_MAX_INST];
+};
+void launch_gemm_fp64_inst(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
+                           const GemmInstSet& bases, int ninst, cudaStream_t st);
 void launch_diag(const DiagOut* outs, const DiagTerm* terms, int nouts, double* dbase, cudaStream_t st);
 
 // Split-TF32 tensor-core variant of the grouped GEMM.
@@ -112,6 +149,7 @@ struct TcTileHdr {
   int accumulate;
   int t_rp, t_k;      // TC-matrix output: padded rows, valid K (= output columns)
   int inst;           // batched launches: instance whose y receives a c_rel == 1 output
+  int vslots, vrows, vvalid, vstride;   // row slots (c_rel == 5)
 };
 struct TcSegRec {
   const float* a_hi;  // TC matrix A (rows = output rows) and B (rows = output columns)
@@ -122,6 +160,7 @@ struct TcSegRec {
   int k;              // valid K
   float scale;
   int64_t b_vstride;  // c_rel 4: floats between the B matrices of consecutive vectors
+  int64_t a_vstride;  // c_rel 5: floats between the A matrices of consecutive vectors
 };
 // Stacked tiles (c_rel == 3): the tile's 128 rows hold several short products that share
 // their B operand and K; header.C points at the tile's piece items, header.inst counts
@@ -144,6 +183,12 @@ struct TcPieceRec {
 // b + j * b_vstride; the epilogue writes slot j into the piece's intermediate plus
 // j * header.c_off floats.  Narrow products (a few columns per vector) thereby fill
 // the tile's columns with the vectors of a block-Davidson step.
+// Row-slot tiles (c_rel == 5): an FP64 output of few rows (phase 2 of sigma, y = sum
+// T Y^T) takes header.vslots vectors in the tile's rows, slot j = rows [j vrows, (j + 1)
+// vrows) holding vector v0 + j.  The producer copies slot j's A rows from a + j *
+// a_vstride; the epilogue writes the slot's first vvalid rows to y + c_off + j * vstride.
+// Every segment's A matrix has vrows padded rows and lies in a per-vector pool; B (an
+// operator block) is shared by the vectors.
 constexpr int TC_ITEM_TILE = 1, TC_ITEM_SEG = 2, TC_ITEM_PIECE = 3;
 constexpr int TC_MAX_PIECES = 16;
 struct TcItem {
@@ -186,7 +231,7 @@ void launch_tc_pack(const TcPack* d, int n, const double* base, int64_t src_stri
                     int64_t dst_stride, int nvec, cudaStream_t st);
 int tc_tile_m();
 
-constexpr int GATHER_TILE = 32;
+constexpr int GATHER_CHUNK = 1024;   // destination elements per gather work item
 constexpr int GEMM_TM = 64;   // output tile rows
 constexpr int GEMM_TN = 32;   // output tile columns
 
@@ -229,6 +274,10 @@ void launch_vdots(const double* A, int64_t lda, const double* B, int64_t ldb, in
                   bool accumulate, double* work, cudaStream_t st);
 void launch_pair_dots_strided(const double* A, int64_t lda, int na, const double* B, int64_t ldb, int nb, int64_t n,
                               double* out, double* work, cudaStream_t st);
+// out[d] += sum_{j in [beg[d], beg[d + 1])} coef[j] * src[idx[j]], d < nout (one thread per
+// output, terms in list order: deterministic)
+void launch_gather_sum(const double* src, const int* beg, const int* idx, const double* coef, int nout, double* out,
+                       cudaStream_t st);
 // Hr[a * l + b] += D1[a * l + b] + D2[a * l + b] + D2[b * l + a];  Sr += D3  (Eqs. hleft2, sleft2)
 void launch_reduced_acc(const double* D1, const double* D2, const double* D3, int l, double* Hr, double* Sr,
                         cudaStream_t st);

@@ -304,9 +304,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           first_seg = false;
           // rows of the two matrices this tile reads (multiples of 8: whole swizzle atoms)
           uint32_t ra = (uint32_t)min(TC_M, g.a_rp - hdr.m0);
-          if (hdr.c_rel >= 3) {
+          if (hdr.c_rel == 3 || hdr.c_rel == 4) {
             ra = 0;
             for (int j = 0; j < npieces; ++j) ra += (uint32_t)pieces[j].nrows;
+          } else if (hdr.c_rel == 5) {
+            ra = (uint32_t)(hdr.vslots * g.a_rp);   // row slots: all rows of each vector's A
           }
           // vector slots: hdr.accumulate slots of hdr.ldc rows, each all of one vector's B
           const bool slots = hdr.c_rel == 4;
@@ -323,7 +325,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
             const uint32_t st = sbase + stage * Tile<TN>::STAGE_BYTES;
             const int64_t ao = ((int64_t)q * g.a_rp + hdr.m0) * TC_K, bo = ((int64_t)q * g.b_rp + hdr.n0) * TC_K;
             mbar_arrive_tx(&full_bar[stage], bytes);
-            if (hdr.c_rel >= 3) {
+            if (hdr.c_rel == 5) {
+              for (int j = 0; j < hdr.vslots; ++j) {
+                const int64_t vo = (int64_t)j * g.a_vstride + (int64_t)q * g.a_rp * TC_K;
+                const uint32_t so = (uint32_t)(j * g.a_rp) * 128u;
+                bulk_g2s(st + so, g.a_hi + vo, 128u * (uint32_t)g.a_rp, &full_bar[stage]);
+                bulk_g2s(st + A_BYTES + so, g.a_lo + vo, 128u * (uint32_t)g.a_rp, &full_bar[stage]);
+              }
+            } else if (hdr.c_rel >= 3) {
               for (int j = 0; j < npieces; ++j) {
                 const TcPieceRec& pc = pieces[j];
                 const int64_t po = ((int64_t)q * pc.a_rp + pc.a_row0) * TC_K;
@@ -510,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
               break;
             }
           }
-        } else if (t.c_rel >= 2) {
+        } else if (t.c_rel == 2 || t.c_rel == 3) {
           // Intermediate: this warp's rows as a TC-matrix image (two chunks of 32
           // columns, hi and lo planes; row r's 16-byte groups permuted by r mod 8),
           // then one bulk store per chunk and plane: rows [m0 + 32 w, + nrows) of a
@@ -569,9 +578,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tf32x3_kernel(const TcItem
           for (int c = 0; c < TN; ++c)
             *(double*)(stg + (rr * Tile<TN>::STG_LD + c) * 8) = (double)sum[c] - (double)cmp[c];
           __syncwarp();
-          double* C = (t.c_rel == 1 ? (out.ys ? out.ys[t.inst] : out.y) + t.c_off : t.C);
+          double* C = (t.c_rel != 0 ? (out.ys ? out.ys[t.inst] : out.y) + t.c_off : t.C);
           for (int r = 0; r < nrows; ++r) {
-            double* dst = C + (int64_t)(t.m0 + rbase + r) * t.ldc + t.n0;
+            int R = t.m0 + rbase + r;
+            double* dst = C;
+            if (t.c_rel == 5) {
+              // row slots: slot j is vector v0 + j, its padding rows are not written
+              const int j = R / t.vrows;
+              R -= j * t.vrows;
+              if (j >= t.vslots || R >= t.vvalid) continue;
+              dst += (int64_t)j * t.vstride;
+            }
+            dst += (int64_t)R * t.ldc + t.n0;
             for (int c = lane; c < t.nt; c += 32) {
               const double v = *(const double*)(stg + (r * Tile<TN>::STG_LD + c) * 8);
               dst[c] = t.accumulate ? dst[c] + v : v;

@@ -4,7 +4,8 @@ The sigma phases sum, per output tile, many short block products (Eqs. hzero_sb,
 hleft_sb: one product per operator pair of the "x" summation).  The kernel packs
 their contracted indices along one K axis and stages 32 positions at a time; the
 plan decides which thread copies which element.  This test compiles the plan as
-plain C++ and checks, for random segment lists, tile shapes and storage orders,
+plain C++ and checks, for random segment lists, tile shapes, storage orders and vector
+blockings (a tile spanning the same product for several trial vectors),
 that every element of every staged chunk is copied exactly once, from the right
 address, and that nothing outside the chunk is written.  It needs no GPU.
 """
@@ -43,13 +44,21 @@ int main() {
       s.transA = rnd(2);
       s.transB = rnd(2);
       s.scale = 1.0;
-      // A is (m0 + mt) x k, B is k x (n0 + nt); leading dimensions padded at random
-      const int ar = s.transA ? k : m0 + mt, ac = s.transA ? m0 + mt : k;
-      const int br = s.transB ? n0 + nt : k, bc = s.transB ? k : n0 + nt;
+      // vector blocking in half the cases: rows of A (columns of B) in blocks of avr (bvc),
+      // block v of the operand at v * avs (v * bvs)
+      s.avr = rnd(2) ? 1 + rnd(20) : 0;
+      s.bvc = rnd(2) ? 1 + rnd(12) : 0;
+      const int arows = s.avr ? s.avr : m0 + mt, bcols = s.bvc ? s.bvc : n0 + nt;
+      const int nva = s.avr ? (m0 + mt + s.avr - 1) / s.avr : 1, nvb = s.bvc ? (n0 + nt + s.bvc - 1) / s.bvc : 1;
+      // A is (m0 + mt) x k, B is k x (n0 + nt) (per vector block); leading dimensions padded at random
+      const int ar = s.transA ? k : arows, ac = s.transA ? arows : k;
+      const int br = s.transB ? bcols : k, bc = s.transB ? k : bcols;
       s.lda = ac + rnd(4);
       s.ldb = bc + rnd(4);
-      store[2 * q].assign((size_t)ar * s.lda + 1, 0.0);
-      store[2 * q + 1].assign((size_t)br * s.ldb + 1, 0.0);
+      s.avs = (int64_t)ar * s.lda + rnd(5);
+      s.bvs = (int64_t)br * s.ldb + rnd(5);
+      store[2 * q].assign((size_t)(nva * s.avs) + 1, 0.0);
+      store[2 * q + 1].assign((size_t)(nvb * s.bvs) + 1, 0.0);
       s.A = store[2 * q].data();
       s.B = store[2 * q + 1].data();
       sd[q] = s;
@@ -81,14 +90,19 @@ int main() {
         const SegS& s = sd[q];
         const int kl = p - kst[q];
         for (int i = 0; i < mt; ++i) {
-          const double* want = s.transA ? s.A + (size_t)kl * s.lda + m0 + i : s.A + (size_t)(m0 + i) * s.lda + kl;
+          // independent statement of the address: vector block and row inside it
+          const int gr = m0 + i, va = s.avr ? gr / s.avr : 0, ra = s.avr ? gr % s.avr : gr;
+          const double* base = s.A + (size_t)va * (size_t)s.avs;
+          const double* want = s.transA ? base + (size_t)kl * s.lda + ra : base + (size_t)ra * s.lda + kl;
           if (a_n[i][kk] != 1 || a_src[i][kk] != want) {
             printf("A element (%d, %d) copied %d times, case %d\n", i, kk, a_n[i][kk], it);
             return 1;
           }
         }
         for (int j = 0; j < nt; ++j) {
-          const double* want = s.transB ? s.B + (size_t)(n0 + j) * s.ldb + kl : s.B + (size_t)kl * s.ldb + n0 + j;
+          const int gc = n0 + j, vb = s.bvc ? gc / s.bvc : 0, cb = s.bvc ? gc % s.bvc : gc;
+          const double* base = s.B + (size_t)vb * (size_t)s.bvs;
+          const double* want = s.transB ? base + (size_t)cb * s.ldb + kl : base + (size_t)kl * s.ldb + cb;
           if (b_n[kk][j] != 1 || b_src[kk][j] != want) {
             printf("B element (%d, %d) copied %d times, case %d\n", kk, j, b_n[kk][j], it);
             return 1;
