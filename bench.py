@@ -32,12 +32,13 @@ import synth  # noqa: E402
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the two
-# sigma launches of the middle position (profiles/gemm_*_ppp_k12_M256_twosite.md), valid only
-# for the kernel source it was taken on (sha256 prefix); otherwise the bench reports null.
+# DRAM bytes (read + write) per launch of the dominant kernel: the FP64 sigma launches of one
+# timed step of this workload (48 launches, one ncu capture of dram__bytes_read/write.sum,
+# profiles/gemm_fp64_water_k24_M500_sigma_step.md), valid only for the kernel source it was
+# taken on (sha256 prefix); otherwise, and for the mixed form, the bench reports null.
 TRAFFIC = {
-    "fp64": {"source": "lrt_kernels.cu", "sha256": "bb2c0751cad8230e", "bytes": (9.020e6 + 52.461e6) / 2},
-    "mixed": {"source": "lrt_tc.cu", "sha256": "d4c9ba3ef56446b3", "bytes": (90.125e6 + 150.770e6) / 2},
+    "fp64": {"source": "lrt_kernels.cu", "sha256": "fcd888b88ec1ae30", "bytes": 939.11e6},
+    "mixed": {"source": "lrt_tc.cu", "sha256": "", "bytes": None},
 }
 
 
@@ -50,7 +51,7 @@ def traffic(precision):
             h = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    return t["bytes"] if h == t["sha256"] else None
+    return t["bytes"] if t["bytes"] and h == t["sha256"] else None
 
 
 def tf32_peak():
@@ -79,9 +80,12 @@ def parse():
                    help="also the TDA to convergence on the k = 24, M = 500 workload (long)")
     p.add_argument("--no-fe2s2", action="store_true",
                    help="skip the side measurement on the k = 36, M = 1500 workload")
-    p.add_argument("--profile", choices=["fp64", "mixed", "gather"],
+    p.add_argument("--profile", choices=["fp64", "mixed", "gather", "tda"],
                    help="profiler run: one sigma (fp64 / mixed) or one enlargement + renormalization "
-                        "(gather) at the middle position, between cudaProfilerStart and Stop")
+                        "(gather) at the middle position, or three TDA sweeps on the PPP workload (tda), "
+                        "between cudaProfilerStart and Stop")
+    p.add_argument("--profile-step", action="store_true",
+                   help="bracket the first timed step with cudaProfilerStart and Stop")
     p.add_argument("--profile-M", type=int, default=0, help="bond dimension of the profiler run (0: 500)")
     return p.parse_args()
 
@@ -216,7 +220,7 @@ class SigmaStep:
             if ev is not None:
                 ev[n][1].record(stream)
 
-    def timed(self, stream, steps, warmup, flush, sampler=None):
+    def timed(self, stream, steps, warmup, flush, sampler=None, profile_first=False):
         """(step ms, sigma ms, clocks) over `steps` timed steps, L2 flushed before each."""
         import torch
         for _ in range(warmup):
@@ -225,7 +229,11 @@ class SigmaStep:
         if sampler:
             sampler.start()
         step_ms, sigma_ms = [], []
-        for _ in range(steps):
+        for rep in range(steps):
+            if profile_first and rep == 0:
+                torch.cuda.profiler.start()
+            if profile_first and rep == 1:
+                torch.cuda.profiler.stop()
             flush.zero_()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in self.positions]
@@ -237,6 +245,8 @@ class SigmaStep:
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             sigma_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        if profile_first and steps == 1:
+            torch.cuda.profiler.stop()
         clocks = sampler.stop() if sampler else None
         return step_ms, sigma_ms, clocks
 
@@ -259,7 +269,8 @@ def run_ours(args):
     S = SigmaStep(ctx, positions, sizes, nvec, nsite, device, prec)
     if world > 1:
         torch.distributed.barrier()
-    step_ms, sigma_ms, clocks = S.timed(stream, args.steps, args.warmup, flush, ClockSampler(device))
+    step_ms, sigma_ms, clocks = S.timed(stream, args.steps, args.warmup, flush, ClockSampler(device),
+                                        profile_first=args.profile_step)
     ms_per_step, value = replica_throughput(sum(step_ms), args.steps, S.flops, world,
                                             f"cuda:{device}" if world > 1 else "cpu")
     achieved = S.flops / (sum(sigma_ms) / args.steps * 1e-3) / 1e12
@@ -559,6 +570,8 @@ def run_profile(args):
     import paper_1311_1646_gb300 as pkg
     device = 0
     torch.cuda.set_device(device)
+    if args.profile == "tda":
+        return run_profile_tda(pkg, device)
     cfg = synth.config(3)
     H = cfg["ham"]
     k, na, nb, nvec = H.k, H.n_alpha, H.n_beta, cfg["nroots"]
@@ -593,6 +606,39 @@ def run_profile(args):
     print(json.dumps({"profile": args.profile, "M": M, "site": i, "device_gb": _device_gb(device),
                       "flops": st["flops"], "launches": st["launches"]}))
     ctx.close()
+
+
+def run_profile_tda(pkg, device):
+    """TDA sweeps of the PPP polyene (12 sites, 6a6b, M = 256, 6 roots) for ncu: the ground
+    state on the GPU, two warm-up sweeps (plans and templates built), then three sweeps
+    between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+    cfg = synth.config(2)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    g = pkg.Context(device)
+    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+    g.sweep_gs([64, 128, 256], max_sweeps=14, e_tol=1e-12, dav_tol=1e-10, onesite_sweeps=20)
+    bonds, sites = g.mps_get()
+    g.close()
+    t = pkg.Context(device)
+    t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    t.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
+    t.tda_prepare()
+    kw = dict(eps=1e-9, allow_noconv=True, keep=3 * nr, **TDA_KW)
+    t.sweep_tda(nr, max_iter=2, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    t.sweep_tda(nr, max_iter=3, **kw)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile": "tda", "workload": "ppp_k12_M256_6roots", "sweeps": t.sweeps(), "wall_s": dt,
+                      "device_gb": _device_gb(device)}))
+    t.close()
 
 
 def _oracle_setup(H, left, right, i, nsite):
