@@ -33,9 +33,9 @@ import synth  # noqa: E402
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 
 # DRAM bytes (read + write) per launch of the dominant kernel: the FP64 sigma launches of one
-# timed step of this workload (48 launches, one ncu capture of dram__bytes_read/write.sum,
-# profiles/gemm_fp64_water_k24_M500_sigma_step.md), valid only for the kernel source it was
-# taken on (sha256 prefix); otherwise, and for the mixed form, the bench reports null.
+# timed step of this workload (48 launches, one ncu capture of dram__bytes_read/write.sum with
+# --profile-step), valid only for the kernel source it was taken on (sha256 prefix);
+# otherwise, and for the mixed form, the bench reports null.
 TRAFFIC = {
     "fp64": {"source": "lrt_kernels.cu", "sha256": "fcd888b88ec1ae30", "bytes": 939.11e6},
     "mixed": {"source": "lrt_tc.cu", "sha256": "", "bytes": None},
