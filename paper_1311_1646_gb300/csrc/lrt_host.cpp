@@ -712,14 +712,20 @@ struct GatherPlan {
 };
 
 struct GemmPlan {
-  DevArray<GemmOut> outs;
+  DevArray<GemmOut> outs;    // the plan's outputs, then the K parts of split tiles
   DevArray<GemmSeg> segs;
   DevArray<int3> tiles;      // FP64 kernel tiles
   int ntiles = 0;
+  int nbase = 0;             // outputs before the K parts
+  DevArray<SplitTile> splits;
+  int nsplit = 0;
+  DevBuf ws;                 // partial tiles of the split tiles
   double flops = 0.0;
   void run(cudaStream_t st, const double* xb, double* yb, double* tb = nullptr, const GemmExtra* ex = nullptr) const {
-    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st, ex);
+    launch_gemm_fp64(outs.p, segs.p, tiles.p, ntiles, xb, yb, tb, st, ex, ws.p);
+    if (nsplit > 0) launch_split_reduce(outs.p, splits.p, nsplit, ws.p, yb, tb, st);
   }
+  int launches() const { return (ntiles > 0) + (nsplit > 0); }
 };
 
 static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vector<GatherSrc>& srcs,
@@ -736,34 +742,78 @@ static void build_gather(GatherPlan& P, std::vector<GatherTask>& tasks, std::vec
   P.ntiles = (int)tiles.size();
 }
 
-static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std::vector<GemmSeg>& segs,
-                       cudaStream_t st) {
+static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs_in, const std::vector<GemmSeg>& segs,
+                       cudaStream_t st, bool split = false) {
   // A tile costs its warps of outputs times its K chunks of DFMA issue, plus a fixed
   // cost per chunk.  Tiles far longer than an even share of the launch (an output with
-  // many long K segments) would run on after all others finished, so they are cut into
-  // row slices of at most that share; then the longest go first.
-  std::vector<int64_t> ktot(outs.size(), 0);
+  // many long K segments) would run on after all others finished.  With `split`, an
+  // output that sums several segments (y or T outputs) and at least 2 GEMM_SPLIT_K of K
+  // has each of its tiles cut along its segment list into K parts of about GEMM_SPLIT_K:
+  // each part a partial tile in the workspace, added in order by the reduction launch.
+  // The parts depend on the output's own segments only, so an element is summed in the
+  // same grouping whichever call (vector count, batch) the output belongs to.  Otherwise
+  // tiles above an even share are cut into row slices.  Then the longest go first.  (Row
+  // slices of a quarter share were measured 2.5x slower on the k = 24 workload's phase 2:
+  // every slice stages the whole K range of B for a few rows; a K part stages only its
+  // own range.)
+  std::vector<GemmOut> outs = outs_in;
+  std::vector<int64_t> ktot(outs_in.size(), 0);
   double fl = 0.0;
-  for (size_t i = 0; i < outs.size(); ++i)
-    for (int s = 0; s < outs[i].seg_count; ++s) {
-      ktot[i] += segs[outs[i].seg_begin + s].k;
-      fl += 2.0 * outs[i].m * (double)outs[i].n * segs[outs[i].seg_begin + s].k;
+  for (size_t i = 0; i < outs_in.size(); ++i)
+    for (int s = 0; s < outs_in[i].seg_count; ++s) {
+      ktot[i] += segs[outs_in[i].seg_begin + s].k;
+      fl += 2.0 * outs_in[i].m * (double)outs_in[i].n * segs[outs_in[i].seg_begin + s].k;
     }
   auto cost = [](int64_t mt, int64_t nt, int64_t k) {
     return ((k + GEMM_KC - 1) / GEMM_KC) * (32 * ((mt * nt + 31) / 32) + 64) + 64;
   };
   int64_t total = 0;
-  for (size_t i = 0; i < outs.size(); ++i)
-    for (int m0 = 0; m0 < outs[i].m; m0 += GEMM_TM)
-      for (int n0 = 0; n0 < outs[i].n; n0 += GEMM_TN)
-        total += cost(std::min(GEMM_TM, outs[i].m - m0), std::min(GEMM_TN, outs[i].n - n0), ktot[i]);
+  for (size_t i = 0; i < outs_in.size(); ++i)
+    for (int m0 = 0; m0 < outs_in[i].m; m0 += GEMM_TM)
+      for (int n0 = 0; n0 < outs_in[i].n; n0 += GEMM_TN)
+        total += cost(std::min(GEMM_TM, outs_in[i].m - m0), std::min(GEMM_TN, outs_in[i].n - n0), ktot[i]);
   const int64_t cap = std::max<int64_t>(1, total / gemm_fp64_slots());
   std::vector<std::pair<int64_t, int3>> tl;
-  for (size_t i = 0; i < outs.size(); ++i)
-    for (int m0 = 0; m0 < outs[i].m; m0 += GEMM_TM)
-      for (int n0 = 0; n0 < outs[i].n; n0 += GEMM_TN) {
-        const int mt = std::min(GEMM_TM, outs[i].m - m0), nt = std::min(GEMM_TN, outs[i].n - n0);
+  std::vector<SplitTile> sp;
+  int64_t wsz = 0;
+  for (size_t i = 0; i < outs_in.size(); ++i) {
+    const GemmOut& O = outs_in[i];
+    for (int m0 = 0; m0 < O.m; m0 += GEMM_TM)
+      for (int n0 = 0; n0 < O.n; n0 += GEMM_TN) {
+        const int mt = std::min(GEMM_TM, O.m - m0), nt = std::min(GEMM_TN, O.n - n0);
         const int64_t c = cost(mt, nt, ktot[i]);
+        const int want = (int)std::min<int64_t>(O.seg_count, ktot[i] / GEMM_SPLIT_K);
+        if (split && want >= 2 && O.c_rel <= 2 && outs.size() < (size_t)INT32_MAX) {
+          // contiguous runs of the segment list, each about ktot / want of K
+          SplitTile t{wsz, (int)i, 0, m0, mt, n0, nt};
+          int sb = 0;
+          int64_t acc = 0;
+          for (int q = 0; q < O.seg_count; ++q) {
+            acc += segs[O.seg_begin + q].k;
+            const bool last = q + 1 == O.seg_count;
+            if (last || acc * want >= ktot[i] * (t.nparts + 1)) {
+              GemmOut po = O;
+              po.C = nullptr;
+              po.c_rel = GEMM_C_SPLIT;
+              po.c_off = wsz + (int64_t)t.nparts * mt * nt - ((int64_t)m0 * nt + n0);
+              po.ldc = nt;
+              po.accumulate = 0;
+              po.c_vr = po.c_vc = 0;
+              po.c_vs = 0;
+              po.seg_begin = O.seg_begin + sb;
+              po.seg_count = q + 1 - sb;
+              int64_t kp = 0;
+              for (int u = sb; u <= q; ++u) kp += segs[O.seg_begin + u].k;
+              outs.push_back(po);
+              tl.push_back({cost(mt, nt, kp), gemm_tile((int)outs.size() - 1, m0, mt, n0, nt)});
+              ++t.nparts;
+              sb = q + 1;
+            }
+          }
+          wsz += (int64_t)t.nparts * mt * nt;
+          sp.push_back(t);
+          continue;
+        }
         const int parts = (int)std::min<int64_t>(mt, (c + cap - 1) / cap);
         for (int p = 0, r = m0; p < parts; ++p) {
           const int rows = mt / parts + (p < mt % parts ? 1 : 0);
@@ -771,6 +821,7 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
           r += rows;
         }
       }
+  }
   std::stable_sort(tl.begin(), tl.end(), [](const std::pair<int64_t, int3>& a, const std::pair<int64_t, int3>& b) {
     return a.first > b.first;
   });
@@ -780,6 +831,10 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs, const std:
   P.segs.upload(segs, st);
   P.tiles.upload(tiles, st);
   P.ntiles = (int)tiles.size();
+  P.nbase = (int)outs_in.size();
+  P.splits.upload(sp, st);
+  P.nsplit = (int)sp.size();
+  if (wsz > 0) P.ws.ensure((size_t)wsz);
   P.flops = fl;
 }
 
@@ -1891,7 +1946,7 @@ static std::unique_ptr<SigmaPlan> plan_sigma_sets(lrt_ctx* c, const OpSet& X, co
     O2.push_back(y);
   }
   build_gemm(plan->p1, O1, S1, c->st);
-  build_gemm(plan->p2, O2, S2, c->st);
+  build_gemm(plan->p2, O2, S2, c->st, !rel_ops);   // kept relative plans are replayed over instances
   // tensor-core twin: phase-2 outputs, one per (y block, column group)
   plan->has_tc = tc;
   for (size_t w = 0; w < wb.size() && tc; ++w)
@@ -4843,6 +4898,7 @@ static void merge_fp64(GemmPlan& out, const std::vector<SigmaPlan*>& plans, bool
   for (size_t j = 0; j < plans.size(); ++j) {
     const GemmPlan& g = phase2 ? plans[j]->p2 : plans[j]->p1;
     std::vector<GemmOut> o = download(g.outs, st);
+    o.resize(g.nbase);   // not the K parts of split tiles: the merged plan tiles anew
     std::vector<GemmSeg> sg = download(g.segs, st);
     const int sb = (int)S.size();
     for (GemmOut x : o) {
@@ -5215,7 +5271,7 @@ int sigma(lrt_t ctx, int site, int nsite, int nvec, const double* x_dev, double*
     CK(cudaGetLastError());
     ctx->last.flops = p.flops_alg;
     ctx->last.flops_issued = p.p1.flops + p.p2.flops;
-    ctx->last.launches = (p.p1.ntiles > 0) + (p.p2.ntiles > 0);
+    ctx->last.launches = p.p1.launches() + p.p2.launches();
     ctx->last.n_terms = p.n_terms;
     ctx->last.n_products = p.n_products;
     ctx->last.op_bytes = p.op_bytes;

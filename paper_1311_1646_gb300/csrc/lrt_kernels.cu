@@ -175,7 +175,7 @@ static_assert(GEMM_MAXE == 16, "the switch below lists the output counts 1..16")
 template <class Extra>
 __device__ __forceinline__ void gemm_fp64_tile(const GemmOut* __restrict__ outs, const GemmSeg* __restrict__ segs,
                                                const int3 wi, const double* xbase, double* ybase, double* tbase,
-                                               const GemmOut& o, const Extra& extra) {
+                                               double* wbase, const GemmOut& o, const Extra& extra) {
   extern __shared__ __align__(16) unsigned char gemm_smem_raw[];
   GemmSmem& S = *reinterpret_cast<GemmSmem*>(gemm_smem_raw);
   const int m0 = wi.y >> 8, mt = wi.y & 255, n0 = wi.z >> 8, nt = wi.z & 255;
@@ -265,7 +265,8 @@ __device__ __forceinline__ void gemm_fp64_tile(const GemmOut* __restrict__ outs,
       __syncthreads();           // buffer buf is free for chunk c + 2
     }
   }
-  double* cbase = o.c_rel ? (o.c_rel == 1 ? ybase : o.c_rel == 2 ? tbase : extra(o.c_rel - 3)) + o.c_off : o.C;
+  double* cbase = o.c_rel == GEMM_C_SPLIT ? wbase + o.c_off
+                 : o.c_rel ? (o.c_rel == 1 ? ybase : o.c_rel == 2 ? tbase : extra(o.c_rel - 3)) + o.c_off : o.C;
 #pragma unroll
   for (int j = 0; j < GEMM_MAXE; ++j) {
     if (j >= cnt) break;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(cons
                                                                     double* __restrict__ ybase,
                                                                     double* __restrict__ tbase,
                                                                     const GemmBases* __restrict__ multi,
-                                                                    const GemmExtra ex) {
+                                                                    const GemmExtra ex, double* __restrict__ wbase) {
   const int w = blockIdx.x;
   if (w >= ntiles) return;
   const int3 wi = tiles[w];
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_kernel(cons
     ybase = b.y;
     tbase = b.t;
   }
-  gemm_fp64_tile(outs, segs, wi, xbase, ybase, tbase, o, [&](int i) { return extra_base(ex, i); });
+  gemm_fp64_tile(outs, segs, wi, xbase, ybase, tbase, wbase, o, [&](int i) { return extra_base(ex, i); });
 }
 
 __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_inst_kernel(const GemmOut* __restrict__ outs,
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, GEMM_CTAS) gemm_fp64_inst_kernel
   const GemmInst* b = &P.b[blockIdx.x % ninst];
   const int3 wi = tiles[w];
   const GemmOut o = outs[wi.x];
-  gemm_fp64_tile(outs, segs, wi, b->x, b->y, b->t, o, [&](int i) { return b->e[i]; });
+  gemm_fp64_tile(outs, segs, wi, b->x, b->y, b->t, nullptr, o, [&](int i) { return b->e[i]; });
 }
 
 static cudaError_t gemm_fp64_smem_attr() {
@@ -360,12 +361,49 @@ static cudaError_t gemm_fp64_smem_attr() {
 }
 
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
-                      const double* xbase, double* ybase, double* tbase, cudaStream_t st, const GemmExtra* extra) {
+                      const double* xbase, double* ybase, double* tbase, cudaStream_t st, const GemmExtra* extra,
+                      double* wbase) {
   if (ntiles <= 0) return;
   if (gemm_fp64_smem_attr() != cudaSuccess) return;
   const GemmExtra ex = extra ? *extra : GemmExtra{};
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, xbase, ybase, tbase,
-                                                                  nullptr, ex);
+                                                                  nullptr, ex, wbase);
+}
+
+// One CTA per split tile: each element sums its parts in part order (deterministic), then
+// lands where the tile's output puts it, vector blocking included, as in the GEMM epilogue.
+__global__ void __launch_bounds__(256) split_reduce_kernel(const GemmOut* __restrict__ outs,
+                                                           const SplitTile* __restrict__ tiles,
+                                                           const double* __restrict__ wbase,
+                                                           double* __restrict__ ybase, double* __restrict__ tbase) {
+  const SplitTile t = tiles[blockIdx.x];
+  const GemmOut o = outs[t.o];
+  double* cbase = o.c_rel == 1 ? ybase + o.c_off : o.c_rel == 2 ? tbase + o.c_off : o.C;
+  const int ne = t.mt * t.nt;
+  const double* w = wbase + t.ws_off;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < t.nparts; ++p) s += w[(int64_t)p * ne + e];
+    int r = t.m0 + e / t.nt, col = t.n0 + e % t.nt;
+    double* c = cbase;
+    if (o.c_vr > 0) {
+      const int v = r / o.c_vr;
+      c += (int64_t)v * o.c_vs;
+      r -= v * o.c_vr;
+    } else if (o.c_vc > 0) {
+      const int v = col / o.c_vc;
+      c += (int64_t)v * o.c_vs;
+      col -= v * o.c_vc;
+    }
+    c += (int64_t)r * o.ldc + col;
+    *c = o.accumulate ? (*c + s) : s;
+  }
+}
+
+void launch_split_reduce(const GemmOut* outs, const SplitTile* tiles, int ntiles, const double* wbase, double* ybase,
+                         double* tbase, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  split_reduce_kernel<<<ntiles, 256, 0, st>>>(outs, tiles, wbase, ybase, tbase);
 }
 
 void launch_gemm_fp64_inst(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
@@ -382,7 +420,7 @@ void launch_gemm_fp64_multi(const GemmOut* outs, const GemmSeg* segs, const int3
   if (ntiles <= 0) return;
   if (gemm_fp64_smem_attr() != cudaSuccess) return;
   gemm_fp64_kernel<<<ntiles, GEMM_THREADS, sizeof(GemmSmem), st>>>(outs, segs, tiles, ntiles, nullptr, nullptr,
-                                                                  nullptr, bases, GemmExtra{});
+                                                                  nullptr, bases, GemmExtra{}, nullptr);
 }
 
 // ---------------------------------------------------------------------------

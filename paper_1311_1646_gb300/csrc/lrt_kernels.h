@@ -99,7 +99,21 @@ struct GemmExtra {
 };
 void launch_gemm_fp64(const GemmOut* outs, const GemmSeg* segs, const int3* tiles, int ntiles,
                       const double* xbase, double* ybase, double* tbase, cudaStream_t st,
-                      const GemmExtra* extra = nullptr);
+                      const GemmExtra* extra = nullptr, double* wbase = nullptr);
+// Split K: an output tile whose segment list is long is cut into parts, each a contiguous
+// run of its segments written as a partial tile (c_rel GEMM_C_SPLIT: wbase + c_off, row
+// stride nt) into the plan's workspace; split_reduce then adds the parts in order and
+// stores the sum where the output's own addressing puts it (c_rel 0, 1 or 2).
+constexpr int GEMM_C_SPLIT = 15;
+constexpr int GEMM_SPLIT_K = 512;   // K per part of a split tile
+struct SplitTile {
+  int64_t ws_off;     // part p of the tile at ws_off + p * mt * nt
+  int o;              // the output the tile belongs to
+  int nparts;
+  int m0, mt, n0, nt;
+};
+void launch_split_reduce(const GemmOut* outs, const SplitTile* tiles, int ntiles, const double* wbase, double* ybase,
+                         double* tbase, cudaStream_t st);
 // batched form: the bases of output o are bases[o.inst] (device array)
 struct GemmBases {
   const double* x;
