@@ -37,7 +37,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 # --profile-step), valid only for the kernel source it was taken on (sha256 prefix);
 # otherwise, and for the mixed form, the bench reports null.
 TRAFFIC = {
-    "fp64": {"source": "lrt_kernels.cu", "sha256": "fcd888b88ec1ae30", "bytes": 939.11e6},
+    "fp64": {"source": "lrt_kernels.cu", "sha256": "2ffbe1492898dd21", "bytes": 1107.18e6},
     "mixed": {"source": "lrt_tc.cu", "sha256": "", "bytes": None},
 }
 
@@ -428,6 +428,48 @@ def _tda_converged(pkg, device, cfg_idx, schedule, eps, max_iter):
                 "until sum |r|^2 < 1e-6, then FP64 sweeps to eps" % schedule}
 
 
+def _tda_sweep_times(pkg, device, cfg_idx=3, iters=3):
+    """Wall time per TDA sweep on the k = 24, M = 500 water workload (6 roots), FP64
+    against the mixed form, on a random right-orthonormal reference of the workload's
+    sector structure (the cost of a sweep does not depend on how far the roots have
+    converged; a converged run needs the M = 500 ground state first, minutes of GPU time).
+    Each form runs the start sweep and `iters` sweeps; the mixed form's last third is FP64
+    (its refinement), so sweeps are compared index by index where both forms ran their own
+    arithmetic."""
+    cfg = synth.config(cfg_idx)
+    H = cfg["ham"]
+    nr = cfg["nroots"]
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, cfg["M"], 7, "right")
+    out = {}
+    for name, prec in (("fp64", pkg.LRT_FP64), ("mixed", pkg.LRT_MIXED)):
+        t = pkg.Context(device)
+        try:
+            t.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+            t.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+            t.tda_prepare()
+            t0 = time.perf_counter()
+            t.sweep_tda(nr, max_iter=iters, eps=1e-30, allow_noconv=True, precision=prec, keep=3 * nr, **TDA_KW)
+            dt = time.perf_counter() - t0
+            log = t.sweep_log()
+        finally:
+            t.close()
+        out[name] = {"total_s": dt, "setup_s": dt - sum(x for x, _ in log), "sweep_s": [x for x, _ in log],
+                     "tensor_core_sweep": [f for _, f in log]}
+    fp, mx = out["fp64"], out["mixed"]
+    both = [j for j in range(1, min(len(fp["sweep_s"]), len(mx["sweep_s"]))) if mx["tensor_core_sweep"][j]]
+    if both:
+        a = sum(fp["sweep_s"][j] for j in both)
+        b = sum(mx["sweep_s"][j] for j in both)
+        out["compared_sweeps"] = both
+        out["fp64_s_per_sweep"] = a / len(both)
+        out["mixed_s_per_sweep"] = b / len(both)
+        out["mixed_speedup_per_sweep"] = a / b
+    out["note"] = ("random right-orthonormal reference with the workload's sectors, M = 500, 6 roots, subspace "
+                   "growing by 6 vectors per sweep (thick restart settings of the converged runs); "
+                   "sweep_s[0] is the start sweep")
+    return out
+
+
 def extras(pkg, ctx, device, S, stream, flush, args):
     """Side measurements, outside the timed steps."""
     import torch
@@ -502,6 +544,10 @@ def extras(pkg, ctx, device, S, stream, flush, args):
     out["tda_abinitio_k8_M64_4roots"] = _tda_converged(pkg, device, 1, [32, 64], 1e-9, 200)
     if not args.quick_tda:
         out["tda_ppp_k12_M256_6roots"] = _tda_converged(pkg, device, 2, [64, 128, 256], 1e-9, 200)
+        try:
+            out["tda_water_k24_M500_sweep_time"] = _tda_sweep_times(pkg, device)
+        except Exception as e:   # a side measurement never costs the metric line
+            out["tda_water_k24_M500_sweep_time"] = {"error": repr(e)}
     if args.tda_water:
         out["tda_water_k24_M500_6roots"] = _tda_converged(pkg, device, 3, [128, 256, 500], 1e-8, 200)
     return out

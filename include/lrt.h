@@ -261,6 +261,12 @@ int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* params, doubl
 /* lrt_sweeps: *sweeps = the number of sweeps the last sweep_gs (two-site sweeps) or
  * sweep_tda (Davidson iterations after the start sweep) on this context ran. */
 int lrt_sweeps(lrt_t ctx, int* sweeps);
+/* lrt_sweep_log: the wall time of every sweep of the last sweep_tda on this context (the
+ * start sweep first; each time from the sweep's start to the host synchronization that
+ * ends it, so it includes all its device work) and whether its H_0 site products ran on
+ * the tensor cores (1) or in FP64 (0).  Writes min(cap, n) entries to seconds and mixed
+ * (host arrays of cap elements; NULL allowed when cap is 0) and the number of sweeps to *n. */
+int lrt_sweep_log(lrt_t ctx, int cap, double* seconds, int* mixed, int* n);
 /* sweep_tda_batched: the DMRG-TDA sweeps of Fig. alg:dmrgtda for n_inst independent
  * instances, each its own context (its own Hamiltonian and reference, prepared by
  * tda_load or tda_prepare), run concurrently: host threads (at most the host's hardware

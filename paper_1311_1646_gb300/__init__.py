@@ -22,7 +22,7 @@ LRT_CORR_SWEEP = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "sweep_tda_density", "lrt_sweeps", "lrt_set_wait_limit", "sigma_batched",
+           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "sweep_tda_density", "lrt_sweeps", "lrt_sweep_log", "lrt_set_wait_limit", "sigma_batched",
            "sweep_tda_batched"]
 
 _lib = None
@@ -104,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tda_prepare.argtypes = [vp, dp]
     lib.tda_stationarity.argtypes = [vp, dp, dp]
     lib.lrt_sweeps.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.lrt_sweep_log.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.lrt_set_wait_limit.argtypes = [vp, d, i]
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
@@ -300,6 +301,16 @@ class Context:
         n = ctypes.c_int()
         self._check(self.lib.lrt_sweeps(self.h, ctypes.byref(n)), "lrt_sweeps")
         return n.value
+
+    def sweep_log(self):
+        """[(seconds, mixed)] of every sweep of the last sweep_tda (the start sweep first)."""
+        n = ctypes.c_int()
+        self._check(self.lib.lrt_sweep_log(self.h, 0, None, None, ctypes.byref(n)), "lrt_sweep_log")
+        cap = n.value
+        sec = np.zeros(max(cap, 1))
+        mx = (ctypes.c_int * max(cap, 1))()
+        self._check(self.lib.lrt_sweep_log(self.h, cap, _dptr(sec), mx, ctypes.byref(n)), "lrt_sweep_log")
+        return [(float(sec[j]), int(mx[j])) for j in range(min(cap, n.value))]
 
     def tda_stationarity(self):
         """(sum_i |Q^C (H_0^[i] - E0) C0_i|^2, E0) of the loaded reference."""

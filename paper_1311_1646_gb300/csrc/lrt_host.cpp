@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <deque>
 #include <map>
 #include <memory>
@@ -1025,6 +1026,7 @@ struct lrt_ctx {
   std::map<std::tuple<int, int, int>, std::unique_ptr<lrt::SigmaPlan>> plans;
   lrt_sigma_stats last{};
   int last_sweeps = 0;
+  std::vector<std::pair<double, int>> sweep_log;   // last sweep_tda: seconds and mixed flag per sweep
   uint64_t tc_wait_ns = 0;   // limit of the tensor-core pipeline waits (0: the default)
   int tc_stall = 0;          // test hook: the next tensor-core launch stalls on a wait
   int* derr = nullptr;   // device flag set by a kernel whose bounded wait expired
@@ -4456,7 +4458,10 @@ struct TdaRunner {
     bool any_gs = false;
     int m = 0, it = 0;
     bool first = true;
+    c->sweep_log.clear();
     for (;;) {
+      const auto t_sweep = std::chrono::steady_clock::now();
+      const bool sweep_mixed = mixed;
       if (!first) {
         std::vector<double> w, U;
         solve_gep(Hr, Sr, lold, w, U);
@@ -4634,6 +4639,8 @@ struct TdaRunner {
       CK(cudaMemcpyAsync(r2.data(), d_r2.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
       CK(cudaGetLastError());
+      c->sweep_log.push_back(
+          {std::chrono::duration<double>(std::chrono::steady_clock::now() - t_sweep).count(), sweep_mixed ? 1 : 0});
       if (!first) {
         ++it;
         bool conv = true;
@@ -5422,6 +5429,18 @@ int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next) {
     if (!(seconds >= 0.0) || seconds > 60.0) throw Error(LRT_EINVAL, "lrt_set_wait_limit: seconds in [0, 60]");
     ctx->tc_wait_ns = (uint64_t)(seconds * 1e9);
     ctx->tc_stall = stall_next ? 1 : 0;
+  });
+}
+
+int lrt_sweep_log(lrt_t ctx, int cap, double* seconds, int* mixed, int* n) {
+  return guard(ctx, [&] {
+    if (!n || cap < 0 || (cap > 0 && (!seconds || !mixed))) throw Error(LRT_EINVAL, "lrt_sweep_log: bad arguments");
+    const int m = (int)ctx->sweep_log.size();
+    for (int j = 0; j < std::min(cap, m); ++j) {
+      seconds[j] = ctx->sweep_log[j].first;
+      mixed[j] = ctx->sweep_log[j].second;
+    }
+    *n = m;
   });
 }
 

@@ -192,11 +192,18 @@ def test_tda_mixed_precision_matches_fp64_and_the_definition(pkg):
     sites = _stationary_sites(H, M)
     L0, R0, C0, Lam, _ = om.mixed_canonical(sites)
     w, E0, dim = tda.tangent_rr(H, L0, R0, C0, Lam, n)
-    out = {}
+    out, logs = {}, {}
     for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
         ctx = _prepared(pkg, H, sites)
         out[prec] = ctx.sweep_tda(n, max_iter=120, eps=1e-10, keep=4, precision=prec)
+        logs[prec] = (ctx.sweep_log(), ctx.sweeps())
         ctx.close()
+    # the sweep log: the start sweep and every Davidson sweep, timed; the mixed form starts
+    # on the tensor cores and ends in FP64 (its refinement), the FP64 form never uses them
+    for prec, (log, nsw) in logs.items():
+        assert len(log) == nsw + 1 and all(t > 0.0 for t, _ in log)
+    assert not any(f for _, f in logs[pkg.LRT_FP64][0])
+    assert logs[pkg.LRT_MIXED][0][0][1] == 1 and logs[pkg.LRT_MIXED][0][-1][1] == 0
     (w64, r64, e64), (wmx, rmx, emx) = out[pkg.LRT_FP64], out[pkg.LRT_MIXED]
     assert abs(e64 - emx) < 1e-12          # the reference energy is FP64 in both
     assert np.all(rmx < 1e-10)
