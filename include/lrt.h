@@ -67,9 +67,10 @@ const char* lrt_last_error(lrt_t ctx);
 
 /* Hamiltonian (the Hamiltonian of Sec. "Illustrative Applications", ab initio form).
  * h: k*k row-major one-electron integrals; eri: k^4 chemist (ij|kl) row-major, or NULL
- * when the factor B (n_factor*k*k, (ij|kl) = sum_L B[L,i,j] B[L,k,l]) is given instead.
- * Integrals must have the 8-fold real symmetry.  Replaces any previous Hamiltonian
- * and drops all renormalized blocks. */
+ * when the factor B (n_factor*k*k, (ij|kl) = sum_L B[L,i,j] B[L,k,l]) is given instead;
+ * eri NULL, n_factor 0 and B NULL give a one-body operator (no two-electron part, e.g. the
+ * perturbation of sweep_response).  Integrals must have the 8-fold real symmetry.
+ * Replaces any previous Hamiltonian and drops all renormalized blocks. */
 int op_build(lrt_t ctx, int k, const double* h, const double* eri, int n_factor,
              const double* B, double e_core);
 
@@ -258,6 +259,30 @@ int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next);
  * Arguments and status as for sweep_tda; gamma holds nroots * k * k doubles (host). */
 int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* params, double* omega, double* resid, double* e0,
                       double* gamma);
+/* Frequency-dependent linear response at the Tamm-Dancoff level (Sec. "Time-Dependent DMRG
+ * Equation and Linear Response Theory (LRT)", Eqs. pt_ext, realresp, imagresp, psi1st).
+ * A one-body perturbation V = sum_pq d_pq sum_sigma a+_{p sigma} a_{q sigma} drives the
+ * reference; its two first-order components X, Y in the tangent space solve, site by site,
+ *   Q^C (H_0^[i] - (E0 +- omega)) C1_i = -Q^C (dH_i C0 + V_i C0)
+ * (dH_i C0: the first-order products of the rest of the component, as in the TDA sigma),
+ * in forward sweeps (each site solved by preconditioned MINRES, the rest fixed) with
+ * backward sweeps carrying the gauge.  alpha(omega) = <V Psi0|X> + <V Psi0|Y>, whose poles
+ * are the TDA excitation energies; at omega = 0 it is the static response.  The site
+ * iteration converges below the first pole; near and above it the sweeps need not. */
+typedef struct {
+  int max_sweeps;      /* forward + backward sweeps per component (0: 40) */
+  double tol;          /* sum_i |site residual|^2 at which a component stops (0: 1e-16) */
+  int minres_max;      /* MINRES iterations per site solve (0: 200) */
+  double minres_tol;   /* relative preconditioned residual of a site solve (0: 1e-12) */
+  double pinv_cut;     /* as in lrt_tda_params (0: 1e-12) */
+} lrt_resp_params;
+/* sweep_response: ctx holds H and the reference (op_build, mps_load, tda_prepare); vctx holds
+ * V as a one-body Hamiltonian (op_build with h = d, no two-electron part, e_core 0) and the
+ * same MPS, also tda_prepare'd (both references must agree bit for bit, else LRT_EINVAL).
+ * FP64.  Writes *alpha, resid[2] (the last sweep's sum of squared site residuals of X and of
+ * Y) and sweeps[2]; omega >= 0.  LRT_EINVAL on bad arguments, LRT_ESTATE on call order. */
+int sweep_response(lrt_t ctx, lrt_t vctx, double omega, const lrt_resp_params* params, double* alpha, double* resid,
+                   int* sweeps);
 /* lrt_sweeps: *sweeps = the number of sweeps the last sweep_gs (two-site sweeps) or
  * sweep_tda (Davidson iterations after the start sweep) on this context ran. */
 int lrt_sweeps(lrt_t ctx, int* sweeps);

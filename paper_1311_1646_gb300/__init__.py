@@ -22,7 +22,7 @@ LRT_CORR_SWEEP = 1
 
 EXPORTS = ["lrt_create", "lrt_destroy", "lrt_last_error", "op_build", "mps_load", "wfn_layout",
            "renormalize", "sigma", "heff_diag", "sigma_stats", "sigma_noalloc", "sweep_gs",
-           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "sweep_tda_density", "lrt_sweeps", "lrt_sweep_log", "lrt_set_wait_limit", "sigma_batched",
+           "mps_save", "mps_get_bonds", "mps_get_site", "tda_load", "tda_prepare", "tda_stationarity", "sweep_tda", "sweep_tda_density", "sweep_response", "lrt_sweeps", "lrt_sweep_log", "lrt_set_wait_limit", "sigma_batched",
            "sweep_tda_batched"]
 
 _lib = None
@@ -66,6 +66,11 @@ class TdaParams(ctypes.Structure):
                 ("corr_tol", ctypes.c_double), ("start_shift", ctypes.c_double)]
 
 
+class RespParams(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double), ("minres_max", ctypes.c_int),
+                ("minres_tol", ctypes.c_double), ("pinv_cut", ctypes.c_double)]
+
+
 class LrtError(RuntimeError):
     pass
 
@@ -105,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.tda_stationarity.argtypes = [vp, dp, dp]
     lib.lrt_sweeps.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.lrt_sweep_log.argtypes = [vp, i, dp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.sweep_response.argtypes = [vp, vp, d, ctypes.POINTER(RespParams), dp, dp, ctypes.POINTER(ctypes.c_int)]
     lib.lrt_set_wait_limit.argtypes = [vp, d, i]
     lib.sigma_batched.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i,
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i]
@@ -301,6 +307,19 @@ class Context:
         n = ctypes.c_int()
         self._check(self.lib.lrt_sweeps(self.h, ctypes.byref(n)), "lrt_sweeps")
         return n.value
+
+    def sweep_response(self, vctx: "Context", omega: float, max_sweeps: int = 0, tol: float = 0.0,
+                       minres_max: int = 0, minres_tol: float = 0.0, pinv_cut: float = 0.0):
+        """Tamm-Dancoff linear response alpha(omega) to the one-body perturbation held by
+        `vctx` (op_build with h = d and no two-electron part, the same MPS, tda_prepare'd).
+        Returns (alpha, resid[2], sweeps[2])."""
+        a = ctypes.c_double()
+        rs = np.zeros(2)
+        sw = (ctypes.c_int * 2)()
+        p = RespParams(max_sweeps, tol, minres_max, minres_tol, pinv_cut)
+        self._check(self.lib.sweep_response(self.h, vctx.h, float(omega), ctypes.byref(p), ctypes.byref(a), _dptr(rs),
+                                            sw), "sweep_response")
+        return a.value, rs, (sw[0], sw[1])
 
     def sweep_log(self):
         """[(seconds, mixed)] of every sweep of the last sweep_tda (the start sweep first)."""

@@ -4673,6 +4673,224 @@ struct TdaRunner {
       m = (l + n <= N) ? l : keep;
     }
   }
+
+  // ---- frequency-dependent linear response at the Tamm-Dancoff level ----
+  // (Eqs. realresp, imagresp): the first-order wavefunction X of a one-body perturbation V
+  // in the tangent space, from the site equations
+  //     Q^C (H_0^[i] - shift) Q^C C1_i = -Q^C (ΔH_i C0 + V_i C0),
+  // ΔH_i C0 the products of the first-order left and right sets of the rest of X (as in the
+  // TDA's sigma, Eq. sigv2) and V_i C0 the site-i effective V applied to C0 (`vc0`).  Each
+  // forward sweep solves every site in turn, the rest of X fixed (site Gauss-Seidel), by
+  // preconditioned MINRES (the shifted equations may be indefinite); the backward sweep
+  // carries the gauge and builds the first-order right sets as in the TDA.  Returns
+  // <V Psi0|X> = sum_i <piece_i, V_i C0> over the centred one-site pieces of X (the
+  // decomposition of the transition densities); res2 = the last sweep's sum_i |site
+  // residual|^2 before its solve.
+  DevBuf rtmp;
+  double dotd(const double* a, const double* b, int64_t n) {
+    rtmp.ensure(8);
+    return dev_dot(a, b, n, rtmp.p, c->st);
+  }
+  // y = a x + b y
+  void axpbyd(double a, const double* x, double b, double* y, int64_t n) {
+    rtmp.ensure(8);
+    CK(cudaMemcpyAsync(rtmp.p, &a, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_lincomb(x, n, 1, rtmp.p, n, y, b, c->st);
+    CK(cudaStreamSynchronize(c->st));
+  }
+  void projCd(int i, double* x) { axpbyd(-dotd(C0(i).d, x, T(i)), C0(i).d, 1.0, x, T(i)); }
+  // x = solution of Q (H_0^[i] - shift) Q x = b (b orthogonal to C0_i), x on entry the
+  // start; preconditioned MINRES with M = |diag H_0^[i] - shift|, both projected by Q^C
+  int site_minres(int i, double shift, const double* b, double* x, int maxit, double rtol) {
+    const int64_t n = T(i);
+    if (n == 0) return 0;
+    std::vector<DevBuf> buf(9);
+    for (auto& q : buf) {
+      q.ensure((size_t)n);
+      CK(cudaMemsetAsync(q.p, 0, (size_t)n * sizeof(double), c->st));
+    }
+    double *v0 = buf[0].p, *v1 = buf[1].p, *v2 = buf[2].p, *z1 = buf[3].p, *z2 = buf[4].p, *w0 = buf[5].p,
+           *w1 = buf[6].p, *w2 = buf[7].p, *az = buf[8].p;
+    auto A = [&](const double* in, double* out) {   // out = Q (H_0 - shift) in, in orthogonal to C0
+      run_plan(*h0one[i], in, out, 1, false);
+      axpbyd(-shift, in, 1.0, out, n);
+      projCd(i, out);
+    };
+    auto Minv = [&](const double* in, double* out) {
+      launch_precond_abs(in, diag[i].p, shift, n, out, c->st);
+      projCd(i, out);
+    };
+    projCd(i, x);
+    A(x, az);                                       // v1 = b - A x
+    CK(cudaMemcpyAsync(v1, b, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    axpbyd(-1.0, az, 1.0, v1, n);
+    Minv(v1, z1);
+    double g1 = std::sqrt(std::max(0.0, dotd(z1, v1, n)));
+    const double g_start = g1;
+    if (!(g1 > 0.0)) return 0;
+    double g0 = 1.0, eta = g1, s0 = 0.0, s1 = 0.0, c0 = 1.0, c1 = 1.0;
+    int it = 0;
+    while (it < maxit) {
+      ++it;
+      axpbyd(0.0, z1, 1.0 / g1, z1, n);             // z1 /= g1
+      A(z1, az);
+      const double delta = dotd(az, z1, n);
+      CK(cudaMemcpyAsync(v2, az, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      axpbyd(-delta / g1, v1, 1.0, v2, n);
+      axpbyd(-g1 / g0, v0, 1.0, v2, n);
+      Minv(v2, z2);
+      const double g2 = std::sqrt(std::max(0.0, dotd(z2, v2, n)));
+      const double a0 = c1 * delta - c0 * s1 * g1;
+      const double a1 = std::sqrt(a0 * a0 + g2 * g2);
+      const double a2 = s1 * delta + c0 * c1 * g1;
+      const double a3 = s0 * g1;
+      if (!(a1 > 0.0)) break;
+      const double c2 = a0 / a1, s2 = g2 / a1;
+      // w2 = (z1 - a3 w0 - a2 w1) / a1
+      CK(cudaMemcpyAsync(w2, z1, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      axpbyd(-a3, w0, 1.0, w2, n);
+      axpbyd(-a2, w1, 1.0, w2, n);
+      axpbyd(0.0, w2, 1.0 / a1, w2, n);
+      axpbyd(c2 * eta, w2, 1.0, x, n);
+      eta = -s2 * eta;
+      std::swap(v0, v1);
+      std::swap(v1, v2);
+      std::swap(z1, z2);
+      std::swap(w0, w1);
+      std::swap(w1, w2);
+      g0 = g1;
+      g1 = g2;
+      c0 = c1;
+      c1 = c2;
+      s0 = s1;
+      s1 = s2;
+      if (std::fabs(eta) <= rtol * g_start || !(g2 > 0.0)) break;
+    }
+    return it;
+  }
+
+  double response_component(const std::vector<DevBuf>& vc0, double shift, int max_sweeps, double tol, int mr_max,
+                             double mr_tol, double& res2_out, int& sweeps_out) {
+    blk = 1;
+    std::vector<SiteBatch> oldR1(k);
+    std::vector<SetBatch> oldHR(k + 1);
+    bool have_old = false;
+    std::vector<SiteBatch> keep(k);
+    double res2 = 0.0;
+    int sw = 0;
+    while (sw < max_sweeps) {
+      ++sw;
+      res2 = 0.0;
+      // ---------------- forward sweep: solve every site ----------------
+      SiteBatch Cprev;
+      std::vector<FirstOrder> HL(1);
+      std::vector<SiteBatch> L1(k);
+      for (int i = 0; i < k; ++i) {
+        SiteBatch C1;
+        batch_alloc(c, C1, T(i), 1, 1);
+        // Eq. gauge_fwd: the left part carried in, the right part of the last backward sweep
+        if (i > 0) {
+          BondBatch X;
+          b_lc(i - 1, L0(i - 1), Cprev, 1, X);
+          b_lmulb(i, X, 1, R0(i), C1, false);
+          if (have_old) b_lmul(i, lam[i], oldR1[i], 1, C1, true);
+        } else if (have_old) {
+          b_lmul(i, lam[0], oldR1[i], 1, C1, false);
+        }
+        // rhs = -Q^C (ΔH_i C0 + V_i C0)
+        SiteBatch dl, dr, rhs;
+        batch_alloc(c, dl, T(i), 1, 1);
+        batch_alloc(c, dr, T(i), 1, 1);
+        batch_alloc(c, rhs, T(i), 1, 1);
+        std::vector<Enl> XE = enlarge_left_batch(i, HL);
+        dh_left_batch(i, XE, dl);
+        if (have_old && i + 1 < k && !oldHR[i + 1].empty()) dh_right_batch(i, oldHR[i + 1], 1, dr);
+        if (T(i) > 0) {
+          double* r = rhs.v(0);
+          axpbyd(-1.0, dl.v(0), 0.0, r, T(i));
+          axpbyd(-1.0, dr.v(0), 1.0, r, T(i));
+          axpbyd(-1.0, vc0[i].p, 1.0, r, T(i));
+          projCd(i, r);
+          // the residual of the current C1_i, then the solve from it
+          DevBuf az;
+          az.ensure((size_t)T(i));
+          projCd(i, C1.v(0));
+          run_plan(*h0one[i], C1.v(0), az.p, 1, false);
+          axpbyd(-shift, C1.v(0), 1.0, az.p, T(i));
+          projCd(i, az.p);
+          axpbyd(-1.0, r, 1.0, az.p, T(i));
+          res2 += dotd(az.p, az.p, T(i));
+          site_minres(i, shift, r, C1.v(0), mr_max, mr_tol);
+        }
+        batch_alloc(c, keep[i], T(i), 1, 1);
+        b_copy(C1, 0, 1, keep[i], 0);
+        // Eqs. left1st and lopr1st
+        SiteBatch Ct;
+        batch_alloc(c, Ct, T(i), 1, 1);
+        b_projL(i, C1, 1, Ct);
+        batch_alloc(c, L1[i], T(i), 1, 1);
+        b_rmul(i, Ct, 1, ilam[i + 1], L1[i], false);
+        if (i + 1 < k) HL = grow_HL_batch(i, XE, L1[i], 1);
+        Cprev = std::move(C1);
+      }
+      HL.clear();
+      // ---------------- backward sweep: gauge, R1 and the first-order right sets ----------------
+      std::vector<SiteBatch> newR1(k);
+      std::vector<SetBatch> newHR(k + 1);
+      std::vector<FirstOrder> HR(1);
+      SiteBatch Cb;
+      batch_alloc(c, Cb, T(k - 1), 1, 1);
+      b_rmul(k - 1, L1[k - 1], 1, lam[k], Cb, false);
+      for (int i = k - 1; i >= 0; --i) {
+        if (i < k - 1) {
+          BondBatch Y;
+          b_rc(i + 1, Cb, 1, R0(i + 1), Y);
+          SiteBatch nb;
+          batch_alloc(c, nb, T(i), 1, 1);
+          b_rmul(i, L1[i], 1, lam[i + 1], nb, false);
+          b_rmulb(i, L0(i), Y, 1, nb, true);
+          Cb = std::move(nb);
+        }
+        L1[i] = SiteBatch();
+        SiteBatch pr;
+        batch_alloc(c, pr, T(i), 1, 1);
+        b_projR(i, Cb, 1, pr);
+        batch_alloc(c, newR1[i], T(i), 1, 1);
+        b_lmul(i, ilam[i], pr, 1, newR1[i], false);
+        if (i > 0) {
+          HR = grow_HR_batch(i, HR, newR1[i], 1);
+          set_batch(c, newHR[i], *HR[0].f, *HR[0].r, 1);
+          if (HR[0].f->total > 0)
+            CK(cudaMemcpyAsync(newHR[i].fv(0), HR[0].f->d, (size_t)HR[0].f->total * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->st));
+          if (HR[0].r->total > 0)
+            CK(cudaMemcpyAsync(newHR[i].rv(0), HR[0].r->d, (size_t)HR[0].r->total * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->st));
+        }
+      }
+      HR.clear();
+      oldR1 = std::move(newR1);
+      oldHR = std::move(newHR);
+      have_old = true;
+      CK(cudaStreamSynchronize(c->st));
+      if (sw > 1 && res2 < tol) break;
+    }
+    // <V Psi0|X> over the centred pieces of the last forward sweep
+    const int cc = k / 2;
+    double a = 0.0;
+    for (int i = 0; i < k; ++i) {
+      if (T(i) == 0) continue;
+      SiteBatch P;
+      batch_alloc(c, P, T(i), 1, 1);
+      if (i < cc) b_projL(i, keep[i], 1, P);
+      else if (i == cc) b_copy(keep[i], 0, 1, P, 0);
+      else b_projR(i, keep[i], 1, P);
+      a += dotd(P.v(0), vc0[i].p, T(i));
+    }
+    res2_out = res2;
+    sweeps_out = sw;
+    return a;
+  }
 };
 
 // Mixed-canonical gauge of the whole MPS (the form the TDA sweep works in): on every
@@ -5172,7 +5390,8 @@ const char* lrt_last_error(lrt_t ctx) { return ctx ? ctx->err.c_str() : g_create
 int op_build(lrt_t ctx, int k, const double* h, const double* eri, int n_factor, const double* B,
              double e_core) {
   return guard(ctx, [&] {
-    if (k <= 0 || k > 128 || !h || (!eri && (!B || n_factor <= 0)))
+    // no eri and no factor: a one-body operator
+    if (k <= 0 || k > 128 || !h || n_factor < 0 || (!eri && n_factor > 0 && !B))
       throw Error(LRT_EINVAL, "op_build: bad arguments");
     if (ctx->have_mps && ctx->k != k) throw Error(LRT_EINVAL, "op_build: k differs from the loaded MPS");
     build_ints(ctx->I, k, h, eri, n_factor, B, e_core);
@@ -5422,6 +5641,61 @@ int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* p, double* om
   if (e0) *e0 = E0;
   if (rc != LRT_OK) ctx->err = "sweep_tda_density: not converged within max_iter (results written)";
   return rc;
+}
+
+int sweep_response(lrt_t ctx, lrt_t vctx, double omega, const lrt_resp_params* p, double* alpha, double* resid,
+                   int* sweeps) {
+  return guard(ctx, [&] {
+    if (!p || !alpha || !resid || !sweeps || !vctx || vctx == ctx || !(omega >= 0.0))
+      throw Error(LRT_EINVAL, "sweep_response: bad arguments");
+    if (!ctx->tda || !ctx->tda->loaded) throw Error(LRT_ESTATE, "sweep_response: tda_load or tda_prepare first");
+    if (!vctx->tda || !vctx->tda->loaded || !vctx->have_ham)
+      throw Error(LRT_ESTATE, "sweep_response: the perturbation's context needs op_build and tda_prepare");
+    if (vctx->dev != ctx->dev || vctx->k != ctx->k) throw Error(LRT_EINVAL, "sweep_response: contexts differ in device or k");
+    const int k = ctx->k;
+    lrt_tda_params tp{};
+    tp.precision = LRT_FP64;
+    tp.pinv_cut = p->pinv_cut > 0.0 ? p->pinv_cut : 1e-12;
+    TdaRunner R(ctx, tp);
+    R.setup();
+    // V_i C0 at every site from the perturbation's environment, on the same reference
+    std::vector<DevBuf> vc0(k);
+    for (int i = 0; i < k; ++i) vc0[i].ensure((size_t)std::max<int64_t>(R.T(i), 1));
+    CK(cudaStreamSynchronize(ctx->st));
+    {
+      PoolScope ps(&vctx->pool);
+      TdaRunner V(vctx, tp);
+      V.setup();
+      for (int i = 0; i < k; ++i) {
+        if (V.T(i) != R.T(i)) throw Error(LRT_EINVAL, "sweep_response: the two contexts hold different MPS layouts");
+        if (R.T(i) == 0) continue;
+        // the same reference in both: C0_i bit for bit (tda_prepare is deterministic)
+        DevBuf dif;
+        dif.ensure((size_t)R.T(i));
+        CK(cudaMemcpyAsync(dif.p, R.C0(i).d, (size_t)R.T(i) * sizeof(double), cudaMemcpyDeviceToDevice, vctx->st));
+        V.axpbyd(-1.0, V.C0(i).d, 1.0, dif.p, R.T(i));
+        if (V.dotd(dif.p, dif.p, R.T(i)) != 0.0)
+          throw Error(LRT_EINVAL, "sweep_response: the two contexts hold different references");
+        V.run_plan(*V.h0one[i], R.C0(i).d, vc0[i].p, 1, false);
+      }
+      CK(cudaStreamSynchronize(vctx->st));
+    }
+    const int ms = p->max_sweeps > 0 ? p->max_sweeps : 40;
+    const double tol = p->tol > 0.0 ? p->tol : 1e-16;
+    const int mr = p->minres_max > 0 ? p->minres_max : 200;
+    const double mrt = p->minres_tol > 0.0 ? p->minres_tol : 1e-12;
+    // X: (H - (E0 + omega)) X = -v, Y: (H - (E0 - omega)) Y = -v; alpha = v.(X + Y)
+    double r2x = 0.0, r2y = 0.0;
+    int swx = 0, swy = 0;
+    const double ax = R.response_component(vc0, R.E0 + omega, ms, tol, mr, mrt, r2x, swx);
+    const double ay = R.response_component(vc0, R.E0 - omega, ms, tol, mr, mrt, r2y, swy);
+    *alpha = ax + ay;
+    resid[0] = r2x;
+    resid[1] = r2y;
+    sweeps[0] = swx;
+    sweeps[1] = swy;
+    ctx->last_sweeps = swx + swy;
+  });
 }
 
 int lrt_set_wait_limit(lrt_t ctx, double seconds, int stall_next) {

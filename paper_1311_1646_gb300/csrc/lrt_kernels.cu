@@ -639,6 +639,17 @@ __global__ void __launch_bounds__(256) precond_batch_kernel(const double* __rest
   }
 }
 
+__global__ void __launch_bounds__(256) precond_abs_kernel(const double* __restrict__ R, const double* __restrict__ d,
+                                                          double shift, int64_t n, double* __restrict__ Z) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    Z[e] = R[e] / fmax(fabs(d[e] - shift), 1e-4);
+}
+
+void launch_precond_abs(const double* R, const double* d, double shift, int64_t n, double* Z, cudaStream_t st) {
+  if (n <= 0) return;
+  precond_abs_kernel<<<vec_grid(n), 256, 0, st>>>(R, d, shift, n, Z);
+}
+
 void launch_precond_batch(const double* R, int64_t ldr, const double* d, const double* theta, int nv, int64_t n,
                           double* Z, int64_t ldz, double sign, cudaStream_t st) {
   if (nv <= 0 || n <= 0) return;
