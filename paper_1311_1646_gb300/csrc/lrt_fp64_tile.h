@@ -65,6 +65,27 @@ LRT_HD const double* seg_b(const SegS& s, int kl, int col) {
   return s.transB ? b + (int64_t)col * s.ldb + kl : b + (int64_t)kl * s.ldb + col;
 }
 
+// K parts of an output whose segments have K k[0..nseg) (total ktot): at most `want` runs
+// of whole segments, cut after segment q once the K so far reaches (parts + 1) / want of
+// ktot, the last run taking whatever remains (zero-K segments included);
+// emit(sb, se, kp) for segments [sb, se) with K kp.  Depends on the segment list only.
+template <class F>
+LRT_HD int split_segments(const int* k, int nseg, long long ktot, int want, F&& emit) {
+  int parts = 0, sb = 0;
+  long long acc = 0, kp = 0;
+  for (int q = 0; q < nseg; ++q) {
+    acc += k[q];
+    kp += k[q];
+    if (q + 1 == nseg || (parts + 1 < want && acc * want >= ktot * (parts + 1))) {
+      emit(sb, q + 1, kp);
+      ++parts;
+      sb = q + 1;
+      kp = 0;
+    }
+  }
+  return parts;
+}
+
 // the segment holding K position p (p < kst[nb]), searching forward from q
 LRT_HD int seg_at(const int* kst, int p, int q) {
   while (kst[q + 1] <= p) ++q;

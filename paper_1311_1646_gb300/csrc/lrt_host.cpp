@@ -787,30 +787,23 @@ static void build_gemm(GemmPlan& P, const std::vector<GemmOut>& outs_in, const s
         if (split && want >= 2 && O.c_rel <= 2 && outs.size() < (size_t)INT32_MAX) {
           // contiguous runs of the segment list, each about ktot / want of K
           SplitTile t{wsz, (int)i, 0, m0, mt, n0, nt};
-          int sb = 0;
-          int64_t acc = 0;
-          for (int q = 0; q < O.seg_count; ++q) {
-            acc += segs[O.seg_begin + q].k;
-            const bool last = q + 1 == O.seg_count;
-            if (last || acc * want >= ktot[i] * (t.nparts + 1)) {
-              GemmOut po = O;
-              po.C = nullptr;
-              po.c_rel = GEMM_C_SPLIT;
-              po.c_off = wsz + (int64_t)t.nparts * mt * nt - ((int64_t)m0 * nt + n0);
-              po.ldc = nt;
-              po.accumulate = 0;
-              po.c_vr = po.c_vc = 0;
-              po.c_vs = 0;
-              po.seg_begin = O.seg_begin + sb;
-              po.seg_count = q + 1 - sb;
-              int64_t kp = 0;
-              for (int u = sb; u <= q; ++u) kp += segs[O.seg_begin + u].k;
-              outs.push_back(po);
-              tl.push_back({cost(mt, nt, kp), gemm_tile((int)outs.size() - 1, m0, mt, n0, nt)});
-              ++t.nparts;
-              sb = q + 1;
-            }
-          }
+          std::vector<int> kseg(O.seg_count);
+          for (int q = 0; q < O.seg_count; ++q) kseg[q] = segs[O.seg_begin + q].k;
+          split_segments(kseg.data(), O.seg_count, ktot[i], want, [&](int sb, int se, long long kp) {
+            GemmOut po = O;
+            po.C = nullptr;
+            po.c_rel = GEMM_C_SPLIT;
+            po.c_off = wsz + (int64_t)t.nparts * mt * nt - ((int64_t)m0 * nt + n0);
+            po.ldc = nt;
+            po.accumulate = 0;
+            po.c_vr = po.c_vc = 0;
+            po.c_vs = 0;
+            po.seg_begin = O.seg_begin + sb;
+            po.seg_count = se - sb;
+            outs.push_back(po);
+            tl.push_back({cost(mt, nt, kp), gemm_tile((int)outs.size() - 1, m0, mt, n0, nt)});
+            ++t.nparts;
+          });
           wsz += (int64_t)t.nparts * mt * nt;
           sp.push_back(t);
           continue;

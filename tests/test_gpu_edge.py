@@ -89,3 +89,33 @@ def test_many_right_hand_sides_match_one_at_a_time(pkg):
         ctx.sigma(i, nsite, X[v * n:(v + 1) * n].contiguous(), y1)
         assert float((Y[v * n:(v + 1) * n] - y1).abs().max() / y1.abs().max()) <= 1e-14
     ctx.close()
+
+
+def test_sigma_on_a_second_device_matches_the_first(pkg):
+    """Kernel attributes (dynamic shared memory above 48 KB) are per device: a context on
+    device 1 after one on device 0 runs the same FP64 and mixed sigma, to rounding."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one visible device")
+    H = synth.ab_initio(6, 3, 3, 9)
+    out = []
+    for dev in (0, 1):
+        m = synth.mixed_mps(H.k, H.n_alpha, H.n_beta, 16, 5, center=2)
+        ctx = pkg.Context(dev)
+        ctx.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+        ctx.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 2)
+        for b in range(2):
+            ctx.renormalize(b, +1)
+        for b in range(H.k - 1, 2, -1):
+            ctx.renormalize(b, -1)
+        n, _ = ctx.wfn_layout(2, 1)
+        x = torch.tensor(synth.random_vector(n, 3), dtype=torch.float64, device=f"cuda:{dev}")
+        ys = []
+        for prec in (pkg.LRT_FP64, pkg.LRT_MIXED):
+            y = torch.empty_like(x)
+            ctx.sigma(2, 1, x, y, precision=prec)
+            torch.cuda.synchronize(dev)
+            ys.append(y.cpu().numpy())
+        ctx.close()
+        out.append(ys)
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-12 * np.abs(out[0][0]).max()
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-5 * np.abs(out[0][1]).max()
