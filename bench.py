@@ -472,6 +472,59 @@ def _tda_sweep_times(pkg, device, cfg_idx=3, iters=3):
     return out
 
 
+def _lr_k8(pkg, device, nroots=4):
+    """The 8-orbital workload (M = 64): the TDA roots with their one-particle transition
+    densities (sweep_tda_density; square norms as in Table site_excitation) and the
+    Tamm-Dancoff response alpha(omega) to a seeded one-body perturbation at omega = 0 and
+    at half the lowest TDA root (sweep_response), FP64, on the GPU ground state."""
+    import torch
+    cfg = synth.config(1)
+    H = cfg["ham"]
+    g = pkg.Context(device)
+    g.op_build(H.k, H.h, H.eri, e_core=H.e_core)
+    m = synth.random_mps(H.k, H.n_alpha, H.n_beta, 16, 3, "right")
+    g.mps_load(H.k, H.n_alpha, H.n_beta, m.bonds, m.sites, 0)
+    g.sweep_gs([32, 64], max_sweeps=14, e_tol=1e-12, dav_tol=1e-10, onesite_sweeps=20)
+    bonds, sites = g.mps_get()
+    g.close()
+
+    def prepared(h, eri, e_core):
+        c = pkg.Context(device)
+        c.op_build(H.k, h, eri, e_core=e_core)
+        c.mps_load(H.k, H.n_alpha, H.n_beta, bonds, sites, 0)
+        c.tda_prepare()
+        return c
+
+    out = {}
+    c = prepared(H.h, H.eri, H.e_core)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    om, rs, e0, gam = c.sweep_tda_density(nroots, max_iter=200, eps=1e-9, allow_noconv=True,
+                                          keep=TDA_KEEP * nroots, **TDA_KW)
+    torch.cuda.synchronize()
+    out["density_s_per_root"] = (time.perf_counter() - t0) / nroots
+    out["omega"] = [float(x) for x in om]
+    out["square_norm"] = [float(np.sum(gg * gg)) for gg in gam]
+    out["resid"] = [float(x) for x in rs]
+    d = np.random.default_rng(11).standard_normal((H.k, H.k))
+    d = 0.5 * (d + d.T)
+    v = prepared(d, None, 0.0)
+    resp = []
+    for w in (0.0, 0.5 * float(om[0])):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, r2, sw = c.sweep_response(v, w, tol=1e-20, max_sweeps=80)
+        torch.cuda.synchronize()
+        resp.append({"omega": w, "alpha": a, "resid": [float(x) for x in r2], "sweeps": list(sw),
+                     "s": time.perf_counter() - t0})
+    out["response"] = resp
+    c.close()
+    v.close()
+    out["note"] = ("square_norm = sum_pq gamma_pq^2 with gamma_pq = <Psi^mu| sum_sigma a+_p a_q |Psi0>; "
+                   "response: X and Y components, site equations to sum |r|^2 < 1e-20")
+    return out
+
+
 def extras(pkg, ctx, device, S, stream, flush, args):
     """Side measurements, outside the timed steps."""
     import torch
@@ -544,6 +597,10 @@ def extras(pkg, ctx, device, S, stream, flush, args):
     # (4) TDA s/root at convergence, FP64 against the mixed form: the 8-orbital ab initio
     # workload (M = 64, 4 roots) and the PPP polyene (M = 256, 6 roots)
     out["tda_abinitio_k8_M64_4roots"] = _tda_converged(pkg, device, 1, [32, 64], 1e-9, 200)
+    try:
+        out["linear_response_k8_M64"] = _lr_k8(pkg, device)
+    except Exception as e:
+        out["linear_response_k8_M64"] = {"error": repr(e)}
     if not args.quick_tda:
         out["tda_ppp_k12_M256_6roots"] = _tda_converged(pkg, device, 2, [64, 128, 256], 1e-9, 200)
         try:
