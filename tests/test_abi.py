@@ -98,3 +98,17 @@ def test_binding_checks_host_array_sizes_before_the_call():
     for f in bad:
         with pytest.raises(pkg.LrtError):
             f()
+
+
+def test_new_entries_reject_null_handles_without_a_gpu(lib):
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    out = (ctypes.c_double * 4)()
+    ni = (ctypes.c_int * 2)()
+    lib.sweep_response.argtypes = [vp, vp, d, vp, vp, vp, vp]
+    assert lib.sweep_response(None, None, 0.1, None, out, out, ni) == -1
+    lib.sweep_tda_density.argtypes = [vp, i, vp, vp, vp, vp, vp]
+    assert lib.sweep_tda_density(None, 1, None, out, out, out, out) == -1
+    lib.lrt_sweep_log.argtypes = [vp, i, vp, vp, vp]
+    assert lib.lrt_sweep_log(None, 0, None, None, ni) == -1
+    lib.lrt_set_wait_limit.argtypes = [vp, d, i]
+    assert lib.lrt_set_wait_limit(None, 1.0, 0) == -1
