@@ -186,3 +186,33 @@ def test_state_errors_are_reported(pkg):
         ctx.sigma(1, 1, x, x)              # x and y overlap
     ctx.sigma(1, 1, x, y)
     ctx.close()
+
+
+@pytest.mark.parametrize("nsite", [1, 2])
+def test_sigma_with_factorized_integrals(pkg, nsite):
+    """The two-electron integrals given as the factor B ((ij|kl) = sum_L B_Lij B_Lkl, the form
+    the [2Fe-2S]-shaped workload uses: rank-limited factor, near-degenerate replaced diagonal)
+    instead of the k^4 tensor: the same sigma as from the tensor, and the oracle's."""
+    k = 8
+    d = np.concatenate([np.linspace(-2.0, -1.1, 3), -1.0 + 0.1 * np.linspace(0.0, 1.0, 3), np.linspace(-0.8, 0.0, 2)])
+    H = synth.ab_initio(k, 3, 3, 41, nL=5, diag=d, replace_diag=True)
+    c = Case(pkg, H, 24, 3, nsite, 43)
+    x = synth.random_vector(2 * c.n, 5)
+    y_eri = c.gpu_sigma(x, nvec=2)
+    f = pkg.Context(0)
+    f.op_build(k, H.h, None, B=H.B, e_core=H.e_core)
+    f.mps_load(k, H.n_alpha, H.n_beta, c.m.bonds, c.m.sites, c.i)
+    for b in range(c.i):
+        f.renormalize(b, +1)
+    for b in range(k - 1, c.i + nsite - 1, -1):
+        f.renormalize(b, -1)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda:0")
+    yd = torch.full_like(xd, np.nan)
+    f.sigma(c.i, nsite, xd, yd, nvec=2)
+    torch.cuda.synchronize()
+    y_fac = yd.cpu().numpy()
+    f.close()
+    assert _rel(y_fac, y_eri) < RTOL
+    for v in range(2):
+        assert _rel(y_fac[v * c.n:(v + 1) * c.n], c.oracle_sigma(x[v * c.n:(v + 1) * c.n])) < RTOL
+    c.ctx.close()
