@@ -266,16 +266,28 @@ int sweep_tda_density(lrt_t ctx, int nroots, const lrt_tda_params* params, doubl
  *   Q^C (H_0^[i] - (E0 +- omega)) C1_i = -Q^C (dH_i C0 + V_i C0)
  * (dH_i C0: the first-order products of the rest of the component, as in the TDA sigma),
  * in forward sweeps (each site solved by preconditioned MINRES, the rest fixed) with
- * backward sweeps carrying the gauge.  alpha(omega) = <V Psi0|X> + <V Psi0|Y>, whose poles
- * are the TDA excitation energies; at omega = 0 it is the static response.  The site
- * iteration converges below the first pole; near and above it the sweeps need not. */
+ * backward sweeps carrying the gauge, or (LRT_RESP_SUBSPACE) as the Galerkin solution on a
+ * subspace grown by one preconditioned residual per sweep.  alpha(omega) = <V Psi0|X> +
+ * <V Psi0|Y>, whose poles are the TDA excitation energies; at omega = 0 it is the static
+ * response.  Both forms converge below the first pole.  Between poles the component with
+ * the indefinite equations converges slowly in the subspace form (diagonal preconditioner)
+ * and not at all in the site iteration. */
 typedef struct {
   int max_sweeps;      /* forward + backward sweeps per component (0: 40) */
   double tol;          /* sum_i |site residual|^2 at which a component stops (0: 1e-16) */
   int minres_max;      /* MINRES iterations per site solve (0: 200) */
   double minres_tol;   /* relative preconditioned residual of a site solve (0: 1e-12) */
   double pinv_cut;     /* as in lrt_tda_params (0: 1e-12) */
+  int method;          /* LRT_RESP_SITE (0): the site equations solved in forward sweeps (each
+                          site by MINRES, the rest fixed; converges below the first pole);
+                          LRT_RESP_SUBSPACE (1): the sweep Davidson of the TDA carried to the
+                          linear system (a trial vector per sweep, the Galerkin solution on the
+                          subspace; its residual settles at the floor of the TDA's, so tol
+                          should stay above about 1e-10) */
+  int max_space;       /* LRT_RESP_SUBSPACE: trial vectors before a restart (0: 24) */
 } lrt_resp_params;
+#define LRT_RESP_SITE 0
+#define LRT_RESP_SUBSPACE 1
 /* sweep_response: ctx holds H and the reference (op_build, mps_load, tda_prepare); vctx holds
  * V as a one-body Hamiltonian (op_build with h = d, no two-electron part, e_core 0) and the
  * same MPS, also tda_prepare'd (both references must agree bit for bit, else LRT_EINVAL).

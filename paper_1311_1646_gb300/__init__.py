@@ -68,7 +68,11 @@ class TdaParams(ctypes.Structure):
 
 class RespParams(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double), ("minres_max", ctypes.c_int),
-                ("minres_tol", ctypes.c_double), ("pinv_cut", ctypes.c_double)]
+                ("minres_tol", ctypes.c_double), ("pinv_cut", ctypes.c_double), ("method", ctypes.c_int),
+                ("max_space", ctypes.c_int)]
+
+
+LRT_RESP_SITE, LRT_RESP_SUBSPACE = 0, 1
 
 
 class LrtError(RuntimeError):
@@ -309,14 +313,15 @@ class Context:
         return n.value
 
     def sweep_response(self, vctx: "Context", omega: float, max_sweeps: int = 0, tol: float = 0.0,
-                       minres_max: int = 0, minres_tol: float = 0.0, pinv_cut: float = 0.0):
+                       minres_max: int = 0, minres_tol: float = 0.0, pinv_cut: float = 0.0,
+                       method: int = LRT_RESP_SITE, max_space: int = 0):
         """Tamm-Dancoff linear response alpha(omega) to the one-body perturbation held by
         `vctx` (op_build with h = d and no two-electron part, the same MPS, tda_prepare'd).
         Returns (alpha, resid[2], sweeps[2])."""
         a = ctypes.c_double()
         rs = np.zeros(2)
         sw = (ctypes.c_int * 2)()
-        p = RespParams(max_sweeps, tol, minres_max, minres_tol, pinv_cut)
+        p = RespParams(max_sweeps, tol, minres_max, minres_tol, pinv_cut, method, max_space)
         self._check(self.lib.sweep_response(self.h, vctx.h, float(omega), ctypes.byref(p), ctypes.byref(a), _dptr(rs),
                                             sw), "sweep_response")
         return a.value, rs, (sw[0], sw[1])

@@ -4762,6 +4762,211 @@ struct TdaRunner {
     return it;
   }
 
+  // The same response component in a growing subspace of tangent vectors (the sweep
+  // Davidson of the TDA, Fig. alg:dmrgtda, carried to the linear system): every sweep adds
+  // the preconditioned residual of the current solution X as a new trial vector, and X is
+  // the Galerkin solution of (H - shift) X = -v on the subspace, from the reduced matrices
+  // H_R, S_R of the sweep (Eqs. hleft2, sleft2) and b_R = <trial|V Psi0> summed site by site
+  // over the same left-gauge pieces.  The reduced system is solved through the S-orthonormal
+  // Ritz vectors (c = -sum_k u_k (u_k . b_R) / (w_k - shift)), which takes any shift; with
+  // the diagonal preconditioner the subspace converges fast below the first pole and slowly
+  // for the indefinite component between poles.  Vector 0 of every sweep is the current X; the others are the Ritz
+  // vectors of the last subspace (all but the highest, which X replaces), or the lowest
+  // keep of them at a restart.  Returns <V Psi0|X> for the X whose residual is res2.
+  double response_krylov(const std::vector<DevBuf>& vc0, double shift, int max_iter, double tol, int max_space,
+                         double& res2_out, int& sweeps_out) {
+    blk = 1;
+    const int N = std::max(4, std::min(max_space > 0 ? max_space : 24, JACOBI_MAXN));
+    const int keep = std::max(2, N / 2);
+    std::vector<SiteBatch> oldR1(k);
+    std::vector<SetBatch> oldHR(k + 1);
+    int lold = 0, m = 0, it = 0;
+    bool first = true;
+    std::vector<double> Hr, Sr, bR, alpha, bsite;
+    double r2 = 0.0, a_prev = 0.0;
+    DevBuf d_alpha, d_shift, d_H, d_S, d_D, d_r2, d_b;
+    d_shift.ensure(1);
+    CK(cudaMemcpyAsync(d_shift.p, &shift, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (;;) {
+      if (!first) {
+        std::vector<double> w, U;
+        solve_gep(Hr, Sr, lold, w, U);
+        const int r = (int)w.size();
+        if (r < 1) throw Error(LRT_EINVAL, "sweep_response: the trial subspace is empty");
+        std::vector<double> cvec(lold, 0.0);
+        for (int q = 0; q < r; ++q) {
+          double ub = 0.0;
+          for (int a = 0; a < lold; ++a) ub += U[(size_t)a * r + q] * bR[a];
+          const double den = w[q] - shift;
+          const double f = std::fabs(den) > 1e-300 ? -ub / den : 0.0;
+          for (int a = 0; a < lold; ++a) cvec[a] += f * U[(size_t)a * r + q];
+        }
+        a_prev = 0.0;
+        for (int a = 0; a < lold; ++a) a_prev += bR[a] * cvec[a];
+        const int nritz = (lold + 1 <= N) ? r - 1 : std::min(r, keep) - 1;
+        m = 1 + std::max(0, nritz);
+        alpha.assign((size_t)lold * m, 0.0);
+        for (int a = 0; a < lold; ++a) {
+          alpha[(size_t)a * m] = cvec[a];
+          for (int j = 1; j < m; ++j) alpha[(size_t)a * m + j] = U[(size_t)a * r + (j - 1)];
+        }
+        d_alpha.ensure(alpha.size());
+        CK(cudaMemcpyAsync(d_alpha.p, alpha.data(), alpha.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      }
+      const int l = m + 1;
+      d_H.ensure((size_t)l * l);
+      d_S.ensure((size_t)l * l);
+      d_D.ensure((size_t)3 * l * l);
+      d_r2.ensure(1);
+      d_b.ensure((size_t)k * l);
+      CK(cudaMemsetAsync(d_H.p, 0, (size_t)l * l * sizeof(double), c->st));
+      CK(cudaMemsetAsync(d_S.p, 0, (size_t)l * l * sizeof(double), c->st));
+      CK(cudaMemsetAsync(d_r2.p, 0, sizeof(double), c->st));
+      CK(cudaMemsetAsync(d_b.p, 0, (size_t)k * l * sizeof(double), c->st));
+      dwork.ensure((size_t)dot_work((int64_t)l * l));
+      // ---------------- forward sweep ----------------
+      SiteBatch Cprev;
+      std::vector<FirstOrder> HL(l);
+      std::vector<SiteBatch> L1(k);
+      for (int i = 0; i < k; ++i) {
+        SiteBatch C1;
+        batch_alloc(c, C1, T(i), l, 1);
+        SetBatch HRrot;
+        if (m > 0) {
+          SiteBatch R1;
+          batch_alloc(c, R1, T(i), m, 1);
+          launch_rotate(oldR1[i].buf.p, oldR1[i].stride, lold, d_alpha.p, m, R1.buf.p, R1.stride, T(i), c->st);
+          if (i + 1 < k && !oldHR[i + 1].empty()) {
+            const SetBatch& O = oldHR[i + 1];
+            set_batch(c, HRrot, *O.fp, *O.rp, m);
+            launch_rotate(O.f.p, O.fs, lold, d_alpha.p, m, HRrot.f.p, HRrot.fs, O.fp->total, c->st);
+            launch_rotate(O.r.p, O.rs, lold, d_alpha.p, m, HRrot.r.p, HRrot.rs, O.rp->total, c->st);
+          }
+          if (i > 0) {
+            BondBatch X;
+            b_lc(i - 1, L0(i - 1), Cprev, m, X);
+            b_lmulb(i, X, m, R0(i), C1, false);
+            b_lmul(i, lam[i], R1, m, C1, true);
+          } else {
+            b_lmul(i, lam[0], R1, m, C1, false);
+          }
+        }
+        SiteBatch dHC0;
+        batch_alloc(c, dHC0, T(i), l, 1);
+        std::vector<Enl> XE = enlarge_left_batch(i, HL);
+        dh_left_batch(i, XE, dHC0);
+        if (T(i) > 0) {
+          if (first) {
+            // start: the preconditioned drive, -V_i C0 / (diag - shift)
+            launch_precond_batch(vc0[i].p, T(i), diag[i].p, d_shift.p, 1, T(i), C1.v(0), C1.stride, 1.0, c->st);
+            b_projC(i, C1, 0, 1);
+          } else {
+            // residual of X (vector 0): H_0 C1 + dH C0 - shift C1 + V_i C0, projected
+            SiteBatch sig, t1;
+            batch_alloc(c, sig, T(i), 1, 1);
+            batch_alloc(c, t1, T(i), 1, 1);
+            h0(i, C1, 1, sig);
+            b_axpy(1.0, dHC0, 0, sig, 0, 1);
+            dh_right_batch(i, HRrot, 1, t1);
+            b_axpy(1.0, t1, 0, sig, 0, 1);
+            launch_rank1_batch(C1.v(0), C1.stride, d_shift.p, -1.0, 1, sig.v(0), sig.stride, T(i), c->st);
+            launch_rank1_batch(vc0[i].p, T(i), nullptr, 1.0, 1, sig.v(0), sig.stride, T(i), c->st);
+            b_projC(i, sig, 0, 1);
+            launch_vdots(sig.v(0), sig.stride, sig.v(0), sig.stride, 1, T(i), d_r2.p, true, dwork.p, c->st);
+            // the correction -D^-1 r as the new trial vector
+            launch_precond_batch(sig.v(0), sig.stride, diag[i].p, d_shift.p, 1, T(i), C1.v(m), C1.stride, 1.0, c->st);
+            b_projC(i, C1, m, 1);
+          }
+        }
+        // reduced matrices and the drive b_R (Eqs. cwfn1st, hleft2, sleft2)
+        SiteBatch Ct, H0Ct;
+        batch_alloc(c, Ct, T(i), l, 1);
+        batch_alloc(c, H0Ct, T(i), l, 1);
+        b_projL(i, C1, l, Ct);
+        h0(i, Ct, l, H0Ct);
+        if (T(i) > 0) {
+          double* D1 = d_D.p;
+          double* D2 = D1 + (size_t)l * l;
+          double* D3 = D2 + (size_t)l * l;
+          launch_pair_dots_strided(Ct.v(0), Ct.stride, l, H0Ct.v(0), H0Ct.stride, l, T(i), D1, dwork.p, c->st);
+          launch_pair_dots_strided(Ct.v(0), Ct.stride, l, dHC0.v(0), dHC0.stride, l, T(i), D2, dwork.p, c->st);
+          launch_pair_dots_strided(Ct.v(0), Ct.stride, l, Ct.v(0), Ct.stride, l, T(i), D3, dwork.p, c->st);
+          launch_reduced_acc(D1, D2, D3, l, d_H.p, d_S.p, c->st);
+          launch_pair_dots_strided(Ct.v(0), Ct.stride, l, vc0[i].p, T(i), 1, T(i), d_b.p + (size_t)i * l, dwork.p,
+                                   c->st);
+        }
+        batch_alloc(c, L1[i], T(i), l, 1);
+        b_rmul(i, Ct, l, ilam[i + 1], L1[i], false);
+        if (i + 1 < k) HL = grow_HL_batch(i, XE, L1[i], l);
+        Cprev = std::move(C1);
+      }
+      HL.clear();
+      // ---------------- backward sweep ----------------
+      std::vector<SiteBatch> newR1(k);
+      std::vector<SetBatch> newHR(k + 1);
+      std::vector<FirstOrder> HR(l);
+      SiteBatch Cb;
+      batch_alloc(c, Cb, T(k - 1), l, 1);
+      b_rmul(k - 1, L1[k - 1], l, lam[k], Cb, false);
+      for (int i = k - 1; i >= 0; --i) {
+        if (i < k - 1) {
+          BondBatch Y;
+          b_rc(i + 1, Cb, l, R0(i + 1), Y);
+          SiteBatch nb;
+          batch_alloc(c, nb, T(i), l, 1);
+          b_rmul(i, L1[i], l, lam[i + 1], nb, false);
+          b_rmulb(i, L0(i), Y, l, nb, true);
+          Cb = std::move(nb);
+        }
+        L1[i] = SiteBatch();
+        SiteBatch pr;
+        batch_alloc(c, pr, T(i), l, 1);
+        b_projR(i, Cb, l, pr);
+        batch_alloc(c, newR1[i], T(i), l, 1);
+        b_lmul(i, ilam[i], pr, l, newR1[i], false);
+        if (i > 0) {
+          HR = grow_HR_batch(i, HR, newR1[i], l);
+          set_batch(c, newHR[i], *HR[0].f, *HR[0].r, l);
+          for (int mu = 0; mu < l; ++mu) {
+            if (HR[mu].f->total != HR[0].f->total || HR[mu].r->total != HR[0].r->total)
+              throw Error(LRT_EINVAL, "sweep_response: first-order right sets of different layouts");
+            if (HR[mu].f->total > 0)
+              CK(cudaMemcpyAsync(newHR[i].fv(mu), HR[mu].f->d, (size_t)HR[mu].f->total * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->st));
+            if (HR[mu].r->total > 0)
+              CK(cudaMemcpyAsync(newHR[i].rv(mu), HR[mu].r->d, (size_t)HR[mu].r->total * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->st));
+          }
+        }
+      }
+      HR.clear();
+      oldR1 = std::move(newR1);
+      oldHR = std::move(newHR);
+      lold = l;
+      Hr.assign((size_t)l * l, 0.0);
+      Sr.assign((size_t)l * l, 0.0);
+      bsite.assign((size_t)k * l, 0.0);
+      CK(cudaMemcpyAsync(Hr.data(), d_H.p, Hr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(Sr.data(), d_S.p, Sr.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(bsite.data(), d_b.p, bsite.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(&r2, d_r2.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      CK(cudaGetLastError());
+      bR.assign(l, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int a = 0; a < l; ++a) bR[a] += bsite[(size_t)i * l + a];
+      if (!first) {
+        ++it;
+        if (r2 < tol || it >= max_iter) break;
+      }
+      first = false;
+    }
+    res2_out = r2;
+    sweeps_out = it;
+    return a_prev;
+  }
+
   double response_component(const std::vector<DevBuf>& vc0, double shift, int max_sweeps, double tol, int mr_max,
                              double mr_tol, double& res2_out, int& sweeps_out) {
     blk = 1;
@@ -5680,8 +5885,16 @@ int sweep_response(lrt_t ctx, lrt_t vctx, double omega, const lrt_resp_params* p
     // X: (H - (E0 + omega)) X = -v, Y: (H - (E0 - omega)) Y = -v; alpha = v.(X + Y)
     double r2x = 0.0, r2y = 0.0;
     int swx = 0, swy = 0;
-    const double ax = R.response_component(vc0, R.E0 + omega, ms, tol, mr, mrt, r2x, swx);
-    const double ay = R.response_component(vc0, R.E0 - omega, ms, tol, mr, mrt, r2y, swy);
+    if (p->method != LRT_RESP_SITE && p->method != LRT_RESP_SUBSPACE)
+      throw Error(LRT_EINVAL, "sweep_response: unknown method");
+    double ax, ay;
+    if (p->method == LRT_RESP_SUBSPACE) {
+      ax = R.response_krylov(vc0, R.E0 + omega, ms, tol, p->max_space, r2x, swx);
+      ay = R.response_krylov(vc0, R.E0 - omega, ms, tol, p->max_space, r2y, swy);
+    } else {
+      ax = R.response_component(vc0, R.E0 + omega, ms, tol, mr, mrt, r2x, swx);
+      ay = R.response_component(vc0, R.E0 - omega, ms, tol, mr, mrt, r2y, swy);
+    }
     *alpha = ax + ay;
     resid[0] = r2x;
     resid[1] = r2y;

@@ -276,11 +276,11 @@ void launch_rank1_batch(const double* w, int64_t ldw, const double* coef, double
 void launch_rotate(const double* Vold, int64_t ld_old, int lold, const double* a, int m, double* Vnew,
                    int64_t ld_new, int64_t n, cudaStream_t st);
 // Z_v = sign * (-R_v / (d - theta[v])), |d - theta| clamped to >= 1e-4 (Eq. error)
+void launch_precond_batch(const double* R, int64_t ldr, const double* d, const double* theta, int nv, int64_t n,
+                          double* Z, int64_t ldz, double sign, cudaStream_t st);
 // Z = R / max(|d - shift|, 1e-4): a positive diagonal preconditioner (for MINRES on the
 // indefinite shifted site equations)
 void launch_precond_abs(const double* R, const double* d, double shift, int64_t n, double* Z, cudaStream_t st);
-void launch_precond_batch(const double* R, int64_t ldr, const double* d, const double* theta, int nv, int64_t n,
-                          double* Z, int64_t ldz, double sign, cudaStream_t st);
 // Deterministic dot products in two passes (per-CTA partial sums in `work`, then a fixed-order
 // sum), `work` holding at least DOT_WORK(npairs) doubles:
 //   vdots: out[v] (+)= A_v . B_v  (ldb = 0: one B for all v)
